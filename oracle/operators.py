@@ -1,0 +1,216 @@
+"""Oracle-side interpolating operators (test infrastructure only).
+
+This file is part of the independent CPU reference: only the tests, the smoke
+check and the benchmark's CPU-baseline leg may import it; the GPU product path
+never does.  It shares no code with the product package.
+
+Contents, each following the passage it cites:
+  * Euclidean Dirac matrices in the Dirac-Pauli basis, C = gamma4 gamma2
+    (Sec. II, below Eq. 1.2) and P_pm = (1 pm gamma4)/2 (Sec. III.C).
+  * Nucleon operators p_alpha = eps_abc u^a_alpha u^b_beta (C g5)_{beta eta} d^c_eta
+    and the neutron with u <-> d (Eqs. 1000/1001), as integer weight tables
+    over combined colour-spin indices chi = 4 * colour + spin (Sec. II.A).
+  * Nucleus operators as products of nucleon operators with integer weights
+    (Sec. III.C): the deuteron p(up) n(up), He-3 antisymmetrised in the two
+    proton spins, He-4 p(up) p(down) n(up) n(down).
+
+The operator "upper components" reading: every quark spin (the nucleon spin
+label and the diquark spins) is restricted to the upper Dirac components
+alpha in {0, 1}; with C gamma5 block diagonal in this basis that is the same
+as using C gamma5 P_+ with an upper nucleon spin.
+"""
+from __future__ import annotations
+
+from itertools import permutations, product
+from math import factorial
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# Dirac algebra (Euclidean, Dirac-Pauli basis)
+# ----------------------------------------------------------------------------
+
+def pauli():
+    s1 = np.array([[0, 1], [1, 0]], dtype=complex)
+    s2 = np.array([[0, -1j], [1j, 0]], dtype=complex)
+    s3 = np.array([[1, 0], [0, -1]], dtype=complex)
+    return s1, s2, s3
+
+
+def gammas():
+    """Return (g1, g2, g3, g4, g5) with g_k = [[0, -i s_k], [i s_k, 0]],
+    g4 = diag(1, 1, -1, -1), g5 = g1 g2 g3 g4."""
+    z = np.zeros((2, 2), dtype=complex)
+    gs = []
+    for s in pauli():
+        gs.append(np.block([[z, -1j * s], [1j * s, z]]))
+    g4 = np.diag([1, 1, -1, -1]).astype(complex)
+    g5 = gs[0] @ gs[1] @ gs[2] @ g4
+    return gs[0], gs[1], gs[2], g4, g5
+
+
+def charge_conjugation():
+    """C = gamma4 gamma2 (Sec. II)."""
+    g1, g2, g3, g4, g5 = gammas()
+    return g4 @ g2
+
+
+def cg5():
+    """C gamma5, the diquark spin matrix of Eqs. 1000/1001."""
+    g5 = gammas()[4]
+    return charge_conjugation() @ g5
+
+
+def parity_projector(sign: int):
+    """P_pm = (1 pm gamma4) / 2 (Sec. III.C)."""
+    g4 = gammas()[3]
+    return 0.5 * (np.eye(4) + sign * g4)
+
+
+def levi_civita():
+    e = np.zeros((3, 3, 3), dtype=int)
+    for (a, b, c), sgn in (((0, 1, 2), 1), ((1, 2, 0), 1), ((2, 0, 1), 1),
+                           ((0, 2, 1), -1), ((2, 1, 0), -1), ((1, 0, 2), -1)):
+        e[a, b, c] = sgn
+    return e
+
+
+def integer_matrix(m: np.ndarray) -> np.ndarray:
+    """Return m as an int matrix; fail if it is not real and integral."""
+    if np.max(np.abs(m.imag)) > 1e-12 or np.max(np.abs(m.real - np.round(m.real))) > 1e-12:
+        raise ValueError("spin matrix is not an integer matrix in this basis")
+    return np.round(m.real).astype(int)
+
+
+# ----------------------------------------------------------------------------
+# Nucleon operators as weight tables
+# ----------------------------------------------------------------------------
+
+U, D = 0, 1
+
+
+def nucleon_table(gamma: np.ndarray, spins_nucleon, spins_diquark):
+    """Weight table of N_s = eps_abc q1^a_s q1^b_beta Gamma_{beta eta} q2^c_eta.
+
+    Returns a sorted list of (s, chi1, chi2, chi3, w): slot 1 is the quark that
+    carries the nucleon spin label s, slots 1 and 2 have the pair flavour q1,
+    slot 3 the other flavour q2 (Eq. 1000 for the proton, Eq. 1001 for the
+    neutron).  Only Gamma entries with beta, eta in `spins_diquark` are kept.
+    """
+    G = integer_matrix(gamma)
+    eps = levi_civita()
+    out = {}
+    for s in spins_nucleon:
+        for a, b, c in product(range(3), repeat=3):
+            if eps[a, b, c] == 0:
+                continue
+            for be in spins_diquark:
+                for et in spins_diquark:
+                    w = int(eps[a, b, c] * G[be, et])
+                    if w == 0:
+                        continue
+                    key = (s, 4 * a + s, 4 * b + be, 4 * c + et)
+                    out[key] = out.get(key, 0) + w
+    return sorted((k + (w,)) for k, w in out.items() if w != 0)
+
+
+UPPER = (0, 1)
+ALL_SPINS = (0, 1, 2, 3)
+
+
+def nucleon_ops(form: str = "upper"):
+    """The two block types (proton, neutron) as (pair_flavour, table) tuples."""
+    if form == "upper":
+        tab = nucleon_table(cg5(), UPPER, UPPER)
+    elif form == "full":
+        tab = nucleon_table(cg5(), ALL_SPINS, ALL_SPINS)
+    else:
+        raise ValueError(form)
+    return [(U, tab), (D, tab)]  # op 0 = proton (u u d), op 1 = neutron (d d u)
+
+
+# ----------------------------------------------------------------------------
+# Nucleus operators
+# ----------------------------------------------------------------------------
+
+PROTON, NEUTRON = 0, 1
+
+
+def source_terms(ops, types, spin_terms):
+    """Source weight table C'(chi'_1 .. chi'_3A) of a sum of nucleon products.
+
+    spin_terms: list of (spins tuple, integer coefficient); the nucleon types
+    `types` (one per nucleon position) are the same in every product.  The
+    source tuple lists each nucleon's three quarks in slot order, nucleon by
+    nucleon, and its weight is the coefficient times the product of the nucleon
+    table weights.  Equal tuples are merged; zeros dropped; sorted.
+    """
+    acc = {}
+    for spins, coef in spin_terms:
+        per = []
+        for o, s in zip(types, spins):
+            per.append([e for e in ops[o][1] if e[0] == s])
+        for combo in product(*per):
+            chi = tuple(x for e in combo for x in e[1:4])
+            w = coef
+            for e in combo:
+                w *= e[4]
+            acc[chi] = acc.get(chi, 0) + w
+    return sorted((k, w) for k, w in acc.items() if w != 0)
+
+
+def source_flavours(ops, types):
+    f = []
+    for o in types:
+        q1 = ops[o][0]
+        f += [q1, q1, 1 - q1]
+    return f
+
+
+def nucleus(name: str, form: str = "upper"):
+    """Return the nucleus description used by the oracle.
+
+    dict(A, ops, n_spin, chi, sink=[(types, spins, w)], src=[(chi tuple, w)],
+    src_flav, scale).  Sink and source use the same spin combination.
+    """
+    ops = nucleon_ops(form)
+    if name == "proton":
+        types = (PROTON,)
+        spin_terms = [((0,), 1)]
+    elif name == "deuteron":
+        types = (PROTON, NEUTRON)
+        spin_terms = [((0, 0), 1)]
+    elif name == "he3":
+        types = (PROTON, PROTON, NEUTRON)
+        spin_terms = [((0, 1, 0), 1), ((1, 0, 0), -1)]
+    elif name == "he4":
+        types = (PROTON, PROTON, NEUTRON, NEUTRON)
+        spin_terms = [((0, 1, 0, 1), 1)]
+    else:
+        raise ValueError(name)
+    sink = sorted((tuple(types), tuple(sp), w) for sp, w in spin_terms)
+    src = source_terms(ops, types, spin_terms)
+    n_spin = 2 if form == "upper" else 4
+    chi = [c for c in range(12) if (c % 4) < n_spin]
+    return dict(A=len(types), ops=ops, n_spin=n_spin, chi=chi, sink=sink, src=src,
+                src_flav=source_flavours(ops, types), scale=1.0)
+
+
+def quark_counts(nuc):
+    nu = sum(1 for f in nuc["src_flav"] if f == U)
+    return nu, len(nuc["src_flav"]) - nu
+
+
+def n_raw_terms(nuc) -> int:
+    """|W| |C'| n_u! n_d!: the number of Wick terms before any reduction."""
+    nu, nd = quark_counts(nuc)
+    return len(nuc["sink"]) * len(nuc["src"]) * factorial(nu) * factorial(nd)
+
+
+def all_permutations(n):
+    """Permutations of 0..n-1 in lexicographic order with their signs."""
+    out = []
+    for p in permutations(range(n)):
+        inv = sum(1 for i in range(n) for j in range(i + 1, n) if p[i] > p[j])
+        out.append((p, -1 if inv % 2 else 1))
+    return out
