@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark: He-4 correlator time per gauge configuration on GB300.
+
+Workload: He-4 (p up, p down, n up, n down; upper Dirac components), L=16,
+T=32, 4 sources, complex64 propagators (synthetic i.i.d. Gaussian; the paper's
+HISQ/overlap ensembles are not available).  One step = one configuration:
+wick_build_blocks + wick_contract in MIXED precision for all 4 sources x 32
+time slices, inputs resident in HBM (1.2 GB per configuration, larger than
+L2; two configurations alternate).  The reduced term table is the one-time
+per-nucleus preprocessing (Sec. III.B): it is built once before the timed
+region and its time is reported separately ("reduce").
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank processes its own configurations (weak
+scaling, no data-path collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "He-4 correlator ms/config & Wick terms/s, mixed+batched vs FP64 plain, rel err≤1e-6"
+UNIT = "ms/config"
+WORKLOAD = "He-4 p(up)p(down)n(up)n(down), upper spin components, L=16, T=32, 4 sources, complex64 propagators"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 8:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(rows[0][1]) if rows[0][1].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def block_bytes_per_site(dtype_bytes: int) -> int:
+    """Algorithmic DRAM bytes per site of the upper-component block build: the
+    six sink-upper rows (a, alpha in {0,1}) of S_u and S_d.  Every 32-byte
+    sector of those rows holds a needed (beta in {0,1}) pair, so the rows are
+    the minimum traffic in the paper's propagator layout."""
+    rows, cols = 6, 12
+    return 2 * rows * cols * dtype_bytes
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("blocks.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2411_08962_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    p = os.path.join(ROOT, "profiles", "block_build_he4_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU reference timing (the oracle as it stands, on this host's cores)
+# ---------------------------------------------------------------------------
+def oracle_ms_per_config(Su, Sd, slices, tab):
+    """Time the CPU reference on `slices` (src, t) of one configuration (one
+    call, so its OpenMP loop spans every host core) and scale to the whole
+    configuration."""
+    from oracle import operators as oops
+    from oracle import oracle as O
+    onuc = oops.nucleus("he4")
+    n_src, T = Su.shape[:2]
+    su = np.stack([Su[s, t] for s, t in slices])[None].astype(np.complex128)
+    sd = np.stack([Sd[s, t] for s, t in slices])[None].astype(np.complex128)
+    t0 = time.perf_counter()
+    Bh = O.blocks_single(su, sd, onuc)
+    O.table_correlator(onuc, Bh, tab)
+    dt = time.perf_counter() - t0
+    return 1e3 * dt * (n_src * T) / len(slices), O.num_threads(), dt
+
+
+def he4_oracle_table():
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import make_tables
+    return make_tables.load("he4")[0]
+
+
+def host_props(seed, L, T, n_src):
+    from paper_2411_08962_gb300 import synth
+    return (synth.propagator(seed, 0, L, T, n_src, dtype=np.complex64),
+            synth.propagator(seed, 1, L, T, n_src, dtype=np.complex64))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2411_08962_gb300 import synth
+    w = synth.WORKLOADS["he4"]
+    L, T, n_src = w["L"], w["T"], w["n_src"]
+    Su, Sd = host_props(w["seed"], L, T, n_src)
+    tab = he4_oracle_table()
+    rng = np.random.default_rng(0)
+    per_step = 4
+    times = []
+    for i in range(args.warmup + args.steps):
+        sl = [(int(rng.integers(n_src)), int(rng.integers(T))) for _ in range(per_step)]
+        ms, cores, _ = oracle_ms_per_config(Su, Sd, sl, tab)
+        if i >= args.warmup:
+            times.append(ms)
+    v = float(np.mean(times))
+    sample = f"{per_step} random (source, time-slice) pairs per step, scaled by {n_src * T}/{per_step}"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "L": L, "T": T, "n_src": n_src},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_08962_gb300 import build, operators, synth, wick
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    wick.load()
+    w = synth.WORKLOADS["he4"]
+    L, T, n_src = w["L"], w["T"], w["n_src"]
+    V = L ** 3
+    nuc = operators.nucleus("he4")
+    tabs = wick.Tables(nuc)
+    stream = torch.cuda.current_stream()
+
+    # one-time preprocessing: the reduced term table
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    terms = wick.wick_reduce_terms(tabs)
+    reduce_s = time.perf_counter() - t0
+    (n_raw, n_zero, n_keys, U), bound = terms.stats()
+
+    # inputs: two configurations per rank, resident on the device; pinned host copies for e2e
+    cfg_host, cfg_dev = [], []
+    for c in range(2):
+        Su, Sd = host_props(w["seed"] + 7919 * (rank * 2 + c), L, T, n_src)
+        hu = torch.from_numpy(Su).pin_memory()
+        hd = torch.from_numpy(Sd).pin_memory()
+        cfg_host.append((hu, hd))
+        cfg_dev.append((hu.cuda(), hd.cuda()))
+    blocks = torch.empty((n_src, T, nuc.n_blk), dtype=torch.complex128, device="cuda")
+    Cout = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
+    prec = wick.WICK_MIXED
+
+    def step(i, p=prec, b_ev=None):
+        Su_d, Sd_d = cfg_dev[i % 2]
+        if b_ev is not None:
+            b_ev[0].record(stream)
+        wick.wick_build_blocks(Su_d, Sd_d, tabs, p, blocks, L, T, n_src, stream)
+        if b_ev is not None:
+            b_ev[1].record(stream)
+        wick.wick_contract(blocks, n_src, T, terms, p, Cout, stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for i in range(args.steps):
+        step(i, b_ev=bev[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    elapsed = e0.elapsed_time(e1)
+    build_ms = float(np.mean([a.elapsed_time(b) for a, b in bev]))
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    configs = args.steps * world
+    value = elapsed / configs
+    terms_per_s = U * n_src * T * configs / (elapsed / 1e3)
+    C_mixed = Cout.clone()
+
+    # FP64 plain path on the same inputs (fewer steps)
+    k64 = max(2, min(5, args.steps))
+    step(0, wick.WICK_FP64)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for i in range(k64):
+        step(i, wick.WICK_FP64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = f0.elapsed_time(f1) / k64
+    # precision: mixed vs FP64 GPU path on the last configuration of the timed loop
+    last = (args.steps - 1) % 2
+    step(last, wick.WICK_FP64)
+    torch.cuda.synchronize()
+    C64 = Cout.clone()
+    rel = (C_mixed - C64).abs() / C64.abs()
+    rel_err = float(rel.max().item())
+
+    # end to end through the API with host buffers: H2D of the configuration, both calls, D2H of C
+    h2d = 2 * cfg_host[0][0].numel() * cfg_host[0][0].element_size()
+    d2h = Cout.numel() * Cout.element_size()
+    ke = max(2, min(5, args.steps))
+    Cpin = torch.empty_like(Cout, device="cpu").pin_memory()
+    dbuf = (torch.empty_like(cfg_dev[0][0]), torch.empty_like(cfg_dev[0][1]))
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for i in range(ke):
+        hu, hd = cfg_host[i % 2]
+        dbuf[0].copy_(hu, non_blocking=True)
+        dbuf[1].copy_(hd, non_blocking=True)
+        wick.wick_build_blocks(dbuf[0], dbuf[1], tabs, prec, blocks, L, T, n_src, stream)
+        wick.wick_contract(blocks, n_src, T, terms, prec, Cout, stream)
+        Cpin.copy_(Cout, non_blocking=True)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    e2e = g0.elapsed_time(g1) / ke
+    if world > 1:
+        t = torch.tensor([e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item()) / world
+
+    peak, peak_kind = peaks()
+    bytes_launch = n_src * T * V * block_bytes_per_site(8)
+    achieved = bytes_launch / (build_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": L, "T": T, "n_src": n_src, "precision": "mixed",
+                   "reduced_terms": U, "l2": "inputs larger than L2 (1.2 GB per configuration; 2 alternate)",
+                   "parallelism": f"{world} independent rank(s), configurations sharded"},
+        "wick_terms_per_s": terms_per_s,
+        "fp64_plain": {"value": fp64_ms, "unit": UNIT, "speedup_mixed": fp64_ms / value * world},
+        "rel_err_mixed_vs_fp64_max_per_t": rel_err,
+        "reduce": {"seconds": reduce_s, "raw_terms": n_raw, "zero_terms": n_zero, "distinct_keys": n_keys,
+                   "kept_terms": U, "raw_terms_per_s": n_raw / reduce_s, "false_merge_bound": bound},
+        "roofline": {"kernel": "block build (wick_build_blocks: partial + reduce kernels)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": recorded_traffic(),
+                     "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": build_ms},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        tab = he4_oracle_table()
+        Su, Sd = (cfg_host[0][0].numpy(), cfg_host[0][1].numpy())
+        sl = [(s, t) for s in range(n_src) for t in range(0, T, 4)]
+        ms, cores, dt = oracle_ms_per_config(Su, Sd, sl, tab)
+        line["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{len(sl)} of {n_src * T} (source, time-slice) pairs, "
+                                          f"{dt:.1f} s, scaled to one configuration"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,226 @@
+/*
+ * wick.h -- C ABI of libwick, the GB300 (sm_103a) library for zero-momentum
+ * nuclear two-point correlators with a plane-wave sink (the block algorithm
+ * of arXiv:2411.08962).
+ *
+ * The hot path has three calls:
+ *
+ *   wick_build_blocks  baryon blocks from u/d propagators            (Eq. 2.4/2.5)
+ *   wick_reduce_terms  randomised redundancy elimination of the Wick
+ *                      terms by identity testing modulo 2^61 - 1    (Sec. III.B, App. C)
+ *   wick_contract      signed gather-multiply-sum of the reduced
+ *                      terms over the blocks, for every time slice   (Eq. 2.6, App. D)
+ *
+ * Conventions common to every call
+ *   - Device buffers are allocated and owned by the caller (for example as
+ *     torch tensors) and must stay alive until the stream work completes.
+ *     Only wick_terms objects are owned by the library (wick_terms_free).
+ *   - Every call is asynchronous on the given stream (NULL = legacy default
+ *     stream) unless its comment says it synchronises.
+ *   - Return value: WICK_OK (0) or a negative WICK_E* code; no exception or
+ *     C++ type crosses the ABI.  wick_strerror() names a code.  Errors a
+ *     kernel detects on the device (capacity, overflow, bounded waits that
+ *     ran out) are recorded in a device status word and returned by the next
+ *     call that synchronises (wick_reduce_terms, wick_status).
+ *   - Combined colour-spin index: chi = 4 * colour + spin, colour in 0..2,
+ *     spin in 0..3 (Dirac-Pauli basis; spins 0,1 are the upper components).
+ *   - Complex numbers are stored as interleaved (re, im) pairs.
+ */
+#ifndef WICK_H
+#define WICK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define WICK_OK 0
+#define WICK_EINVAL (-1)    /* bad argument, shape or table */
+#define WICK_ENOMEM (-2)    /* device or host allocation failed */
+#define WICK_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed */
+#define WICK_ECAPACITY (-4) /* a library table (term hash table) is full */
+#define WICK_EOVERFLOW (-5) /* an integer weight or count does not fit */
+#define WICK_ETIMEOUT (-6)  /* a bounded device-side wait ran out */
+#define WICK_EIO (-7)       /* term-table file missing, truncated or corrupt */
+
+/* storage type of a propagator */
+#define WICK_C128 0 /* complex double */
+#define WICK_C64 1  /* complex float  */
+
+/* arithmetic of a call */
+#define WICK_FP64 0  /* FP64 products and sums */
+#define WICK_MIXED 1 /* FP32 products, FP64 sums over sites and terms */
+
+/* quark flavours */
+#define WICK_U 0
+#define WICK_D 1
+
+typedef struct CUstream_st *wick_stream_t; /* a cudaStream_t */
+
+/*
+ * Quark propagator S_q(x, t; x0, 0) for every source, time slice and sink
+ * site, S^{ab}_{alpha beta} with sink colour a / spin alpha first (the layout
+ * the paper reads, App. A):
+ *   data[src][t][x][a][alpha][b][beta], x = (z * L + y) * L + x_  (V = L^3),
+ * complex, device memory, 16-byte aligned, caller-owned.
+ */
+typedef struct wick_prop {
+    const void *data;
+    int L, T, n_src;
+    int dtype; /* WICK_C128 | WICK_C64 */
+} wick_prop;
+
+/*
+ * Nucleon interpolating operator as an integer weight table (Eq. 2.7
+ * restricted to three quarks; Eqs. 1000/1001 for p and n):
+ *   N_s = sum_e w_e q1(chi_e1) q1(chi_e2) q2(chi_e3)      (over e with s_e = s)
+ * entries[e] = (s, chi_e1, chi_e2, chi_e3), int8 x 4; w[e] int32.
+ * Slots 1 and 2 carry the like-flavour pair flav_pair (WICK_U for the proton),
+ * slot 3 the other flavour.  Host memory, read during the call only.
+ */
+typedef struct wick_nucleon_op {
+    int n_entries;
+    const int8_t *entries;
+    const int32_t *w;
+    int flav_pair;
+} wick_nucleon_op;
+
+/*
+ * Which blocks exist and where they live.  Block entry (op, s, i1, i2, i3),
+ * i = position of the source index chi' in chi[], has id
+ *   id = (((op * n_spin + s) * n_chi + i1) * n_chi + i2) * n_chi + i3
+ * and a block buffer holds, per (src, t), wick_block_count() complex128
+ * values B[src][t][id].
+ */
+typedef struct wick_block_layout {
+    int n_ops;      /* number of block types (nucleon operators) */
+    int n_spin;     /* nucleon spin labels s = 0 .. n_spin-1 */
+    int n_chi;      /* number of source indices kept, 1..12 */
+    int8_t chi[12]; /* the kept source indices chi', strictly ascending */
+} wick_block_layout;
+
+/*
+ * Nucleus operator at sink and source (Eq. 2.7, Sec. III.C):
+ *   sink:   sum_i sink_w[i] prod_k N^{sink_type[i][k]}_{sink_spin[i][k]}
+ *   source: sum_m src_w[m] prod_q qbar_{src_flav[q]}(src_chi[m][q]),
+ *           q = 3k + slot lists the 3A source quarks nucleon by nucleon.
+ * All arrays are host memory, row-major, read during the call only.
+ * The correlator is scale * sum of the Wick terms (all weights integers).
+ */
+typedef struct wick_nucleus {
+    int A;                    /* nucleons, 1..8 */
+    int n_sink;
+    const int8_t *sink_type;  /* n_sink x A, index into the op list */
+    const int8_t *sink_spin;  /* n_sink x A */
+    const int64_t *sink_w;    /* n_sink */
+    int n_src;
+    const int8_t *src_chi;    /* n_src x 3A, chi' in 0..11 (must be in layout.chi) */
+    const int64_t *src_w;     /* n_src */
+    const int8_t *src_flav;   /* 3A, WICK_U / WICK_D */
+    double scale;
+} wick_nucleus;
+
+/* Reduced term table, library-owned (host and device copies). */
+typedef struct wick_terms wick_terms;
+
+/* Number of block entries per (src, t) of a layout; 0 if the layout is invalid. */
+size_t wick_block_count(const wick_block_layout *layout);
+
+/*
+ * Baryon blocks, Eq. 2.4/2.5 generalised to any nucleon weight table and
+ * projected to zero momentum (sum over sink sites x, plane-wave sink):
+ *   B^op_s(c1,c2,c3)[src][t] = sum_x sum_e w_e [ S1(x)(chi_e1,c1) S1(x)(chi_e2,c2)
+ *                                               - S1(x)(chi_e1,c2) S1(x)(chi_e2,c1) ] S2(x)(chi_e3,c3)
+ * with S1 the propagator of the op's pair flavour and S2 the other one; the
+ * bracket is the exchange of the two like-flavour source quarks (Eq. 2.4
+ * writes the same exchange on the sink side).
+ *   Su, Sd      propagators (same L, T, n_src; dtype may differ)
+ *   ops         layout->n_ops nucleon operators
+ *   precision   WICK_FP64: FP64 throughout.  WICK_MIXED: per-site products in
+ *               FP32 with FP32 partial sums over a chunk of at most 256 sites,
+ *               FP64 sum of the chunks.
+ *   blocks      device, caller-owned, complex128 [n_src][T][wick_block_count]
+ * Uses a library-cached device workspace for the per-chunk FP64 partials
+ * (allocated on first use and grown when needed: make the first call, with
+ * the largest shape, before any stream capture).
+ * Errors: WICK_EINVAL (shapes, tables, indices), WICK_ENOMEM, WICK_ECUDA.
+ */
+int wick_build_blocks(const wick_prop *Su, const wick_prop *Sd, const wick_nucleon_op *ops,
+                      const wick_block_layout *layout, int precision, void *blocks,
+                      wick_stream_t stream);
+
+/*
+ * Randomised minimal-set search (Sec. III.B "Computation of non-redundant
+ * minimal set", Theorem 1 and its error bound in App. C) for the block
+ * form of the correlator (Eq. 2.6 generalised in App. D):
+ *   raw terms   j = ((i_sink * n_src + i_src) * n_u! + rank(sigma_u)) * n_d! + rank(sigma_d)
+ *               with coefficient c_j = sink_w * src_w * sgn(pairing) and monomial
+ *               prod_k B^{type_k}_{s_k}(chi'_{sigma(k,1)}, chi'_{sigma(k,2)}, chi'_{sigma(k,3)});
+ *               rank = lexicographic rank; sgn(pairing) = parity of the map
+ *               sink quark -> source quark (+1 for the pairing in listed order).
+ *   hashing     every monomial is evaluated at `trials` (1 or 2) random integer
+ *               propagators on `sites` lattice sites, exactly modulo p = 2^61 - 1;
+ *               the sign is canonicalised (first non-zero value <= (p-1)/2) and
+ *               the value tuple is the key.  Keys equal to zero drop the term.
+ *   merging     equal keys are merged: W = sum_j eps_j c_j.  Classes with W = 0
+ *               are dropped.  Each kept term stores its smallest raw index j
+ *               (its representative), that term's block ids and the weight
+ *               W * eps_rep / 2^A (an integer: classes are unions of the 2^A
+ *               like-pair exchange orbits).  Terms are ordered by representative,
+ *               so the table depends only on the partition, not on the seed.
+ * False-merge probability <= C(N_raw, 2) * (3A / p)^trials (reported by
+ * wick_terms_stats).  Synchronises `stream`; the table is library-owned.
+ * Errors: WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA, WICK_ECAPACITY (more distinct
+ * keys than the hash table holds), WICK_EOVERFLOW (weights beyond int64 /
+ * more than 2^62 raw terms), WICK_ETIMEOUT.
+ */
+int wick_reduce_terms(const wick_nucleus *nucleus, const wick_nucleon_op *ops,
+                      const wick_block_layout *layout, uint64_t seed, int trials, int sites,
+                      wick_terms **out, wick_stream_t stream);
+
+/* Accessors of a reduced table. */
+int64_t wick_terms_count(const wick_terms *terms);     /* U, or a negative error */
+int wick_terms_nucleons(const wick_terms *terms);      /* A */
+/* Copy to host arrays: ids [U][A] uint16, w [U] int64, rep [U] int64 (any may be NULL). */
+int wick_terms_copy(const wick_terms *terms, uint16_t *ids, int64_t *w, int64_t *rep);
+/* stats[0] raw terms, [1] identically zero, [2] distinct keys, [3] kept terms;
+ * *bound = the false-merge probability bound of App. C for this reduction. */
+int wick_terms_stats(const wick_terms *terms, int64_t stats[4], double *bound);
+/* Keep only the first n terms in a caller-given order of importance: the
+ * table is replaced by the terms perm[0..n-1] (indices into the current
+ * table), re-sorted by representative.  Used for top-fraction evaluation. */
+int wick_terms_select(wick_terms *terms, const int64_t *perm, int64_t n);
+/* Binary term-table file (versioned header + arrays). */
+int wick_terms_save(const wick_terms *terms, const char *path);
+int wick_terms_load(const char *path, wick_terms **out);
+void wick_terms_free(wick_terms *terms);
+
+/*
+ * Correlator from the reduced table, Eq. 2.6 / App. D in reduced form:
+ *   C[src][t] = scale * sum_u w_u prod_k B[src][t][id_{u,k}]
+ *   blocks     device complex128 [n_src][T][n_blk], from wick_build_blocks with
+ *              the layout the table was reduced for (n_blk is checked)
+ *   precision  WICK_FP64: FP64 products and sums.  WICK_MIXED: blocks rounded
+ *              to complex float, products in FP32, FP64 sum over terms.
+ *   C_out      device complex128 [n_src][T], caller-owned, overwritten.
+ * Deterministic (fixed reduction order).  Errors: WICK_EINVAL, WICK_ECUDA.
+ */
+int wick_contract(const void *blocks, int n_src, int T, const wick_terms *terms, int precision,
+                  void *C_out, wick_stream_t stream);
+
+/* Synchronises `stream` and returns (then clears) the device status word. */
+int wick_status(wick_stream_t stream);
+
+/* Human-readable name of an error code (static string). */
+const char *wick_strerror(int code);
+
+/* Library version, e.g. "0.1.0". */
+const char *wick_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WICK_H */

@@ -1,0 +1,532 @@
+// C ABI of libwick: argument validation, host-side plans, the library-owned
+// term table and the per-device workspace.  All arithmetic of the path runs
+// in the kernels of blocks.cu, dedup.cu and contract.cu.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+
+struct wick_terms {
+    int A = 0;
+    int64_t U = 0;
+    int n_blk = 0, n_ops = 0, n_spin = 0, n_chi = 0;
+    int8_t chi[12] = {0};
+    double scale = 1.0;
+    int64_t stats[4] = {0, 0, 0, 0};
+    double bound = 0.0;
+    std::vector<uint16_t> ids;  // host copies
+    std::vector<int64_t> w, rep;
+    uint16_t *d_ids = nullptr;  // device copies (on the device current at creation)
+    int64_t *d_w = nullptr, *d_rep = nullptr;
+    int device = 0;
+};
+
+namespace wick {
+
+// ---------------------------------------------------------------------------
+// per-device workspace and status word
+// ---------------------------------------------------------------------------
+namespace {
+struct DevState {
+    void *ws[2] = {nullptr, nullptr};
+    size_t ws_bytes[2] = {0, 0};
+    int *status = nullptr;
+};
+std::mutex g_mu;
+std::map<int, DevState> g_dev;
+}  // namespace
+
+void *workspace(int slot, size_t bytes, int *err) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { *err = WICK_ECUDA; return nullptr; }
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState &d = g_dev[dev];
+    if (d.ws_bytes[slot] < bytes) {
+        // cudaFree waits for the device, so work still using the old buffer finishes first
+        if (d.ws[slot]) cudaFree(d.ws[slot]);
+        d.ws[slot] = nullptr;
+        d.ws_bytes[slot] = 0;
+        size_t want = bytes + bytes / 4;
+        if (cudaMalloc(&d.ws[slot], want) != cudaSuccess) {
+            (void)cudaGetLastError();
+            *err = WICK_ENOMEM;
+            return nullptr;
+        }
+        d.ws_bytes[slot] = want;
+    }
+    *err = WICK_OK;
+    return d.ws[slot];
+}
+
+int *status_word(int *err) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { *err = WICK_ECUDA; return nullptr; }
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState &d = g_dev[dev];
+    if (!d.status) {
+        if (cudaMalloc(&d.status, sizeof(int)) != cudaSuccess || cudaMemset(d.status, 0, sizeof(int)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            d.status = nullptr;
+            *err = WICK_ENOMEM;
+            return nullptr;
+        }
+    }
+    *err = WICK_OK;
+    return d.status;
+}
+
+int status_read_clear(cudaStream_t stream) {
+    int err = WICK_OK;
+    int *st = status_word(&err);
+    if (err) return err;
+    int h = 0;
+    WICK_CUDA_TRY(cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    WICK_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(int), stream));
+    WICK_CUDA_TRY(cudaStreamSynchronize(stream));
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+// layouts and plans
+// ---------------------------------------------------------------------------
+static bool layout_ok(const wick_block_layout *l) {
+    if (!l || l->n_ops < 1 || l->n_ops > kMaxOps || l->n_spin < 1 || l->n_spin > kMaxSpin || l->n_chi < 1 ||
+        l->n_chi > 12)
+        return false;
+    for (int i = 0; i < l->n_chi; ++i) {
+        if (l->chi[i] < 0 || l->chi[i] > 11) return false;
+        if (i && l->chi[i] <= l->chi[i - 1]) return false;
+    }
+    return true;
+}
+
+int build_block_plan(const wick_nucleon_op *ops, const wick_block_layout *layout, BlockPlan *plan) {
+    if (!ops || !layout_ok(layout)) return WICK_EINVAL;
+    BlockPlan &P = *plan;
+    memset(&P, 0, sizeof(P));
+    P.n_ops = layout->n_ops;
+    P.n_spin = layout->n_spin;
+    P.n_chi = layout->n_chi;
+    P.n_out = P.n_ops * P.n_spin * P.n_chi * P.n_chi * P.n_chi;
+    for (int i = 0; i < P.n_chi; ++i) P.chi[i] = layout->chi[i];
+    int row_pos[2][12];
+    for (int f = 0; f < 2; ++f)
+        for (int r = 0; r < 12; ++r) row_pos[f][r] = -1;
+    // rows used per flavour
+    for (int o = 0; o < P.n_ops; ++o) {
+        const wick_nucleon_op &op = ops[o];
+        if (op.flav_pair != WICK_U && op.flav_pair != WICK_D) return WICK_EINVAL;
+        if (op.n_entries < 1 || !op.entries || !op.w) return WICK_EINVAL;
+        P.f1[o] = op.flav_pair;
+        for (int e = 0; e < op.n_entries; ++e) {
+            const int8_t *en = op.entries + 4 * e;
+            if (en[0] < 0 || en[0] >= P.n_spin) return WICK_EINVAL;
+            for (int q = 1; q < 4; ++q)
+                if (en[q] < 0 || en[q] > 11) return WICK_EINVAL;
+            if (op.w[e] == 0 || op.w[e] > (1 << 20) || op.w[e] < -(1 << 20)) return WICK_EINVAL;
+            const int f1 = op.flav_pair, f2 = 1 - f1;
+            row_pos[f1][(int)en[1]] = row_pos[f1][(int)en[2]] = 0;
+            row_pos[f2][(int)en[3]] = 0;
+        }
+    }
+    for (int f = 0; f < 2; ++f)
+        for (int r = 0; r < 12; ++r)
+            if (row_pos[f][r] == 0) {
+                row_pos[f][r] = P.n_rows[f];
+                P.rows[f][P.n_rows[f]++] = (int8_t)r;
+            }
+    // diquark lists and (row1, list) terms
+    int n_xt = 0, n_ost = 0;
+    P.x_off[0] = 0;
+    for (int o = 0; o < P.n_ops; ++o) {
+        const wick_nucleon_op &op = ops[o];
+        const int f1 = op.flav_pair, f2 = 1 - f1;
+        std::vector<std::vector<std::pair<std::pair<int, int>, int>>> lists;  // per op, for reuse
+        std::vector<int> list_index;
+        for (int s = 0; s < P.n_spin; ++s) {
+            const int os = o * P.n_spin + s;
+            P.os_off[os] = n_ost;
+            // group entries of spin s by row 1
+            std::map<int, std::map<std::pair<int, int>, int>> by_r1;
+            for (int e = 0; e < op.n_entries; ++e) {
+                const int8_t *en = op.entries + 4 * e;
+                if (en[0] != s) continue;
+                by_r1[en[1]][{en[2], en[3]}] += op.w[e];
+            }
+            for (auto &kv : by_r1) {
+                std::vector<std::pair<std::pair<int, int>, int>> L;
+                for (auto &t : kv.second)
+                    if (t.second != 0) L.push_back({t.first, t.second});
+                if (L.empty()) continue;
+                int li = -1;
+                for (size_t q = 0; q < lists.size(); ++q)
+                    if (lists[q] == L) li = list_index[q];
+                if (li < 0) {
+                    if (P.n_x >= kMaxX || n_xt + (int)L.size() > kMaxXTerms) return WICK_EINVAL;
+                    li = P.n_x++;
+                    P.x_op[li] = o;
+                    for (auto &t : L) {
+                        P.xt_r2[n_xt] = (int8_t)row_pos[f1][t.first.first];
+                        P.xt_r3[n_xt] = (int8_t)row_pos[f2][t.first.second];
+                        P.xt_w[n_xt] = (float)t.second;
+                        ++n_xt;
+                    }
+                    P.x_off[li + 1] = n_xt;
+                    lists.push_back(L);
+                    list_index.push_back(li);
+                }
+                if (n_ost >= kMaxOsTerms) return WICK_EINVAL;
+                P.os_r1[n_ost] = (int8_t)row_pos[f1][kv.first];
+                P.os_x[n_ost] = (int16_t)li;
+                ++n_ost;
+            }
+        }
+    }
+    P.os_off[P.n_ops * P.n_spin] = n_ost;
+    return WICK_OK;
+}
+
+static int prop_ok(const wick_prop *p) {
+    if (!p || !p->data || p->L < 1 || p->T < 1 || p->n_src < 1) return 0;
+    if (p->dtype != WICK_C128 && p->dtype != WICK_C64) return 0;
+    if (((uintptr_t)p->data) % 16) return 0;
+    return 1;
+}
+
+}  // namespace wick
+
+using namespace wick;
+
+extern "C" {
+
+size_t wick_block_count(const wick_block_layout *layout) {
+    if (!layout_ok(layout)) return 0;
+    return (size_t)layout->n_ops * layout->n_spin * layout->n_chi * layout->n_chi * layout->n_chi;
+}
+
+int wick_build_blocks(const wick_prop *Su, const wick_prop *Sd, const wick_nucleon_op *ops,
+                      const wick_block_layout *layout, int precision, void *blocks, wick_stream_t stream) {
+    if (!prop_ok(Su) || !prop_ok(Sd) || !blocks) return WICK_EINVAL;
+    if (Su->L != Sd->L || Su->T != Sd->T || Su->n_src != Sd->n_src || Su->dtype != Sd->dtype) return WICK_EINVAL;
+    if (precision != WICK_FP64 && precision != WICK_MIXED) return WICK_EINVAL;
+    if ((uintptr_t)blocks % 16) return WICK_EINVAL;
+    BlockPlan plan;
+    int err = build_block_plan(ops, layout, &plan);
+    if (err) return err;
+    const int64_t V = (int64_t)Su->L * Su->L * Su->L;
+    const int64_t n_slices = (int64_t)Su->n_src * Su->T;
+    if (V > (1 << 24) || n_slices > 65535) return WICK_EINVAL;
+    int n_splits = 0, chunk = 0;
+    const size_t bytes = block_partials_bytes(plan, (int)V, (int)n_slices, precision, &n_splits, &chunk);
+    if (n_splits > 65535) return WICK_EINVAL;
+    void *ws = workspace(0, bytes, &err);
+    if (err) return err;
+    return launch_block_build(plan, Su->data, Su->dtype, Sd->data, Sd->dtype, (int)V, (int)n_slices, precision,
+                              (double *)ws, n_splits, chunk, (double2 *)blocks, (cudaStream_t)stream);
+}
+
+int wick_reduce_terms(const wick_nucleus *nuc, const wick_nucleon_op *ops, const wick_block_layout *layout,
+                      uint64_t seed, int trials, int sites, wick_terms **out, wick_stream_t stream) {
+    if (!out) return WICK_EINVAL;
+    *out = nullptr;
+    if (!nuc || trials < 1 || trials > 2 || sites < 1 || sites > 64) return WICK_EINVAL;
+    BlockPlan bp;
+    int err = build_block_plan(ops, layout, &bp);
+    if (err) return err;
+    const int A = nuc->A, nq = 3 * A;
+    if (A < 1 || A > kMaxA || nuc->n_sink < 1 || nuc->n_src < 1 || !nuc->sink_type || !nuc->sink_spin ||
+        !nuc->sink_w || !nuc->src_chi || !nuc->src_w || !nuc->src_flav)
+        return WICK_EINVAL;
+    EnumPlan ep;
+    memset(&ep, 0, sizeof(ep));
+    ep.A = A;
+    ep.nq = nq;
+    ep.n_sink = nuc->n_sink;
+    ep.n_src = nuc->n_src;
+    ep.n_spin = layout->n_spin;
+    ep.n_chi = layout->n_chi;
+    ep.n_blk = (int)wick_block_count(layout);
+    for (int q = 0; q < nq; ++q) {
+        if (nuc->src_flav[q] == WICK_U) ep.ju[ep.nu++] = q;
+        else if (nuc->src_flav[q] == WICK_D) ep.jd[ep.nd++] = q;
+        else return WICK_EINVAL;
+    }
+    if (ep.nu > 12 || ep.nd > 12) return WICK_EINVAL;
+    ep.fu = 1;
+    for (int i = 2; i <= ep.nu; ++i) ep.fu *= i;
+    ep.fd = 1;
+    for (int i = 2; i <= ep.nd; ++i) ep.fd *= i;
+    // raw-term count, guarded against overflow
+    long double nr = (long double)ep.n_sink * ep.n_src * (long double)ep.fu * (long double)ep.fd;
+    if (nr > 4.0e18L) return WICK_EOVERFLOW;
+    ep.n_raw = (int64_t)ep.n_sink * ep.n_src * ep.fu * ep.fd;
+    if ((uint64_t)ep.n_sink * ep.n_src * (uint64_t)ep.fu * (uint64_t)((ep.fd + 31) / 32) > (1ull << 62))
+        return WICK_EOVERFLOW;
+    // weights: the in-warp sum of 32 coefficients must fit in int32
+    int64_t max_sw = 0, max_cw = 0;
+    for (int i = 0; i < ep.n_sink; ++i) max_sw = std::max<int64_t>(max_sw, llabs(nuc->sink_w[i]));
+    for (int m = 0; m < ep.n_src; ++m) max_cw = std::max<int64_t>(max_cw, llabs(nuc->src_w[m]));
+    if (max_sw == 0 || max_cw == 0 || (long double)max_sw * max_cw * 32.0L >= 2147483647.0L) return WICK_EOVERFLOW;
+    // source index positions
+    int cidx[12];
+    for (int c = 0; c < 12; ++c) cidx[c] = -1;
+    for (int i = 0; i < layout->n_chi; ++i) cidx[(int)layout->chi[i]] = i;
+    std::vector<int8_t> src_idx((size_t)ep.n_src * nq);
+    for (size_t e = 0; e < src_idx.size(); ++e) {
+        const int c = nuc->src_chi[e];
+        if (c < 0 || c > 11 || cidx[c] < 0) return WICK_EINVAL;
+        src_idx[e] = (int8_t)cidx[c];
+    }
+    // sink quark flavours, flavour ordinals and the identity-pairing parity
+    std::vector<int8_t> sflav((size_t)ep.n_sink * nq), sord((size_t)ep.n_sink * nq), seta(ep.n_sink);
+    for (int i = 0; i < ep.n_sink; ++i) {
+        int mu = 0, md = 0;
+        int pi[3 * kMaxA];
+        for (int k = 0; k < A; ++k) {
+            const int o = nuc->sink_type[i * A + k], s = nuc->sink_spin[i * A + k];
+            if (o < 0 || o >= layout->n_ops || s < 0 || s >= layout->n_spin) return WICK_EINVAL;
+            for (int sl = 0; sl < 3; ++sl) {
+                const int f = sl < 2 ? ops[o].flav_pair : 1 - ops[o].flav_pair;
+                const int q = 3 * k + sl;
+                sflav[(size_t)i * nq + q] = (int8_t)f;
+                const int ord = f == WICK_U ? mu++ : md++;
+                sord[(size_t)i * nq + q] = (int8_t)ord;
+                if (ord >= (f == WICK_U ? ep.nu : ep.nd)) return WICK_EINVAL;
+                pi[q] = f == WICK_U ? ep.ju[ord] : ep.jd[ord];
+            }
+        }
+        if (mu != ep.nu || md != ep.nd) return WICK_EINVAL;
+        int inv = 0;
+        for (int a = 0; a < nq; ++a)
+            for (int b = a + 1; b < nq; ++b) inv += pi[a] > pi[b];
+        seta[i] = (int8_t)((inv & 1) ? -1 : 1);
+    }
+    ReduceResult rr;
+    memset(&rr, 0, sizeof(rr));
+    err = run_reduce(ep, bp, nuc, src_idx.data(), sflav.data(), sord.data(), seta.data(), seed, trials, sites, &rr,
+                     (cudaStream_t)stream);
+    if (err) return err;
+    wick_terms *t = new (std::nothrow) wick_terms();
+    if (!t) {
+        cudaFree(rr.d_ids); cudaFree(rr.d_w); cudaFree(rr.d_rep);
+        return WICK_ENOMEM;
+    }
+    cudaGetDevice(&t->device);
+    t->A = A;
+    t->U = rr.U;
+    t->n_blk = ep.n_blk;
+    t->n_ops = layout->n_ops;
+    t->n_spin = layout->n_spin;
+    t->n_chi = layout->n_chi;
+    memcpy(t->chi, layout->chi, sizeof(t->chi));
+    t->scale = nuc->scale;
+    t->stats[0] = ep.n_raw;
+    t->stats[1] = rr.n_zero;
+    t->stats[2] = rr.n_keys;
+    t->stats[3] = rr.U;
+    const double pairs = 0.5 * (double)ep.n_raw * (double)ep.n_raw;
+    t->bound = std::min(1.0, pairs * pow(3.0 * A / 2305843009213693951.0, trials));
+    t->d_ids = rr.d_ids;
+    t->d_w = rr.d_w;
+    t->d_rep = rr.d_rep;
+    t->ids.resize((size_t)rr.U * A);
+    t->w.resize(rr.U);
+    t->rep.resize(rr.U);
+    if (rr.U > 0 &&
+        (cudaMemcpy(t->ids.data(), rr.d_ids, sizeof(uint16_t) * t->ids.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+         cudaMemcpy(t->w.data(), rr.d_w, sizeof(int64_t) * rr.U, cudaMemcpyDeviceToHost) != cudaSuccess ||
+         cudaMemcpy(t->rep.data(), rr.d_rep, sizeof(int64_t) * rr.U, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+        wick_terms_free(t);
+        return WICK_ECUDA;
+    }
+    *out = t;
+    return WICK_OK;
+}
+
+int64_t wick_terms_count(const wick_terms *t) { return t ? t->U : WICK_EINVAL; }
+int wick_terms_nucleons(const wick_terms *t) { return t ? t->A : WICK_EINVAL; }
+
+int wick_terms_copy(const wick_terms *t, uint16_t *ids, int64_t *w, int64_t *rep) {
+    if (!t) return WICK_EINVAL;
+    if (ids && !t->ids.empty()) memcpy(ids, t->ids.data(), sizeof(uint16_t) * t->ids.size());
+    if (w && !t->w.empty()) memcpy(w, t->w.data(), sizeof(int64_t) * t->w.size());
+    if (rep && !t->rep.empty()) memcpy(rep, t->rep.data(), sizeof(int64_t) * t->rep.size());
+    return WICK_OK;
+}
+
+int wick_terms_stats(const wick_terms *t, int64_t stats[4], double *bound) {
+    if (!t) return WICK_EINVAL;
+    if (stats) memcpy(stats, t->stats, sizeof(t->stats));
+    if (bound) *bound = t->bound;
+    return WICK_OK;
+}
+
+static int upload_terms(wick_terms *t) {
+    cudaFree(t->d_ids); cudaFree(t->d_w); cudaFree(t->d_rep);
+    t->d_ids = nullptr; t->d_w = nullptr; t->d_rep = nullptr;
+    const size_t U = (size_t)(t->U ? t->U : 1);
+    if (cudaMalloc(&t->d_ids, sizeof(uint16_t) * U * t->A) != cudaSuccess ||
+        cudaMalloc(&t->d_w, sizeof(int64_t) * U) != cudaSuccess ||
+        cudaMalloc(&t->d_rep, sizeof(int64_t) * U) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return WICK_ENOMEM;
+    }
+    if (t->U > 0 &&
+        (cudaMemcpy(t->d_ids, t->ids.data(), sizeof(uint16_t) * t->ids.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(t->d_w, t->w.data(), sizeof(int64_t) * t->U, cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(t->d_rep, t->rep.data(), sizeof(int64_t) * t->U, cudaMemcpyHostToDevice) != cudaSuccess))
+        return WICK_ECUDA;
+    cudaGetDevice(&t->device);
+    return WICK_OK;
+}
+
+int wick_terms_select(wick_terms *t, const int64_t *perm, int64_t n) {
+    if (!t || n < 0 || n > t->U || (n > 0 && !perm)) return WICK_EINVAL;
+    std::vector<int64_t> keep(perm, perm + n);
+    std::vector<char> seen((size_t)t->U, 0);
+    for (int64_t v : keep) {
+        if (v < 0 || v >= t->U || seen[(size_t)v]) return WICK_EINVAL;
+        seen[(size_t)v] = 1;
+    }
+    std::sort(keep.begin(), keep.end());  // table order = order of representatives
+    std::vector<uint16_t> ids((size_t)n * t->A);
+    std::vector<int64_t> w(n), rep(n);
+    for (int64_t q = 0; q < n; ++q) {
+        const int64_t u = keep[q];
+        memcpy(&ids[(size_t)q * t->A], &t->ids[(size_t)u * t->A], sizeof(uint16_t) * t->A);
+        w[q] = t->w[u];
+        rep[q] = t->rep[u];
+    }
+    t->ids.swap(ids);
+    t->w.swap(w);
+    t->rep.swap(rep);
+    t->U = n;
+    t->stats[3] = n;
+    return upload_terms(t);
+}
+
+// file format: "WICKTBL1" | u32 version | header fields | arrays | u64 FNV-1a of the arrays
+static uint64_t fnv1a(const void *p, size_t n, uint64_t h) {
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+int wick_terms_save(const wick_terms *t, const char *path) {
+    if (!t || !path) return WICK_EINVAL;
+    FILE *f = fopen(path, "wb");
+    if (!f) return WICK_EIO;
+    const char magic[8] = {'W', 'I', 'C', 'K', 'T', 'B', 'L', '1'};
+    const uint32_t version = 1;
+    int32_t hdr[5] = {t->A, t->n_blk, t->n_ops, t->n_spin, t->n_chi};
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(t->ids.data(), sizeof(uint16_t) * t->ids.size(), h);
+    h = fnv1a(t->w.data(), sizeof(int64_t) * t->w.size(), h);
+    h = fnv1a(t->rep.data(), sizeof(int64_t) * t->rep.size(), h);
+    bool ok = fwrite(magic, 8, 1, f) == 1 && fwrite(&version, 4, 1, f) == 1 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              fwrite(t->chi, 12, 1, f) == 1 && fwrite(&t->U, 8, 1, f) == 1 && fwrite(&t->scale, 8, 1, f) == 1 &&
+              fwrite(t->stats, sizeof(t->stats), 1, f) == 1 && fwrite(&t->bound, 8, 1, f) == 1;
+    if (ok && t->U > 0)
+        ok = fwrite(t->ids.data(), sizeof(uint16_t), t->ids.size(), f) == t->ids.size() &&
+             fwrite(t->w.data(), sizeof(int64_t), t->w.size(), f) == t->w.size() &&
+             fwrite(t->rep.data(), sizeof(int64_t), t->rep.size(), f) == t->rep.size();
+    ok = ok && fwrite(&h, 8, 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? WICK_OK : WICK_EIO;
+}
+
+int wick_terms_load(const char *path, wick_terms **out) {
+    if (!path || !out) return WICK_EINVAL;
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return WICK_EIO;
+    char magic[8];
+    uint32_t version = 0;
+    int32_t hdr[5];
+    wick_terms *t = new (std::nothrow) wick_terms();
+    if (!t) { fclose(f); return WICK_ENOMEM; }
+    bool ok = fread(magic, 8, 1, f) == 1 && memcmp(magic, "WICKTBL1", 8) == 0 && fread(&version, 4, 1, f) == 1 &&
+              version == 1 && fread(hdr, sizeof(hdr), 1, f) == 1 && fread(t->chi, 12, 1, f) == 1 &&
+              fread(&t->U, 8, 1, f) == 1 && fread(&t->scale, 8, 1, f) == 1 &&
+              fread(t->stats, sizeof(t->stats), 1, f) == 1 && fread(&t->bound, 8, 1, f) == 1;
+    if (ok) {
+        t->A = hdr[0]; t->n_blk = hdr[1]; t->n_ops = hdr[2]; t->n_spin = hdr[3]; t->n_chi = hdr[4];
+        ok = t->A >= 1 && t->A <= kMaxA && t->U >= 0 && t->U < (1ll << 40) && t->n_blk > 0;
+    }
+    if (ok) {
+        t->ids.resize((size_t)t->U * t->A);
+        t->w.resize(t->U);
+        t->rep.resize(t->U);
+        if (t->U > 0)
+            ok = fread(t->ids.data(), sizeof(uint16_t), t->ids.size(), f) == t->ids.size() &&
+                 fread(t->w.data(), sizeof(int64_t), t->w.size(), f) == t->w.size() &&
+                 fread(t->rep.data(), sizeof(int64_t), t->rep.size(), f) == t->rep.size();
+    }
+    uint64_t h_file = 0;
+    ok = ok && fread(&h_file, 8, 1, f) == 1;
+    fclose(f);
+    if (ok) {
+        uint64_t h = 1469598103934665603ull;
+        h = fnv1a(t->ids.data(), sizeof(uint16_t) * t->ids.size(), h);
+        h = fnv1a(t->w.data(), sizeof(int64_t) * t->w.size(), h);
+        h = fnv1a(t->rep.data(), sizeof(int64_t) * t->rep.size(), h);
+        ok = h == h_file;
+        for (size_t i = 0; ok && i < t->ids.size(); ++i) ok = t->ids[i] < t->n_blk;
+    }
+    if (!ok) { delete t; return WICK_EIO; }
+    int e = upload_terms(t);
+    if (e) { wick_terms_free(t); return e; }
+    *out = t;
+    return WICK_OK;
+}
+
+void wick_terms_free(wick_terms *t) {
+    if (!t) return;
+    cudaFree(t->d_ids);
+    cudaFree(t->d_w);
+    cudaFree(t->d_rep);
+    delete t;
+}
+
+int wick_contract(const void *blocks, int n_src, int T, const wick_terms *t, int precision, void *C_out,
+                  wick_stream_t stream) {
+    if (!blocks || !t || !C_out || n_src < 1 || T < 1) return WICK_EINVAL;
+    if (precision != WICK_FP64 && precision != WICK_MIXED) return WICK_EINVAL;
+    if ((uintptr_t)blocks % 16 || (uintptr_t)C_out % 16) return WICK_EINVAL;
+    const int64_t n_slices = (int64_t)n_src * T;
+    if (n_slices > 65535) return WICK_EINVAL;
+    int n_chunks = 1;
+    const size_t bytes = contract_partials_bytes((int)n_slices, t->U, t->A, t->n_blk, &n_chunks);
+    int err = WICK_OK;
+    void *ws = workspace(1, bytes, &err);
+    if (err) return err;
+    return launch_contract((const double2 *)blocks, (int)n_slices, t->n_blk, t->A, t->U, t->d_ids, t->d_w, t->scale,
+                           precision, (double2 *)C_out, (double *)ws, n_chunks, (cudaStream_t)stream);
+}
+
+int wick_status(wick_stream_t stream) { return status_read_clear((cudaStream_t)stream); }
+
+const char *wick_strerror(int code) {
+    switch (code) {
+        case WICK_OK: return "ok";
+        case WICK_EINVAL: return "invalid argument";
+        case WICK_ENOMEM: return "out of memory";
+        case WICK_ECUDA: return "CUDA error";
+        case WICK_ECAPACITY: return "term table capacity exceeded";
+        case WICK_EOVERFLOW: return "integer overflow";
+        case WICK_ETIMEOUT: return "bounded device wait ran out";
+        case WICK_EIO: return "term-table file missing, truncated or corrupt";
+        default: return "unknown error";
+    }
+}
+
+const char *wick_version(void) { return "0.1.0"; }
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+// Correlator from the reduced term table (Eq. 2.6 generalised in App. D):
+//   C[slice] = scale * sum_u w_u prod_k B[slice][id_{u,k}]
+//
+// grid = (slice, term chunk).  A CTA stages its slice's blocks in shared
+// memory when they fit (complex128 for FP64, complex64 for MIXED), then each
+// thread walks the chunk's terms with stride blockDim (coalesced reads of the
+// uint16 ids and int64 weights), multiplies the A gathered block entries and
+// accumulates in FP64.  The CTA reduces in a fixed tree; a second kernel sums
+// the chunk partials in chunk order.  Both orders are fixed: the result is
+// bitwise reproducible.
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace wick {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMinTermsPerChunk = 2048;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+template <typename C>
+__device__ __forceinline__ C load_blk(const double2 *p) {
+    const double2 v = __ldg(p);
+    if constexpr (std::is_same<C, float2>::value) return make_float2((float)v.x, (float)v.y);
+    else return v;
+}
+
+template <int A, bool MIXED, bool SMEM>
+__global__ void __launch_bounds__(kThreads)
+contract_kernel(const double2 *__restrict__ blocks, int n_blk, int64_t U, const uint16_t *__restrict__ ids,
+                const int64_t *__restrict__ w, int64_t chunk, int n_slices, double2 *__restrict__ partials) {
+    using C = typename std::conditional<MIXED, float2, double2>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *sB = reinterpret_cast<C *>(smem_raw);
+    const int slice = blockIdx.x;
+    const double2 *gB = blocks + (size_t)slice * n_blk;
+    if constexpr (SMEM) {
+        for (int i = threadIdx.x; i < n_blk; i += kThreads) {
+            const double2 v = gB[i];
+            if constexpr (MIXED) sB[i] = make_float2((float)v.x, (float)v.y);
+            else sB[i] = v;
+        }
+        __syncthreads();
+    }
+    const int64_t u0 = (int64_t)blockIdx.y * chunk;
+    const int64_t u1 = min(U, u0 + chunk);
+    double ax = 0.0, ay = 0.0;
+    for (int64_t u = u0 + threadIdx.x; u < u1; u += kThreads) {
+        const uint16_t *id = ids + u * A;
+        C p;
+        if constexpr (SMEM) p = sB[id[0]];
+        else p = load_blk<C>(gB + id[0]);
+#pragma unroll
+        for (int k = 1; k < A; ++k) {
+            C b;
+            if constexpr (SMEM) b = sB[id[k]];
+            else b = load_blk<C>(gB + id[k]);
+            p = cmul(p, b);
+        }
+        const double wu = (double)w[u];
+        ax = fma(wu, (double)p.x, ax);
+        ay = fma(wu, (double)p.y, ay);
+    }
+    __shared__ double rx[kThreads], ry[kThreads];
+    rx[threadIdx.x] = ax;
+    ry[threadIdx.x] = ay;
+    __syncthreads();
+    for (int off = kThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            rx[threadIdx.x] += rx[threadIdx.x + off];
+            ry[threadIdx.x] += ry[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[(size_t)blockIdx.y * n_slices + slice] = make_double2(rx[0], ry[0]);
+}
+
+__global__ void contract_finish_kernel(const double2 *__restrict__ partials, int n_chunks, int n_slices,
+                                       double scale, double2 *__restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_slices) return;
+    double x = 0, y = 0;
+    for (int c = 0; c < n_chunks; ++c) {
+        const double2 v = partials[(size_t)c * n_slices + s];
+        x += v.x;
+        y += v.y;
+    }
+    out[s] = make_double2(scale * x, scale * y);
+}
+
+template <int A, bool MIXED>
+int launch_a(const double2 *blocks, int n_slices, int n_blk, int64_t U, const uint16_t *ids, const int64_t *w,
+             int64_t chunk, int n_chunks, double2 *partials, cudaStream_t stream) {
+    const size_t esz = MIXED ? sizeof(float2) : sizeof(double2);
+    const size_t smem = esz * (size_t)n_blk;
+    dim3 grid(n_slices, n_chunks);
+    if (smem <= 200 * 1024) {
+        auto k = contract_kernel<A, MIXED, true>;
+        WICK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k<<<grid, kThreads, smem, stream>>>(blocks, n_blk, U, ids, w, chunk, n_slices, partials);
+    } else {
+        contract_kernel<A, MIXED, false><<<grid, kThreads, 0, stream>>>(blocks, n_blk, U, ids, w, chunk, n_slices,
+                                                                        partials);
+    }
+    WICK_CUDA_TRY(cudaGetLastError());
+    return WICK_OK;
+}
+
+template <bool MIXED>
+int launch_p(int A, const double2 *blocks, int n_slices, int n_blk, int64_t U, const uint16_t *ids,
+             const int64_t *w, int64_t chunk, int n_chunks, double2 *partials, cudaStream_t stream) {
+    switch (A) {
+        case 1: return launch_a<1, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
+        case 2: return launch_a<2, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
+        case 3: return launch_a<3, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
+        case 4: return launch_a<4, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
+        case 5: return launch_a<5, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
+        case 6: return launch_a<6, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
+        case 7: return launch_a<7, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
+        case 8: return launch_a<8, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
+        default: return WICK_EINVAL;
+    }
+}
+
+}  // namespace
+
+size_t contract_partials_bytes(int n_slices, int64_t U, int A, int n_blk, int *n_chunks) {
+    (void)A; (void)n_blk;
+    int dev = 0, n_sm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    // enough CTAs for two waves, but never chunks of fewer than kMinTermsPerChunk terms
+    int64_t want = (2 * (int64_t)n_sm + n_slices - 1) / n_slices;
+    const int64_t most = (U + kMinTermsPerChunk - 1) / kMinTermsPerChunk;
+    if (want > most) want = most;
+    if (want < 1) want = 1;
+    *n_chunks = (int)want;
+    return sizeof(double2) * (size_t)want * n_slices;
+}
+
+int launch_contract(const double2 *blocks, int n_slices, int n_blk, int A, int64_t U, const uint16_t *ids,
+                    const int64_t *w, double scale, int precision, double2 *C_out, double *partials_raw,
+                    int n_chunks, cudaStream_t stream) {
+    double2 *partials = reinterpret_cast<double2 *>(partials_raw);
+    const int64_t chunk = (U + n_chunks - 1) / n_chunks;
+    int e = precision == WICK_MIXED
+                ? launch_p<true>(A, blocks, n_slices, n_blk, U, ids, w, chunk > 0 ? chunk : 1, n_chunks, partials, stream)
+                : launch_p<false>(A, blocks, n_slices, n_blk, U, ids, w, chunk > 0 ? chunk : 1, n_chunks, partials, stream);
+    if (e) return e;
+    contract_finish_kernel<<<(n_slices + 127) / 128, 128, 0, stream>>>(partials, n_chunks, n_slices, scale, C_out);
+    WICK_CUDA_TRY(cudaGetLastError());
+    return WICK_OK;
+}
+
+}  // namespace wick

@@ -1,0 +1,168 @@
+"""Integer operator weight tables for the C ABI (host side, no GPU needed).
+
+Builds, from the paper's definitions, the tables `wick_build_blocks` and
+`wick_reduce_terms` take:
+
+* nucleon operators p_s = eps_abc u^a_s u^b_beta Gamma_{beta eta} d^c_eta and
+  n_s with u <-> d (Eqs. 1000/1001), Gamma = C gamma5 with C = gamma4 gamma2
+  (Sec. II) in the Dirac-Pauli basis, optionally times P_pm = (1 pm gamma4)/2
+  (Sec. III.C);
+* nucleus operators as integer combinations of products of nucleon operators
+  (Sec. III.C): the deuteron p(up) n(up), He-3 antisymmetrised in the proton
+  spins, He-4 p(up) p(down) n(up) n(down).
+
+"Upper" form: all quark spins restricted to the upper Dirac components
+(alpha in {0, 1}); the block layout then keeps the 6 source indices with an
+upper spin and 2 nucleon spin labels.
+
+Every table is canonical (sorted, duplicates merged, zeros dropped), so the
+raw-term order of the reduction -- and hence the reduced table byte for byte --
+is a function of the operator alone.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from itertools import permutations
+from math import factorial
+
+import numpy as np
+
+U, D = 0, 1
+PROTON, NEUTRON = 0, 1
+
+_SX = np.array([[0, 1], [1, 0]], dtype=complex)
+_SY = np.array([[0, -1j], [1j, 0]], dtype=complex)
+_SZ = np.array([[1, 0], [0, -1]], dtype=complex)
+_I2 = np.eye(2, dtype=complex)
+
+
+def dirac_matrices():
+    """(g1, g2, g3, g4, g5) in the Dirac-Pauli basis: g_k = sigma_y (x) sigma_k,
+    g4 = sigma_z (x) 1, g5 = g1 g2 g3 g4."""
+    g = [np.kron(_SY, s) for s in (_SX, _SY, _SZ)]
+    g4 = np.kron(_SZ, _I2)
+    return g[0], g[1], g[2], g4, g[0] @ g[1] @ g[2] @ g4
+
+
+def diquark_matrix(parity: int = 0) -> np.ndarray:
+    """C gamma5 (parity 0) or C gamma5 P_pm (parity +1 / -1) as an int matrix."""
+    g1, g2, g3, g4, g5 = dirac_matrices()
+    m = g4 @ g2 @ g5
+    if parity:
+        m = m @ (0.5 * (np.eye(4) + parity * g4))
+    r = np.round(m.real)
+    if np.abs(m - r).max() > 1e-12:
+        raise ValueError("diquark matrix is not integral in this basis")
+    return r.astype(np.int64)
+
+
+def _eps_entries():
+    out = []
+    for p in permutations(range(3)):
+        inv = sum(p[i] > p[j] for i in range(3) for j in range(i + 1, 3))
+        out.append((p, -1 if inv & 1 else 1))
+    return out
+
+
+@dataclass
+class NucleonOp:
+    flav_pair: int                                  # flavour of slots 1, 2
+    entries: list = field(default_factory=list)     # (s, chi1, chi2, chi3, w), canonical
+
+
+def nucleon_op(flav_pair: int, gamma: np.ndarray, nucleon_spins, quark_spins) -> NucleonOp:
+    acc = {}
+    for s in nucleon_spins:
+        for (a, b, c), sg in _eps_entries():
+            for be in quark_spins:
+                for et in quark_spins:
+                    w = sg * int(gamma[be, et])
+                    if w:
+                        k = (s, 4 * a + s, 4 * b + be, 4 * c + et)
+                        acc[k] = acc.get(k, 0) + w
+    return NucleonOp(flav_pair, sorted(k + (w,) for k, w in acc.items() if w))
+
+
+@dataclass
+class Nucleus:
+    name: str
+    A: int
+    ops: list          # NucleonOp per block type
+    n_spin: int
+    chi: list          # source indices kept in the block layout
+    sink: list         # (types tuple, spins tuple, w)
+    src: list          # (chi' tuple of length 3A, w)
+    src_flav: list
+    scale: float = 1.0
+
+    @property
+    def quark_counts(self):
+        nu = sum(1 for f in self.src_flav if f == U)
+        return nu, len(self.src_flav) - nu
+
+    @property
+    def n_raw(self) -> int:
+        nu, nd = self.quark_counts
+        return len(self.sink) * len(self.src) * factorial(nu) * factorial(nd)
+
+    @property
+    def n_blk(self) -> int:
+        return len(self.ops) * self.n_spin * len(self.chi) ** 3
+
+
+def _source_table(ops, types, spin_combos):
+    acc = {}
+    for spins, coef in spin_combos:
+        rows = [[e for e in ops[o].entries if e[0] == s] for o, s in zip(types, spins)]
+        # cartesian product of the nucleons' entries
+        idx = [0] * len(rows)
+        while True:
+            chi, w = [], coef
+            for r, i in zip(rows, idx):
+                chi += list(r[i][1:4])
+                w *= r[i][4]
+            acc[tuple(chi)] = acc.get(tuple(chi), 0) + w
+            k = len(rows) - 1
+            while k >= 0:
+                idx[k] += 1
+                if idx[k] < len(rows[k]):
+                    break
+                idx[k] = 0
+                k -= 1
+            if k < 0:
+                break
+    return sorted((c, w) for c, w in acc.items() if w)
+
+
+_NUCLEI = {
+    "proton": ((PROTON,), [((0,), 1)]),
+    "deuteron": ((PROTON, NEUTRON), [((0, 0), 1)]),
+    "he3": ((PROTON, PROTON, NEUTRON), [((0, 1, 0), 1), ((1, 0, 0), -1)]),
+    "he4": ((PROTON, PROTON, NEUTRON, NEUTRON), [((0, 1, 0, 1), 1)]),
+}
+
+
+def standard_ops(form: str = "upper"):
+    G = diquark_matrix()
+    if form == "upper":
+        sp = (0, 1)
+    elif form == "full":
+        sp = (0, 1, 2, 3)
+    else:
+        raise ValueError(form)
+    return [nucleon_op(U, G, sp, sp), nucleon_op(D, G, sp, sp)]
+
+
+def nucleus(name: str, form: str = "upper") -> Nucleus:
+    """Standard nucleus operators (same spin combination at sink and source)."""
+    types, combos = _NUCLEI[name]
+    ops = standard_ops(form)
+    n_spin = 2 if form == "upper" else 4
+    chi = [c for c in range(12) if c % 4 < n_spin]
+    sink = sorted((tuple(types), tuple(s), w) for s, w in combos)
+    src = _source_table(ops, types, combos)
+    flav = []
+    for o in types:
+        f = ops[o].flav_pair
+        flav += [f, f, 1 - f]
+    return Nucleus(name, len(types), ops, n_spin, chi, sink, src, flav)

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of libwick (include/wick.h): argument marshalling only.
+
+The function names mirror the C ABI.  Device buffers are passed as torch CUDA
+tensors (or raw integer device pointers); operator tables as the dataclasses
+of `operators`.  Every computation runs in the CUDA library; if libwick.so is
+missing this module raises on first use -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import operators as _ops
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwick.so")
+
+WICK_OK, WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA = 0, -1, -2, -3
+WICK_ECAPACITY, WICK_EOVERFLOW, WICK_ETIMEOUT, WICK_EIO = -4, -5, -6, -7
+WICK_C128, WICK_C64 = 0, 1
+WICK_FP64, WICK_MIXED = 0, 1
+WICK_U, WICK_D = 0, 1
+
+EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_reduce_terms", "wick_terms_count",
+           "wick_terms_nucleons", "wick_terms_copy", "wick_terms_stats", "wick_terms_select",
+           "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_status",
+           "wick_strerror", "wick_version")
+
+
+class WickError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class wick_prop(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("L", C.c_int), ("T", C.c_int), ("n_src", C.c_int), ("dtype", C.c_int)]
+
+
+class wick_nucleon_op(C.Structure):
+    _fields_ = [("n_entries", C.c_int), ("entries", C.POINTER(C.c_int8)), ("w", C.POINTER(C.c_int32)),
+                ("flav_pair", C.c_int)]
+
+
+class wick_block_layout(C.Structure):
+    _fields_ = [("n_ops", C.c_int), ("n_spin", C.c_int), ("n_chi", C.c_int), ("chi", C.c_int8 * 12)]
+
+
+class wick_nucleus(C.Structure):
+    _fields_ = [("A", C.c_int), ("n_sink", C.c_int), ("sink_type", C.POINTER(C.c_int8)),
+                ("sink_spin", C.POINTER(C.c_int8)), ("sink_w", C.POINTER(C.c_int64)), ("n_src", C.c_int),
+                ("src_chi", C.POINTER(C.c_int8)), ("src_w", C.POINTER(C.c_int64)),
+                ("src_flav", C.POINTER(C.c_int8)), ("scale", C.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libwick.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"libwick.so not found at {path}: run paper_2411_08962_gb300.build")
+            L = C.CDLL(path)
+            vp, P = C.c_void_p, C.POINTER
+            L.wick_block_count.argtypes = [P(wick_block_layout)]
+            L.wick_block_count.restype = C.c_size_t
+            L.wick_build_blocks.argtypes = [P(wick_prop), P(wick_prop), P(wick_nucleon_op), P(wick_block_layout),
+                                            C.c_int, vp, vp]
+            L.wick_reduce_terms.argtypes = [P(wick_nucleus), P(wick_nucleon_op), P(wick_block_layout), C.c_uint64,
+                                            C.c_int, C.c_int, P(vp), vp]
+            L.wick_terms_count.argtypes = [vp]
+            L.wick_terms_count.restype = C.c_int64
+            L.wick_terms_nucleons.argtypes = [vp]
+            L.wick_terms_copy.argtypes = [vp, vp, vp, vp]
+            L.wick_terms_stats.argtypes = [vp, P(C.c_int64), P(C.c_double)]
+            L.wick_terms_select.argtypes = [vp, P(C.c_int64), C.c_int64]
+            L.wick_terms_save.argtypes = [vp, C.c_char_p]
+            L.wick_terms_load.argtypes = [C.c_char_p, P(vp)]
+            L.wick_terms_free.argtypes = [vp]
+            L.wick_terms_free.restype = None
+            L.wick_contract.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp]
+            L.wick_status.argtypes = [vp]
+            L.wick_strerror.argtypes = [C.c_int]
+            L.wick_strerror.restype = C.c_char_p
+            L.wick_version.restype = C.c_char_p
+            for f in ("wick_build_blocks", "wick_reduce_terms", "wick_terms_nucleons", "wick_terms_copy",
+                      "wick_terms_stats", "wick_terms_select", "wick_terms_save", "wick_terms_load",
+                      "wick_contract", "wick_status"):
+                getattr(L, f).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().wick_strerror(code).decode()
+    except RuntimeError:
+        return f"error {code}"
+
+
+def _check(rc, what):
+    if rc != WICK_OK:
+        raise WickError(rc, what)
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (or an int)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _np_ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class Tables:
+    """ctypes views of a `operators.Nucleus` (keeps the numpy arrays alive)."""
+
+    def __init__(self, nuc: _ops.Nucleus):
+        self.nuc = nuc
+        self._keep = []
+        n_ops = len(nuc.ops)
+        self.ops = (wick_nucleon_op * n_ops)()
+        for o, op in enumerate(nuc.ops):
+            ent = np.array([e[:4] for e in op.entries], dtype=np.int8).reshape(-1)
+            w = np.array([e[4] for e in op.entries], dtype=np.int32)
+            self._keep += [ent, w]
+            self.ops[o] = wick_nucleon_op(len(op.entries), _np_ptr(ent, C.c_int8), _np_ptr(w, C.c_int32),
+                                          op.flav_pair)
+        chi = (C.c_int8 * 12)(*(list(nuc.chi) + [0] * (12 - len(nuc.chi))))
+        self.layout = wick_block_layout(n_ops, nuc.n_spin, len(nuc.chi), chi)
+        A = nuc.A
+        st = np.array([t for t, _, _ in nuc.sink], dtype=np.int8).reshape(-1)
+        ss = np.array([s for _, s, _ in nuc.sink], dtype=np.int8).reshape(-1)
+        sw = np.array([w for _, _, w in nuc.sink], dtype=np.int64)
+        sc = np.array([c for c, _ in nuc.src], dtype=np.int8).reshape(-1)
+        cw = np.array([w for _, w in nuc.src], dtype=np.int64)
+        fl = np.array(nuc.src_flav, dtype=np.int8)
+        self._keep += [st, ss, sw, sc, cw, fl]
+        self.nucleus = wick_nucleus(A, len(nuc.sink), _np_ptr(st, C.c_int8), _np_ptr(ss, C.c_int8),
+                                    _np_ptr(sw, C.c_int64), len(nuc.src), _np_ptr(sc, C.c_int8),
+                                    _np_ptr(cw, C.c_int64), _np_ptr(fl, C.c_int8), float(nuc.scale))
+
+
+def wick_block_count(tables: Tables) -> int:
+    return int(load().wick_block_count(C.byref(tables.layout)))
+
+
+def wick_build_blocks(Su, Sd, tables: Tables, precision: int, blocks, L: int, T: int, n_src: int, stream=None):
+    """Blocks[src][t][n_blk] complex128 (torch.complex128 CUDA tensor) from Su, Sd."""
+    def prop(S):
+        dt = WICK_C64 if str(S.dtype) == "torch.complex64" else WICK_C128
+        return wick_prop(_ptr(S), L, T, n_src, dt)
+    pu, pd = prop(Su), prop(Sd)
+    _check(load().wick_build_blocks(C.byref(pu), C.byref(pd), tables.ops, C.byref(tables.layout), precision,
+                                    _ptr(blocks), _stream(stream)), "wick_build_blocks")
+
+
+class Terms:
+    """Library-owned reduced term table."""
+
+    def __init__(self, handle):
+        self.h = C.c_void_p(handle)
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "h", None) and self.h.value:
+            load().wick_terms_free(self.h)
+            self.h = C.c_void_p(None)
+
+    @property
+    def count(self) -> int:
+        return int(load().wick_terms_count(self.h))
+
+    @property
+    def nucleons(self) -> int:
+        return int(load().wick_terms_nucleons(self.h))
+
+    def copy(self):
+        U, A = self.count, self.nucleons
+        ids = np.zeros((U, A), dtype=np.uint16)
+        w = np.zeros(U, dtype=np.int64)
+        rep = np.zeros(U, dtype=np.int64)
+        _check(load().wick_terms_copy(self.h, ids.ctypes.data, w.ctypes.data, rep.ctypes.data), "wick_terms_copy")
+        return dict(ids=ids, w=w, rep=rep)
+
+    def stats(self):
+        st = np.zeros(4, dtype=np.int64)
+        b = C.c_double(0)
+        _check(load().wick_terms_stats(self.h, _np_ptr(st, C.c_int64), C.byref(b)), "wick_terms_stats")
+        return tuple(int(x) for x in st), float(b.value)
+
+    def select(self, perm):
+        p = np.ascontiguousarray(perm, dtype=np.int64)
+        _check(load().wick_terms_select(self.h, _np_ptr(p, C.c_int64), len(p)), "wick_terms_select")
+
+    def save(self, path: str):
+        _check(load().wick_terms_save(self.h, path.encode()), "wick_terms_save")
+
+    @classmethod
+    def load_file(cls, path: str) -> "Terms":
+        h = C.c_void_p(None)
+        _check(load().wick_terms_load(path.encode(), C.byref(h)), "wick_terms_load")
+        return cls(h.value)
+
+
+def wick_reduce_terms(tables: Tables, seed: int = 0x2411, trials: int = 2, sites: int = 1, stream=None) -> Terms:
+    h = C.c_void_p(None)
+    _check(load().wick_reduce_terms(C.byref(tables.nucleus), tables.ops, C.byref(tables.layout), seed, trials, sites,
+                                    C.byref(h), _stream(stream)), "wick_reduce_terms")
+    return Terms(h.value)
+
+
+def wick_contract(blocks, n_src: int, T: int, terms: Terms, precision: int, C_out, stream=None):
+    _check(load().wick_contract(_ptr(blocks), n_src, T, terms.h, precision, _ptr(C_out), _stream(stream)),
+           "wick_contract")
+
+
+def wick_status(stream=None) -> int:
+    return int(load().wick_status(_stream(stream)))
+
+
+def wick_version() -> str:
+    return load().wick_version().decode()
