@@ -52,7 +52,7 @@ extern "C" {
 
 /* arithmetic of a call */
 #define WICK_FP64 0  /* FP64 products and sums */
-#define WICK_MIXED 1 /* FP32 products, FP64 sums over sites and terms */
+#define WICK_MIXED 1 /* double-FP32 products on the float pipes, FP64 sums over site chunks and terms */
 
 /* quark flavours */
 #define WICK_U 0
@@ -139,9 +139,11 @@ size_t wick_block_count(const wick_block_layout *layout);
  * writes the same exchange on the sink side).
  *   Su, Sd      propagators (same L, T, n_src; dtype may differ)
  *   ops         layout->n_ops nucleon operators
- *   precision   WICK_FP64: FP64 throughout.  WICK_MIXED: per-site products in
- *               FP32 with FP32 partial sums over a chunk of at most 256 sites,
- *               FP64 sum of the chunks.
+ *   precision   WICK_FP64: FP64 throughout.  WICK_MIXED: double-FP32 on the float
+ *               pipes -- products of the float propagator entries formed exactly
+ *               with FMA, sums as float pairs (about 44 significant bits) over a
+ *               chunk of at most 256 sites -- and an FP64 sum of the chunks.
+ *               C128 input is rounded to float first under WICK_MIXED.
  *   blocks      device, caller-owned, complex128 [n_src][T][wick_block_count]
  * Uses a library-cached device workspace for the per-chunk FP64 partials
  * (allocated on first use and grown when needed: make the first call, with
@@ -203,8 +205,9 @@ void wick_terms_free(wick_terms *terms);
  *   C[src][t] = scale * sum_u w_u prod_k B[src][t][id_{u,k}]
  *   blocks     device complex128 [n_src][T][n_blk], from wick_build_blocks with
  *              the layout the table was reduced for (n_blk is checked)
- *   precision  WICK_FP64: FP64 products and sums.  WICK_MIXED: blocks rounded
- *              to complex float, products in FP32, FP64 sum over terms.
+ *   precision  WICK_FP64: FP64 products and sums.  WICK_MIXED: block entries
+ *              split into float pairs, products in double-FP32 on the float
+ *              pipes, FP64 sum over terms.
  *   C_out      device complex128 [n_src][T], caller-owned, overwritten.
  * Deterministic (fixed reduction order).  Errors: WICK_EINVAL, WICK_ECUDA.
  */

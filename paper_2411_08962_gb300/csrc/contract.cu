@@ -5,12 +5,15 @@
 // memory when they fit (complex128 for FP64, complex64 for MIXED), then each
 // thread walks the chunk's terms with stride blockDim (coalesced reads of the
 // uint16 ids and int64 weights), multiplies the A gathered block entries and
-// accumulates in FP64.  The CTA reduces in a fixed tree; a second kernel sums
+// accumulates in FP64.  MIXED keeps every block entry as a double-FP32 pair
+// and forms the products with error-free float operations (about 44 bits),
+// so the float pipes do the products and only the term sum is FP64.  The CTA reduces in a fixed tree; a second kernel sums
 // the chunk partials in chunk order.  Both orders are fixed: the result is
 // bitwise reproducible.
 #include <type_traits>
 
 #include "common.cuh"
+#include "df32.cuh"
 
 namespace wick {
 
@@ -22,32 +25,40 @@ constexpr int kMinTermsPerChunk = 2048;
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
 
-template <typename C>
-__device__ __forceinline__ C load_blk(const double2 *p) {
-    const double2 v = __ldg(p);
-    if constexpr (std::is_same<C, float2>::value) return make_float2((float)v.x, (float)v.y);
-    else return v;
-}
+__device__ __forceinline__ cdf to_cdf(double2 v) { return {split_double(v.x), split_double(v.y)}; }
+
+template <bool MIXED>
+struct Elem;
+template <>
+struct Elem<true> {
+    using T = cdf;
+    static __device__ __forceinline__ T from(double2 v) { return to_cdf(v); }
+    static __device__ __forceinline__ T mul(const T &a, const T &b) { return cdf_mul(a, b); }
+    static __device__ __forceinline__ double re(const T &a) { return to_double(a.x); }
+    static __device__ __forceinline__ double im(const T &a) { return to_double(a.y); }
+};
+template <>
+struct Elem<false> {
+    using T = double2;
+    static __device__ __forceinline__ T from(double2 v) { return v; }
+    static __device__ __forceinline__ T mul(const T &a, const T &b) { return cmul(a, b); }
+    static __device__ __forceinline__ double re(const T &a) { return a.x; }
+    static __device__ __forceinline__ double im(const T &a) { return a.y; }
+};
 
 template <int A, bool MIXED, bool SMEM>
 __global__ void __launch_bounds__(kThreads)
 contract_kernel(const double2 *__restrict__ blocks, int n_blk, int64_t U, const uint16_t *__restrict__ ids,
                 const int64_t *__restrict__ w, int64_t chunk, int n_slices, double2 *__restrict__ partials) {
-    using C = typename std::conditional<MIXED, float2, double2>::type;
+    using E = Elem<MIXED>;
+    using C = typename E::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sB = reinterpret_cast<C *>(smem_raw);
     const int slice = blockIdx.x;
     const double2 *gB = blocks + (size_t)slice * n_blk;
     if constexpr (SMEM) {
-        for (int i = threadIdx.x; i < n_blk; i += kThreads) {
-            const double2 v = gB[i];
-            if constexpr (MIXED) sB[i] = make_float2((float)v.x, (float)v.y);
-            else sB[i] = v;
-        }
+        for (int i = threadIdx.x; i < n_blk; i += kThreads) sB[i] = E::from(gB[i]);
         __syncthreads();
     }
     const int64_t u0 = (int64_t)blockIdx.y * chunk;
@@ -57,17 +68,17 @@ contract_kernel(const double2 *__restrict__ blocks, int n_blk, int64_t U, const 
         const uint16_t *id = ids + u * A;
         C p;
         if constexpr (SMEM) p = sB[id[0]];
-        else p = load_blk<C>(gB + id[0]);
+        else p = E::from(__ldg(gB + id[0]));
 #pragma unroll
         for (int k = 1; k < A; ++k) {
             C b;
             if constexpr (SMEM) b = sB[id[k]];
-            else b = load_blk<C>(gB + id[k]);
-            p = cmul(p, b);
+            else b = E::from(__ldg(gB + id[k]));
+            p = E::mul(p, b);
         }
         const double wu = (double)w[u];
-        ax = fma(wu, (double)p.x, ax);
-        ay = fma(wu, (double)p.y, ay);
+        ax = fma(wu, E::re(p), ax);
+        ay = fma(wu, E::im(p), ay);
     }
     __shared__ double rx[kThreads], ry[kThreads];
     rx[threadIdx.x] = ax;
@@ -99,8 +110,7 @@ __global__ void contract_finish_kernel(const double2 *__restrict__ partials, int
 template <int A, bool MIXED>
 int launch_a(const double2 *blocks, int n_slices, int n_blk, int64_t U, const uint16_t *ids, const int64_t *w,
              int64_t chunk, int n_chunks, double2 *partials, cudaStream_t stream) {
-    const size_t esz = MIXED ? sizeof(float2) : sizeof(double2);
-    const size_t smem = esz * (size_t)n_blk;
+    const size_t smem = sizeof(typename Elem<MIXED>::T) * (size_t)n_blk;
     dim3 grid(n_slices, n_chunks);
     if (smem <= 200 * 1024) {
         auto k = contract_kernel<A, MIXED, true>;
