@@ -45,6 +45,7 @@ extern "C" {
 #define WICK_EOVERFLOW (-5) /* an integer weight or count does not fit */
 #define WICK_ETIMEOUT (-6)  /* a bounded device-side wait ran out */
 #define WICK_EIO (-7)       /* term-table file missing, truncated or corrupt */
+#define WICK_ESCRATCH (-8)  /* request larger than the fixed scratch of wick_contract_noalloc */
 
 /* storage type of a propagator */
 #define WICK_C128 0 /* complex double */
@@ -213,6 +214,34 @@ void wick_terms_free(wick_terms *terms);
  */
 int wick_contract(const void *blocks, int n_src, int T, const wick_terms *terms, int precision,
                   void *C_out, wick_stream_t stream);
+
+/*
+ * wick_contract without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- for
+ * example an application whose caching allocator has already reserved the
+ * device memory it is allowed to use, or a runtime that forbids driver-level
+ * allocations (and the implicit device synchronisation of cudaMalloc/cudaFree)
+ * once its set-up phase is over.  wick_contract itself allocates its scratch
+ * on first use; this variant never does.
+ *
+ * Same arguments, result and errors as wick_contract.  Its scratch (the FP64
+ * partial sums, one complex128 per (term chunk, slice)) is a fixed array of
+ * 65,536 complex128 values (1 MiB) that every GPU loading the library holds
+ * until the process exits.  At most 65,536 slices (n_src * T) per call; larger
+ * requests fail with WICK_ESCRATCH.  When the usual chunking would not fit,
+ * fewer term chunks are used (the sum order then differs from wick_contract's
+ * within rounding).
+ *   - The first call on a device looks up the array's device address for that
+ *     device (cudaGetSymbolAddress, with that device current); make that first
+ *     call before any stream capture.
+ *   - Every call shares the one array and it keeps the last call's contents;
+ *     each call writes every partial it reads, so nothing needs clearing, but
+ *     calls that overlap on the GPU (concurrent streams, other host threads)
+ *     race on it: order them.
+ * Errors: as wick_contract, plus WICK_ESCRATCH.
+ */
+int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms *terms, int precision,
+                          void *C_out, wick_stream_t stream);
 
 /* Synchronises `stream` and returns (then clears) the device status word. */
 int wick_status(wick_stream_t stream);

@@ -511,6 +511,25 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *t, int
                            precision, (double2 *)C_out, (double *)ws, n_chunks, (cudaStream_t)stream);
 }
 
+int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms *t, int precision, void *C_out,
+                          wick_stream_t stream) {
+    if (!blocks || !t || !C_out || n_src < 1 || T < 1) return WICK_EINVAL;
+    if (precision != WICK_FP64 && precision != WICK_MIXED) return WICK_EINVAL;
+    if ((uintptr_t)blocks % 16 || (uintptr_t)C_out % 16) return WICK_EINVAL;
+    const int64_t n_slices = (int64_t)n_src * T;
+    if (n_slices > 65535) return WICK_EINVAL;
+    double2 *scratch = nullptr;
+    size_t cap = 0;
+    int err = noalloc_partials(&scratch, &cap);
+    if (err) return err;
+    if ((size_t)n_slices > cap) return WICK_ESCRATCH;
+    int n_chunks = 1;
+    contract_partials_bytes((int)n_slices, t->U, t->A, t->n_blk, &n_chunks);
+    if ((size_t)n_chunks * (size_t)n_slices > cap) n_chunks = (int)(cap / (size_t)n_slices);
+    return launch_contract((const double2 *)blocks, (int)n_slices, t->n_blk, t->A, t->U, t->d_ids, t->d_w, t->scale,
+                           precision, (double2 *)C_out, (double *)scratch, n_chunks, (cudaStream_t)stream);
+}
+
 int wick_status(wick_stream_t stream) { return status_read_clear((cudaStream_t)stream); }
 
 const char *wick_strerror(int code) {
@@ -523,6 +542,7 @@ const char *wick_strerror(int code) {
         case WICK_EOVERFLOW: return "integer overflow";
         case WICK_ETIMEOUT: return "bounded device wait ran out";
         case WICK_EIO: return "term-table file missing, truncated or corrupt";
+        case WICK_ESCRATCH: return "request exceeds the fixed scratch of wick_contract_noalloc";
         default: return "unknown error";
     }
 }

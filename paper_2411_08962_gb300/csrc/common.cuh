@@ -85,6 +85,9 @@ int launch_contract(const double2 *blocks, int n_slices, int n_blk, int A, int64
                     const int64_t *w, double scale, int precision, double2 *C_out, double *partials,
                     int n_chunks, cudaStream_t stream);
 size_t contract_partials_bytes(int n_slices, int64_t U, int A, int n_blk, int *n_chunks);
+// fixed scratch of wick_contract_noalloc (complex128 partials, per device)
+constexpr size_t kNoAllocPartials = 65536;
+int noalloc_partials(double2 **ptr, size_t *capacity);
 
 // ---------------------------------------------------------------------------
 // library workspace (api.cu)

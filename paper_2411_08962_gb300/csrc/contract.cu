@@ -10,6 +10,7 @@
 // so the float pipes do the products and only the term sum is FP64.  The CTA reduces in a fixed tree; a second kernel sums
 // the chunk partials in chunk order.  Both orders are fixed: the result is
 // bitwise reproducible.
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -141,6 +142,46 @@ int launch_p(int A, const double2 *blocks, int n_slices, int n_blk, int64_t U, c
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Fixed scratch of wick_contract_noalloc: the FP64 partial sums, one complex128
+// per (term chunk, slice), in a file-scope device array instead of the
+// library's cudaMalloc'd workspace.  Every device that loads the library holds
+// these kNoAllocPartials * 16 bytes (1 MiB) until the process exits.  Each call
+// writes every partial it later reads, so nothing has to start at zero.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double2 g_noalloc_partials[kNoAllocPartials];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+int noalloc_partials(double2 **ptr, size_t *capacity) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return WICK_ECUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) return WICK_EINVAL;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        // In host code the array's name is only a host-side stand-in; the
+        // device address comes from the runtime, once per device, with that
+        // device current.
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return WICK_ECUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *ptr = static_cast<double2 *>(g_noalloc_addr[dev]);
+    *capacity = kNoAllocPartials;
+    return WICK_OK;
+}
 
 size_t contract_partials_bytes(int n_slices, int64_t U, int A, int n_blk, int *n_chunks) {
     (void)A; (void)n_blk;

@@ -19,14 +19,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwick.so")
 
 WICK_OK, WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA = 0, -1, -2, -3
-WICK_ECAPACITY, WICK_EOVERFLOW, WICK_ETIMEOUT, WICK_EIO = -4, -5, -6, -7
+WICK_ECAPACITY, WICK_EOVERFLOW, WICK_ETIMEOUT, WICK_EIO, WICK_ESCRATCH = -4, -5, -6, -7, -8
 WICK_C128, WICK_C64 = 0, 1
 WICK_FP64, WICK_MIXED = 0, 1
 WICK_U, WICK_D = 0, 1
 
 EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_reduce_terms", "wick_terms_count",
            "wick_terms_nucleons", "wick_terms_copy", "wick_terms_stats", "wick_terms_select",
-           "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_status",
+           "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_contract_noalloc",
+           "wick_status",
            "wick_strerror", "wick_version")
 
 
@@ -86,13 +87,14 @@ def load(path: str = LIB_PATH):
             L.wick_terms_free.argtypes = [vp]
             L.wick_terms_free.restype = None
             L.wick_contract.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp]
+            L.wick_contract_noalloc.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp]
             L.wick_status.argtypes = [vp]
             L.wick_strerror.argtypes = [C.c_int]
             L.wick_strerror.restype = C.c_char_p
             L.wick_version.restype = C.c_char_p
             for f in ("wick_build_blocks", "wick_reduce_terms", "wick_terms_nucleons", "wick_terms_copy",
                       "wick_terms_stats", "wick_terms_select", "wick_terms_save", "wick_terms_load",
-                      "wick_contract", "wick_status"):
+                      "wick_contract", "wick_contract_noalloc", "wick_status"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -238,6 +240,13 @@ def wick_reduce_terms(tables: Tables, seed: int = 0x2411, trials: int = 2, sites
 def wick_contract(blocks, n_src: int, T: int, terms: Terms, precision: int, C_out, stream=None):
     _check(load().wick_contract(_ptr(blocks), n_src, T, terms.h, precision, _ptr(C_out), _stream(stream)),
            "wick_contract")
+
+
+def wick_contract_noalloc(blocks, n_src: int, T: int, terms: Terms, precision: int, C_out, stream=None):
+    """wick_contract for callers that cannot allocate device memory: its scratch
+    is a fixed 1 MiB device array inside the library (see include/wick.h)."""
+    _check(load().wick_contract_noalloc(_ptr(blocks), n_src, T, terms.h, precision, _ptr(C_out), _stream(stream)),
+           "wick_contract_noalloc")
 
 
 def wick_status(stream=None) -> int:
