@@ -44,15 +44,31 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-slab", choices=["mixed", "fp64"], default=None,
+                    help="only run the block build on one source of the workload (for ncu captures)")
     return ap.parse_args()
 
 
 def peaks():
+    """(HBM GB/s, SM max MHz, kind) from the measured-peaks file, else the fallback."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return float(d["hbm_gbs"]), "measured"
-    return FALLBACK_HBM_GBS, "fallback"
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return FALLBACK_HBM_GBS, 2070.0, "fallback"
+
+
+N_SM = 152
+FP32_LANES = 128          # FP32 pipe lanes per SM
+FP64_NOMINAL_TFLOPS = 1.25
+
+# Complex multiply-adds per site of the upper-spin block build (both block
+# types): the diquark lists 2 ops x 3 lists x 36 entries x 4 terms and the
+# update 2 ops x 2 spins x 216 entries x 3 terms.
+CMAC_PER_SITE = 2 * 3 * 36 * 4 + 2 * 2 * 216 * 3
+# FP32-pipe operations per real multiply-add in double-FP32: TwoProd (2), the
+# low-part FMA (1), TwoSum (6) and the two low-part adds (2).
+DF32_OPS_PER_MAC = 11
 
 
 class Clocks:
@@ -115,19 +131,25 @@ def block_bytes_per_site(dtype_bytes: int) -> int:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("blocks.cu", "common.cuh"):
+    for f in ("blocks.cu", "common.cuh", "df32.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2411_08962_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic():
-    p = os.path.join(ROOT, "profiles", "block_build_he4_traffic.json")
+    """DRAM bytes per launch from the committed ncu record, or None when the
+    kernel sources changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "block_build_he4_traffic.txt")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
+    d = {}
+    for line in open(p):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            d[k.strip()] = v.strip()
     if d.get("source_hash") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    return int(d["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in d else None
 
 
 # ---------------------------------------------------------------------------
@@ -318,25 +340,35 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e = float(t.item()) / world
 
-    peak, peak_kind = peaks()
+    hbm_peak, sm_mhz, peak_kind = peaks()
     bytes_launch = n_src * T * V * block_bytes_per_site(8)
-    achieved = bytes_launch / (build_ms / 1e3) / 1e9
+    sites = n_src * T * V
+    ops_launch = sites * CMAC_PER_SITE * 4 * DF32_OPS_PER_MAC
+    alu_peak = N_SM * FP32_LANES * sm_mhz * 1e6 / 1e12      # Top/s, one op per lane per clock
+    achieved = ops_launch / (build_ms / 1e3) / 1e12
+    fp64_block_ms = fp64_ms  # the FP64 step is dominated by its block build
+    fp64_tflops = sites * CMAC_PER_SITE * 8 / (fp64_block_ms / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "L": L, "T": T, "n_src": n_src, "precision": "mixed",
+        "config": {"workload": WORKLOAD, "L": L, "T": T, "n_src": n_src, "precision": "mixed (double-FP32)",
                    "reduced_terms": U, "l2": "inputs larger than L2 (1.2 GB per configuration; 2 alternate)",
                    "parallelism": f"{world} independent rank(s), configurations sharded"},
         "wick_terms_per_s": terms_per_s,
-        "fp64_plain": {"value": fp64_ms, "unit": UNIT, "speedup_mixed": fp64_ms / value * world},
+        "fp64_plain": {"value": fp64_ms, "unit": UNIT, "speedup_mixed": fp64_ms / value * world,
+                       "fp64_tflops_vs_nominal": fp64_tflops / FP64_NOMINAL_TFLOPS},
         "rel_err_mixed_vs_fp64_max_per_t": rel_err,
         "reduce": {"seconds": reduce_s, "raw_terms": n_raw, "zero_terms": n_zero, "distinct_keys": n_keys,
                    "kept_terms": U, "raw_terms_per_s": n_raw / reduce_s, "false_merge_bound": bound},
-        "roofline": {"kernel": "block build (wick_build_blocks: partial + reduce kernels)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind, "traffic": recorded_traffic(),
-                     "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": build_ms},
+        "roofline": {"kernel": "block build, double-FP32 (block_partial_kernel + block_reduce_kernel)",
+                     "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
+                     "frac": achieved / alu_peak, "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES} FP32 lanes x "
+                                                              f"{sm_mhz:.0f} MHz ({peak_kind} clock)",
+                     "ops_per_launch": ops_launch, "traffic": recorded_traffic(),
+                     "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": build_ms,
+                     "hbm": {"achieved_gbs": bytes_launch / (build_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
+                             "frac": bytes_launch / (build_ms / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind}},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
@@ -344,7 +376,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         tab = he4_oracle_table()
         Su, Sd = (cfg_host[0][0].numpy(), cfg_host[0][1].numpy())
-        sl = [(s, t) for s in range(n_src) for t in range(0, T, 4)]
+        sl = [(s, t) for s in range(n_src) for t in range(T)]   # the whole configuration
         ms, cores, dt = oracle_ms_per_config(Su, Sd, sl, tab)
         line["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{len(sl)} of {n_src * T} (source, time-slice) pairs, "
@@ -355,9 +387,38 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_slab(args):
+    """Block build only, on source 0 of the workload (32 slices, 302 MB of
+    complex64 input): the launch that ncu captures for the kernel summaries."""
+    import torch
+
+    from paper_2411_08962_gb300 import build, operators, synth, wick
+    build.build()
+    wick.load()
+    w = synth.WORKLOADS["he4"]
+    L, T = w["L"], w["T"]
+    Su = torch.from_numpy(synth.propagator(w["seed"], 0, L, T, 1, dtype=np.complex64)).cuda()
+    Sd = torch.from_numpy(synth.propagator(w["seed"], 1, L, T, 1, dtype=np.complex64)).cuda()
+    tabs = wick.Tables(operators.nucleus("he4"))
+    B = torch.empty((1, T, tabs.nuc.n_blk), dtype=torch.complex128, device="cuda")
+    prec = wick.WICK_MIXED if args.profile_slab == "mixed" else wick.WICK_FP64
+    for _ in range(max(2, args.warmup)):
+        wick.wick_build_blocks(Su, Sd, tabs, prec, B, L, T, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        wick.wick_build_blocks(Su, Sd, tabs, prec, B, L, T, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_slab": args.profile_slab, "ms_per_launch": e0.elapsed_time(e1) / args.steps}))
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.profile_slab:
+        run_profile_slab(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

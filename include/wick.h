@@ -243,6 +243,41 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *terms,
 int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms *terms, int precision,
                           void *C_out, wick_stream_t stream);
 
+/*
+ * Batched executor (the paper evaluates one configuration at a time; this
+ * batches many configurations and nuclei into one CUDA graph).
+ * wick_batch_create captures, for n_cfg configurations resident in device
+ * memory, the block build of each configuration followed by wick_contract of
+ * every table in `tables` (all reduced for `layout`, so the nuclei share the
+ * blocks), and instantiates the graph.  The batch owns its scratch; the
+ * caller's buffers must stay valid for the batch's lifetime:
+ *   Su, Sd    n_cfg propagator pairs (same L, T, n_src, dtype)
+ *   blocks    device complex128 [n_cfg][n_src][T][n_blk] (written per run)
+ *   C_out     device complex128 [n_cfg][n_tables][n_src][T]
+ * wick_batch_run launches the whole batch on `stream` (asynchronous).
+ * Errors: WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA.
+ */
+typedef struct wick_batch wick_batch;
+int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n_cfg, const wick_nucleon_op *ops,
+                      const wick_block_layout *layout, const wick_terms *const *tables, int n_tables,
+                      int precision, void *blocks, void *C_out, wick_batch **out);
+int wick_batch_run(wick_batch *batch, wick_stream_t stream);
+int wick_batch_launches(const wick_batch *batch);   /* kernels per run */
+void wick_batch_free(wick_batch *batch);
+
+/*
+ * Synthetic propagator (input generation; no counterpart in the paper, which
+ * reads HISQ/overlap propagators): i.i.d. complex Gaussians with variance 1/2
+ * per component from counter-based SplitMix64 and Box-Muller, one stream per
+ * (seed, flavour, src), written as data[t][x][a][alpha][b][beta] of one source
+ * (out: device, T * L^3 * 144 complex of `dtype`).  The same definition as the
+ * Python package's host generator (values may differ in the last bits: the
+ * device uses CUDA's log and sincospi).  Asynchronous.  Errors: WICK_EINVAL,
+ * WICK_ECUDA.
+ */
+int wick_synth_propagator(uint64_t seed, int flavour, int src, int L, int T, int dtype, void *out,
+                          wick_stream_t stream);
+
 /* Synchronises `stream` and returns (then clears) the device status word. */
 int wick_status(wick_stream_t stream);
 

@@ -96,6 +96,16 @@ int status_read_clear(cudaStream_t stream) {
 // ---------------------------------------------------------------------------
 // layouts and plans
 // ---------------------------------------------------------------------------
+int terms_view(const wick_terms *t, int *A, int64_t *U, int *n_blk, const uint16_t **ids, const int64_t **w,
+               double *scale) {
+    if (!t) return WICK_EINVAL;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return WICK_EINVAL;  // the device copies live on another GPU
+    *A = t->A; *U = t->U; *n_blk = t->n_blk; *ids = t->d_ids; *w = t->d_w; *scale = t->scale;
+    return WICK_OK;
+}
+
 static bool layout_ok(const wick_block_layout *l) {
     if (!l || l->n_ops < 1 || l->n_ops > kMaxOps || l->n_spin < 1 || l->n_spin > kMaxSpin || l->n_chi < 1 ||
         l->n_chi > 12)
@@ -190,6 +200,11 @@ int build_block_plan(const wick_nucleon_op *ops, const wick_block_layout *layout
         }
     }
     P.os_off[P.n_ops * P.n_spin] = n_ost;
+    P.pow2_w = 1;
+    for (int q = 0; q < n_xt; ++q) {
+        const int a = (int)fabsf(P.xt_w[q]);
+        if (a == 0 || (a & (a - 1)) != 0) P.pow2_w = 0;
+    }
     return WICK_OK;
 }
 

@@ -17,7 +17,11 @@
 // Arithmetic: WICK_FP64 -- double throughout.  WICK_MIXED -- double-FP32:
 // products of the (float) propagator entries are formed exactly with FMA
 // (TwoProd) and accumulated as float pairs with TwoSum (about 44 significant
-// bits), on the FP32 pipes; chunk partials in FP64.
+// bits), on the FP32 pipes; chunk partials in FP64.  When every diquark weight
+// is a signed power of two (all operators of Eqs. 1000/1001) the double-FP32
+// steps run on the packed f32x2 instructions: each output keeps one packed
+// accumulator with lanes (re, im) and one with lanes (im, re), so both halves
+// of a complex product use the same operand pair.
 #include <type_traits>
 
 #include "common.cuh"
@@ -27,9 +31,24 @@ namespace wick {
 
 namespace {
 
-constexpr int kThreads = 288;  // 9 warps: one output group per thread for the upper-spin tables
-constexpr int kGroups = 2;     // output groups per thread
-constexpr int kChunk = 256;    // sites per accumulation chunk
+#ifndef WICK_BLK_GROUPS
+#define WICK_BLK_GROUPS 2
+#endif
+#ifndef WICK_BLK_MINB
+#define WICK_BLK_MINB 2
+#endif
+#ifndef WICK_BLK_NS
+#define WICK_BLK_NS 16
+#endif
+#ifndef WICK_BLK_SMEM_KB
+#define WICK_BLK_SMEM_KB 72
+#endif
+constexpr int kThreads = 288;               // 9 warps: one output group per thread for the upper-spin tables
+constexpr int kGroups = WICK_BLK_GROUPS;    // output groups per thread
+constexpr int kMinBlocks = WICK_BLK_MINB;   // resident CTAs per SM the register budget aims at
+constexpr int kMaxNs = WICK_BLK_NS;         // sites staged per tile, at most
+constexpr int kSmemBudget = WICK_BLK_SMEM_KB * 1024;
+constexpr int kChunk = 256;                 // sites per accumulation chunk
 
 __device__ __forceinline__ float2 to_f2(float2 v) { return v; }
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
@@ -43,21 +62,54 @@ __device__ __forceinline__ void cfma(double2 &acc, double2 a, double2 b) {
     acc.y = fma(a.y, b.x, acc.y);
 }
 
-template <bool DF> struct Types;
-template <> struct Types<true> { using S = float2; using X = cdf; };
-template <> struct Types<false> { using S = double2; using X = double2; };
+// arithmetic modes of the block kernel
+constexpr int kFP64 = 0, kDF32 = 1, kDF32X2 = 2;
+
+template <int MODE> struct Types;
+template <> struct Types<kDF32X2> { using S = float2; using X = pdf; };
+template <> struct Types<kDF32> { using S = float2; using X = cdf; };
+template <> struct Types<kFP64> { using S = double2; using X = double2; };
+
+// accumulator of one output: packed mode keeps two (see above)
+template <int MODE> struct Acc { typename Types<MODE>::X v; };
+template <> struct Acc<kDF32X2> { pdf a, b; };
 
 __device__ __forceinline__ void zero(cdf &a) { a.x = {0.f, 0.f}; a.y = {0.f, 0.f}; }
 __device__ __forceinline__ void zero(double2 &a) { a = make_double2(0.0, 0.0); }
-__device__ __forceinline__ double2 out_d2(const cdf &a) { return make_double2(to_double(a.x), to_double(a.y)); }
-__device__ __forceinline__ double2 out_d2(const double2 &a) { return a; }
+__device__ __forceinline__ void zero(pdf &a) { a.h = 0ull; a.l = 0ull; }
+__device__ __forceinline__ void zero(Acc<kFP64> &a) { zero(a.v); }
+__device__ __forceinline__ void zero(Acc<kDF32> &a) { zero(a.v); }
+__device__ __forceinline__ void zero(Acc<kDF32X2> &a) { zero(a.a); zero(a.b); }
+__device__ __forceinline__ double2 out_d2(const Acc<kFP64> &a) { return a.v; }
+__device__ __forceinline__ double2 out_d2(const Acc<kDF32> &a) { return make_double2(to_double(a.v.x), to_double(a.v.y)); }
+__device__ __forceinline__ double2 out_d2(const Acc<kDF32X2> &a) {
+    float ah0, ah1, al0, al1, bh0, bh1, bl0, bl1;
+    upk(a.a.h, ah0, ah1); upk(a.a.l, al0, al1);   // lanes (re, im)
+    upk(a.b.h, bh0, bh1); upk(a.b.l, bl0, bl1);   // lanes (im, re)
+    return make_double2(((double)ah0 + (double)bh1) + ((double)al0 + (double)bl1),
+                        ((double)ah1 + (double)bh0) + ((double)al1 + (double)bl0));
+}
 
-template <bool DF, typename ST>
-__global__ void __launch_bounds__(kThreads, 2)
+// X(c2,c3) += w * a * b (a, b exact float complex), per mode
+__device__ __forceinline__ void x_term(double2 &v, float w, double2 a, double2 b) {
+    const double wd = (double)w;
+    const double2 aw = make_double2(wd * a.x, wd * a.y);
+    v.x = fma(aw.x, b.x, v.x); v.x = fma(-aw.y, b.y, v.x);
+    v.y = fma(aw.x, b.y, v.y); v.y = fma(aw.y, b.x, v.y);
+}
+__device__ __forceinline__ void x_term(cdf &v, float w, float2 a, float2 b) { cacc_fma3(v, w, a, b); }
+
+// P += a * X, per mode
+__device__ __forceinline__ void p_term(Acc<kFP64> &acc, double2 a, const double2 &x) { cfma(acc.v, a, x); }
+__device__ __forceinline__ void p_term(Acc<kDF32> &acc, float2 a, const cdf &x) { cacc_fma(acc.v, a, x); }
+
+template <int MODE, typename ST>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
 block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ Su, const ST *__restrict__ Sd,
                      int V, int n_slices, int chunk, int ns_tile, double2 *__restrict__ partials) {
-    using SC = typename Types<DF>::S;
-    using XC = typename Types<DF>::X;
+    constexpr bool DF = MODE != kFP64;
+    using SC = typename Types<MODE>::S;
+    using XC = typename Types<MODE>::X;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nc = plan.n_chi, nc2 = nc * nc, nc3 = nc2 * nc;
     const int nr0 = plan.n_rows[0], nr1 = plan.n_rows[1], nr = nr0 + nr1;
@@ -71,7 +123,7 @@ block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restric
     const int n_groups = plan.n_ops * plan.n_spin * nc * gpr;
 
     int g_os[kGroups], g_i1[kGroups], g_i23[kGroups], g_cnt[kGroups], g_f[kGroups];
-    XC acc[kGroups][3];
+    Acc<MODE> acc[kGroups][3];
 #pragma unroll
     for (int k = 0; k < kGroups; ++k) {
         const int g = blockIdx.z * (kThreads * kGroups) + threadIdx.x + k * kThreads;
@@ -115,18 +167,27 @@ block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restric
             const int f1 = plan.f1[plan.x_op[l]];
             const SC *s1 = sS + (size_t)site * nr * nc + (f1 == 0 ? 0 : nr0 * nc);
             const SC *s2 = sS + (size_t)site * nr * nc + (f1 == 0 ? nr0 * nc : 0);
-            XC v;
-            zero(v);
-            for (int t = plan.x_off[l]; t < plan.x_off[l + 1]; ++t) {
-                const SC a = s1[plan.xt_r2[t] * nc + i2], b = s2[plan.xt_r3[t] * nc + i3];
-                if constexpr (DF) {
-                    cacc_fma3(v, plan.xt_w[t], a, b);
-                } else {
-                    const double w = (double)plan.xt_w[t];
-                    cfma(v, make_double2(w * a.x, w * a.y), b);
+            if constexpr (MODE == kDF32X2) {
+                // lanes (re, im) += w a.x (b.x, b.y);  lanes (im, re) += w a.y (b.x, -b.y)
+                pdf va, vb;
+                zero(va);
+                zero(vb);
+                for (int t = plan.x_off[l]; t < plan.x_off[l + 1]; ++t) {
+                    const float2 a = s1[plan.xt_r2[t] * nc + i2], b = s2[plan.xt_r3[t] * nc + i3];
+                    const float w = plan.xt_w[t];
+                    const float ax = w * a.x, ay = w * a.y;  // exact: w is +-2^k
+                    const f2x B = pk(b.x, b.y);
+                    pacc_exact(va, pk(ax, ax), pk(-ax, -ax), B);
+                    pacc_exact(vb, pk(ay, -ay), pk(-ay, ay), B);
                 }
+                sX[e] = padd(va, pdf{swap2(vb.h), swap2(vb.l)});
+            } else {
+                XC v;
+                zero(v);
+                for (int t = plan.x_off[l]; t < plan.x_off[l + 1]; ++t)
+                    x_term(v, plan.xt_w[t], s1[plan.xt_r2[t] * nc + i2], s2[plan.xt_r3[t] * nc + i3]);
+                sX[e] = v;
             }
-            sX[e] = v;
         }
         __syncthreads();
         // P update: three outputs per group share the S1 entry
@@ -140,12 +201,21 @@ block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restric
                 for (int t = plan.os_off[os]; t < plan.os_off[os + 1]; ++t) {
                     const SC a = s1[plan.os_r1[t] * nc + g_i1[k]];
                     const XC *xl = xs + plan.os_x[t] * nc2;
+                    if constexpr (MODE == kDF32X2) {
+                        const f2x A1 = pk(a.x, a.x), nA1 = pk(-a.x, -a.x);
+                        const f2x A2 = pk(a.y, -a.y), nA2 = pk(-a.y, a.y);
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        if (q < g_cnt[k]) {
-                            if constexpr (DF) cacc_fma(acc[k][q], a, xl[q]);
-                            else cfma(acc[k][q], a, xl[q]);
+                        for (int q = 0; q < 3; ++q) {
+                            if (q < g_cnt[k]) {
+                                const pdf x = xl[q];
+                                pacc(acc[k][q].a, A1, nA1, x.h, x.l);  // (a.x X.re, a.x X.im)
+                                pacc(acc[k][q].b, A2, nA2, x.h, x.l);  // (a.y X.re, -a.y X.im)
+                            }
                         }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+                            if (q < g_cnt[k]) p_term(acc[k][q], a, xl[q]);
                     }
                 }
             }
@@ -182,17 +252,17 @@ __global__ void block_reduce_kernel(const double2 *__restrict__ partials, int n_
     blocks[i] = make_double2(ax - bx, ay - by);
 }
 
-template <bool DF, typename ST>
+template <int MODE, typename ST>
 int launch_typed(const BlockPlan &plan, const void *Su, const void *Sd, int V, int n_slices, double2 *partials,
                  int n_splits, int chunk, double2 *blocks, cudaStream_t stream) {
-    using SC = typename Types<DF>::S;
-    using XC = typename Types<DF>::X;
+    using SC = typename Types<MODE>::S;
+    using XC = typename Types<MODE>::X;
     const int nr = plan.n_rows[0] + plan.n_rows[1];
     const size_t per_site = sizeof(SC) * (size_t)nr * plan.n_chi + sizeof(XC) * (size_t)plan.n_x * plan.n_chi * plan.n_chi;
-    int ns = (int)((72 * 1024) / per_site);
-    ns = ns < 1 ? 1 : (ns > 16 ? 16 : ns);
+    int ns = (int)(kSmemBudget / per_site);
+    ns = ns < 1 ? 1 : (ns > kMaxNs ? kMaxNs : ns);
     const size_t smem = per_site * ns;
-    auto kern = block_partial_kernel<DF, ST>;
+    auto kern = block_partial_kernel<MODE, ST>;
     WICK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int gpr = (plan.n_chi * plan.n_chi + 2) / 3;
     const int n_groups = plan.n_ops * plan.n_spin * plan.n_chi * gpr;
@@ -222,13 +292,18 @@ int launch_block_build(const BlockPlan &plan, const void *Su, int dtype_u, const
     if (dtype_u != dtype_d) return WICK_EINVAL;
     double2 *part = reinterpret_cast<double2 *>(partials);
     if (precision == WICK_MIXED) {
+        if (plan.pow2_w) {
+            if (dtype_u == WICK_C64)
+                return launch_typed<kDF32X2, float2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
+            return launch_typed<kDF32X2, double2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
+        }
         if (dtype_u == WICK_C64)
-            return launch_typed<true, float2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
-        return launch_typed<true, double2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
+            return launch_typed<kDF32, float2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
+        return launch_typed<kDF32, double2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
     }
     if (dtype_u == WICK_C64)
-        return launch_typed<false, float2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
-    return launch_typed<false, double2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
+        return launch_typed<kFP64, float2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
+    return launch_typed<kFP64, double2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
 }
 
 }  // namespace wick

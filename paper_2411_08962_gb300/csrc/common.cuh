@@ -40,6 +40,7 @@ struct BlockPlan {
     int8_t xt_r2[kMaxXTerms];  // compact row of S_{f1(op)}
     int8_t xt_r3[kMaxXTerms];  // compact row of S_{f2(op)}
     float xt_w[kMaxXTerms];    // integer weights (exact in float)
+    int pow2_w;                // every diquark weight is +-2^k (exact scaling of a float)
     int os_off[kMaxOps * kMaxSpin + 1];
     int8_t os_r1[kMaxOsTerms]; // compact row of S_{f1(op)}
     int16_t os_x[kMaxOsTerms];

@@ -91,6 +91,87 @@ __device__ __forceinline__ df df_add(df a, df b) {
 
 __device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
 
+// ---------------------------------------------------------------------------
+// Packed form on the sm_100-family f32x2 instructions: one 64-bit register
+// holds two float lanes, and add/sub/mul/fma.rn.f32x2 work on both at once.
+// A packed double-FP32 value is a pair (h, l) of such registers.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2x;
+
+__device__ __forceinline__ f2x pk(float a, float b) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2x v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+    f2x r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+    f2x r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+    f2x r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+    f2x r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+struct pdf {
+    f2x h, l;
+};
+
+// acc += A * (Bh + Bl) lane-wise, given nA = -A.  np = RN(-A*Bh) = -RN(A*Bh), so
+// fma(A, Bh, np) is the exact product error (TwoProd); the high sum is the
+// TwoSum of acc.h and RN(A*Bh) written with np; low parts are collected in acc.l.
+__device__ __forceinline__ void pacc(pdf &acc, f2x A, f2x nA, f2x Bh, f2x Bl) {
+    const f2x np = mul2(nA, Bh);
+    f2x e = fma2(A, Bh, np);
+    e = fma2(A, Bl, e);
+    const f2x s = sub2(acc.h, np);
+    const f2x bb = sub2(s, acc.h);
+    const f2x t = sub2(acc.h, sub2(s, bb));
+    const f2x u = add2(np, bb);
+    acc.h = s;
+    acc.l = add2(acc.l, add2(sub2(t, u), e));
+}
+
+// the same with an exact (float) second factor: no low part to multiply
+__device__ __forceinline__ void pacc_exact(pdf &acc, f2x A, f2x nA, f2x B) {
+    const f2x np = mul2(nA, B);
+    const f2x e = fma2(A, B, np);
+    const f2x s = sub2(acc.h, np);
+    const f2x bb = sub2(s, acc.h);
+    const f2x t = sub2(acc.h, sub2(s, bb));
+    const f2x u = add2(np, bb);
+    acc.h = s;
+    acc.l = add2(acc.l, add2(sub2(t, u), e));
+}
+
+__device__ __forceinline__ f2x swap2(f2x v) {
+    float a, b;
+    upk(v, a, b);
+    return pk(b, a);
+}
+
+// a + b for packed double-FP32 values, renormalised
+__device__ __forceinline__ pdf padd(pdf a, pdf b) {
+    const f2x s = add2(a.h, b.h);
+    const f2x bb = sub2(s, a.h);
+    const f2x err = add2(sub2(a.h, sub2(s, bb)), sub2(b.h, bb));
+    const f2x lo = add2(add2(a.l, b.l), err);
+    const f2x r = add2(s, lo);
+    return {r, sub2(lo, sub2(r, s))};
+}
+
 __device__ __forceinline__ cdf cdf_mul(const cdf &a, const cdf &b) {
     return {df_add(df_mul(a.x, b.x), df_neg(df_mul(a.y, b.y))), df_add(df_mul(a.x, b.y), df_mul(a.y, b.x))};
 }

@@ -27,8 +27,8 @@ WICK_U, WICK_D = 0, 1
 EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_reduce_terms", "wick_terms_count",
            "wick_terms_nucleons", "wick_terms_copy", "wick_terms_stats", "wick_terms_select",
            "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_contract_noalloc",
-           "wick_status",
-           "wick_strerror", "wick_version")
+           "wick_status", "wick_batch_create", "wick_batch_run", "wick_batch_launches", "wick_batch_free",
+           "wick_synth_propagator", "wick_strerror", "wick_version")
 
 
 class WickError(RuntimeError):
@@ -89,12 +89,20 @@ def load(path: str = LIB_PATH):
             L.wick_contract.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp]
             L.wick_contract_noalloc.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp]
             L.wick_status.argtypes = [vp]
+            L.wick_batch_create.argtypes = [P(wick_prop), P(wick_prop), C.c_int, P(wick_nucleon_op),
+                                            P(wick_block_layout), P(vp), C.c_int, C.c_int, vp, vp, P(vp)]
+            L.wick_batch_run.argtypes = [vp, vp]
+            L.wick_batch_launches.argtypes = [vp]
+            L.wick_batch_free.argtypes = [vp]
+            L.wick_batch_free.restype = None
+            L.wick_synth_propagator.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
             L.wick_strerror.argtypes = [C.c_int]
             L.wick_strerror.restype = C.c_char_p
             L.wick_version.restype = C.c_char_p
             for f in ("wick_build_blocks", "wick_reduce_terms", "wick_terms_nucleons", "wick_terms_copy",
                       "wick_terms_stats", "wick_terms_select", "wick_terms_save", "wick_terms_load",
-                      "wick_contract", "wick_contract_noalloc", "wick_status"):
+                      "wick_contract", "wick_contract_noalloc", "wick_status", "wick_batch_create",
+                      "wick_batch_run", "wick_batch_launches", "wick_synth_propagator"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -247,6 +255,50 @@ def wick_contract_noalloc(blocks, n_src: int, T: int, terms: Terms, precision: i
     is a fixed 1 MiB device array inside the library (see include/wick.h)."""
     _check(load().wick_contract_noalloc(_ptr(blocks), n_src, T, terms.h, precision, _ptr(C_out), _stream(stream)),
            "wick_contract_noalloc")
+
+
+class Batch:
+    """A captured batch (wick_batch_create); keeps its inputs alive."""
+
+    def __init__(self, Su_list, Sd_list, tables: Tables, terms_list, precision, blocks, C_out, L, T, n_src):
+        n = len(Su_list)
+
+        def props(lst):
+            arr = (wick_prop * n)()
+            for i, S in enumerate(lst):
+                dt = WICK_C64 if str(S.dtype) == "torch.complex64" else WICK_C128
+                arr[i] = wick_prop(_ptr(S), L, T, n_src, dt)
+            return arr
+        self._keep = (Su_list, Sd_list, tables, terms_list, blocks, C_out)
+        self.su, self.sd = props(Su_list), props(Sd_list)
+        handles = (C.c_void_p * len(terms_list))(*[t.h.value for t in terms_list])
+        h = C.c_void_p(None)
+        _check(load().wick_batch_create(self.su, self.sd, n, tables.ops, C.byref(tables.layout), handles,
+                                        len(terms_list), precision, _ptr(blocks), _ptr(C_out), C.byref(h)),
+               "wick_batch_create")
+        self.h = h
+
+    def run(self, stream=None):
+        _check(load().wick_batch_run(self.h, _stream(stream)), "wick_batch_run")
+
+    @property
+    def launches(self) -> int:
+        return int(load().wick_batch_launches(self.h))
+
+    def free(self):
+        if getattr(self, "h", None) and self.h.value:
+            load().wick_batch_free(self.h)
+            self.h = C.c_void_p(None)
+
+    def __del__(self):
+        self.free()
+
+
+def wick_synth_propagator(seed: int, flavour: int, src: int, L: int, T: int, out, stream=None):
+    """Device-generated synthetic propagator of one (flavour, source) into `out`."""
+    dt = WICK_C64 if str(out.dtype) == "torch.complex64" else WICK_C128
+    _check(load().wick_synth_propagator(seed, flavour, src, L, T, dt, _ptr(out), _stream(stream)),
+           "wick_synth_propagator")
 
 
 def wick_status(stream=None) -> int:

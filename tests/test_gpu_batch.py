@@ -1,0 +1,121 @@
+"""GPU tests of the batched executor and the device-side input generator.
+
+* wick_synth_propagator reproduces the host generator (same counter-based
+  definition; CUDA's log/sincospi may move the last bits);
+* a captured batch (wick_batch_create / wick_batch_run) gives bit-for-bit the
+  results of the individual calls, for several configurations and the three
+  nuclei sharing one block build per configuration;
+* the batched workload's lattice (L=32, T=64, two sources, complex64,
+  device-generated) on sampled slices against the CPU reference.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import operators as oops  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+from paper_2411_08962_gb300 import build, operators, synth, wick  # noqa: E402
+
+sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
+import make_tables  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-6
+NUCLEI = ("deuteron", "he3", "he4")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    wick.load()
+
+
+def device_props(seed, L, T, n_src, dtype=torch.complex64):
+    V = L ** 3
+    out = []
+    for f in (0, 1):
+        S = torch.empty((n_src, T, V, 3, 4, 3, 4), dtype=dtype, device="cuda")
+        for s in range(n_src):
+            wick.wick_synth_propagator(seed, f, s, L, T, S[s])
+        out.append(S)
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_device_generator_matches_host(dtype):
+    L, T, n_src, seed = 3, 2, 2, 424242
+    Su, Sd = device_props(seed, L, T, n_src, dtype)
+    npdt = np.complex128 if dtype == torch.complex128 else np.complex64
+    for f, S in ((0, Su), (1, Sd)):
+        h = synth.propagator(seed, f, L, T, n_src, dtype=npdt)
+        d = S.cpu().numpy()
+        if dtype == torch.complex128:
+            assert np.max(np.abs(d - h)) < 1e-13
+        else:
+            diff = d != h
+            assert diff.mean() < 1e-4                                  # rounding-boundary cases only
+            assert np.max(np.abs(d - h) / np.maximum(np.abs(h), 1e-30)) < 2.5e-7
+
+
+def test_batch_equals_individual_calls():
+    L, T, n_src, n_cfg = 4, 4, 2, 3
+    tabs = wick.Tables(operators.nucleus("he4"))     # the upper-spin p, n blocks serve all three nuclei
+    terms = [wick.wick_reduce_terms(wick.Tables(operators.nucleus(n))) for n in NUCLEI]
+    cfgs = [device_props(1000 + c, L, T, n_src) for c in range(n_cfg)]
+    nb = tabs.nuc.n_blk
+    for prec in (wick.WICK_MIXED, wick.WICK_FP64):
+        blocks = torch.zeros((n_cfg, n_src, T, nb), dtype=torch.complex128, device="cuda")
+        C = torch.zeros((n_cfg, len(NUCLEI), n_src, T), dtype=torch.complex128, device="cuda")
+        batch = wick.Batch([c[0] for c in cfgs], [c[1] for c in cfgs], tabs, terms, prec, blocks, C, L, T, n_src)
+        assert batch.launches == n_cfg * (2 + 2 * len(NUCLEI))
+        batch.run()
+        batch.run()                                       # a second launch reproduces the first
+        torch.cuda.synchronize()
+        for c, (Su, Sd) in enumerate(cfgs):
+            b1 = torch.empty((n_src, T, nb), dtype=torch.complex128, device="cuda")
+            wick.wick_build_blocks(Su, Sd, tabs, prec, b1, L, T, n_src)
+            assert torch.equal(b1, blocks[c])
+            for k, t in enumerate(terms):
+                c1 = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
+                wick.wick_contract(b1, n_src, T, t, prec, c1)
+                torch.cuda.synchronize()
+                assert torch.equal(c1, C[c, k])
+        batch.free()
+
+
+def test_batched_workload_lattice_sampled():
+    """L=32, T=64, two sources, complex64, device-generated; two configurations
+    in one batch; sampled (config, source, slice) against the CPU reference."""
+    L, T, n_src, n_cfg = 32, 64, 2, 2
+    tabs = wick.Tables(operators.nucleus("he4"))
+    terms = [wick.wick_reduce_terms(wick.Tables(operators.nucleus(n))) for n in NUCLEI]
+    seeds = [0x24110005 + 7919 * c for c in range(n_cfg)]
+    cfgs = [device_props(s, L, T, n_src) for s in seeds]
+    blocks = torch.empty((n_cfg, n_src, T, tabs.nuc.n_blk), dtype=torch.complex128, device="cuda")
+    C = torch.empty((n_cfg, len(NUCLEI), n_src, T), dtype=torch.complex128, device="cuda")
+    batch = wick.Batch([c[0] for c in cfgs], [c[1] for c in cfgs], tabs, terms, wick.WICK_MIXED, blocks, C, L, T, n_src)
+    batch.run()
+    torch.cuda.synchronize()
+    Cn = C.cpu().numpy()
+    onuc = {n: oops.nucleus(n) for n in NUCLEI}
+    otab = {"deuteron": O.dedup(onuc["deuteron"]), "he3": O.dedup(onuc["he3"]), "he4": make_tables.load("he4")[0]}
+    for c, s, t in ((0, 0, 5), (1, 1, 40)):
+        su = synth.propagator(seeds[c], 0, L, T, n_src, dtype=np.complex64, t_range=(t, t + 1))[s:s + 1]
+        sd = synth.propagator(seeds[c], 1, L, T, n_src, dtype=np.complex64, t_range=(t, t + 1))[s:s + 1]
+        # the device generator and the host generator agree up to rare rounding-boundary
+        # entries (one float ulp); the reference is fed the host generator's values
+        for f, h in ((0, su), (1, sd)):
+            assert np.count_nonzero(cfgs[c][f][s, t].cpu().numpy() != h[0, 0]) <= 2
+        Bh = O.blocks_single(su.astype(np.complex128), sd.astype(np.complex128), onuc["he4"])
+        for k, n in enumerate(NUCLEI):
+            ref = O.table_correlator(onuc[n], Bh, otab[n])[0, 0]
+            assert abs(Cn[c, k, s, t] - ref) / abs(ref) < MIXED_TOL, (n, c, s, t)
+    batch.free()

@@ -96,6 +96,23 @@ def test_blocks_match_oracle(L, T, n_src, form, precision):
     assert block_err(B, ref) < tol
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_blocks_general_integer_weights(precision):
+    """Diquark weights that are not powers of two (3 C gamma5) take the scalar
+    double-FP32 path of the mixed block kernel."""
+    G3 = 3 * operators.diquark_matrix()
+    nuc = operators.nucleus("deuteron")
+    nuc.ops = [operators.nucleon_op(operators.U, G3, (0, 1), (0, 1)),
+               operators.nucleon_op(operators.D, G3, (0, 1), (0, 1))]
+    Su, Sd = props(3, 2, 1, seed=17, dtype=np.complex64)
+    B = gpu_blocks(Su, Sd, wick.Tables(nuc), precision).cpu().numpy()
+    onuc = oops.nucleus("deuteron")
+    tab3 = oops.nucleon_table(3 * oops.cg5(), oops.UPPER, oops.UPPER)
+    onuc["ops"] = [(oops.U, tab3), (oops.D, tab3)]
+    ref = O.antisymmetric_blocks(O.blocks_single(Su.astype(np.complex128), Sd.astype(np.complex128), onuc), onuc)
+    assert block_err(B, ref) < (FP64_TOL if precision == "fp64" else MIXED_TOL)
+
+
 def test_blocks_c64_storage_fp64_arithmetic():
     Su, Sd = props(4, 2, 1, seed=5, dtype=np.complex64)
     tabs = wick.Tables(operators.nucleus("deuteron"))
