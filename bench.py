@@ -173,9 +173,10 @@ def oracle_ms_per_config(Su, Sd, slices, tab):
 
 
 def he4_oracle_table():
-    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
-    import make_tables
-    return make_tables.load("he4")[0]
+    """The CPU reference's reduced He-4 table (its one-time preprocessing)."""
+    from oracle import operators as oops
+    from oracle import oracle as O
+    return O.dedup(oops.nucleus("he4"))
 
 
 def host_props(seed, L, T, n_src):

@@ -159,11 +159,18 @@ int wick_build_blocks(const wick_prop *Su, const wick_prop *Sd, const wick_nucle
  * Randomised minimal-set search (Sec. III.B "Computation of non-redundant
  * minimal set", Theorem 1 and its error bound in App. C) for the block
  * form of the correlator (Eq. 2.6 generalised in App. D):
- *   raw terms   j = ((i_sink * n_src + i_src) * n_u! + rank(sigma_u)) * n_d! + rank(sigma_d)
- *               with coefficient c_j = sink_w * src_w * sgn(pairing) and monomial
- *               prod_k B^{type_k}_{s_k}(chi'_{sigma(k,1)}, chi'_{sigma(k,2)}, chi'_{sigma(k,3)});
- *               rank = lexicographic rank; sgn(pairing) = parity of the map
- *               sink quark -> source quark (+1 for the pairing in listed order).
+ *   source      first antisymmetrised (method B of Sec. III.C): a source tuple
+ *               whose u (or d) indices repeat cancels in the permutation sum;
+ *               every other tuple is a signed reordering of its sorted multiset
+ *               pair M, so the source becomes the nonzero multisets (listed in
+ *               lexicographic order) with C'(M) = sum C'_m sgn(sort_u) sgn(sort_d).
+ *   raw terms   j = ((i_sink * n_M + M) * n_u! + rank(tau_u)) * n_d! + rank(tau_d):
+ *               the sink quark of flavour-ordinal q takes entry tau(q) of M's
+ *               sorted list; coefficient c_j = sink_w * C'(M) * sgn(tau_u) *
+ *               sgn(tau_d) * eta (eta = parity of the identity flavour pairing,
+ *               +1 when the source lists quarks in the sink's flavour order);
+ *               monomial prod_k B^{type_k}_{s_k}(entries of the nucleon's three quarks);
+ *               rank = lexicographic rank of the permutation.
  *   hashing     every monomial is evaluated at `trials` (1 or 2) random integer
  *               propagators on `sites` lattice sites, exactly modulo p = 2^61 - 1;
  *               the sign is canonicalised (first non-zero value <= (p-1)/2) and
@@ -174,8 +181,8 @@ int wick_build_blocks(const wick_prop *Su, const wick_prop *Sd, const wick_nucle
  *               W * eps_rep / 2^A (an integer: classes are unions of the 2^A
  *               like-pair exchange orbits).  Terms are ordered by representative,
  *               so the table depends only on the partition, not on the seed.
- * False-merge probability <= C(N_raw, 2) * (3A / p)^trials (reported by
- * wick_terms_stats).  Synchronises `stream`; the table is library-owned.
+ * False-merge probability <= C(N_raw, 2) * (3A / p)^trials, N_raw the raw terms
+ * above (reported by wick_terms_stats).  Synchronises `stream`; the table is library-owned.
  * Errors: WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA, WICK_ECAPACITY (more distinct
  * keys than the hash table holds), WICK_EOVERFLOW (weights beyond int64 /
  * more than 2^62 raw terms), WICK_ETIMEOUT.
@@ -242,6 +249,15 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *terms,
  */
 int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms *terms, int precision,
                           void *C_out, wick_stream_t stream);
+
+/*
+ * Cluster sink (Sec. V.A: Li-7 as a He-4 cluster and a triton cluster, each
+ * projected to zero momentum on its own): with no quark exchanged between
+ * clusters the correlator is the product of the cluster correlators,
+ *   out[i] = Ca[i] * Cb[i]   (device complex128, n entries, asynchronous).
+ * Errors: WICK_EINVAL, WICK_ECUDA.
+ */
+int wick_cluster_product(const void *Ca, const void *Cb, int64_t n, void *out, wick_stream_t stream);
 
 /*
  * Batched executor (the paper evaluates one configuration at a time; this

@@ -214,3 +214,82 @@ def all_permutations(n):
         inv = sum(1 for i in range(n) for j in range(i + 1, n) if p[i] > p[j])
         out.append((p, -1 if inv % 2 else 1))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Cluster operators of the Li-7 reading (Sec. III.C, Eqs. He4_op and Li7):
+# nucleon types p+-, n+- with C gamma5 P+- and all four spins; source quarks
+# listed flavour-grouped (u first, then d, each in nucleon-slot order) with
+# the Grassmann sign of that reordering, since the nucleon types vary between
+# the terms of one operator.
+# ----------------------------------------------------------------------------
+P_PLUS, P_MINUS, N_PLUS, N_MINUS = 0, 1, 2, 3
+
+
+def pm_ops():
+    """[p+, p-, n+, n-]: eps_abc q1^a_s q1^b_beta (C g5 P_pm)_{beta delta} q2^c_delta."""
+    cgp = cg5() @ parity_projector(+1)
+    cgm = cg5() @ parity_projector(-1)
+    tp = nucleon_table(cgp, ALL_SPINS, ALL_SPINS)
+    tm = nucleon_table(cgm, ALL_SPINS, ALL_SPINS)
+    return [(U, tp), (U, tm), (D, tp), (D, tm)]
+
+
+def _grouped_source(ops, terms):
+    """Source table of sum_t coef_t prod_k N^{type_k}_{spin_k}: each product tuple
+    reordered flavour-grouped (u quarks first, then d, stable) with the parity
+    of that reordering folded into its weight; equal tuples merged."""
+    acc = {}
+    flav_out = None
+    for types, spins, coef in terms:
+        per = [[e for e in ops[o][1] if e[0] == s] for o, s in zip(types, spins)]
+        flav = []
+        for o in types:
+            f = ops[o][0]
+            flav += [f, f, 1 - f]
+        order = [q for q in range(len(flav)) if flav[q] == U] + [q for q in range(len(flav)) if flav[q] == D]
+        inv = sum(1 for a in range(len(order)) for b in range(a + 1, len(order)) if order[a] > order[b])
+        sgn = -1 if inv % 2 else 1
+        fo = [flav[q] for q in order]
+        assert flav_out is None or fo == flav_out
+        flav_out = fo
+        for combo in product(*per):
+            chi = [x for e in combo for x in e[1:4]]
+            w = coef * sgn
+            for e in combo:
+                w *= e[4]
+            key = tuple(chi[q] for q in order)
+            acc[key] = acc.get(key, 0) + w
+    return sorted((k, w) for k, w in acc.items() if w != 0), flav_out
+
+
+def _cluster(ops, terms, scale):
+    sink = sorted((tuple(t), tuple(s), w) for t, s, w in terms)
+    src, flav = _grouped_source(ops, terms)
+    return dict(A=len(terms[0][0]), ops=ops, n_spin=4, chi=list(range(12)), sink=sink, src=src, src_flav=flav,
+                scale=scale)
+
+
+def he4_cluster():
+    """O_He4 = (chibar eta - chi etabar)/sqrt2 with p+, n+ (Eq. He4_op): spin
+    patterns chi, chibar and isospin patterns eta, etabar over four nucleons;
+    integer weights chibar_s eta_i - chi_s etabar_i and scale 1/96 for
+    sink x source."""
+    pats = [(0, 1, 0, 1), (1, 0, 1, 0), (0, 1, 1, 0), (1, 0, 0, 1), (0, 0, 1, 1), (1, 1, 0, 0)]
+    c = [1, 1, -1, -1, 0, 0]          # chi, times 1/2
+    cb = [1, 1, 1, 1, -2, -2]         # chibar, times 1/sqrt(12)
+    iso = [tuple(P_PLUS if x == 0 else N_PLUS for x in p) for p in pats]   # up -> p, down -> n
+    terms = []
+    for a, s in enumerate(pats):
+        for b, t in enumerate(iso):
+            w = cb[a] * c[b] - c[a] * cb[b]
+            if w:
+                terms.append((t, s, w))
+    return _cluster(pm_ops(), terms, 1.0 / 96.0)
+
+
+def triton_cluster(J: int = 0):
+    """n_-^T C g5 p_+ n_+^J (the three-nucleon factor of Eq. Li7)."""
+    G = integer_matrix(cg5())
+    terms = [((N_MINUS, P_PLUS, N_PLUS), (a, b, J), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b]]
+    return _cluster(pm_ops(), terms, 1.0)

@@ -63,8 +63,10 @@ def lib():
             L.oracle_dedup.argtypes = [P, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int64, i64p, i64p, u16p, i64p]
             L.oracle_modp_raw.argtypes = [P, C.c_uint64, u64p]
             L.oracle_modp_table.argtypes = [P, C.c_uint64, C.c_int64, u16p, i64p, u64p]
+            i8p = C.POINTER(C.c_int8)
+            L.oracle_source_multisets.argtypes = [P, C.c_int64, i8p, i8p, i64p, i64p]
             for f in ("oracle_blocks", "oracle_raw_correlator", "oracle_table_correlator", "oracle_dedup",
-                      "oracle_modp_raw", "oracle_modp_table", "oracle_num_threads"):
+                      "oracle_modp_raw", "oracle_modp_table", "oracle_num_threads", "oracle_source_multisets"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -161,13 +163,27 @@ def table_correlator(nuc, Bhat: np.ndarray, table) -> np.ndarray:
     return out.reshape(shp)
 
 
-def dedup(nuc, seed: int = 0x0BAC1E, trials: int = 2, V0: int = 1, mode: str = "hash", cap: int | None = None):
-    """Reduced term table: dict(rep, w, ids[U][A], stats=(raw, zero, classes, kept))."""
+def source_multisets(nuc):
+    """Antisymmetrised source: dict(Mu[n_M][n_u], Md[n_M][n_d], CM[n_M], n_red)."""
     pk = _Packed(nuc)
-    from math import factorial
     nu = int(np.sum(pk.src_flav == 0))
     nd = len(pk.src_flav) - nu
-    n_raw = len(pk.sink_w) * len(pk.src_w) * factorial(nu) * factorial(nd)
+    cap = max(1, len(pk.src_w))
+    Mu = np.zeros((cap, max(nu, 1)), dtype=np.int8)
+    Md = np.zeros((cap, max(nd, 1)), dtype=np.int8)
+    CM = np.zeros(cap, dtype=np.int64)
+    counts = np.zeros(2, dtype=np.int64)
+    _check(lib().oracle_source_multisets(C.byref(pk.p), cap, _ptr(Mu, C.c_int8), _ptr(Md, C.c_int8),
+                                         _ptr(CM, C.c_int64), _ptr(counts, C.c_int64)), "source_multisets")
+    n = int(counts[0])
+    return dict(Mu=Mu[:n, :nu].copy(), Md=Md[:n, :nd].copy(), CM=CM[:n].copy(), n_red=int(counts[1]))
+
+
+def dedup(nuc, seed: int = 0x0BAC1E, trials: int = 2, V0: int = 1, mode: str = "hash", cap: int | None = None):
+    """Reduced term table: dict(rep, w, ids[U][A], stats=(raw terms of the
+    reduction, identically zero, classes, kept))."""
+    pk = _Packed(nuc)
+    n_raw = source_multisets(nuc)["n_red"]
     if cap is None:
         cap = max(1, min(n_raw, 1 << 24))
     rep = np.zeros(cap, dtype=np.int64)

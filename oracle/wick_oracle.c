@@ -35,12 +35,20 @@
  *                        exactly modulo p at a fresh random integer propagator
  *                        (Theorem 1, App. C), used to pin the reduced table.
  *
- * Term order (fixes the table byte for byte): raw index
- *   j = ((i_sink * n_src + i_src) * n_u! + rank(sigma_u)) * n_d! + rank(sigma_d)
- * with rank the lexicographic rank of the permutation.  A reduced term keeps
- * the raw term of smallest j in its class as representative (its block ids
- * and its sign), its weight is sum_{j in class} c_j * (term_j / term_rep) / 2^A,
- * and terms are listed by increasing representative.
+ * Raw terms of the reduction (method B of Sec. III.C: antisymmetrise the source
+ * coefficients first).  A source tuple whose u (or d) indices repeat cancels
+ * in the sum over sigma; every other tuple m is a signed reordering of the
+ * sorted multiset pair M = (sorted u indices, sorted d indices):
+ *   C'(M) = sum_{m -> M} C'_m sgn(sort_u(m)) sgn(sort_d(m)).
+ * Nonzero multisets are listed in lexicographic order; the raw terms are
+ *   j = ((i_sink * n_M + M) * n_u! + rank(tau_u)) * n_d! + rank(tau_d)
+ * where tau assigns sorted index tau(q) to the sink quark of flavour-ordinal q,
+ * with coefficient sink_w * eta * C'(M) * sgn(tau_u) * sgn(tau_d).  Summed with
+ * the same products this equals the plain sum over source tuples and sigma.
+ * A reduced term keeps the raw term of smallest j in its class as
+ * representative (its block ids and its sign), its weight is
+ * sum_{j in class} c_j * (term_j / term_rep) / 2^A, and terms are listed by
+ * increasing representative.
  */
 #include <complex.h>
 #include <math.h>
@@ -126,10 +134,76 @@ typedef struct {
     int *fslot;                  /* n_sink x nq: flavour-ordinal of sink quark (k,slot) */
     int *sflav;                  /* n_sink x nq: flavour of sink quark (k,slot) */
     int *eta;                    /* n_sink: parity of the identity flavour pairing */
-    int64_t n_raw;
+    int64_t n_raw;               /* sink x source tuples x sigma_u x sigma_d (plain sum) */
+    int64_t n_M;                 /* nonzero antisymmetrised source multisets */
+    int8_t *Mu, *Md;             /* n_M x nu, n_M x nd: sorted layout indices */
+    int64_t *CM;                 /* n_M: C'(M) */
+    int64_t n_red;               /* raw terms of the reduction: sink x n_M x n_u! x n_d! */
 } ctx;
 
-static void ctx_free(ctx *c) { free(c->pu); free(c->pd); free(c->su); free(c->sd); free(c->fslot); free(c->sflav); free(c->eta); }
+static void ctx_free(ctx *c) { free(c->pu); free(c->pd); free(c->su); free(c->sd); free(c->fslot); free(c->sflav); free(c->eta); free(c->Mu); free(c->Md); free(c->CM); }
+
+/* ------------------------------------------------------------------------- */
+/* antisymmetrised source: sorted multisets with their summed signed weights */
+/* ------------------------------------------------------------------------- */
+typedef struct { int8_t v[24]; int64_t w; } msrec;
+static int ms_len;  /* nu + nd of the records being compared */
+static int cmp_ms(const void *a, const void *b) {
+    return memcmp(((const msrec *)a)->v, ((const msrec *)b)->v, (size_t)ms_len);
+}
+
+/* sort x[0..n) ascending by insertion; return -1 if two entries are equal,
+ * else the parity (+1/-1) of the sorting permutation */
+static int sort_sign(int8_t *x, int n) {
+    int sgn = 1;
+    for (int a = 1; a < n; ++a)
+        for (int b = a; b > 0 && x[b - 1] >= x[b]; --b) {
+            if (x[b - 1] == x[b]) return 0;
+            int8_t t = x[b]; x[b] = x[b - 1]; x[b - 1] = t;
+            sgn = -sgn;
+        }
+    for (int a = 1; a < n; ++a) if (x[a - 1] == x[a]) return 0;
+    return sgn;
+}
+
+static int ms_build(ctx *c) {
+    const problem *P = c->P;
+    msrec *r = malloc(sizeof(msrec) * (size_t)P->n_src);
+    if (!r) return ENOMEM_;
+    int64_t n = 0;
+    for (int m = 0; m < P->n_src; ++m) {
+        msrec x;
+        memset(&x, 0, sizeof(x));
+        for (int k = 0; k < c->nu; ++k) x.v[k] = (int8_t)c->cidx[(int)P->src_chi[m * c->nq + c->ju[k]]];
+        for (int k = 0; k < c->nd; ++k) x.v[c->nu + k] = (int8_t)c->cidx[(int)P->src_chi[m * c->nq + c->jd[k]]];
+        const int su = sort_sign(x.v, c->nu), sd = sort_sign(x.v + c->nu, c->nd);
+        if (su == 0 || sd == 0) continue;    /* repeated index within a flavour: cancels */
+        x.w = P->src_w[m] * su * sd;
+        r[n++] = x;
+    }
+    ms_len = c->nu + c->nd;
+    qsort(r, (size_t)n, sizeof(msrec), cmp_ms);
+    int64_t k = 0;
+    for (int64_t a = 0; a < n; ) {
+        int64_t b = a, w = 0;
+        while (b < n && memcmp(r[b].v, r[a].v, (size_t)ms_len) == 0) w += r[b++].w;
+        if (w != 0) { r[k] = r[a]; r[k].w = w; ++k; }
+        a = b;
+    }
+    c->n_M = k;
+    c->Mu = malloc((size_t)(k ? k : 1) * (c->nu ? c->nu : 1));
+    c->Md = malloc((size_t)(k ? k : 1) * (c->nd ? c->nd : 1));
+    c->CM = malloc(sizeof(int64_t) * (size_t)(k ? k : 1));
+    if (!c->Mu || !c->Md || !c->CM) { free(r); return ENOMEM_; }
+    for (int64_t q = 0; q < k; ++q) {
+        memcpy(c->Mu + q * c->nu, r[q].v, (size_t)c->nu);
+        memcpy(c->Md + q * c->nd, r[q].v + c->nu, (size_t)c->nd);
+        c->CM[q] = r[q].w;
+    }
+    c->n_red = (int64_t)P->n_sink * k * c->fu * c->fd;
+    free(r);
+    return OK;
+}
 
 static int ctx_init(ctx *c, const problem *P) {
     memset(c, 0, sizeof(*c));
@@ -181,16 +255,17 @@ static int ctx_init(ctx *c, const problem *P) {
     for (int m = 0; m < P->n_src * c->nq; ++m)
         if (P->src_chi[m] < 0 || P->src_chi[m] > 11 || c->cidx[(int)P->src_chi[m]] < 0) return EINVAL_;
     c->n_raw = (int64_t)P->n_sink * P->n_src * c->fu * c->fd;
-    return OK;
+    return ms_build(c);
 }
 
 static inline int blk_id(const problem *P, int o, int s, int i1, int i2, int i3) {
     return (((o * P->n_spin + s) * P->n_chi + i1) * P->n_chi + i2) * P->n_chi + i3;
 }
 
-/* Decode raw term j: its integer coefficient c_j and, per nucleon k, the
- * (op, spin, i1, i2, i3) of the block it multiplies. */
-static void term_decode(const ctx *c, int64_t j, int64_t *coef, int *bo, int *bs, int *bi) {
+/* Decode term j of the plain sum (sink, source tuple, sigma_u, sigma_d): its
+ * integer coefficient and, per nucleon k, the (op, spin, i1, i2, i3) of the
+ * block it multiplies. */
+static void raw_decode(const ctx *c, int64_t j, int64_t *coef, int *bo, int *bs, int *bi) {
     const problem *P = c->P;
     int64_t rd = j % c->fd; j /= c->fd;
     int64_t ru = j % c->fu; j /= c->fu;
@@ -208,6 +283,26 @@ static void term_decode(const ctx *c, int64_t j, int64_t *coef, int *bo, int *bs
         }
     }
     *coef = P->sink_w[i] * P->src_w[m] * c->su[ru] * c->sd[rd] * c->eta[i];
+}
+
+/* Decode raw term j of the reduction (sink, multiset M, tau_u, tau_d). */
+static void term_decode(const ctx *c, int64_t j, int64_t *coef, int *bo, int *bs, int *bi) {
+    const problem *P = c->P;
+    int64_t rd = j % c->fd; j /= c->fd;
+    int64_t ru = j % c->fu; j /= c->fu;
+    int64_t M = j % c->n_M;
+    int64_t i = j / c->n_M;
+    const int *pu = c->pu + ru * c->nu, *pd = c->pd + rd * c->nd;
+    for (int k = 0; k < P->A; ++k) {
+        bo[k] = P->sink_type[i * P->A + k];
+        bs[k] = P->sink_spin[i * P->A + k];
+        for (int sl = 0; sl < 3; ++sl) {
+            int q = 3 * k + sl;
+            int f = c->sflav[i * c->nq + q], ord = c->fslot[i * c->nq + q];
+            bi[3 * k + sl] = (f == 0) ? c->Mu[M * c->nu + pu[ord]] : c->Md[M * c->nd + pd[ord]];
+        }
+    }
+    *coef = P->sink_w[i] * c->CM[M] * c->su[ru] * c->sd[rd] * c->eta[i];
 }
 
 /* ------------------------------------------------------------------------- */
@@ -277,7 +372,7 @@ int oracle_raw_correlator(const problem *P, const double *Bhat, int n_slices, do
         int bo[8], bs[8], bi[24];
         int64_t coef;
         for (int64_t j = 0; j < c.n_raw; ++j) {
-            term_decode(&c, j, &coef, bo, bs, bi);
+            raw_decode(&c, j, &coef, bo, bs, bi);
             cplx prod = (double)coef;
             for (int k = 0; k < P->A; ++k) {
                 int id = blk_id(P, bo[k], bs[k], bi[3 * k], bi[3 * k + 1], bi[3 * k + 2]);
@@ -498,7 +593,7 @@ int oracle_dedup(const problem *P, uint64_t seed, int trials, int V0, int mode, 
         tid = omp_get_thread_num();
 #endif
 #pragma omp for schedule(dynamic, 4096)
-        for (int64_t j = 0; j < c.n_raw; ++j) {
+        for (int64_t j = 0; j < c.n_red; ++j) {
             int64_t coef; uint64_t k0, k1; int eps;
             if (!term_key(&c, mode, trials, R, n_blk, j, &coef, &k0, &k1, &eps)) { nzero[tid]++; continue; }
             if (map_put(&loc[tid], k0, k1, eps * coef, j)) err = ENOMEM_;
@@ -537,7 +632,7 @@ int oracle_dedup(const problem *P, uint64_t seed, int trials, int V0, int mode, 
         for (int k = 0; k < P->A; ++k)
             out_ids[u * P->A + k] = (uint16_t)blk_id(P, bo[k], bs[k], bi[3 * k], bi[3 * k + 1], bi[3 * k + 2]);
     }
-    stats[0] = c.n_raw; stats[1] = nz; stats[2] = g.n; stats[3] = U;
+    stats[0] = c.n_red; stats[1] = nz; stats[2] = g.n; stats[3] = U;
     free(rec); free(g.s); free(R);
     ctx_free(&c);
     return err;
@@ -558,7 +653,7 @@ int oracle_modp_raw(const problem *P, uint64_t seed, uint64_t *out) {
 #pragma omp for schedule(dynamic, 4096)
         for (int64_t j = 0; j < c.n_raw; ++j) {
             int64_t coef; int bo[8], bs[8], bi[24];
-            term_decode(&c, j, &coef, bo, bs, bi);
+            raw_decode(&c, j, &coef, bo, bs, bi);
             uint64_t v = mfrom(coef);
             for (int k = 0; k < P->A; ++k)
                 v = mmul(v, R[blk_id(P, bo[k], bs[k], bi[3 * k], bi[3 * k + 1], bi[3 * k + 2])]);
@@ -588,6 +683,23 @@ int oracle_modp_table(const problem *P, uint64_t seed, int64_t U, const uint16_t
     *out = total;
     free(R);
     return OK;
+}
+
+/* The antisymmetrised source table: counts[0] = n_M, counts[1] = raw terms
+ * of the reduction; Mu/Md/CM filled up to cap entries. */
+int oracle_source_multisets(const problem *P, int64_t cap, int8_t *Mu, int8_t *Md, int64_t *CM, int64_t *counts) {
+    ctx c;
+    int err = ctx_init(&c, P);
+    if (err) { ctx_free(&c); return err; }
+    counts[0] = c.n_M;
+    counts[1] = c.n_red;
+    for (int64_t q = 0; q < c.n_M && q < cap; ++q) {
+        memcpy(Mu + q * c.nu, c.Mu + q * c.nu, (size_t)c.nu);
+        memcpy(Md + q * c.nd, c.Md + q * c.nd, (size_t)c.nd);
+        CM[q] = c.CM[q];
+    }
+    ctx_free(&c);
+    return c.n_M > cap ? ECAP_ : OK;
 }
 
 int oracle_num_threads(void) {

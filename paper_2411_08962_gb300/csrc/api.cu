@@ -264,7 +264,6 @@ int wick_reduce_terms(const wick_nucleus *nuc, const wick_nucleon_op *ops, const
     ep.A = A;
     ep.nq = nq;
     ep.n_sink = nuc->n_sink;
-    ep.n_src = nuc->n_src;
     ep.n_spin = layout->n_spin;
     ep.n_chi = layout->n_chi;
     ep.n_blk = (int)wick_block_count(layout);
@@ -278,27 +277,59 @@ int wick_reduce_terms(const wick_nucleus *nuc, const wick_nucleon_op *ops, const
     for (int i = 2; i <= ep.nu; ++i) ep.fu *= i;
     ep.fd = 1;
     for (int i = 2; i <= ep.nd; ++i) ep.fd *= i;
-    // raw-term count, guarded against overflow
-    long double nr = (long double)ep.n_sink * ep.n_src * (long double)ep.fu * (long double)ep.fd;
-    if (nr > 4.0e18L) return WICK_EOVERFLOW;
-    ep.n_raw = (int64_t)ep.n_sink * ep.n_src * ep.fu * ep.fd;
-    if ((uint64_t)ep.n_sink * ep.n_src * (uint64_t)ep.fu * (uint64_t)((ep.fd + 31) / 32) > (1ull << 62))
-        return WICK_EOVERFLOW;
-    // weights: the in-warp sum of 32 coefficients must fit in int32
-    int64_t max_sw = 0, max_cw = 0;
-    for (int i = 0; i < ep.n_sink; ++i) max_sw = std::max<int64_t>(max_sw, llabs(nuc->sink_w[i]));
-    for (int m = 0; m < ep.n_src; ++m) max_cw = std::max<int64_t>(max_cw, llabs(nuc->src_w[m]));
-    if (max_sw == 0 || max_cw == 0 || (long double)max_sw * max_cw * 32.0L >= 2147483647.0L) return WICK_EOVERFLOW;
-    // source index positions
+    // source index positions in the layout
     int cidx[12];
     for (int c = 0; c < 12; ++c) cidx[c] = -1;
     for (int i = 0; i < layout->n_chi; ++i) cidx[(int)layout->chi[i]] = i;
-    std::vector<int8_t> src_idx((size_t)ep.n_src * nq);
-    for (size_t e = 0; e < src_idx.size(); ++e) {
+    for (size_t e = 0; e < (size_t)nuc->n_src * nq; ++e) {
         const int c = nuc->src_chi[e];
         if (c < 0 || c > 11 || cidx[c] < 0) return WICK_EINVAL;
-        src_idx[e] = (int8_t)cidx[c];
     }
+    // Antisymmetrised source (method B of Sec. III.C): a source tuple whose u
+    // (or d) indices repeat cancels in the sum over permutations; every other
+    // tuple is a signed reordering of its sorted multiset pair, so the source
+    // collapses onto the sorted multisets with summed signed weights.
+    std::map<std::vector<int8_t>, int64_t> msets;
+    auto sort_sign = [](int8_t *x, int n) {
+        int sgn = 1;
+        for (int a = 1; a < n; ++a)
+            for (int b = a; b > 0 && x[b - 1] >= x[b]; --b) {
+                if (x[b - 1] == x[b]) return 0;
+                std::swap(x[b], x[b - 1]);
+                sgn = -sgn;
+            }
+        for (int a = 1; a < n; ++a)
+            if (x[a - 1] == x[a]) return 0;
+        return sgn;
+    };
+    for (int m = 0; m < nuc->n_src; ++m) {
+        std::vector<int8_t> key((size_t)(ep.nu + ep.nd));
+        for (int k = 0; k < ep.nu; ++k) key[k] = (int8_t)cidx[(int)nuc->src_chi[(size_t)m * nq + ep.ju[k]]];
+        for (int k = 0; k < ep.nd; ++k) key[ep.nu + k] = (int8_t)cidx[(int)nuc->src_chi[(size_t)m * nq + ep.jd[k]]];
+        const int su = sort_sign(key.data(), ep.nu), sd = sort_sign(key.data() + ep.nu, ep.nd);
+        if (!su || !sd) continue;
+        msets[key] += nuc->src_w[m] * su * sd;
+    }
+    std::vector<int8_t> Mu, Md;
+    std::vector<int64_t> CM;
+    for (auto &kv : msets) {
+        if (kv.second == 0) continue;
+        Mu.insert(Mu.end(), kv.first.begin(), kv.first.begin() + ep.nu);
+        Md.insert(Md.end(), kv.first.begin() + ep.nu, kv.first.end());
+        CM.push_back(kv.second);
+    }
+    ep.n_M = (int)CM.size();
+    if (Mu.empty()) Mu.push_back(0);
+    if (Md.empty()) Md.push_back(0);
+    // raw-term count, guarded against overflow
+    long double nr = (long double)ep.n_sink * ep.n_M * (long double)ep.fu * (long double)ep.fd;
+    if (nr > 4.0e18L) return WICK_EOVERFLOW;
+    ep.n_raw = (int64_t)ep.n_sink * ep.n_M * ep.fu * ep.fd;
+    // weights: the in-warp sum of 32 coefficients must fit in int32
+    int64_t max_sw = 0, max_cw = 0;
+    for (int i = 0; i < ep.n_sink; ++i) max_sw = std::max<int64_t>(max_sw, llabs(nuc->sink_w[i]));
+    for (int64_t w : CM) max_cw = std::max<int64_t>(max_cw, llabs(w));
+    if ((long double)max_sw * max_cw * 32.0L >= 2147483647.0L) return WICK_EOVERFLOW;
     // sink quark flavours, flavour ordinals and the identity-pairing parity
     std::vector<int8_t> sflav((size_t)ep.n_sink * nq), sord((size_t)ep.n_sink * nq), seta(ep.n_sink);
     for (int i = 0; i < ep.n_sink; ++i) {
@@ -325,8 +356,8 @@ int wick_reduce_terms(const wick_nucleus *nuc, const wick_nucleon_op *ops, const
     }
     ReduceResult rr;
     memset(&rr, 0, sizeof(rr));
-    err = run_reduce(ep, bp, nuc, src_idx.data(), sflav.data(), sord.data(), seta.data(), seed, trials, sites, &rr,
-                     (cudaStream_t)stream);
+    err = run_reduce(ep, bp, nuc, Mu.data(), Md.data(), CM.data(), sflav.data(), sord.data(), seta.data(), seed,
+                     trials, sites, &rr, (cudaStream_t)stream);
     if (err) return err;
     wick_terms *t = new (std::nothrow) wick_terms();
     if (!t) {

@@ -141,6 +141,20 @@ block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restric
         for (int q = 0; q < 3; ++q) zero(acc[k][q]);
     }
 
+    // diquark lists needed by this CTA's outputs (lists are ordered by op)
+    int l_lo = plan.n_x, l_hi = 0;
+    {
+        const int g0 = blockIdx.z * (kThreads * kGroups);
+        const int g1 = min(n_groups, g0 + kThreads * kGroups) - 1;
+        const int o_lo = (g0 / gpr) / nc / plan.n_spin, o_hi = (g1 / gpr) / nc / plan.n_spin;
+        for (int l = 0; l < plan.n_x; ++l)
+            if (plan.x_op[l] >= o_lo && plan.x_op[l] <= o_hi) {
+                l_lo = min(l_lo, l);
+                l_hi = max(l_hi, l + 1);
+            }
+    }
+    const int n_xl = max(0, l_hi - l_lo);
+
     const ST *slice_u = Su + (size_t)slice * V * 144;
     const ST *slice_d = Sd + (size_t)slice * V * 144;
     for (int xb = x_begin; xb < x_end; xb += ns_tile) {
@@ -159,10 +173,11 @@ block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restric
         }
         __syncthreads();
         // diquark lists X[site][l][i2 * nc + i3]
-        for (int e = threadIdx.x; e < ns * plan.n_x * nc2; e += kThreads) {
-            const int site = e / (plan.n_x * nc2);
-            const int rem = e - site * plan.n_x * nc2;
-            const int l = rem / nc2, i23 = rem - l * nc2;
+        for (int e2 = threadIdx.x; e2 < ns * n_xl * nc2; e2 += kThreads) {
+            const int site = e2 / (n_xl * nc2);
+            const int rem = e2 - site * n_xl * nc2;
+            const int l = l_lo + rem / nc2, i23 = rem % nc2;
+            const int e = (site * plan.n_x + l) * nc2 + i23;
             const int i2 = i23 / nc, i3 = i23 - i2 * nc;
             const int f1 = plan.f1[plan.x_op[l]];
             const SC *s1 = sS + (size_t)site * nr * nc + (f1 == 0 ? 0 : nr0 * nc);

@@ -60,9 +60,9 @@ size_t block_partials_bytes(const BlockPlan &plan, int V, int n_slices, int prec
 // ---------------------------------------------------------------------------
 struct EnumPlan {
     int A, nq, nu, nd;
-    int n_sink, n_src;
+    int n_sink, n_M;           // sink terms, antisymmetrised source multisets
     int64_t fu, fd;            // n_u!, n_d!
-    int64_t n_raw;
+    int64_t n_raw;             // n_sink * n_M * n_u! * n_d!
     int ju[24], jd[24];        // source positions of u / d quarks
     int n_spin, n_chi, n_blk;
 };
@@ -74,10 +74,13 @@ struct ReduceResult {
     int64_t *d_rep;   // [U]
 };
 
-int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc,
-               const int8_t *src_idx /* host, n_src x nq, positions in chi[] */,
-               const int8_t *sink_flav, const int8_t *sink_ord, const int8_t *sink_eta,
-               uint64_t seed, int trials, int sites, ReduceResult *out, cudaStream_t stream);
+// Antisymmetrised source (host-prepared): n_M multisets, each the sorted
+// layout indices of its u quarks (Mu, n_M x nu) and d quarks (Md, n_M x nd),
+// with the summed signed source weight CM.
+int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc, const int8_t *Mu,
+               const int8_t *Md, const int64_t *CM, const int8_t *sink_flav, const int8_t *sink_ord,
+               const int8_t *sink_eta, uint64_t seed, int trials, int sites, ReduceResult *out,
+               cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Contraction (contract.cu)

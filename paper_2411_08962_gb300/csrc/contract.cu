@@ -211,4 +211,22 @@ int launch_contract(const double2 *blocks, int n_slices, int n_blk, int A, int64
     return WICK_OK;
 }
 
+namespace {
+__global__ void product_kernel(const double2 *__restrict__ a, const double2 *__restrict__ b, int64_t n,
+                               double2 *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = cmul(a[i], b[i]);
+}
+}  // namespace
+
 }  // namespace wick
+
+extern "C" int wick_cluster_product(const void *Ca, const void *Cb, int64_t n, void *out, wick_stream_t stream) {
+    if (!Ca || !Cb || !out || n < 0) return WICK_EINVAL;
+    if ((uintptr_t)Ca % 16 || (uintptr_t)Cb % 16 || (uintptr_t)out % 16) return WICK_EINVAL;
+    if (n == 0) return WICK_OK;
+    wick::product_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        (const double2 *)Ca, (const double2 *)Cb, n, (double2 *)out);
+    WICK_CUDA_TRY(cudaGetLastError());
+    return WICK_OK;
+}

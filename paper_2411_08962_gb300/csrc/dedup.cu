@@ -5,8 +5,8 @@
 //   1. modp_blocks_kernel  block values R[trial][id] of the antisymmetric blocks
 //                          (Eq. 2.4) at random integer propagators on `sites`
 //                          sites, exactly modulo p = 2^61 - 1.
-//   2. enum_hash_kernel    every raw Wick term j: decode (sink, source, sigma_u,
-//                          sigma_d), hash h_r = prod_k R[r][id_k] mod p, canonical
+//   2. enum_hash_kernel    every raw Wick term j: decode (sink, source multiset,
+//                          tau_u, tau_d), hash h_r = prod_k R[r][id_k] mod p, canonical
 //                          sign, then one insertion per group of equal keys in a
 //                          warp (match + reduce) into an open-addressing table
 //                          holding (key, sum of eps*c, smallest j).
@@ -104,15 +104,16 @@ struct TermTables {
     const int64_t *sink_w;                // [n_sink]
     const int8_t *sink_flav, *sink_ord;   // [n_sink][nq]
     const int8_t *sink_eta;               // [n_sink]
-    const int8_t *src_idx;                // [n_src][nq] positions in the layout's chi list
-    const int64_t *src_w;                 // [n_src]
+    const int8_t *Mu, *Md;                // [n_M][nu], [n_M][nd]: sorted layout positions
+    const int64_t *CM;                    // [n_M] antisymmetrised source weight
     const uint8_t *pu, *pd;               // permutation tables [n!][n]
     const int8_t *su, *sd;                // their signs
     const uint64_t *R;                    // [trials][n_blk]
 };
 
-// Block ids of raw term (i, m, ru, rd) and its coefficient.
-__device__ __forceinline__ int64_t term_ids(const EnumPlan &ep, const TermTables &tt, int i, int m, int64_t ru,
+// Block ids of raw term (i, M, ru, rd) and its coefficient: the sink quark of
+// flavour-ordinal q takes the tau(q)-th entry of the multiset's sorted list.
+__device__ __forceinline__ int64_t term_ids(const EnumPlan &ep, const TermTables &tt, int i, int M, int64_t ru,
                                             int64_t rd, int *ids) {
     const uint8_t *pu = tt.pu + ru * ep.nu, *pd = tt.pd + rd * ep.nd;
     const int nc = ep.n_chi;
@@ -122,13 +123,12 @@ __device__ __forceinline__ int64_t term_ids(const EnumPlan &ep, const TermTables
         for (int sl = 0; sl < 3; ++sl) {
             const int q = 3 * k + sl;
             const int f = tt.sink_flav[i * ep.nq + q], ord = tt.sink_ord[i * ep.nq + q];
-            const int pos = f == 0 ? ep.ju[pu[ord]] : ep.jd[pd[ord]];
-            ix[sl] = tt.src_idx[m * ep.nq + pos];
+            ix[sl] = f == 0 ? tt.Mu[M * ep.nu + pu[ord]] : tt.Md[M * ep.nd + pd[ord]];
         }
         const int o = tt.sink_type[i * ep.A + k], s = tt.sink_spin[i * ep.A + k];
         ids[k] = (((o * ep.n_spin + s) * nc + ix[0]) * nc + ix[1]) * nc + ix[2];
     }
-    return tt.sink_w[i] * tt.src_w[m] * tt.su[ru] * tt.sd[rd] * tt.sink_eta[i];
+    return tt.sink_w[i] * tt.CM[M] * tt.su[ru] * tt.sd[rd] * tt.sink_eta[i];
 }
 
 // Hash of a monomial; returns false for a zero key.  *eps = canonical sign.
@@ -215,7 +215,7 @@ enum_hash_kernel(const __grid_constant__ EnumPlan ep, const TermTables tt, int t
         const int64_t rd = (int64_t)(task - row * rd_tiles) * 32 + lane;
         const int64_t ru = (int64_t)(row % (uint64_t)ep.fu);
         const uint64_t im = row / (uint64_t)ep.fu;
-        const int m = (int)(im % (uint64_t)ep.n_src), i = (int)(im / (uint64_t)ep.n_src);
+        const int m = (int)(im % (uint64_t)ep.n_M), i = (int)(im / (uint64_t)ep.n_M);
         const bool valid = rd < ep.fd;
         int ids[kMaxA];
         uint64_t h0 = 0, h1 = 0;
@@ -353,7 +353,7 @@ __global__ void finalize_kernel(const __grid_constant__ EnumPlan ep, const TermT
     const int64_t rd = (int64_t)(j - row * (uint64_t)ep.fd);
     const int64_t ru = (int64_t)(row % (uint64_t)ep.fu);
     const uint64_t im = row / (uint64_t)ep.fu;
-    const int m = (int)(im % (uint64_t)ep.n_src), i = (int)(im / (uint64_t)ep.n_src);
+    const int m = (int)(im % (uint64_t)ep.n_M), i = (int)(im / (uint64_t)ep.n_M);
     int ids[kMaxA];
     term_ids(ep, tt, i, m, ru, rd, ids);
     uint64_t h0, h1;
@@ -386,9 +386,10 @@ uint64_t next_pow2(uint64_t v) { uint64_t p = 1; while (p < v) p <<= 1; return p
 
 }  // namespace
 
-int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc, const int8_t *src_idx,
-               const int8_t *sink_flav, const int8_t *sink_ord, const int8_t *sink_eta, uint64_t seed,
-               int trials, int sites, ReduceResult *out, cudaStream_t stream) {
+int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc, const int8_t *Mu,
+               const int8_t *Md, const int64_t *CM, const int8_t *sink_flav, const int8_t *sink_ord,
+               const int8_t *sink_eta, uint64_t seed, int trials, int sites, ReduceResult *out,
+               cudaStream_t stream) {
     int err = WICK_OK;
     int *status = status_word(&err);
     if (err) return err;
@@ -418,7 +419,7 @@ int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc,
     perm_table(ep.nu, hpu, hsu);
     perm_table(ep.nd, hpd, hsd);
 
-    DevBuf<int8_t> d_type, d_spin, d_flav, d_ord, d_eta, d_src, d_su, d_sd;
+    DevBuf<int8_t> d_type, d_spin, d_flav, d_ord, d_eta, d_mu, d_md, d_su, d_sd;
     DevBuf<int64_t> d_sw, d_cw;
     DevBuf<uint8_t> d_pu, d_pd;
     DevBuf<uint64_t> d_R;
@@ -426,8 +427,9 @@ int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc,
     if ((err = d_type.upload(nuc->sink_type, nsA, stream)) || (err = d_spin.upload(nuc->sink_spin, nsA, stream)) ||
         (err = d_sw.upload(nuc->sink_w, ep.n_sink, stream)) || (err = d_flav.upload(sink_flav, nsq, stream)) ||
         (err = d_ord.upload(sink_ord, nsq, stream)) || (err = d_eta.upload(sink_eta, ep.n_sink, stream)) ||
-        (err = d_src.upload(src_idx, (size_t)ep.n_src * ep.nq, stream)) ||
-        (err = d_cw.upload(nuc->src_w, ep.n_src, stream)) || (err = d_pu.upload(hpu.data(), hpu.size(), stream)) ||
+        (err = d_mu.upload(Mu, (size_t)ep.n_M * ep.nu, stream)) ||
+        (err = d_md.upload(Md, (size_t)ep.n_M * ep.nd, stream)) ||
+        (err = d_cw.upload(CM, ep.n_M, stream)) || (err = d_pu.upload(hpu.data(), hpu.size(), stream)) ||
         (err = d_pd.upload(hpd.data(), hpd.size(), stream)) || (err = d_su.upload(hsu.data(), hsu.size(), stream)) ||
         (err = d_sd.upload(hsd.data(), hsd.size(), stream)) || (err = d_R.alloc((size_t)2 * ep.n_blk)))
         return err;
@@ -435,11 +437,11 @@ int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc,
     modp_blocks_kernel<<<(trials * ep.n_blk + 127) / 128, 128, 0, stream>>>(bp, seed, trials, sites, d_R.p, ep.n_blk);
     WICK_CUDA_TRY(cudaGetLastError());
 
-    TermTables tt{d_type.p, d_spin.p, d_sw.p, d_flav.p, d_ord.p, d_eta.p, d_src.p, d_cw.p,
+    TermTables tt{d_type.p, d_spin.p, d_sw.p, d_flav.p, d_ord.p, d_eta.p, d_mu.p, d_md.p, d_cw.p,
                   d_pu.p, d_pd.p, d_su.p, d_sd.p, d_R.p};
 
     const uint32_t rd_tiles = (uint32_t)((ep.fd + 31) / 32);
-    const uint64_t n_rows = (uint64_t)ep.n_sink * ep.n_src * (uint64_t)ep.fu;
+    const uint64_t n_rows = (uint64_t)ep.n_sink * ep.n_M * (uint64_t)ep.fu;
     const uint64_t n_tasks = n_rows * rd_tiles;
     // table size: start from an estimate and double while it overflows
     const uint64_t upper = (uint64_t)(ep.n_raw >> ep.A) + 1024;
@@ -464,6 +466,7 @@ int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc,
         uint64_t blocks = (n_tasks * 32 + 255) / 256;
         const uint64_t max_blocks = (uint64_t)n_sm * 8;
         if (blocks > max_blocks) blocks = max_blocks;
+        if (blocks == 0) blocks = 1;  // no raw terms: the kernel exits at once
         enum_hash_kernel<<<(unsigned)blocks, 256, 0, stream>>>(ep, tt, trials, ht, d_cnt.p + 1, status, n_tasks,
                                                               rd_tiles);
         WICK_CUDA_TRY(cudaGetLastError());

@@ -166,3 +166,77 @@ def nucleus(name: str, form: str = "upper") -> Nucleus:
         f = ops[o].flav_pair
         flav += [f, f, 1 - f]
     return Nucleus(name, len(types), ops, n_spin, chi, sink, src, flav)
+
+
+# ---------------------------------------------------------------------------
+# Li-7 clusters (Sec. III.C, Eqs. He4_op and Li7): block types p+, p-, n+, n-
+# (C gamma5 P_pm, all four spins, every source index).  The isospin wave
+# function moves p and n between nucleon positions, so the source quarks of
+# every term are stored flavour-grouped (u first, then d, each in nucleon-slot
+# order) and the parity of that reordering is folded into the term's weight.
+# ---------------------------------------------------------------------------
+P_PLUS, P_MINUS, N_PLUS, N_MINUS = 0, 1, 2, 3
+
+
+def pm_ops():
+    sp = (0, 1, 2, 3)
+    gp, gm = diquark_matrix(+1), diquark_matrix(-1)
+    return [nucleon_op(U, gp, sp, sp), nucleon_op(U, gm, sp, sp), nucleon_op(D, gp, sp, sp),
+            nucleon_op(D, gm, sp, sp)]
+
+
+def _flavour_grouped(ops, terms):
+    acc = {}
+    flav_ref = None
+    for types, spins, coef in terms:
+        flav = []
+        for o in types:
+            f = ops[o].flav_pair
+            flav += [f, f, 1 - f]
+        perm = sorted(range(len(flav)), key=lambda q: (flav[q], q))      # stable: u first
+        parity = 1
+        seen = [False] * len(perm)
+        for start in range(len(perm)):                                  # parity from the cycle lengths
+            if not seen[start]:
+                n, q = 0, start
+                while not seen[q]:
+                    seen[q] = True
+                    q = perm[q]
+                    n += 1
+                if n % 2 == 0:
+                    parity = -parity
+        grouped = [flav[q] for q in perm]
+        if flav_ref is not None and grouped != flav_ref:
+            raise ValueError("terms of one operator must carry the same quarks")
+        flav_ref = grouped
+        for chi, w in _source_table(ops, types, [(spins, coef * parity)]):
+            key = tuple(chi[q] for q in perm)
+            acc[key] = acc.get(key, 0) + w
+    return sorted((c, w) for c, w in acc.items() if w), flav_ref
+
+
+def cluster(name: str) -> Nucleus:
+    """'he4_cluster': (chibar eta - chi etabar)/sqrt2 with p+, n+ and up/down
+    spins (scale 1/96 for sink x source);  'triton': n_-^T C g5 p_+ n_+^(J=up)."""
+    ops = pm_ops()
+    if name == "he4_cluster":
+        pats = [(0, 1, 0, 1), (1, 0, 1, 0), (0, 1, 1, 0), (1, 0, 0, 1), (0, 0, 1, 1), (1, 1, 0, 0)]
+        chi_w = [1, 1, -1, -1, 0, 0]       # times 1/2
+        chibar_w = [1, 1, 1, 1, -2, -2]    # times 1/sqrt(12)
+        terms = []
+        for a, spins in enumerate(pats):
+            for b, iso in enumerate(pats):
+                w = chibar_w[a] * chi_w[b] - chi_w[a] * chibar_w[b]
+                if w:
+                    terms.append((tuple(P_PLUS if x == 0 else N_PLUS for x in iso), spins, w))
+        scale = 1.0 / 96.0
+    elif name == "triton":
+        G = diquark_matrix()
+        terms = [((N_MINUS, P_PLUS, N_PLUS), (a, b, 0), int(G[a, b])) for a in range(4) for b in range(4)
+                 if G[a, b]]
+        scale = 1.0
+    else:
+        raise ValueError(name)
+    src, flav = _flavour_grouped(ops, terms)
+    sink = sorted((tuple(t), tuple(s), w) for t, s, w in terms)
+    return Nucleus(name, len(terms[0][0]), ops, 4, list(range(12)), sink, src, flav, scale)

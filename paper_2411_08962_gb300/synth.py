@@ -101,4 +101,5 @@ WORKLOADS = {
     "he3": dict(L=8, T=16, n_src=2, dtype="c128", seed=0x24110003),
     "he4": dict(L=16, T=32, n_src=4, dtype="c64", seed=0x24110004),
     "li7": dict(L=24, T=48, n_src=1, dtype="c64", seed=0x24110007),
+    "batched": dict(L=32, T=64, n_src=2, dtype="c64", seed=0x24110005, n_cfg=64),
 }

@@ -28,7 +28,7 @@ EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_reduce_terms", "wick_t
            "wick_terms_nucleons", "wick_terms_copy", "wick_terms_stats", "wick_terms_select",
            "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_contract_noalloc",
            "wick_status", "wick_batch_create", "wick_batch_run", "wick_batch_launches", "wick_batch_free",
-           "wick_synth_propagator", "wick_strerror", "wick_version")
+           "wick_synth_propagator", "wick_cluster_product", "wick_strerror", "wick_version")
 
 
 class WickError(RuntimeError):
@@ -96,13 +96,14 @@ def load(path: str = LIB_PATH):
             L.wick_batch_free.argtypes = [vp]
             L.wick_batch_free.restype = None
             L.wick_synth_propagator.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
+            L.wick_cluster_product.argtypes = [vp, vp, C.c_int64, vp, vp]
             L.wick_strerror.argtypes = [C.c_int]
             L.wick_strerror.restype = C.c_char_p
             L.wick_version.restype = C.c_char_p
             for f in ("wick_build_blocks", "wick_reduce_terms", "wick_terms_nucleons", "wick_terms_copy",
                       "wick_terms_stats", "wick_terms_select", "wick_terms_save", "wick_terms_load",
                       "wick_contract", "wick_contract_noalloc", "wick_status", "wick_batch_create",
-                      "wick_batch_run", "wick_batch_launches", "wick_synth_propagator"):
+                      "wick_batch_run", "wick_batch_launches", "wick_synth_propagator", "wick_cluster_product"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -299,6 +300,12 @@ def wick_synth_propagator(seed: int, flavour: int, src: int, L: int, T: int, out
     dt = WICK_C64 if str(out.dtype) == "torch.complex64" else WICK_C128
     _check(load().wick_synth_propagator(seed, flavour, src, L, T, dt, _ptr(out), _stream(stream)),
            "wick_synth_propagator")
+
+
+def wick_cluster_product(Ca, Cb, out, stream=None):
+    """out = Ca * Cb elementwise (complex128 device tensors of equal size)."""
+    _check(load().wick_cluster_product(_ptr(Ca), _ptr(Cb), Ca.numel(), _ptr(out), _stream(stream)),
+           "wick_cluster_product")
 
 
 def wick_status(stream=None) -> int:

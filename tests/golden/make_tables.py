@@ -2,12 +2,12 @@
 
     python tests/golden/make_tables.py
 
-The He-4 (p up, p down, n up, n down; upper components) reduction enumerates
-1.07e10 raw Wick terms, minutes of CPU time, too slow for every test run.  This
-script runs the CPU reference once, checks the table against the raw Wick sum
-exactly modulo 2^61 - 1 at a fresh random point (Theorem 1, App. C), and
-stores it with a SHA-256 digest of its canonical bytes (rep int64, w int64,
-ids uint16, little endian, in that order).  It imports nothing but `oracle/`.
+The He-4 (p up, p down, n up, n down; upper components) table is checked here
+exactly modulo 2^61 - 1 at a fresh random point (Theorem 1, App. C) against the
+plain Wick sum over all 1.07e10 (sink, source tuple, sigma_u, sigma_d) terms --
+minutes of CPU time, too slow for every test run -- and stored with a SHA-256
+digest of its canonical bytes (rep int64, w int64, ids uint16, little endian,
+in that order).  It imports nothing but `oracle/`.
 """
 import hashlib
 import json

@@ -156,8 +156,14 @@ def test_reduced_table_bit_exact(name):
     assert 0.0 <= bound < 1e-9
 
 
-def test_reduced_table_he4_matches_golden():
+def test_reduced_table_he4_matches_oracle_and_golden():
+    """He-4: bit-exact against the oracle, and against the stored table whose
+    generation checked it exactly mod p against all 1.07e10 terms of the plain sum."""
     _, g, (stats, _) = gpu_table("he4")
+    o = O.dedup(oops.nucleus("he4"))
+    for k in ("rep", "w", "ids"):
+        assert np.array_equal(g[k], o[k])
+    assert stats == o["stats"]
     tab, info = make_tables.load("he4")
     assert make_tables.digest(g["rep"], g["w"], g["ids"]) == info["sha256"]
     assert list(stats) == info["stats"]
@@ -222,7 +228,7 @@ def test_he3_workload_fp64():
 def he4_case():
     w = synth.WORKLOADS["he4"]
     Su, Sd = props(w["L"], w["T"], w["n_src"], seed=w["seed"], dtype=np.complex64)
-    tab, _ = make_tables.load("he4")
+    tab = O.dedup(oops.nucleus("he4"))
     terms, _, _ = gpu_table("he4")
     return Su, Sd, tab, terms
 

@@ -210,7 +210,9 @@ def test_reduced_equals_raw_fp64(name):
     Bh = O.blocks_single(Su, Sd, nuc)
     tab = O.dedup(nuc)
     assert rel(O.table_correlator(nuc, Bh, tab), O.raw_correlator(nuc, Bh)) < 1e-12
-    assert tab["stats"][0] == ops.n_raw_terms(nuc)
+    ms = O.source_multisets(nuc)
+    nu, nd = ops.quark_counts(nuc)
+    assert tab["stats"][0] == ms["n_red"] == len(nuc["sink"]) * len(ms["CM"]) * factorial(nu) * factorial(nd)
 
 
 @pytest.mark.parametrize("name", ["deuteron", "he3"])
@@ -259,8 +261,30 @@ def test_deuteron_at_most_nine_classes_per_source_tuple():
         one["src"] = [(chi, w)]
         t = O.dedup(one)
         counts.append(len(t["w"]))
-        assert t["stats"][0] == factorial(3) * factorial(3)
+        # one source tuple: one multiset (3! 3! orderings) unless a flavour repeats an index
+        assert t["stats"][0] in (0, factorial(3) * factorial(3))
     assert max(counts) <= 9 and max(counts) > 0
+
+
+def test_antisymmetrised_source():
+    """Method B of Sec. III.C: the source collapses onto sorted multisets.  For
+    He-4 (6 u and 6 d quarks in 6 upper colour-spin states each) Pauli leaves
+    exactly one multiset pair, every state once; its weight is the signed sum
+    of all 12^4 product tuples that are reorderings of it."""
+    he4 = O.source_multisets(ops.nucleus("he4"))
+    assert len(he4["CM"]) == 1 and he4["n_red"] == factorial(6) ** 2
+    assert list(he4["Mu"][0]) == list(range(6)) and list(he4["Md"][0]) == list(range(6))
+    # brute force over the source tuples for the weight
+    nuc = ops.nucleus("he4")
+    flav = nuc["src_flav"]
+    tot = 0
+    for chi, w in nuc["src"]:
+        u = [c for c, f in zip(chi, flav) if f == 0]
+        d = [c for c, f in zip(chi, flav) if f == 1]
+        if len(set(u)) == 6 and len(set(d)) == 6:
+            inv = sum(a > b for seq in (u, d) for i, a in enumerate(seq) for b in seq[i + 1:])
+            tot += w * (-1) ** inv
+    assert he4["CM"][0] == tot and tot != 0
 
 
 def test_weights_are_integers_after_pair_folding():
