@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["he4", "li7", "batched"], default="he4",
+                    help="he4: the metric's workload (default); li7 / batched: the other scope rows")
     ap.add_argument("--profile-slab", choices=["mixed", "fp64"], default=None,
                     help="only run the block build on one source of the workload (for ncu captures)")
     return ap.parse_args()
@@ -221,7 +223,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2411_08962_gb300 import build, operators, synth, wick
+    from paper_2411_08962_gb300 import build, operators, sharding, synth, wick
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -248,8 +250,8 @@ def run_ours(args):
 
     # inputs: two configurations per rank, resident on the device; pinned host copies for e2e
     cfg_host, cfg_dev = [], []
-    for c in range(2):
-        Su, Sd = host_props(w["seed"] + 7919 * (rank * 2 + c), L, T, n_src)
+    for c in sharding.shard(2 * world, rank, world):
+        Su, Sd = host_props(sharding.config_seed(w["seed"], c), L, T, n_src)
         hu = torch.from_numpy(Su).pin_memory()
         hd = torch.from_numpy(Sd).pin_memory()
         cfg_host.append((hu, hd))
@@ -287,12 +289,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop() if clocks else None
-    elapsed = e0.elapsed_time(e1)
+    elapsed = sharding.max_over_ranks(e0.elapsed_time(e1), device="cuda")
     build_ms = float(np.mean([a.elapsed_time(b) for a, b in bev]))
-    if world > 1:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
     configs = args.steps * world
     value = elapsed / configs
     terms_per_s = U * n_src * T * configs / (elapsed / 1e3)
@@ -335,11 +333,26 @@ def run_ours(args):
         Cpin.copy_(Cout, non_blocking=True)
     g1.record(stream)
     torch.cuda.synchronize()
-    e2e = g0.elapsed_time(g1) / ke
-    if world > 1:
-        t = torch.tensor([e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item()) / world
+    e2e = sharding.max_over_ranks(g0.elapsed_time(g1) / ke, device="cuda") / world
+
+    # the same configurations through the batched executor: one CUDA-graph launch per pair
+    bblocks = torch.empty((len(cfg_dev), n_src, T, nuc.n_blk), dtype=torch.complex128, device="cuda")
+    bC = torch.empty((len(cfg_dev), 1, n_src, T), dtype=torch.complex128, device="cuda")
+    batch = wick.Batch([c[0] for c in cfg_dev], [c[1] for c in cfg_dev], tabs, [terms], prec, bblocks, bC,
+                       L, T, n_src)
+    for _ in range(2):
+        batch.run(stream)
+    torch.cuda.synchronize()
+    kb = max(2, min(10, args.steps))
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(kb):
+        batch.run(stream)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = h0.elapsed_time(h1) / (kb * len(cfg_dev))
+    batch_launches = batch.launches
+    batch.free()
 
     hbm_peak, sm_mhz, peak_kind = peaks()
     bytes_launch = n_src * T * V * block_bytes_per_site(8)
@@ -360,6 +373,8 @@ def run_ours(args):
         "fp64_plain": {"value": fp64_ms, "unit": UNIT, "speedup_mixed": fp64_ms / value * world,
                        "fp64_tflops_vs_nominal": fp64_tflops / FP64_NOMINAL_TFLOPS},
         "rel_err_mixed_vs_fp64_max_per_t": rel_err,
+        "batched_graph": {"value": batched_ms, "unit": UNIT, "configs_per_launch": len(cfg_dev),
+                          "kernels_per_launch": batch_launches},
         "reduce": {"seconds": reduce_s, "raw_terms": n_raw, "zero_terms": n_zero, "distinct_keys": n_keys,
                    "kept_terms": U, "raw_terms_per_s": n_raw / reduce_s, "false_merge_bound": bound},
         "roofline": {"kernel": "block build, double-FP32 (block_partial_kernel + block_reduce_kernel)",
@@ -415,10 +430,170 @@ def run_profile_slab(args):
     print(json.dumps({"profile_slab": args.profile_slab, "ms_per_launch": e0.elapsed_time(e1) / args.steps}))
 
 
+# ---------------------------------------------------------------------------
+# the other scope rows: Li-7 clusters and the batched multi-configuration job
+# ---------------------------------------------------------------------------
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_li7(args):
+    """Li-7 = He-4 cluster x triton cluster, L=24, T=48, one source (one configuration per step)."""
+    import torch
+
+    from paper_2411_08962_gb300 import build, operators, synth, wick
+    build.build()
+    wick.load()
+    w = synth.WORKLOADS["li7"]
+    L, T, n_src = w["L"], w["T"], w["n_src"]
+    stream = torch.cuda.current_stream()
+    tabs = {n: wick.Tables(operators.cluster(n)) for n in ("he4_cluster", "triton")}
+    t0 = time.perf_counter()
+    terms = {n: wick.wick_reduce_terms(t) for n, t in tabs.items()}
+    reduce_s = time.perf_counter() - t0
+    Su = torch.empty((n_src, T, L ** 3, 3, 4, 3, 4), dtype=torch.complex64, device="cuda")
+    Sd = torch.empty_like(Su)
+    for s in range(n_src):
+        wick.wick_synth_propagator(w["seed"], 0, s, L, T, Su[s])
+        wick.wick_synth_propagator(w["seed"], 1, s, L, T, Sd[s])
+    tb = tabs["triton"]
+    B = torch.empty((n_src, T, tb.nuc.n_blk), dtype=torch.complex128, device="cuda")
+    Cs = {n: torch.empty((n_src, T), dtype=torch.complex128, device="cuda") for n in tabs}
+    Cli = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
+
+    def step(prec):
+        wick.wick_build_blocks(Su, Sd, tb, prec, B, L, T, n_src, stream)
+        for n in tabs:
+            wick.wick_contract(B, n_src, T, terms[n], prec, Cs[n], stream)
+        wick.wick_cluster_product(Cs["he4_cluster"], Cs["triton"], Cli, stream)
+
+    ms = _timed(lambda: step(wick.WICK_MIXED), args.steps, args.warmup, stream)
+    c_mixed = Cli.clone()
+    ms64 = _timed(lambda: step(wick.WICK_FP64), max(1, min(3, args.steps)), 1, stream)
+    rel = float(((c_mixed - Cli).abs() / Cli.abs()).max().item())
+    print(json.dumps({"workload": "li7", "metric": "Li-7 correlator ms/config (He-4 cluster x triton)",
+                      "value": ms, "unit": UNIT, "higher_is_better": False, "steps": args.steps,
+                      "config": {"L": L, "T": T, "n_src": n_src, "block_types": 4, "spins": 4,
+                                 "terms": {n: t.count for n, t in terms.items()}},
+                      "fp64_plain": {"value": ms64, "unit": UNIT},
+                      "rel_err_mixed_vs_fp64_max_per_t": rel, "reduce_seconds": reduce_s,
+                      "gpu_launches_per_step": 2 + 2 * len(tabs) + 1}), flush=True)
+
+
+def run_batched(args):
+    """64 configurations x {deuteron, He-3, He-4} x 2 sources, L=32, T=64,
+    complex64, generated on the device and streamed through two buffers
+    (generation of the next configuration overlaps the current one)."""
+    import torch
+
+    from paper_2411_08962_gb300 import build, operators, sharding, synth, wick
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    wick.load()
+    w = synth.WORKLOADS["batched"]
+    L, T, n_src, n_cfg = w["L"], w["T"], w["n_src"], w["n_cfg"]
+    mine = list(sharding.shard(n_cfg, rank, world))
+    nuclei = ("deuteron", "he3", "he4")
+    tabs = wick.Tables(operators.nucleus("he4"))            # the upper-spin blocks serve all three
+    terms = [wick.wick_reduce_terms(wick.Tables(operators.nucleus(n))) for n in nuclei]
+    comp = torch.cuda.current_stream()
+    gen = torch.cuda.Stream()
+    bufs = [(torch.empty((n_src, T, L ** 3, 3, 4, 3, 4), dtype=torch.complex64, device="cuda"),
+             torch.empty((n_src, T, L ** 3, 3, 4, 3, 4), dtype=torch.complex64, device="cuda")) for _ in range(2)]
+    ready = [torch.cuda.Event() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    B = torch.empty((n_src, T, tabs.nuc.n_blk), dtype=torch.complex128, device="cuda")
+    C = torch.empty((len(mine), len(nuclei), n_src, T), dtype=torch.complex128, device="cuda")
+
+    def generate(i, slot):
+        with torch.cuda.stream(gen):
+            gen.wait_event(done[slot])
+            seed = sharding.config_seed(w["seed"], mine[i])
+            for f in (0, 1):
+                for s in range(n_src):
+                    wick.wick_synth_propagator(seed, f, s, L, T, bufs[slot][f][s], gen)
+            ready[slot].record(gen)
+
+    def job(prec):
+        for slot in range(2):
+            done[slot].record(comp)
+        generate(0, 0)
+        for i in range(len(mine)):
+            slot = i % 2
+            if i + 1 < len(mine):
+                generate(i + 1, 1 - slot)
+            comp.wait_event(ready[slot])
+            wick.wick_build_blocks(bufs[slot][0], bufs[slot][1], tabs, prec, B, L, T, n_src, comp)
+            for k, t in enumerate(terms):
+                wick.wick_contract(B, n_src, T, t, prec, C[i, k], comp)
+            done[slot].record(comp)
+
+    # streamed wall time (device generation overlapped with the previous configuration)
+    streamed = _timed(lambda: job(wick.WICK_MIXED), 1, 0, comp)
+    streamed = sharding.max_over_ranks(streamed, device="cuda")
+    gen_ms = _timed(lambda: (generate(0, 0), comp.wait_event(ready[0])), 2, 1, comp)
+
+    # correlator throughput: the same per-configuration work on resident inputs
+    # (two 9.7 GB configurations alternate, larger than L2)
+    generate(0, 0)
+    generate(1, 1)
+    comp.wait_event(ready[0])
+    comp.wait_event(ready[1])
+
+    def compute(prec):
+        for i in range(len(mine)):
+            slot = i % 2
+            wick.wick_build_blocks(bufs[slot][0], bufs[slot][1], tabs, prec, B, L, T, n_src, comp)
+            for k, t in enumerate(terms):
+                wick.wick_contract(B, n_src, T, t, prec, C[i, k], comp)
+    ms = _timed(lambda: compute(wick.WICK_MIXED), args.steps, min(args.warmup, 1), comp)
+    ms = sharding.max_over_ranks(ms, device="cuda")
+    cm = C[0].clone()
+
+    # precision on the first configuration: the FP64 path on the same inputs
+    def one64():
+        wick.wick_build_blocks(bufs[0][0], bufs[0][1], tabs, wick.WICK_FP64, B, L, T, n_src, comp)
+        for k, t in enumerate(terms):
+            wick.wick_contract(B, n_src, T, t, wick.WICK_FP64, C[0, k], comp)
+    t64 = _timed(one64, 1, 0, comp)
+    rel = float(((cm - C[0]).abs() / C[0].abs()).max().item())
+    n_corr = n_cfg * len(nuclei) * n_src
+    if rank == 0:
+        print(json.dumps({"workload": "batched", "metric": "correlators/s (C(t) vectors over all T)",
+                          "value": n_corr / (ms / 1e3), "unit": "correlators/s", "higher_is_better": True,
+                          "ms_per_step": ms, "ms_per_config": ms / n_cfg * world, "n_gpus": world,
+                          "scaling": "weak" if world > 1 else None,
+                          "config": {"n_cfg": n_cfg, "nuclei": list(nuclei), "L": L, "T": T, "n_src": n_src,
+                                     "inputs": "resident, two 9.7 GB configurations alternate"},
+                          "streamed": {"ms_per_step": streamed, "generation_ms_per_config": gen_ms,
+                                       "note": "device generation (FP64 Box-Muller) overlapped with compute"},
+                          "fp64_plain_one_config_ms": t64, "rel_err_mixed_vs_fp64_max_per_t": rel,
+                          "gpu_launches_per_step": len(mine) * (2 + 2 * len(nuclei))}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.profile_slab:
         run_profile_slab(a)
+    elif a.impl == "ours" and a.workload == "li7":
+        run_li7(a)
+    elif a.impl == "ours" and a.workload == "batched":
+        run_batched(a)
     elif a.impl == "reference":
         run_reference(a)
     else:
