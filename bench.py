@@ -479,6 +479,12 @@ def run_li7(args):
 
     ms = _timed(lambda: step(wick.WICK_MIXED), args.steps, args.warmup, stream)
     c_mixed = Cli.clone()
+    # where the mixed step's time goes: the block build and each table's contraction alone
+    phases = {"blocks": _timed(lambda: wick.wick_build_blocks(Su, Sd, tb, wick.WICK_MIXED, B, L, T, n_src, stream),
+                               args.steps, 1, stream)}
+    for n in tabs:
+        phases["contract_" + n] = _timed(lambda n=n: wick.wick_contract(B, n_src, T, terms[n], wick.WICK_MIXED,
+                                                                        Cs[n], stream), args.steps, 1, stream)
     ms64 = _timed(lambda: step(wick.WICK_FP64), max(1, min(3, args.steps)), 1, stream)
     rel = float(((c_mixed - Cli).abs() / Cli.abs()).max().item())
     print(json.dumps({"workload": "li7", "metric": "Li-7 correlator ms/config (He-4 cluster x triton)",
@@ -487,6 +493,7 @@ def run_li7(args):
                                  "terms": {n: t.count for n, t in terms.items()}},
                       "fp64_plain": {"value": ms64, "unit": UNIT},
                       "rel_err_mixed_vs_fp64_max_per_t": rel, "reduce_seconds": reduce_s,
+                      "mixed_phases_ms": phases,
                       "gpu_launches_per_step": 2 + 2 * len(tabs) + 1}), flush=True)
 
 

@@ -54,6 +54,7 @@ extern "C" {
 /* arithmetic of a call */
 #define WICK_FP64 0  /* FP64 products and sums */
 #define WICK_MIXED 1 /* double-FP32 products on the float pipes, FP64 sums over site chunks and terms */
+#define WICK_MIXED_SIMT 2 /* wick_build_blocks only: WICK_MIXED without the tensor-core update stage */
 
 /* quark flavours */
 #define WICK_U 0
@@ -144,7 +145,12 @@ size_t wick_block_count(const wick_block_layout *layout);
  *               pipes -- products of the float propagator entries formed exactly
  *               with FMA, sums as float pairs (about 44 significant bits) over a
  *               chunk of at most 256 sites -- and an FP64 sum of the chunks.
- *               C128 input is rounded to float first under WICK_MIXED.
+ *               C128 input is rounded to float first under WICK_MIXED.  For the
+ *               upper-spin tables the update sum over sites runs on the tensor
+ *               cores (tcgen05, bf16) as an exact sliced product: 16-site chunks,
+ *               5 x 5 fixed-point slices of 8 bits, every chunk sum exact in FP32,
+ *               slice pairs combined in double-FP32 (same accuracy class).
+ *               WICK_MIXED_SIMT requests the CUDA-core double-FP32 kernel.
  *   blocks      device, caller-owned, complex128 [n_src][T][wick_block_count]
  * Uses a library-cached device workspace for the per-chunk FP64 partials
  * (allocated on first use and grown when needed: make the first call, with

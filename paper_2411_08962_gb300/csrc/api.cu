@@ -230,7 +230,7 @@ int wick_build_blocks(const wick_prop *Su, const wick_prop *Sd, const wick_nucle
                       const wick_block_layout *layout, int precision, void *blocks, wick_stream_t stream) {
     if (!prop_ok(Su) || !prop_ok(Sd) || !blocks) return WICK_EINVAL;
     if (Su->L != Sd->L || Su->T != Sd->T || Su->n_src != Sd->n_src || Su->dtype != Sd->dtype) return WICK_EINVAL;
-    if (precision != WICK_FP64 && precision != WICK_MIXED) return WICK_EINVAL;
+    if (precision != WICK_FP64 && precision != WICK_MIXED && precision != WICK_MIXED_SIMT) return WICK_EINVAL;
     if ((uintptr_t)blocks % 16) return WICK_EINVAL;
     BlockPlan plan;
     int err = build_block_plan(ops, layout, &plan);

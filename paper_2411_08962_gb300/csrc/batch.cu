@@ -77,6 +77,9 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
     if (cudaMalloc(&bt->block_partials, pbytes) != cudaSuccess ||
         cudaMalloc(&bt->contract_partials, cbytes) != cudaSuccess)
         return fail(WICK_ENOMEM);
+    int serr = WICK_OK;
+    (void)status_word(&serr);  // the device status word exists before capture (kernels report timeouts there)
+    if (serr) return fail(serr);
     cudaStream_t cap;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return fail(WICK_ECUDA);
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {

@@ -295,7 +295,7 @@ int launch_typed(const BlockPlan &plan, const void *Su, const void *Sd, int V, i
 }  // namespace
 
 size_t block_partials_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int *n_splits, int *chunk) {
-    (void)precision;
+    if (precision == WICK_MIXED && tc_applicable(plan)) return tc_partials_bytes(plan, V, n_slices, n_splits, chunk);
     *chunk = kChunk;
     *n_splits = (V + kChunk - 1) / kChunk;
     return sizeof(double2) * (size_t)(*n_splits) * n_slices * plan.n_out;
@@ -306,7 +306,13 @@ int launch_block_build(const BlockPlan &plan, const void *Su, int dtype_u, const
                        cudaStream_t stream) {
     if (dtype_u != dtype_d) return WICK_EINVAL;
     double2 *part = reinterpret_cast<double2 *>(partials);
-    if (precision == WICK_MIXED) {
+    if (precision == WICK_MIXED && tc_applicable(plan)) {
+        int err = WICK_OK;
+        int *status = status_word(&err);
+        if (err) return err;
+        return launch_block_tc(plan, Su, Sd, dtype_u, V, n_slices, partials, n_splits, blocks, status, stream);
+    }
+    if (precision == WICK_MIXED || precision == WICK_MIXED_SIMT) {
         if (plan.pow2_w) {
             if (dtype_u == WICK_C64)
                 return launch_typed<kDF32X2, float2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);

@@ -54,6 +54,11 @@ int launch_block_build(const BlockPlan &plan, const void *Su, int dtype_u, const
                        double2 *blocks, cudaStream_t stream);
 size_t block_partials_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int *n_splits,
                             int *chunk);
+// tensor-core update stage (blocks_tc.cu): upper-spin plans, double-FP32-exact
+bool tc_applicable(const BlockPlan &plan);
+size_t tc_partials_bytes(const BlockPlan &plan, int V, int n_slices, int *n_splits, int *chunk);
+int launch_block_tc(const BlockPlan &plan, const void *Su, const void *Sd, int dtype, int V, int n_slices,
+                    double *partials, int n_splits, double2 *blocks, int *status, cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Term reduction (dedup.cu)

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libwick.so")
 WICK_OK, WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA = 0, -1, -2, -3
 WICK_ECAPACITY, WICK_EOVERFLOW, WICK_ETIMEOUT, WICK_EIO, WICK_ESCRATCH = -4, -5, -6, -7, -8
 WICK_C128, WICK_C64 = 0, 1
-WICK_FP64, WICK_MIXED = 0, 1
+WICK_FP64, WICK_MIXED, WICK_MIXED_SIMT = 0, 1, 2
 WICK_U, WICK_D = 0, 1
 
 EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_reduce_terms", "wick_terms_count",
