@@ -35,6 +35,7 @@ METRIC = "He-4 correlator ms/config & Wick terms/s, mixed+batched vs FP64 plain,
 UNIT = "ms/config"
 WORKLOAD = "He-4 p(up)p(down)n(up)n(down), upper spin components, L=16, T=32, 4 sources, complex64 propagators"
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 
 
 def parse():
@@ -49,6 +50,13 @@ def parse():
     ap.add_argument("--profile-slab", choices=["mixed", "fp64"], default=None,
                     help="only run the block build on one source of the workload (for ncu captures)")
     return ap.parse_args()
+
+
+def bf16_peak_tflops():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p)).get("bf16_tflops", FALLBACK_BF16_TFLOPS))
+    return FALLBACK_BF16_TFLOPS
 
 
 def peaks():
@@ -71,6 +79,18 @@ CMAC_PER_SITE = 2 * 3 * 36 * 4 + 2 * 2 * 216 * 3
 # FP32-pipe operations per real multiply-add in double-FP32: TwoProd (2), the
 # low-part FMA (1), TwoSum (6) and the two low-part adds (2).
 DF32_OPS_PER_MAC = 11
+
+# The tensor-core block build (WICK_MIXED) per site, both block types: the
+# FP32-pipe work of preparing the operands, in lane operations --
+#   216 diquark values (2 types x 3 lists x 36 entries): 4 terms x 2 exact
+#   packed product-accumulations (9 f32x2 ops = 18 lane ops), one packed
+#   renormalising add (18), 6 packed slices (11 f32x2 ops = 22 lane ops each);
+#   72 propagator values (2 types x 2 spins x 6 x 3 terms): 5 packed slices
+#   (4 f32x2 ops = 8 lane ops each)
+# -- and the MMA work: per type 6 MMAs of M=128 (5 stacked slices x 24 rows,
+# padded), N=48 (36 columns, padded), over K = 6 per site.
+TC_LANE_OPS_PER_SITE = 216 * (4 * 2 * 18 + 18 + 6 * 22) + 72 * 5 * 8
+TC_MMA_FLOPS_PER_SITE = 2 * 6 * 2 * 128 * 48 * 6
 
 
 class Clocks:
@@ -133,7 +153,7 @@ def block_bytes_per_site(dtype_bytes: int) -> int:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("blocks.cu", "common.cuh", "df32.cuh"):
+    for f in ("blocks_tc.cu", "common.cuh", "df32.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2411_08962_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -141,7 +161,7 @@ def kernel_source_hash():
 def recorded_traffic():
     """DRAM bytes per launch from the committed ncu record, or None when the
     kernel sources changed since the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "block_build_he4_traffic.txt")
+    p = os.path.join(ROOT, "profiles", "block_tc_he4_traffic.txt")
     if not os.path.exists(p):
         return None
     d = {}
@@ -352,12 +372,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     batched_ms = h0.elapsed_time(h1) / (kb * len(cfg_dev))
     batch_launches = batch.launches
+    kernels_per_config = batch_launches // len(cfg_dev)   # the library's own count of its launches
     batch.free()
 
+    # the CUDA-core double-FP32 block kernel on the same input, for comparison
+    simt_ms = _timed(lambda: wick.wick_build_blocks(cfg_dev[0][0], cfg_dev[0][1], tabs, wick.WICK_MIXED_SIMT, blocks,
+                                                    L, T, n_src, stream), max(2, min(5, args.steps)), 1, stream)
+
     hbm_peak, sm_mhz, peak_kind = peaks()
+    bf16_peak = bf16_peak_tflops()
     bytes_launch = n_src * T * V * block_bytes_per_site(8)
     sites = n_src * T * V
-    ops_launch = sites * CMAC_PER_SITE * 4 * DF32_OPS_PER_MAC
+    ops_launch = sites * TC_LANE_OPS_PER_SITE
+    mma_flops = sites * TC_MMA_FLOPS_PER_SITE
     alu_peak = N_SM * FP32_LANES * sm_mhz * 1e6 / 1e12      # Top/s, one op per lane per clock
     achieved = ops_launch / (build_ms / 1e3) / 1e12
     fp64_block_ms = fp64_ms  # the FP64 step is dominated by its block build
@@ -377,16 +404,21 @@ def run_ours(args):
                           "kernels_per_launch": batch_launches},
         "reduce": {"seconds": reduce_s, "raw_terms": n_raw, "zero_terms": n_zero, "distinct_keys": n_keys,
                    "kept_terms": U, "raw_terms_per_s": n_raw / reduce_s, "false_merge_bound": bound},
-        "roofline": {"kernel": "block build, double-FP32 (block_partial_kernel + block_reduce_kernel)",
+        "roofline": {"kernel": "block build on the tensor cores (tc_bounds_kernel + block_tc_kernel + "
+                               "tc_reduce_kernel; block_tc_kernel dominates)",
                      "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                      "frac": achieved / alu_peak, "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES} FP32 lanes x "
                                                               f"{sm_mhz:.0f} MHz ({peak_kind} clock)",
                      "ops_per_launch": ops_launch, "traffic": recorded_traffic(),
                      "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": build_ms,
                      "hbm": {"achieved_gbs": bytes_launch / (build_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
-                             "frac": bytes_launch / (build_ms / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind}},
+                             "frac": bytes_launch / (build_ms / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind},
+                     "tensor": {"achieved_tflops": mma_flops / (build_ms / 1e3) / 1e12, "peak_tflops": bf16_peak,
+                                "frac": mma_flops / (build_ms / 1e3) / 1e12 / bf16_peak,
+                                "peak_kind": "measured bf16 burst (the MMAs issued, padding included)"},
+                     "cuda_core_kernel_ms": simt_ms},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": kernels_per_config * args.steps,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -92,7 +92,7 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
         double2 *bc = (double2 *)blocks + (size_t)c * blk_stride;
         launch_err = launch_block_build(plan, Su[c].data, dtype, Sd[c].data, dtype, (int)V, (int)n_slices, precision,
                                         (double *)bt->block_partials, n_splits, chunk, bc, cap);
-        bt->n_launches += 2;
+        bt->n_launches += block_build_launches(plan, precision);
         for (int k = 0; k < n_tables && !launch_err; ++k) {
             double2 *co = (double2 *)C_out + ((size_t)c * n_tables + k) * n_slices;
             launch_err = launch_contract(bc, (int)n_slices, tv[k].n_blk, tv[k].A, tv[k].U, tv[k].ids, tv[k].w,

@@ -301,6 +301,10 @@ size_t block_partials_bytes(const BlockPlan &plan, int V, int n_slices, int prec
     return sizeof(double2) * (size_t)(*n_splits) * n_slices * plan.n_out;
 }
 
+int block_build_launches(const BlockPlan &plan, int precision) {
+    return precision == WICK_MIXED && tc_applicable(plan) ? 3 : 2;
+}
+
 int launch_block_build(const BlockPlan &plan, const void *Su, int dtype_u, const void *Sd, int dtype_d, int V,
                        int n_slices, int precision, double *partials, int n_splits, int chunk, double2 *blocks,
                        cudaStream_t stream) {

@@ -27,8 +27,9 @@
 // Layout.  The U slices are stacked along M (row i*R + r, R = 2 n_spin n_chi)
 // and cut into M tiles of 128 rows; tile t meets only the X slices
 // j <= 5 - (first slice in t), one MMA each (6 for the upper-spin tables,
-// 6+5+4+2 for the full-spin ones).  A CTA owns (range of 512 sites, slice,
-// block type, column tile of the (c2, c3) columns).  Per chunk of 8 sites:
+// 6+5+4+2 for the full-spin ones).  A CTA owns (block type, column tile of the
+// (c2, c3) columns, range of 512 sites, slice); the first two vary fastest in
+// the grid so that the CTAs reading the same rows of S run together.  Per chunk of 8 sites:
 // the CTA builds the U and X slices of chunk c into one of two operand buffers
 // from S staged two chunks ahead (three staging buffers, cp.async), meets at one
 // barrier, and thread 0 issues the chunk's MMAs and commits them to the
@@ -96,6 +97,8 @@ template <int NC_, int NS_, int NT_, int NMT_> struct Shape {
     static_assert(NC2 <= NT || NC2 % NT == 0, "column tiles");
     static_assert(TMEM_USED <= 512 && CW % 4 == 0 && CW <= 32, "TMEM / readout");
     static_assert(NXJOB % 32 == 0, "X jobs fill whole warps");
+    static_assert(NXJOB + NUJOB <= 2 * kThr, "two jobs per thread");
+    static_assert(R % 8 == 0, "U slices start on a core-matrix row group");
     static_assert(kSlices * R * NT * 8 <= 2 * (A_BYTES + B_BYTES), "combine buffer");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -116,8 +119,6 @@ __device__ __forceinline__ double exp2d(int k) {
     return __longlong_as_double((long long)(k + 1023) << 52);
 }
 
-// round to the nearest integer (ties to even) for |t| < 2^22
-__device__ __forceinline__ float rnd(float t) { return __fadd_rn(__fadd_rn(t, 12582912.f), -12582912.f); }
 
 // smallest E >= -100 with m < 2^E (m >= 0); -100 stands for "zero"
 __host__ __device__ __forceinline__ int exponent_bound(float m) {
@@ -141,32 +142,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     return d;
 }
 
-// two exact small-integer floats as a bf16x2 word (lo at the lower address)
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
-}
-
-// v = 2^E sum_i q_i 2^(-7-8i); sc = 2^-E, |v| < 2^E
-__device__ __forceinline__ void slice_u(float v, float sc, float *q) {
-    float r = __fmul_rn(__fmul_rn(v, sc), 128.f);
-#pragma unroll
-    for (int i = 0; i < kSlices; ++i) {
-        q[i] = rnd(r);
-        r = __fmul_rn(__fsub_rn(r, q[i]), 256.f);
-    }
-}
-
-// (h + l) = 2^F sum_j q_j 2^(-7-8j) + O(2^(F-48)); sc = 2^-F
-__device__ __forceinline__ void slice_x(float h, float l, float sc, float *q) {
-    float rh = __fmul_rn(__fmul_rn(h, sc), 128.f), rl = __fmul_rn(__fmul_rn(l, sc), 128.f);
-#pragma unroll
-    for (int j = 0; j < kSlicesX; ++j) {
-        q[j] = rnd(rh);
-        const df r = two_sum(__fsub_rn(rh, q[j]), rl);
-        rh = __fmul_rn(r.h, 256.f);
-        rl = __fmul_rn(r.l, 256.f);
-    }
-}
 
 __device__ __forceinline__ float2 to_f2(float2 v) { return v; }
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
@@ -230,6 +205,141 @@ tc_bounds_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ 
     }
 }
 
+// Packed slicing: lanes (re, im) of a complex value at once on the f32x2
+// instructions.  Rounding to the nearest integer adds and subtracts 1.5 * 2^23
+// (exact for |t| < 2^22); a slice, an integer of at most 128 in magnitude, is
+// exact in bf16, whose bits are the upper half of the float's.
+// U: v = 2^E sum_i q_i 2^(-7-8i); returns the re-row word (q_re, -q_im) and the
+// im-row word (q_im, q_re) of every slice as bf16x2.
+// sc = 2^(7-E), a power of two (clamped to the float range; zero rows stay zero)
+__device__ __forceinline__ void slice_u2(float2 v, float sc, uint32_t *wre, uint32_t *wim) {
+    const f2x magic = pk(12582912.f, 12582912.f), k256 = pk(256.f, 256.f);
+    f2x r = mul2(pk(v.x, v.y), pk(sc, sc));  // exact: power-of-two scale
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i) {
+        const f2x q = sub2(add2(r, magic), magic);
+        uint32_t lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(q));
+        wre[i] = __byte_perm(lo, hi, 0x7632) ^ 0x80000000u;  // (q_re, -q_im)
+        wim[i] = __byte_perm(hi, lo, 0x7632);                // (q_im, q_re)
+        r = mul2(sub2(r, q), k256);
+    }
+}
+
+// X = (h + l) lane-wise: 2^F sum_j q_j 2^(-7-8j) + O(2^(F-48)); words (q_re, q_im) per slice;
+// sc = 2^(7-F)
+__device__ __forceinline__ void slice_x2(f2x h, f2x l, float sc, uint32_t *w) {
+    const f2x magic = pk(12582912.f, 12582912.f), k256 = pk(256.f, 256.f), s2 = pk(sc, sc);
+    f2x rh = mul2(h, s2), rl = mul2(l, s2);
+#pragma unroll
+    for (int j = 0; j < kSlicesX; ++j) {
+        const f2x q = sub2(add2(rh, magic), magic);
+        uint32_t lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(q));
+        w[j] = __byte_perm(lo, hi, 0x7632);
+        // (rh - q) + rl exactly as a pair (TwoSum), then the next 8 bits up
+        const f2x d = sub2(rh, q);
+        const f2x t = add2(d, rl);
+        const f2x bb = sub2(t, d);
+        const f2x e = add2(sub2(d, sub2(t, bb)), sub2(rl, bb));
+        rh = mul2(t, k256);
+        rl = mul2(e, k256);
+    }
+}
+
+constexpr int kListMax = 4;  // terms per diquark list the tensor-core path takes
+
+// double-FP32 list sum X_{o,a}[c23] of one staged site (lanes re, im)
+__device__ __forceinline__ pdf x_value(const BlockPlan &plan, const float2 *s1, const float2 *s2, int l, int nc) {
+    pdf va, vb;
+    va.h = va.l = vb.h = vb.l = 0ull;
+    const int q0 = plan.x_off[l], len = plan.x_off[l + 1] - q0;
+#pragma unroll
+    for (int t = 0; t < kListMax; ++t) {
+        if (t < len) {
+            const float2 u = s1[plan.xt_r2[q0 + t] * nc];
+            const float2 d = s2[plan.xt_r3[q0 + t] * nc];
+            const float w = plan.xt_w[q0 + t];
+            const float ax = w * u.x, ay = w * u.y;  // exact: w is +-2^k
+            const f2x Bd = pk(d.x, d.y);
+            pacc_exact(va, pk(ax, ax), pk(-ax, -ax), Bd);
+            pacc_exact(vb, pk(ay, -ay), pk(-ay, ay), Bd);
+        }
+    }
+    return padd(va, pdf{swap2(vb.h), swap2(vb.l)});
+}
+
+// X job jb: column n, combo gc = (site, a); 6 slices into B_j[n][(site, a, part)]
+template <typename SH>
+__device__ __forceinline__ void x_job(const BlockPlan &plan, const float2 *S, int nr, int off1, int off2, int col0,
+                                      int t0, int n_a, const int *sF, __nv_bfloat16 *B, int jb) {
+    constexpr int NC = SH::NC, NT = SH::NT;
+    const int n = jb % SH::NCTA, gc = jb / SH::NCTA, site = gc / kKa, a = gc % kKa;
+    uint32_t w[kSlicesX];
+    if (a < n_a) {
+        const int c23 = col0 + n;
+        const pdf X = x_value(plan, S + site * nr * NC + off1 + c23 / NC, S + site * nr * NC + off2 + c23 % NC,
+                              plan.os_x[t0 + a], NC);
+        slice_x2(X.h, X.l, exp2i(7 - sF[n]), w);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kSlicesX; ++j) w[j] = 0u;
+    }
+    __nv_bfloat16 *dst = B + tile_off(n, gc * 2);
+#pragma unroll
+    for (int j = 0; j < kSlicesX; ++j) *reinterpret_cast<uint32_t *>(dst + j * NT * kKc) = w[j];
+}
+
+// two X jobs with independent chains (both jA, jB < NXJOB)
+template <typename SH>
+__device__ __forceinline__ void x_job2(const BlockPlan &plan, const float2 *S, int nr, int off1, int off2, int col0,
+                                       int t0, int n_a, const int *sF, __nv_bfloat16 *B, int jA, int jB) {
+    constexpr int NC = SH::NC, NT = SH::NT;
+    const int nA = jA % SH::NCTA, gA = jA / SH::NCTA, nB = jB % SH::NCTA, gB = jB / SH::NCTA;
+    const int aA = gA % kKa, aB = gB % kKa;
+    const int cA = col0 + nA, cB = col0 + nB;
+    const float2 *bA = S + (gA / kKa) * nr * NC, *bB = S + (gB / kKa) * nr * NC;
+    const int lA = plan.os_x[t0 + (aA < n_a ? aA : 0)], lB = plan.os_x[t0 + (aB < n_a ? aB : 0)];
+    pdf XA = x_value(plan, bA + off1 + cA / NC, bA + off2 + cA % NC, lA, NC);
+    pdf XB = x_value(plan, bB + off1 + cB / NC, bB + off2 + cB % NC, lB, NC);
+    if (aA >= n_a) XA.h = XA.l = 0ull;
+    if (aB >= n_a) XB.h = XB.l = 0ull;
+    uint32_t wA[kSlicesX], wB[kSlicesX];
+    slice_x2(XA.h, XA.l, exp2i(7 - sF[nA]), wA);
+    slice_x2(XB.h, XB.l, exp2i(7 - sF[nB]), wB);
+    __nv_bfloat16 *dA = B + tile_off(nA, gA * 2), *dB = B + tile_off(nB, gB * 2);
+#pragma unroll
+    for (int j = 0; j < kSlicesX; ++j) {
+        *reinterpret_cast<uint32_t *>(dA + j * NT * kKc) = wA[j];
+        *reinterpret_cast<uint32_t *>(dB + j * NT * kKc) = wB[j];
+    }
+}
+
+// U job ju: row (s, c1), combos 2 gp and 2 gp + 1; 5 slices into A[(i, part, s, c1)][(site, a, part')]
+template <typename SH>
+__device__ __forceinline__ void u_job(const BlockPlan &plan, const float2 *S, int nr, int off1, int o, int n_a,
+                                      const int *sEU, __nv_bfloat16 *A, int ju) {
+    constexpr int NC = SH::NC, NS = SH::NS, R = SH::R;
+    const int sc1 = ju % (NS * NC), gp = ju / (NS * NC);
+    const int s = sc1 / NC, c1 = sc1 % NC;
+    const float scu = exp2i(7 - sEU[c1]);
+    uint32_t wre[2][kSlices], wim[2][kSlices];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int gc = 2 * gp + h, site = gc / kKa, a = gc % kKa;
+        float2 u = make_float2(0.f, 0.f);
+        if (a < n_a) u = S[site * nr * NC + off1 + plan.os_r1[plan.os_off[o * NS + s] + a] * NC + c1];
+        slice_u2(u, scu, wre[h], wim[h]);
+    }
+    // re row: U_re X_re - U_im X_im ; im row: U_im X_re + U_re X_im
+    __nv_bfloat16 *dre = A + tile_off(s * NC + c1, gp * 4), *dim = A + tile_off(NS * NC + s * NC + c1, gp * 4);
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i) {
+        *reinterpret_cast<uint2 *>(dre + tile_off(i * R, 0)) = make_uint2(wre[0][i], wre[1][i]);
+        *reinterpret_cast<uint2 *>(dim + tile_off(i * R, 0)) = make_uint2(wim[0][i], wim[1][i]);
+    }
+}
+
 template <typename ST, typename SH>
 __global__ void __launch_bounds__(kThr, 1)
 block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ Su, const ST *__restrict__ Sd,
@@ -238,8 +348,9 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
     constexpr int NC = SH::NC, NS = SH::NS, NT = SH::NT, R = SH::R, NCTA = SH::NCTA;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int rng = blockIdx.x, slice = blockIdx.y;
-    const int o = blockIdx.z / SH::NCT, ct = blockIdx.z % SH::NCT;
+    // the CTAs of one (slice, range) are adjacent in the grid: they read the same rows of S (L2 reuse)
+    const int o = blockIdx.x / SH::NCT, ct = blockIdx.x % SH::NCT;
+    const int rng = blockIdx.y, slice = blockIdx.z;
     const int nr0 = plan.n_rows[0], nr = nr0 + plan.n_rows[1];
     const int f1 = plan.f1[o];
     const int col0 = ct * NT;
@@ -340,68 +451,15 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
             else bad = 1;
         }
         if (!bad) {
-            for (int jb = tid; jb < SH::NXJOB + SH::NUJOB; jb += kThr) {
-                if (jb < SH::NXJOB) {
-                    // X value of column n, (site, a) = combo gc: double-FP32 list sum, then 6 slices
-                    const int n = jb % NCTA, gc = jb / NCTA, site = gc / kKa, a = gc % kKa;
-                    float sx[kSlicesX], sy[kSlicesX];
-                    if (a < n_a) {
-                        const int c23 = col0 + n, i2 = c23 / NC, i3 = c23 % NC;
-                        const int l = plan.os_x[t0 + a];
-                        const float2 *s1 = S + site * nr * NC + off1 + i2;
-                        const float2 *s2 = S + site * nr * NC + off2 + i3;
-                        pdf va, vb;
-                        va.h = va.l = vb.h = vb.l = 0ull;
-                        for (int qq = plan.x_off[l]; qq < plan.x_off[l + 1]; ++qq) {
-                            const float2 u = s1[plan.xt_r2[qq] * NC];
-                            const float2 d = s2[plan.xt_r3[qq] * NC];
-                            const float w = plan.xt_w[qq];
-                            const float ax = w * u.x, ay = w * u.y;  // exact: w is +-2^k
-                            const f2x Bd = pk(d.x, d.y);
-                            pacc_exact(va, pk(ax, ax), pk(-ax, -ax), Bd);
-                            pacc_exact(vb, pk(ay, -ay), pk(-ay, ay), Bd);
-                        }
-                        const pdf X = padd(va, pdf{swap2(vb.h), swap2(vb.l)});
-                        float xh, yh, xl, yl;
-                        upk(X.h, xh, yh);
-                        upk(X.l, xl, yl);
-                        const float sc = exp2i(-sF[n]);
-                        slice_x(xh, xl, sc, sx);
-                        slice_x(yh, yl, sc, sy);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < kSlicesX; ++j) sx[j] = sy[j] = 0.f;
-                    }
-                    const int k = gc * 2;
-#pragma unroll
-                    for (int j = 0; j < kSlicesX; ++j)
-                        *reinterpret_cast<uint32_t *>(B + j * NT * kKc + tile_off(n, k)) = pack_bf16(sx[j], sy[j]);
-                } else {
-                    // two U values of row (s, c1): combos 2 gp and 2 gp + 1, 5 slices each
-                    const int ju = jb - SH::NXJOB;
-                    const int sc1 = ju % (NS * NC), gp = ju / (NS * NC);
-                    const int s = sc1 / NC, c1 = sc1 % NC;
-                    const float scu = exp2i(-sEU[c1]);
-                    float ux[2][kSlices], uy[2][kSlices];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int gc = 2 * gp + h, site = gc / kKa, a = gc % kKa;
-                        float2 u = make_float2(0.f, 0.f);
-                        if (a < n_a) u = S[site * nr * NC + off1 + plan.os_r1[plan.os_off[o * NS + s] + a] * NC + c1];
-                        slice_u(u.x, scu, ux[h]);
-                        slice_u(u.y, scu, uy[h]);
-                    }
-                    const int k = gp * 4;
-                    const int rre = s * NC + c1, rim = NS * NC + s * NC + c1;
-#pragma unroll
-                    for (int i = 0; i < kSlices; ++i) {
-                        // re row: U_re X_re - U_im X_im ; im row: U_im X_re + U_re X_im
-                        *reinterpret_cast<uint2 *>(A + tile_off(i * R + rre, k)) =
-                            make_uint2(pack_bf16(ux[0][i], -uy[0][i]), pack_bf16(ux[1][i], -uy[1][i]));
-                        *reinterpret_cast<uint2 *>(A + tile_off(i * R + rim, k)) =
-                            make_uint2(pack_bf16(uy[0][i], ux[0][i]), pack_bf16(uy[1][i], ux[1][i]));
-                    }
-                }
+            // jobs tid and tid + kThr: two X values are built side by side (independent chains)
+            const int jA = tid, jB = tid + kThr;
+            constexpr int NJ = SH::NXJOB + SH::NUJOB;
+            if (jB < SH::NXJOB) {
+                x_job2<SH>(plan, S, nr, off1, off2, col0, t0, n_a, sF, B, jA, jB);
+            } else {
+                if (jA < SH::NXJOB) x_job<SH>(plan, S, nr, off1, off2, col0, t0, n_a, sF, B, jA);
+                else if (jA < NJ) u_job<SH>(plan, S, nr, off1, o, n_a, sEU, A, jA - SH::NXJOB);
+                if (jB < NJ) u_job<SH>(plan, S, nr, off1, o, n_a, sEU, A, jB - SH::NXJOB);
             }
         }
         // staged rows of chunk c + 1 complete (this thread's copies); operands of chunk c written
@@ -539,8 +597,8 @@ __global__ void tc_reduce_kernel(const double2 *__restrict__ partials, int n_spl
 }
 
 // Which compiled shape a plan takes (0: none, 1: upper, 2: full): weights
-// +-2^k, at most 3 colour lists per block type, the same lists for every spin,
-// and at most 12 staged rows per flavour.
+// +-2^k, at most 3 colour lists per block type of at most 4 terms each, the
+// same lists for every spin, and at most 12 staged rows per flavour.
 int tc_family(const BlockPlan &plan) {
     if (!plan.pow2_w || plan.n_ops < 1 || plan.n_rows[0] + plan.n_rows[1] > kMaxRows) return 0;
     const int ns = plan.n_spin;
@@ -548,6 +606,10 @@ int tc_family(const BlockPlan &plan) {
         const int b0 = plan.os_off[o * ns];
         const int n_a = plan.os_off[o * ns + 1] - b0;
         if (n_a < 1 || n_a > kKa) return 0;
+        for (int a = 0; a < n_a; ++a) {
+            const int l = plan.os_x[b0 + a];
+            if (plan.x_off[l + 1] - plan.x_off[l] > kListMax) return 0;
+        }
         for (int s = 0; s < ns; ++s) {
             const int t0 = plan.os_off[o * ns + s];
             if (plan.os_off[o * ns + s + 1] - t0 != n_a) return 0;
@@ -563,10 +625,9 @@ int tc_family(const BlockPlan &plan) {
 template <typename SH, typename ST>
 int launch_shape(const BlockPlan &plan, const ST *Su, const ST *Sd, int V, int n_slices, int n_ranges,
                  const int *bounds, const WeightExp &ew, double2 *part, int *status, cudaStream_t stream) {
-    if (plan.n_ops * SH::NCT > 65535) return WICK_EINVAL;
     auto k = block_tc_kernel<ST, SH>;
     WICK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM));
-    dim3 grid(n_ranges, n_slices, plan.n_ops * SH::NCT);
+    dim3 grid(plan.n_ops * SH::NCT, n_ranges, n_slices);
     k<<<grid, kThr, SH::SMEM, stream>>>(plan, Su, Sd, V, n_slices, n_ranges, bounds, ew, part, status);
     return WICK_OK;
 }

@@ -56,6 +56,7 @@ size_t block_partials_bytes(const BlockPlan &plan, int V, int n_slices, int prec
                             int *chunk);
 // tensor-core update stage (blocks_tc.cu): upper-spin plans, double-FP32-exact
 bool tc_applicable(const BlockPlan &plan);
+int block_build_launches(const BlockPlan &plan, int precision);  // kernels one launch_block_build issues
 size_t tc_partials_bytes(const BlockPlan &plan, int V, int n_slices, int *n_splits, int *chunk);
 int launch_block_tc(const BlockPlan &plan, const void *Su, const void *Sd, int dtype, int V, int n_slices,
                     double *partials, int n_splits, double2 *blocks, int *status, cudaStream_t stream);

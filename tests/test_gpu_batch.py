@@ -69,7 +69,9 @@ def test_batch_equals_individual_calls():
         blocks = torch.zeros((n_cfg, n_src, T, nb), dtype=torch.complex128, device="cuda")
         C = torch.zeros((n_cfg, len(NUCLEI), n_src, T), dtype=torch.complex128, device="cuda")
         batch = wick.Batch([c[0] for c in cfgs], [c[1] for c in cfgs], tabs, terms, prec, blocks, C, L, T, n_src)
-        assert batch.launches == n_cfg * (2 + 2 * len(NUCLEI))
+        # block build: grid bounds + tensor-core kernel + reduction (mixed) or partials + reduction (FP64)
+        n_block = 3 if prec == wick.WICK_MIXED else 2
+        assert batch.launches == n_cfg * (n_block + 2 * len(NUCLEI))
         batch.run()
         batch.run()                                       # a second launch reproduces the first
         torch.cuda.synchronize()
