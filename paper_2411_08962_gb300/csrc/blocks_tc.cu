@@ -32,8 +32,8 @@
 // the grid so that the CTAs reading the same rows of S run together.  Per chunk of 8 sites:
 // the CTA builds the U and X slices of chunk c into one of two operand buffers
 // from S staged two chunks ahead (three staging buffers, cp.async), meets at one
-// barrier, and thread 0 issues the chunk's MMAs and commits them to the
-// buffer's mbarrier while the others go on to chunk c + 1.  The work of a chunk
+// barrier, and one thread of the least-loaded warp issues the chunk's MMAs and
+// commits them to the buffer's mbarrier while the others go on to chunk c + 1.  The work of a chunk
 // is a list of jobs -- one X value, or two U values -- ordered so that every
 // warp does one kind.  Every wait on an mbarrier is bounded.
 #include <cuda_bf16.h>
@@ -99,6 +99,7 @@ template <int NC_, int NS_, int NT_, int NMT_> struct Shape {
     static_assert(NXJOB % 32 == 0, "X jobs fill whole warps");
     static_assert(NXJOB + NUJOB <= 2 * kThr, "two jobs per thread");
     static_assert(R % 8 == 0, "U slices start on a core-matrix row group");
+    static_assert(NCTA % 8 == 0 || NCTA % 8 == 4, "X job map");
     static_assert(kSlices * R * NT * 8 <= 2 * (A_BYTES + B_BYTES), "combine buffer");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -269,12 +270,30 @@ __device__ __forceinline__ pdf x_value(const BlockPlan &plan, const float2 *s1, 
     return padd(va, pdf{swap2(vb.h), swap2(vb.l)});
 }
 
+// X job jb -> (column n, combo gc = (site, a)).  A warp takes 8 columns x 4
+// combos: its 32-bit stores then fall on 8 rows x 4 words of a core matrix,
+// 32 different banks (the leftover 4 columns of a 36-column tile: 4 x 8, two
+// ways).  Consecutive columns of one combo would meet only 8 banks.
+template <typename SH> __device__ __forceinline__ void x_map(int jb, int &n, int &gc) {
+    constexpr int NG = SH::NCTA / 8, GW = kNX * kKa / 4;
+    const int w = jb >> 5, lane = jb & 31;
+    if (w < NG * GW) {
+        n = 8 * (w % NG) + (lane & 7);
+        gc = 4 * (w / NG) + (lane >> 3);
+    } else {
+        n = 8 * NG + (lane & 3);
+        gc = 8 * (w - NG * GW) + (lane >> 2);
+    }
+}
+
 // X job jb: column n, combo gc = (site, a); 6 slices into B_j[n][(site, a, part)]
 template <typename SH>
 __device__ __forceinline__ void x_job(const BlockPlan &plan, const float2 *S, int nr, int off1, int off2, int col0,
                                       int t0, int n_a, const int *sF, __nv_bfloat16 *B, int jb) {
     constexpr int NC = SH::NC, NT = SH::NT;
-    const int n = jb % SH::NCTA, gc = jb / SH::NCTA, site = gc / kKa, a = gc % kKa;
+    int n, gc;
+    x_map<SH>(jb, n, gc);
+    const int site = gc / kKa, a = gc % kKa;
     uint32_t w[kSlicesX];
     if (a < n_a) {
         const int c23 = col0 + n;
@@ -295,7 +314,9 @@ template <typename SH>
 __device__ __forceinline__ void x_job2(const BlockPlan &plan, const float2 *S, int nr, int off1, int off2, int col0,
                                        int t0, int n_a, const int *sF, __nv_bfloat16 *B, int jA, int jB) {
     constexpr int NC = SH::NC, NT = SH::NT;
-    const int nA = jA % SH::NCTA, gA = jA / SH::NCTA, nB = jB % SH::NCTA, gB = jB / SH::NCTA;
+    int nA, gA, nB, gB;
+    x_map<SH>(jA, nA, gA);
+    x_map<SH>(jB, nB, gB);
     const int aA = gA % kKa, aB = gB % kKa;
     const int cA = col0 + nA, cB = col0 + nB;
     const float2 *bA = S + (gA / kKa) * nr * NC, *bB = S + (gB / kKa) * nr * NC;
@@ -472,7 +493,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const bool fresh = c % kChunksPerRound == 0;
-        if (tid == 0) {
+        if (tid == kThr - 1) {  // the last warp has the fewest jobs
             const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
 #pragma unroll
             for (int ks = 0; ks < kKc / 16; ++ks)
