@@ -293,3 +293,108 @@ def triton_cluster(J: int = 0):
     G = integer_matrix(cg5())
     terms = [((N_MINUS, P_PLUS, N_PLUS), (a, b, J), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b]]
     return _cluster(pm_ops(), terms, 1.0)
+
+
+# ----------------------------------------------------------------------------
+# Point-sink operators of the determinant algorithm (Sec. III.C, "Implementation
+# of the proposed algorithm": Eqs. NP_op, He3_op, He4_op).  Each is a weight
+# table over flavour-grouped quark index tuples (u quarks first, then d, each
+# in nucleon-slot order, the Grassmann sign of that regrouping folded into the
+# weight), the same form for sink and source.  Pinned by the operator term
+# counts of the paper's determinant table (2H 356, 3He 1026 per spin
+# component, 4He 2716), which count the flavour-ordered index lists with a
+# non-zero antisymmetrised coefficient.
+#
+# Readings: the 2H and 4He operators are built from the nucleons of Eqs.
+# 1000/1001 (all four spins, no projection; 4He with the spin and isospin
+# wave functions chi, chibar, eta, etabar of Eq. He4_op).  The projected
+# nucleons p+-, n+- of the 3He operator carry C gamma5 P with the paper's
+# P+- = (1 -+ gamma4)/2 of this Dirac-Pauli basis (the paper's gamma4 has the
+# opposite sign): with (1 +- gamma4)/2 the 3He count would be 744, not 1026;
+# the 2H and 4He counts are the same under either sign.
+# ----------------------------------------------------------------------------
+
+def plain_nucleons():
+    """[proton, neutron] of Eqs. 1000/1001 with all four spins."""
+    tab = nucleon_table(cg5(), ALL_SPINS, ALL_SPINS)
+    return [(U, tab), (D, tab)]
+
+
+def paper_projector(sign: int) -> np.ndarray:
+    """The paper's P_pm in this basis: (1 -+ gamma4)/2 (see the reading above)."""
+    return parity_projector(-sign)
+
+
+def grouped_operator(ops, terms):
+    """(table, flavours) of sum_t coef_t prod_k N^{type_k}_{spin_k}, flavour-grouped."""
+    return _grouped_source(ops, terms)
+
+
+def paper_deuteron():
+    """O_2H = n^T (C gamma5 P+) p (Eq. NP_op), nucleon spins contracted."""
+    G = integer_matrix(cg5() @ paper_projector(+1))
+    terms = [((NEUTRON, PROTON), (a, b), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b]]
+    return grouped_operator(plain_nucleons(), terms)
+
+
+def paper_he3(J: int = 0):
+    """O_3He^J = p_-^T (C gamma5) n_+ p_+^J (Eq. He3_op)."""
+    cgp = cg5() @ paper_projector(+1)
+    cgm = cg5() @ paper_projector(-1)
+    ops = [(U, nucleon_table(cgm, ALL_SPINS, ALL_SPINS)),   # p-
+           (D, nucleon_table(cgp, ALL_SPINS, ALL_SPINS)),   # n+
+           (U, nucleon_table(cgp, ALL_SPINS, ALL_SPINS))]   # p+
+    G = integer_matrix(cg5())
+    terms = [((0, 1, 2), (a, b, J), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b]]
+    return grouped_operator(ops, terms)
+
+
+def paper_he4():
+    """O_4He = (chibar eta - chi etabar)/sqrt2 (Eq. He4_op) with the plain p, n:
+    integer weights chibar_s eta_i - chi_s etabar_i (overall factor 1/(2 sqrt24)
+    per operator, 1/96 for sink x source)."""
+    pats = [(0, 1, 0, 1), (1, 0, 1, 0), (0, 1, 1, 0), (1, 0, 0, 1), (0, 0, 1, 1), (1, 1, 0, 0)]
+    c = [1, 1, -1, -1, 0, 0]
+    cb = [1, 1, 1, 1, -2, -2]
+    iso = [tuple(PROTON if x == 0 else NEUTRON for x in p) for p in pats]
+    terms = [(iso[b], s, cb[a] * c[b] - c[a] * cb[b]) for a, s in enumerate(pats) for b in range(6)
+             if cb[a] * c[b] - c[a] * cb[b]]
+    return grouped_operator(plain_nucleons(), terms)
+
+
+def paper_point_nucleus(name: str):
+    """Plane-wave description (for the block oracle) of the same operators:
+    dict as `nucleus` with the grouped source and sink = the nucleon products."""
+    if name == "deuteron":
+        G = integer_matrix(cg5() @ paper_projector(+1))
+        ops = plain_nucleons()
+        terms = [((NEUTRON, PROTON), (a, b), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b]]
+    elif name == "he3":
+        cgp = cg5() @ paper_projector(+1)
+        cgm = cg5() @ paper_projector(-1)
+        ops = [(U, nucleon_table(cgm, ALL_SPINS, ALL_SPINS)), (D, nucleon_table(cgp, ALL_SPINS, ALL_SPINS)),
+               (U, nucleon_table(cgp, ALL_SPINS, ALL_SPINS))]
+        G = integer_matrix(cg5())
+        terms = [((0, 1, 2), (a, b, 0), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b]]
+    else:
+        raise ValueError(name)
+    return _cluster(ops, terms, 1.0)
+
+
+def antisymmetrised(table, n_u: int):
+    """C^[M] over flavour-ordered index lists M = (sorted u indices, sorted d indices):
+    sum over the orderings of each flavour's indices with the sign of the ordering;
+    zero entries dropped (Sec. III.C, method A)."""
+    acc = {}
+    for chi, w in table:
+        u, d = list(chi[:n_u]), list(chi[n_u:])
+        if len(set(u)) < len(u) or len(set(d)) < len(d):
+            continue
+        key = (tuple(sorted(u)), tuple(sorted(d)))
+        acc[key] = acc.get(key, 0) + w * _perm_sign(u) * _perm_sign(d)
+    return {k: v for k, v in acc.items() if v != 0}
+
+
+def _perm_sign(x) -> int:
+    inv = sum(1 for i in range(len(x)) for j in range(i + 1, len(x)) if x[i] > x[j])
+    return -1 if inv % 2 else 1

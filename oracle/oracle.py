@@ -22,6 +22,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "wick_oracle.c")
+SRC_DET = os.path.join(HERE, "det_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -29,8 +30,9 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the C reference (gcc -O2 -fopenmp); returns the .so path."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", "-o", LIB + ".tmp", SRC, "-lm"]
+    newest = max(os.path.getmtime(SRC), os.path.getmtime(SRC_DET))
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", "-o", LIB + ".tmp", SRC, SRC_DET, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(LIB + ".tmp", LIB)
     return LIB
@@ -65,7 +67,11 @@ def lib():
             L.oracle_modp_table.argtypes = [P, C.c_uint64, C.c_int64, u16p, i64p, u64p]
             i8p = C.POINTER(C.c_int8)
             L.oracle_source_multisets.argtypes = [P, C.c_int64, i8p, i8p, i64p, i64p]
-            for f in ("oracle_blocks", "oracle_raw_correlator", "oracle_table_correlator", "oracle_dedup",
+            L.oracle_point_correlator.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, i8p, i8p,
+                                                  C.c_int64, i8p, i8p, C.c_int64, i64p, i64p, dp, dp]
+            L.oracle_det_modp.argtypes = [u64p, C.c_int, C.c_int64, i8p, i8p, u64p]
+            for f in ("oracle_point_correlator", "oracle_det_modp",
+                      "oracle_blocks", "oracle_raw_correlator", "oracle_table_correlator", "oracle_dedup",
                       "oracle_modp_raw", "oracle_modp_table", "oracle_num_threads", "oracle_source_multisets"):
                 getattr(L, f).restype = C.c_int
             _lib = L
