@@ -300,6 +300,64 @@ void wick_batch_free(wick_batch *batch);
 int wick_synth_propagator(uint64_t seed, int flavour, int src, int L, int T, int dtype, void *out,
                           wick_stream_t stream);
 
+/*
+ * Point-sink correlators by the determinant algorithm (Sec. III.A, Eq. 2.9;
+ * Sec. III.C, improved method B; App. A, Eqs. a1-a4).  With every quark of
+ * the sink operator at the same site x,
+ *   G(t) = scale * sum_x sum_{M, M'} C[M] C'[M'] det M^u(x; M_u, M'_u) det M^d(x; M_d, M'_d),
+ *   M^f_ij = S_f(x, t)(chi_i, chi'_j)   (row: sink index, column: source index),
+ * with C, C' antisymmetrised within each flavour (M, M' are flavour-ordered
+ * index lists), evaluated as
+ *   G(t) = scale * sum_x sum_{(k, l)} Theta(k, l) det M^u(x; zeta_u[k]) det M^d(x; zeta_d[l])
+ * over the minimal sets of distinct determinants (Eq. a1).
+ *
+ * wick_quark_operator: an operator sum_terms w * u(chi_1)..u(chi_nu) d(chi_nu+1)..d(chi_n)
+ *   n_u, n_d   quarks of each flavour (0..6 each, at least one quark)
+ *   chi        n_terms x (n_u + n_d) indices 4*colour + spin (0..11), u quarks first
+ *              (any regrouping of the fields into this order has its sign in w)
+ *   w          integer weights, |w| < 2^31
+ * Host memory, read during the call.
+ */
+typedef struct {
+    int n_u, n_d;
+    int n_terms;
+    const int8_t *chi;
+    const int64_t *w;
+} wick_quark_operator;
+
+/*
+ * wick_det_reduce: antisymmetrises sink and source within each flavour,
+ * forms the determinant pairs of every (M, M'), finds the distinct
+ * determinants by evaluating each candidate mod p = 2^61 - 1 at `trials`
+ * random integer matrices derived from `seed` (the randomised identity
+ * testing of Sec. III.B / App. C: equal value vectors are one determinant,
+ * up to a sign made canonical; all-zero vectors drop their terms), and
+ * merges the integer weights into Theta.  Runs on the current device;
+ * *out is library-owned (wick_det_free).  Synchronous.
+ * Errors: WICK_EINVAL (sizes, indices, weights), WICK_ENOMEM, WICK_ECUDA,
+ * WICK_EOVERFLOW (a Theta weight reaches 2^53).
+ */
+typedef struct wick_det_plan wick_det_plan;
+int wick_det_reduce(const wick_quark_operator *sink, const wick_quark_operator *source, uint64_t seed, int trials,
+                    wick_det_plan **out);
+/* out[6]: sink terms, source terms (antisymmetrised), |zeta_u|, |zeta_d|, Theta non-zeros, n_u * 8 + n_d */
+int wick_det_stats(const wick_det_plan *plan, int64_t *out);
+/* Copies Theta (k, l, weight) and the minimal sets to host arrays sized from
+ * wick_det_stats (any pointer may be NULL): zu rows/cols [|zeta_u|][n_u],
+ * zd rows/cols [|zeta_d|][n_d]. */
+int wick_det_copy(const wick_det_plan *plan, int32_t *k, int32_t *l, int64_t *w, int8_t *zu_rows, int8_t *zu_cols,
+                  int8_t *zd_rows, int8_t *zd_cols);
+/*
+ * wick_det_contract: G[src][t] for propagators Su, Sd (device, caller-owned,
+ * complex64 or complex128; arithmetic in FP64) into C_out (device
+ * complex128 [n_src][T]).  Asynchronous on `stream`; scratch from the
+ * library's per-device workspace.  precision: WICK_FP64.
+ * Errors: WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA.
+ */
+int wick_det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_det_plan *plan, double scale,
+                      int precision, void *C_out, wick_stream_t stream);
+void wick_det_free(wick_det_plan *plan);
+
 /* Synchronises `stream` and returns (then clears) the device status word. */
 int wick_status(wick_stream_t stream);
 

@@ -35,8 +35,8 @@ namespace wick {
 // ---------------------------------------------------------------------------
 namespace {
 struct DevState {
-    void *ws[2] = {nullptr, nullptr};
-    size_t ws_bytes[2] = {0, 0};
+    void *ws[3] = {nullptr, nullptr, nullptr};   // block partials, contraction partials, determinant scratch
+    size_t ws_bytes[3] = {0, 0, 0};
     int *status = nullptr;
 };
 std::mutex g_mu;

@@ -1,0 +1,617 @@
+// Point-sink correlators by the determinant algorithm (Sec. III.A, Eq. 2.9;
+// Sec. III.C, improved method B; App. A, Eqs. a1-a4).
+//
+// Reduction (host + device, once per operator pair):
+//   1. antisymmetrise sink and source within each flavour: every index tuple
+//      is sorted per flavour with the sign of the sorting, tuples with a
+//      repeated index of one flavour vanish, equal tuples are merged (the
+//      flavour-ordered lists M, M' of method A);
+//   2. the candidate determinants are the pairs (sink index set, source index
+//      set) of each flavour -- every distinct sink set meets every distinct
+//      source set;
+//   3. identity testing (Sec. III.B, App. C): each candidate is evaluated
+//      mod p = 2^61 - 1 at `trials` random integer 12 x 12 matrices on the
+//      device; equal value vectors (up to a canonical sign) are one
+//      determinant of the minimal set zeta_f, all-zero vectors vanish;
+//   4. Theta(k, l) = sum over (M, M') of C[M] C'[M'] times the signs of the
+//      two determinants relative to their representatives (exact int64,
+//      merged by sorting).
+// Evaluation (device, FP64): a persistent grid walks (slice, chunk of sites);
+// per site the CTA stages S_u(x), S_d(x) (12 x 12 complex each), computes
+// every determinant of zeta_u and zeta_d into its scratch (one thread per
+// determinant: explicit forms up to 3 x 3, LU with partial pivoting above),
+// and sums Theta(k, l) U_k D_l; chunk partials are reduced in a fixed order.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+struct wick_det_plan {
+    int n_u = 0, n_d = 0, device = 0;
+    int64_t n_snk = 0, n_src = 0, n_zu = 0, n_zd = 0, n_theta = 0;
+    int8_t *d_zu = nullptr, *d_zd = nullptr;  // [n][2][n_f]: rows (sink indices) then columns (source indices)
+    int32_t *d_k = nullptr, *d_l = nullptr;
+    double *d_w = nullptr;
+    std::vector<int8_t> zu, zd;
+    std::vector<int32_t> k, l;
+    std::vector<int64_t> w;
+};
+
+namespace wick {
+
+namespace {
+
+constexpr int kDetThreads = 256;
+constexpr int kDetChunk = 32;  // sites per work item
+constexpr uint64_t kP61 = (1ull << 61) - 1;
+
+// ---------------------------------------------------------------------------
+// mod-p determinants (identity testing)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t mulmod(uint64_t a, uint64_t b) {
+    const uint64_t lo = a * b, hi = __umul64hi(a, b);
+    uint64_t s = (lo & kP61) + ((lo >> 61) | (hi << 3));  // a, b < p: both parts < 2^61
+    s = (s & kP61) + (s >> 61);
+    return s >= kP61 ? s - kP61 : s;
+}
+__device__ __forceinline__ uint64_t submod(uint64_t a, uint64_t b) { return a >= b ? a - b : a + kP61 - b; }
+__device__ uint64_t powmod(uint64_t a, uint64_t e) {
+    uint64_t r = 1;
+    while (e) {
+        if (e & 1) r = mulmod(r, a);
+        a = mulmod(a, a);
+        e >>= 1;
+    }
+    return r;
+}
+
+// random 12 x 12 matrix entry e of (seed, trial, flavour), uniform in [0, p) up to a 2^-61 bias
+__device__ __forceinline__ uint64_t rand_entry(uint64_t seed, int trial, int flavour, int e) {
+    const uint64_t key = mix64(seed ^ (0xA5A5000000000000ull + 16ull * (uint64_t)trial + (uint64_t)flavour));
+    return mix64(key + (uint64_t)(e + 1) * 0x9E3779B97F4A7C15ull) % kP61;
+}
+
+// det mod p of M[rows][cols] for every (sink set i, source set j): Gaussian elimination mod p
+__global__ void det_modp_kernel(const int8_t *__restrict__ snk_sets, int n_snk_sets, const int8_t *__restrict__ src_sets,
+                                int n_src_sets, int n, uint64_t seed, int trials, int flavour,
+                                uint64_t *__restrict__ out) {
+    __shared__ uint64_t M[144];
+    const int64_t total = (int64_t)n_snk_sets * n_src_sets;
+    for (int tr = 0; tr < trials; ++tr) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 144; e += blockDim.x) M[e] = rand_entry(seed, tr, flavour, e);
+        __syncthreads();
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
+            const int8_t *r = snk_sets + (c / n_src_sets) * n, *q = src_sets + (c % n_src_sets) * n;
+            uint64_t a[6][6];
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) a[i][j] = M[r[i] * 12 + q[j]];
+            uint64_t det = 1;
+            for (int col = 0; col < n && det; ++col) {
+                int p = col;
+                while (p < n && a[p][col] == 0) ++p;
+                if (p == n) {
+                    det = 0;
+                    break;
+                }
+                if (p != col) {
+                    for (int j = 0; j < n; ++j) {
+                        const uint64_t t = a[p][j];
+                        a[p][j] = a[col][j];
+                        a[col][j] = t;
+                    }
+                    det = kP61 - det;
+                }
+                det = mulmod(det, a[col][col]);
+                const uint64_t inv = powmod(a[col][col], kP61 - 2);
+                for (int i = col + 1; i < n; ++i) {
+                    const uint64_t f = mulmod(a[i][col], inv);
+                    for (int j = col; j < n; ++j) a[i][j] = submod(a[i][j], mulmod(f, a[col][j]));
+                }
+            }
+            out[c * trials + tr] = det % kP61;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 determinants of submatrices of a 12 x 12 complex matrix in shared memory
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+template <int N>
+__device__ __forceinline__ double2 det_lu(const double2 *S, const int8_t *rc) {
+    double2 a[N][N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) a[i][j] = S[rc[i] * 12 + rc[N + j]];
+    double2 det = make_double2(1.0, 0.0);
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        // partial pivoting on |re| + |im|, rows swapped by selects (no dynamic register indexing)
+        int p = c;
+        double best = fabs(a[c][c].x) + fabs(a[c][c].y);
+#pragma unroll
+        for (int r = c + 1; r < N; ++r) {
+            const double m = fabs(a[r][c].x) + fabs(a[r][c].y);
+            if (m > best) {
+                best = m;
+                p = r;
+            }
+        }
+        if (best == 0.0) return make_double2(0.0, 0.0);
+        if (p != c) det = make_double2(-det.x, -det.y);
+#pragma unroll
+        for (int r = c + 1; r < N; ++r) {
+            if (r == p) {
+#pragma unroll
+                for (int j = c; j < N; ++j) {
+                    const double2 t = a[r][j];
+                    a[r][j] = a[c][j];
+                    a[c][j] = t;
+                }
+            }
+        }
+        det = cmul(det, a[c][c]);
+        const double2 d = a[c][c];
+        const double inv_n = 1.0 / (d.x * d.x + d.y * d.y);
+        const double2 inv = make_double2(d.x * inv_n, -d.y * inv_n);
+#pragma unroll
+        for (int r = c + 1; r < N; ++r) {
+            const double2 f = cmul(a[r][c], inv);
+#pragma unroll
+            for (int j = c + 1; j < N; ++j) a[r][j] = csub(a[r][j], cmul(f, a[c][j]));
+        }
+    }
+    return det;
+}
+
+// rc: n row indices then n column indices
+__device__ __forceinline__ double2 det_small(const double2 *S, const int8_t *rc, int n) {
+    switch (n) {
+    case 1:
+        return S[rc[0] * 12 + rc[1]];
+    case 2: {
+        const double2 a = S[rc[0] * 12 + rc[2]], b = S[rc[0] * 12 + rc[3]];
+        const double2 c = S[rc[1] * 12 + rc[2]], d = S[rc[1] * 12 + rc[3]];
+        return csub(cmul(a, d), cmul(b, c));
+    }
+    case 3: {
+        const double2 *r0 = S + rc[0] * 12, *r1 = S + rc[1] * 12, *r2 = S + rc[2] * 12;
+        const int c0 = rc[3], c1 = rc[4], c2 = rc[5];
+        const double2 m0 = csub(cmul(r1[c1], r2[c2]), cmul(r1[c2], r2[c1]));
+        const double2 m1 = csub(cmul(r1[c0], r2[c2]), cmul(r1[c2], r2[c0]));
+        const double2 m2 = csub(cmul(r1[c0], r2[c1]), cmul(r1[c1], r2[c0]));
+        return cadd(csub(cmul(r0[c0], m0), cmul(r0[c1], m1)), cmul(r0[c2], m2));
+    }
+    case 4:
+        return det_lu<4>(S, rc);
+    case 5:
+        return det_lu<5>(S, rc);
+    case 6:
+        return det_lu<6>(S, rc);
+    default:
+        return make_double2(1.0, 0.0);  // no quark of this flavour
+    }
+}
+
+struct DetArgs {
+    int n_u, n_d;
+    int64_t n_zu, n_zd, n_theta;
+    const int8_t *zu, *zd;
+    const int32_t *k, *l;
+    const double *w;
+};
+
+template <typename ST>
+__global__ void __launch_bounds__(kDetThreads)
+det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict__ Sd, int V, int n_slices,
+                int n_chunks, double2 *__restrict__ scratch, double2 *__restrict__ partials) {
+    __shared__ double2 sS[2][144];
+    __shared__ double2 red[kDetThreads];
+    double2 *U = scratch + (size_t)blockIdx.x * (a.n_zu + a.n_zd);
+    double2 *D = U + a.n_zu;
+    const int tid = threadIdx.x;
+    const int64_t items = (int64_t)n_slices * n_chunks;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int slice = (int)(it / n_chunks), chunk = (int)(it % n_chunks);
+        const int x0 = chunk * kDetChunk, x1 = min(V, x0 + kDetChunk);
+        double2 acc = make_double2(0.0, 0.0);
+        for (int x = x0; x < x1; ++x) {
+            __syncthreads();  // the previous site's determinants are consumed
+            for (int e = tid; e < 288; e += kDetThreads) {
+                const ST *src = (e < 144 ? Su : Sd) + ((size_t)slice * V + x) * 144 + (e % 144);
+                const ST v = *src;
+                sS[e / 144][e % 144] = make_double2((double)v.x, (double)v.y);
+            }
+            __syncthreads();
+            for (int64_t q = tid; q < a.n_zu; q += kDetThreads) U[q] = det_small(sS[0], a.zu + q * 2 * a.n_u, a.n_u);
+            for (int64_t q = tid; q < a.n_zd; q += kDetThreads) D[q] = det_small(sS[1], a.zd + q * 2 * a.n_d, a.n_d);
+            __syncthreads();
+            for (int64_t e = tid; e < a.n_theta; e += kDetThreads) {
+                const double2 p = cmul(U[a.k[e]], D[a.l[e]]);
+                acc.x = fma(a.w[e], p.x, acc.x);
+                acc.y = fma(a.w[e], p.y, acc.y);
+            }
+        }
+        // fixed-order block reduction of the chunk's sum
+        red[tid] = acc;
+        __syncthreads();
+        for (int s = kDetThreads / 2; s > 0; s >>= 1) {
+            if (tid < s) red[tid] = cadd(red[tid], red[tid + s]);
+            __syncthreads();
+        }
+        if (tid == 0) partials[(size_t)slice * n_chunks + chunk] = red[0];
+    }
+}
+
+__global__ void det_finish_kernel(const double2 *__restrict__ partials, int n_slices, int n_chunks, double scale,
+                                  double2 *__restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_slices) return;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = 0; c < n_chunks; ++c) acc = cadd(acc, partials[(size_t)s * n_chunks + c]);
+    out[s] = make_double2(scale * acc.x, scale * acc.y);
+}
+
+// ---------------------------------------------------------------------------
+// host: antisymmetrisation and the minimal sets
+// ---------------------------------------------------------------------------
+using Key = std::vector<int8_t>;
+
+struct Antisym {
+    std::map<std::pair<Key, Key>, int64_t> terms;  // (sorted u set, sorted d set) -> weight
+};
+
+int antisymmetrise(const wick_quark_operator *op, Antisym &out) {
+    if (!op || op->n_u < 0 || op->n_d < 0 || op->n_u > 6 || op->n_d > 6 || op->n_u + op->n_d < 1 ||
+        op->n_terms < 0 || (op->n_terms > 0 && (!op->chi || !op->w)))
+        return WICK_EINVAL;
+    const int n = op->n_u + op->n_d;
+    for (int t = 0; t < op->n_terms; ++t) {
+        const int8_t *c = op->chi + (size_t)t * n;
+        const int64_t w = op->w[t];
+        if (w >= (1ll << 31) || w <= -(1ll << 31)) return WICK_EINVAL;
+        Key u(c, c + op->n_u), d(c + op->n_u, c + n);
+        int sign = 1;
+        bool zero = false;
+        for (Key *f : {&u, &d}) {
+            for (int8_t v : *f)
+                if (v < 0 || v > 11) return WICK_EINVAL;
+            // insertion sort counting transpositions; a repeated index makes the term vanish
+            for (size_t i = 1; i < f->size(); ++i)
+                for (size_t j = i; j > 0 && (*f)[j - 1] >= (*f)[j]; --j) {
+                    if ((*f)[j - 1] == (*f)[j]) zero = true;
+                    std::swap((*f)[j - 1], (*f)[j]);
+                    sign = -sign;
+                }
+        }
+        if (zero || w == 0) continue;
+        out.terms[{u, d}] += sign * w;
+    }
+    for (auto it = out.terms.begin(); it != out.terms.end();)
+        it = it->second == 0 ? out.terms.erase(it) : std::next(it);
+    return WICK_OK;
+}
+
+// distinct index sets of one flavour, in increasing order, and the set id of every term
+void set_ids(const Antisym &A, bool d_part, std::vector<Key> &sets, std::vector<int> &ids) {
+    std::map<Key, int> idx;
+    for (auto &kv : A.terms) idx.emplace(d_part ? kv.first.second : kv.first.first, 0);
+    int i = 0;
+    for (auto &kv : idx) {
+        kv.second = i++;
+        sets.push_back(kv.first);
+    }
+    for (auto &kv : A.terms) ids.push_back(idx[d_part ? kv.first.second : kv.first.first]);
+}
+
+struct Classes {
+    std::vector<int> cls;    // per candidate (sink set * n_src_sets + source set): class or -1
+    std::vector<int> sign;   // relative to the class representative
+    std::vector<int64_t> rep;  // candidate index of each class's representative
+};
+
+int classify(const std::vector<Key> &snk, const std::vector<Key> &src, int n, uint64_t seed, int trials, int flavour,
+             Classes &out) {
+    const int64_t total = (int64_t)snk.size() * (int64_t)src.size();
+    out.cls.assign(total, -1);
+    out.sign.assign(total, 0);
+    if (total == 0) return WICK_OK;
+    if (n == 0) {  // no quark of this flavour: one determinant, equal to 1
+        for (int64_t c = 0; c < total; ++c) {
+            out.cls[c] = 0;
+            out.sign[c] = 1;
+        }
+        out.rep.push_back(0);
+        return WICK_OK;
+    }
+    std::vector<int8_t> hs(snk.size() * n), hq(src.size() * n);
+    for (size_t i = 0; i < snk.size(); ++i) std::copy(snk[i].begin(), snk[i].end(), hs.begin() + i * n);
+    for (size_t i = 0; i < src.size(); ++i) std::copy(src[i].begin(), src[i].end(), hq.begin() + i * n);
+    int8_t *ds = nullptr, *dq = nullptr;
+    uint64_t *dv = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(ds);
+        cudaFree(dq);
+        cudaFree(dv);
+    };
+    if (cudaMalloc(&ds, hs.size()) != cudaSuccess || cudaMalloc(&dq, hq.size()) != cudaSuccess ||
+        cudaMalloc(&dv, sizeof(uint64_t) * total * trials) != cudaSuccess) {
+        cleanup();
+        (void)cudaGetLastError();
+        return WICK_ENOMEM;
+    }
+    std::vector<uint64_t> hv((size_t)total * trials);
+    int err = WICK_OK;
+    if (cudaMemcpy(ds, hs.data(), hs.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dq, hq.data(), hq.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        err = WICK_ECUDA;
+    if (!err) {
+        const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+        det_modp_kernel<<<blocks, 256>>>(ds, (int)snk.size(), dq, (int)src.size(), n, seed, trials, flavour, dv);
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(hv.data(), dv, sizeof(uint64_t) * hv.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+            err = WICK_ECUDA;
+    }
+    cleanup();
+    if (err) return err;
+    struct VecHash {
+        size_t operator()(const std::vector<uint64_t> &v) const {
+            uint64_t h = 0x9E3779B97F4A7C15ull;
+            for (uint64_t x : v) h = mix64(h ^ x);
+            return (size_t)h;
+        }
+    };
+    std::unordered_map<std::vector<uint64_t>, int, VecHash> map;
+    std::vector<int> rep_sign;
+    std::vector<uint64_t> key(trials);
+    for (int64_t c = 0; c < total; ++c) {
+        bool nz = false;
+        int s = 1;
+        uint64_t first = 0;
+        for (int t = 0; t < trials; ++t) {
+            key[t] = hv[c * trials + t];
+            if (!nz && key[t]) {
+                nz = true;
+                first = key[t];
+            }
+        }
+        if (!nz) continue;  // identically zero determinant
+        if (first > (kP61 - 1) / 2) {
+            s = -1;
+            for (auto &v : key) v = v ? kP61 - v : 0;
+        }
+        auto it = map.find(key);
+        int cl;
+        if (it == map.end()) {
+            cl = (int)out.rep.size();
+            map.emplace(key, cl);
+            out.rep.push_back(c);
+            rep_sign.push_back(s);
+        } else {
+            cl = it->second;
+        }
+        out.cls[c] = cl;
+        out.sign[c] = s * rep_sign[cl];
+    }
+    return WICK_OK;
+}
+
+void free_plan(wick_det_plan *p) {
+    if (!p) return;
+    cudaFree(p->d_zu);
+    cudaFree(p->d_zd);
+    cudaFree(p->d_k);
+    cudaFree(p->d_l);
+    cudaFree(p->d_w);
+    delete p;
+}
+
+template <typename T> int upload(T **dst, const std::vector<T> &src) {
+    const size_t bytes = sizeof(T) * std::max<size_t>(src.size(), 1);
+    if (cudaMalloc(dst, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *dst = nullptr;
+        return WICK_ENOMEM;
+    }
+    if (!src.empty() && cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return WICK_ECUDA;
+    return WICK_OK;
+}
+
+}  // namespace
+
+}  // namespace wick
+
+using namespace wick;
+
+extern "C" {
+
+int wick_det_reduce(const wick_quark_operator *sink, const wick_quark_operator *source, uint64_t seed, int trials,
+                    wick_det_plan **out) {
+    if (!out || !sink || !source || trials < 1 || trials > 8) return WICK_EINVAL;
+    *out = nullptr;
+    if (sink->n_u != source->n_u || sink->n_d != source->n_d) return WICK_EINVAL;
+    Antisym As, Aq;
+    int err = antisymmetrise(sink, As);
+    if (!err) err = antisymmetrise(source, Aq);
+    if (err) return err;
+    const int nu = sink->n_u, nd = sink->n_d;
+    std::vector<Key> su, sd, qu, qd;
+    std::vector<int> isu, isd, iqu, iqd;
+    set_ids(As, false, su, isu);
+    set_ids(As, true, sd, isd);
+    set_ids(Aq, false, qu, iqu);
+    set_ids(Aq, true, qd, iqd);
+    if ((int64_t)su.size() * (int64_t)qu.size() > (1ll << 30) || (int64_t)sd.size() * (int64_t)qd.size() > (1ll << 30))
+        return WICK_EINVAL;
+    Classes cu, cd;
+    err = classify(su, qu, nu, seed, trials, 0, cu);
+    if (!err) err = classify(sd, qd, nd, seed, trials, 1, cd);
+    if (err) return err;
+    // Theta: every (M, M') -> (class_u, class_d), merged by sorting (key, weight)
+    std::vector<int64_t> ws, wq;
+    for (auto &kv : As.terms) ws.push_back(kv.second);
+    for (auto &kv : Aq.terms) wq.push_back(kv.second);
+    const int64_t n_cd = (int64_t)cd.rep.size();
+    std::vector<std::pair<int64_t, int64_t>> acc;
+    acc.reserve(ws.size() * wq.size());
+    for (size_t a = 0; a < ws.size(); ++a)
+        for (size_t b = 0; b < wq.size(); ++b) {
+            const int64_t ca = (int64_t)isu[a] * (int64_t)qu.size() + iqu[b];
+            const int64_t cb = (int64_t)isd[a] * (int64_t)qd.size() + iqd[b];
+            const int ku = cu.cls[ca], kd = cd.cls[cb];
+            if (ku < 0 || kd < 0) continue;
+            acc.push_back({(int64_t)ku * n_cd + kd, ws[a] * wq[b] * cu.sign[ca] * cd.sign[cb]});
+        }
+    std::sort(acc.begin(), acc.end(), [](const std::pair<int64_t, int64_t> &x, const std::pair<int64_t, int64_t> &y) {
+        return x.first < y.first;
+    });
+    wick_det_plan *p = new (std::nothrow) wick_det_plan();
+    if (!p) return WICK_ENOMEM;
+    p->n_u = nu;
+    p->n_d = nd;
+    p->n_snk = (int64_t)ws.size();
+    p->n_src = (int64_t)wq.size();
+    cudaGetDevice(&p->device);
+    for (size_t i = 0; i < acc.size();) {
+        size_t j = i;
+        int64_t sum = 0;
+        for (; j < acc.size() && acc[j].first == acc[i].first; ++j) sum += acc[j].second;
+        if (sum != 0) {
+            if (sum >= (1ll << 53) || sum <= -(1ll << 53)) {
+                free_plan(p);
+                return WICK_EOVERFLOW;
+            }
+            p->k.push_back((int32_t)(acc[i].first / n_cd));
+            p->l.push_back((int32_t)(acc[i].first % n_cd));
+            p->w.push_back(sum);
+        }
+        i = j;
+    }
+    // the minimal sets as (rows, columns) of each representative
+    auto pack = [](const Classes &c, const std::vector<Key> &snk, const std::vector<Key> &src, int n,
+                   std::vector<int8_t> &dst) {
+        for (int64_t r : c.rep) {
+            const int64_t i = src.empty() ? 0 : r / (int64_t)src.size(), j = src.empty() ? 0 : r % (int64_t)src.size();
+            for (int q = 0; q < n; ++q) dst.push_back(snk[i][q]);
+            for (int q = 0; q < n; ++q) dst.push_back(src[j][q]);
+        }
+    };
+    pack(cu, su, qu, nu, p->zu);
+    pack(cd, sd, qd, nd, p->zd);
+    p->n_zu = (int64_t)cu.rep.size();
+    p->n_zd = (int64_t)cd.rep.size();
+    p->n_theta = (int64_t)p->w.size();
+    std::vector<double> wd(p->w.begin(), p->w.end());
+    err = upload(&p->d_zu, p->zu);
+    if (!err) err = upload(&p->d_zd, p->zd);
+    if (!err) err = upload(&p->d_k, p->k);
+    if (!err) err = upload(&p->d_l, p->l);
+    if (!err) err = upload(&p->d_w, wd);
+    if (err) {
+        free_plan(p);
+        return err;
+    }
+    *out = p;
+    return WICK_OK;
+}
+
+int wick_det_stats(const wick_det_plan *p, int64_t *out) {
+    if (!p || !out) return WICK_EINVAL;
+    out[0] = p->n_snk;
+    out[1] = p->n_src;
+    out[2] = p->n_zu;
+    out[3] = p->n_zd;
+    out[4] = p->n_theta;
+    out[5] = p->n_u * 8 + p->n_d;
+    return WICK_OK;
+}
+
+int wick_det_copy(const wick_det_plan *p, int32_t *k, int32_t *l, int64_t *w, int8_t *zu_rows, int8_t *zu_cols,
+                  int8_t *zd_rows, int8_t *zd_cols) {
+    if (!p) return WICK_EINVAL;
+    if (k) std::copy(p->k.begin(), p->k.end(), k);
+    if (l) std::copy(p->l.begin(), p->l.end(), l);
+    if (w) std::copy(p->w.begin(), p->w.end(), w);
+    for (int64_t i = 0; i < p->n_zu; ++i)
+        for (int q = 0; q < p->n_u; ++q) {
+            if (zu_rows) zu_rows[i * p->n_u + q] = p->zu[(i * 2) * p->n_u + q];
+            if (zu_cols) zu_cols[i * p->n_u + q] = p->zu[(i * 2 + 1) * p->n_u + q];
+        }
+    for (int64_t i = 0; i < p->n_zd; ++i)
+        for (int q = 0; q < p->n_d; ++q) {
+            if (zd_rows) zd_rows[i * p->n_d + q] = p->zd[(i * 2) * p->n_d + q];
+            if (zd_cols) zd_cols[i * p->n_d + q] = p->zd[(i * 2 + 1) * p->n_d + q];
+        }
+    return WICK_OK;
+}
+
+int wick_det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_det_plan *plan, double scale,
+                      int precision, void *C_out, wick_stream_t stream) {
+    if (!Su || !Sd || !plan || !C_out || precision != WICK_FP64) return WICK_EINVAL;
+    if (!Su->data || !Sd->data || Su->L != Sd->L || Su->T != Sd->T || Su->n_src != Sd->n_src ||
+        Su->dtype != Sd->dtype || Su->L < 1 || Su->T < 1 || Su->n_src < 1 ||
+        (Su->dtype != WICK_C64 && Su->dtype != WICK_C128))
+        return WICK_EINVAL;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != plan->device) return WICK_EINVAL;
+    const int64_t V = (int64_t)Su->L * Su->L * Su->L, n_slices = (int64_t)Su->n_src * Su->T;
+    if (V > (1 << 24) || n_slices > (1 << 24)) return WICK_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan->n_theta == 0) {
+        WICK_CUDA_TRY(cudaMemsetAsync(C_out, 0, sizeof(double2) * n_slices, st));
+        return WICK_OK;
+    }
+    const int n_chunks = (int)((V + kDetChunk - 1) / kDetChunk);
+    const int64_t items = n_slices * n_chunks;
+    int n_sm = 0, occ = 0;
+    WICK_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    if (Su->dtype == WICK_C64)
+        WICK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, det_eval_kernel<float2>, kDetThreads, 0));
+    else
+        WICK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, det_eval_kernel<double2>, kDetThreads, 0));
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(occ, 1)));
+    const size_t scratch_bytes = sizeof(double2) * (size_t)grid * (size_t)(plan->n_zu + plan->n_zd);
+    const size_t part_bytes = sizeof(double2) * (size_t)items;
+    int err = WICK_OK;
+    unsigned char *ws = (unsigned char *)workspace(2, scratch_bytes + part_bytes + 256, &err);
+    if (err) return err;
+    double2 *scratch = (double2 *)ws;
+    double2 *partials = (double2 *)(ws + (scratch_bytes + 255) / 256 * 256);
+    DetArgs a{plan->n_u, plan->n_d, plan->n_zu, plan->n_zd, plan->n_theta, plan->d_zu, plan->d_zd,
+              plan->d_k, plan->d_l, plan->d_w};
+    if (Su->dtype == WICK_C64)
+        det_eval_kernel<float2><<<(unsigned)grid, kDetThreads, 0, st>>>(a, (const float2 *)Su->data,
+                                                                       (const float2 *)Sd->data, (int)V, (int)n_slices,
+                                                                       n_chunks, scratch, partials);
+    else
+        det_eval_kernel<double2><<<(unsigned)grid, kDetThreads, 0, st>>>(a, (const double2 *)Su->data,
+                                                                        (const double2 *)Sd->data, (int)V,
+                                                                        (int)n_slices, n_chunks, scratch, partials);
+    WICK_CUDA_TRY(cudaGetLastError());
+    det_finish_kernel<<<(unsigned)((n_slices + 127) / 128), 128, 0, st>>>(partials, (int)n_slices, n_chunks, scale,
+                                                                          (double2 *)C_out);
+    WICK_CUDA_TRY(cudaGetLastError());
+    return WICK_OK;
+}
+
+void wick_det_free(wick_det_plan *plan) { free_plan(plan); }
+
+}  // extern "C"

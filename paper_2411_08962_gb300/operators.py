@@ -240,3 +240,55 @@ def cluster(name: str) -> Nucleus:
     src, flav = _flavour_grouped(ops, terms)
     sink = sorted((tuple(t), tuple(s), w) for t, s, w in terms)
     return Nucleus(name, len(terms[0][0]), ops, 4, list(range(12)), sink, src, flav, scale)
+
+
+# ---------------------------------------------------------------------------
+# Point-sink operators of the determinant algorithm (Sec. III.C, Eqs. NP_op,
+# He3_op, He4_op) for wick_det_reduce: flavour-grouped quark index tuples
+# (u quarks first, then d, each in nucleon-slot order, regrouping parity in
+# the weight).  2H and 4He use the nucleons of Eqs. 1000/1001 with all spins;
+# the projected nucleons of 3He take the paper's P+- = (1 -+ gamma4)/2 of this
+# basis (its gamma4 has the opposite sign), with which the operators have the
+# 356 / 1026 / 2716 terms of the paper's determinant table.
+# ---------------------------------------------------------------------------
+@dataclass
+class QuarkOperator:
+    name: str
+    n_u: int
+    n_d: int
+    chi: np.ndarray      # int8 [n_terms][n_u + n_d]
+    w: np.ndarray        # int64 [n_terms]
+    scale: float = 1.0   # overall factor of sink x source
+
+
+def point_operator(name: str) -> QuarkOperator:
+    sp = (0, 1, 2, 3)
+    G = diquark_matrix()
+    plain = [nucleon_op(U, G, sp, sp), nucleon_op(D, G, sp, sp)]
+    scale = 1.0
+    if name == "deuteron":                                 # n^T (C g5 P+) p
+        Gp = diquark_matrix(-1)
+        ops, terms = plain, [((NEUTRON, PROTON), (a, b), int(Gp[a, b])) for a in range(4) for b in range(4)
+                             if Gp[a, b]]
+    elif name == "he3":                                    # p-^T (C g5) n+ p+^(J=0)
+        ops = [nucleon_op(U, diquark_matrix(+1), sp, sp), nucleon_op(D, diquark_matrix(-1), sp, sp),
+               nucleon_op(U, diquark_matrix(-1), sp, sp)]
+        terms = [((0, 1, 2), (a, b, 0), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b]]
+    elif name == "he4":                                    # (chibar eta - chi etabar)/sqrt2, plain p, n
+        pats = [(0, 1, 0, 1), (1, 0, 1, 0), (0, 1, 1, 0), (1, 0, 0, 1), (0, 0, 1, 1), (1, 1, 0, 0)]
+        chi_w = [1, 1, -1, -1, 0, 0]
+        chibar_w = [1, 1, 1, 1, -2, -2]
+        ops, terms = plain, []
+        for a, spins in enumerate(pats):
+            for b, iso in enumerate(pats):
+                w = chibar_w[a] * chi_w[b] - chi_w[a] * chibar_w[b]
+                if w:
+                    terms.append((tuple(PROTON if x == 0 else NEUTRON for x in iso), spins, w))
+        scale = 1.0 / 96.0
+    else:
+        raise ValueError(name)
+    table, flav = _flavour_grouped(ops, terms)
+    n_u = sum(1 for f in flav if f == U)
+    chi = np.array([c for c, _ in table], dtype=np.int8).reshape(len(table), len(flav))
+    w = np.array([x for _, x in table], dtype=np.int64)
+    return QuarkOperator(name, n_u, len(flav) - n_u, chi, w, scale)

@@ -28,7 +28,8 @@ EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_reduce_terms", "wick_t
            "wick_terms_nucleons", "wick_terms_copy", "wick_terms_stats", "wick_terms_select",
            "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_contract_noalloc",
            "wick_status", "wick_batch_create", "wick_batch_run", "wick_batch_launches", "wick_batch_free",
-           "wick_synth_propagator", "wick_cluster_product", "wick_strerror", "wick_version")
+           "wick_synth_propagator", "wick_cluster_product", "wick_det_reduce", "wick_det_stats", "wick_det_copy",
+           "wick_det_contract", "wick_det_free", "wick_strerror", "wick_version")
 
 
 class WickError(RuntimeError):
@@ -55,6 +56,11 @@ class wick_nucleus(C.Structure):
                 ("sink_spin", C.POINTER(C.c_int8)), ("sink_w", C.POINTER(C.c_int64)), ("n_src", C.c_int),
                 ("src_chi", C.POINTER(C.c_int8)), ("src_w", C.POINTER(C.c_int64)),
                 ("src_flav", C.POINTER(C.c_int8)), ("scale", C.c_double)]
+
+
+class wick_quark_operator(C.Structure):
+    _fields_ = [("n_u", C.c_int), ("n_d", C.c_int), ("n_terms", C.c_int), ("chi", C.POINTER(C.c_int8)),
+                ("w", C.POINTER(C.c_int64))]
 
 
 _lock = threading.Lock()
@@ -97,13 +103,20 @@ def load(path: str = LIB_PATH):
             L.wick_batch_free.restype = None
             L.wick_synth_propagator.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
             L.wick_cluster_product.argtypes = [vp, vp, C.c_int64, vp, vp]
+            L.wick_det_reduce.argtypes = [P(wick_quark_operator), P(wick_quark_operator), C.c_uint64, C.c_int, P(vp)]
+            L.wick_det_stats.argtypes = [vp, P(C.c_int64)]
+            L.wick_det_copy.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+            L.wick_det_contract.argtypes = [P(wick_prop), P(wick_prop), vp, C.c_double, C.c_int, vp, vp]
+            L.wick_det_free.argtypes = [vp]
+            L.wick_det_free.restype = None
             L.wick_strerror.argtypes = [C.c_int]
             L.wick_strerror.restype = C.c_char_p
             L.wick_version.restype = C.c_char_p
             for f in ("wick_build_blocks", "wick_reduce_terms", "wick_terms_nucleons", "wick_terms_copy",
                       "wick_terms_stats", "wick_terms_select", "wick_terms_save", "wick_terms_load",
                       "wick_contract", "wick_contract_noalloc", "wick_status", "wick_batch_create",
-                      "wick_batch_run", "wick_batch_launches", "wick_synth_propagator", "wick_cluster_product"):
+                      "wick_batch_run", "wick_batch_launches", "wick_synth_propagator", "wick_cluster_product",
+                      "wick_det_reduce", "wick_det_stats", "wick_det_copy", "wick_det_contract"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -314,3 +327,70 @@ def wick_status(stream=None) -> int:
 
 def wick_version() -> str:
     return load().wick_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# point-sink determinant algorithm
+# ---------------------------------------------------------------------------
+def _quark_op(q):
+    chi = np.ascontiguousarray(q.chi, dtype=np.int8)
+    w = np.ascontiguousarray(q.w, dtype=np.int64)
+    s = wick_quark_operator(int(q.n_u), int(q.n_d), len(w), chi.ctypes.data_as(C.POINTER(C.c_int8)),
+                            w.ctypes.data_as(C.POINTER(C.c_int64)))
+    return s, (chi, w)
+
+
+class DetPlan:
+    """Library-owned minimal sets zeta_u, zeta_d and Theta of a point-sink operator pair (wick_det_reduce)."""
+
+    def __init__(self, sink, source=None, seed: int = 0x2411D7, trials: int = 2):
+        source = sink if source is None else source
+        a, keep_a = _quark_op(sink)
+        b, keep_b = _quark_op(source)
+        h = C.c_void_p()
+        _check(load().wick_det_reduce(C.byref(a), C.byref(b), seed, trials, C.byref(h)), "wick_det_reduce")
+        self.h = h
+        self.scale = float(getattr(sink, "scale", 1.0))
+
+    def stats(self) -> dict:
+        out = (C.c_int64 * 6)()
+        _check(load().wick_det_stats(self.h, out), "wick_det_stats")
+        return dict(n_sink=out[0], n_source=out[1], zeta_u=out[2], zeta_d=out[3], theta=out[4],
+                    n_u=out[5] // 8, n_d=out[5] % 8)
+
+    def copy(self) -> dict:
+        st = self.stats()
+        k = np.zeros(max(st["theta"], 1), np.int32)
+        l = np.zeros_like(k)
+        w = np.zeros(max(st["theta"], 1), np.int64)
+        zu = [np.zeros((max(st["zeta_u"], 1), max(st["n_u"], 1)), np.int8) for _ in range(2)]
+        zd = [np.zeros((max(st["zeta_d"], 1), max(st["n_d"], 1)), np.int8) for _ in range(2)]
+        _check(load().wick_det_copy(self.h, k.ctypes.data, l.ctypes.data, w.ctypes.data, zu[0].ctypes.data,
+                                    zu[1].ctypes.data, zd[0].ctypes.data, zd[1].ctypes.data), "wick_det_copy")
+        n = st["theta"]
+        return dict(k=k[:n], l=l[:n], w=w[:n], zu_rows=zu[0][:st["zeta_u"], :st["n_u"]],
+                    zu_cols=zu[1][:st["zeta_u"], :st["n_u"]], zd_rows=zd[0][:st["zeta_d"], :st["n_d"]],
+                    zd_cols=zd[1][:st["zeta_d"], :st["n_d"]])
+
+    def free(self):
+        if self.h:
+            load().wick_det_free(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def wick_det_contract(Su, Sd, plan: DetPlan, C_out, L: int, T: int, n_src: int, scale=None,
+                      precision: int = WICK_FP64, stream=None):
+    """C_out[src][t] (torch complex128 CUDA tensor) = point-sink correlator of the plan."""
+    def prop(S):
+        dt = WICK_C64 if str(S.dtype) == "torch.complex64" else WICK_C128
+        return wick_prop(_ptr(S), L, T, n_src, dt)
+    pu, pd = prop(Su), prop(Sd)
+    sc = plan.scale if scale is None else float(scale)
+    _check(load().wick_det_contract(C.byref(pu), C.byref(pd), plan.h, sc, precision, _ptr(C_out), _stream(stream)),
+           "wick_det_contract")
