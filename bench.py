@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["he4", "li7", "batched"], default="he4",
+    ap.add_argument("--workload", choices=["he4", "li7", "batched", "point"], default="he4",
                     help="he4: the metric's workload (default); li7 / batched: the other scope rows")
     ap.add_argument("--profile-slab", choices=["mixed", "fp64"], default=None,
                     help="only run the block build on one source of the workload (for ncu captures)")
@@ -479,6 +479,82 @@ def _timed(fn, steps, warmup, stream):
     return a.elapsed_time(b) / steps
 
 
+# FP64 flops of one determinant as evaluated on the device: explicit forms up
+# to 3 x 3 (2 x 2: two complex products and a difference; 3 x 3: three 2 x 2
+# minors and three products), pivoted LU above (per column: the pivot product
+# and reciprocal, 14; per lower row: the multiplier, 6, and 8 per updated
+# entry); a Theta term: one complex product and two FMAs (10).
+def det_flops(n: int) -> int:
+    if n <= 1:
+        return 0
+    if n == 2:
+        return 14
+    if n == 3:
+        return 64
+    return sum(14 + (n - c - 1) * (6 + 8 * (n - c - 1)) for c in range(n))
+
+
+THETA_FLOPS = 10
+# the paper's point-sink 2H time per time slice on one A100 (24^3), seconds (context, other hardware)
+PAPER_A100_2H_POINT_S = 0.15
+
+
+def run_point(args):
+    """Point-sink correlators by the determinant algorithm (FP64): 2H on the
+    paper's 24^3 lattice, 3He on 8^3; one configuration, one source; the
+    metric is ms per time slice."""
+    import torch
+
+    from paper_2411_08962_gb300 import build, operators, wick
+    build.build()
+    wick.load()
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, L, T, seed in (("deuteron", 24, 4, 0x2411D2), ("he3", 8, 4, 0x2411D3)):
+        q = operators.point_operator(name)
+        t0 = time.perf_counter()
+        plan = wick.DetPlan(q)
+        reduce_s = time.perf_counter() - t0
+        st = plan.stats()
+        Su = torch.empty((1, T, L ** 3, 3, 4, 3, 4), dtype=torch.complex64, device="cuda")
+        Sd = torch.empty_like(Su)
+        wick.wick_synth_propagator(seed, 0, 0, L, T, Su[0])
+        wick.wick_synth_propagator(seed, 1, 0, L, T, Sd[0])
+        C = torch.empty((1, T), dtype=torch.complex128, device="cuda")
+        ms = _timed(lambda: wick.wick_det_contract(Su, Sd, plan, C, L, T, 1, stream=stream), args.steps,
+                    max(1, args.warmup), stream)
+        sites = L ** 3 * T
+        flops = sites * (st["zeta_u"] * det_flops(st["n_u"]) + st["zeta_d"] * det_flops(st["n_d"])
+                         + st["theta"] * THETA_FLOPS)
+        tf = flops / (ms / 1e3) / 1e12
+        res[name] = {"L": L, "T": T, "ms_per_time_slice": ms / T, "reduce_seconds": reduce_s,
+                     "zeta_u": st["zeta_u"], "zeta_d": st["zeta_d"], "theta": st["theta"],
+                     "operator_terms": st["n_sink"],
+                     "roofline": {"bound": "fp64", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                                  "frac": tf / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal FP64",
+                                  "flops_per_site": flops // sites}}
+        if name == "deuteron" and not args.no_cpu_baseline:
+            from oracle import det as DT
+            tab, nu, nd, sc = DT.operator(name)
+            stc = DT.pair_structure(tab, tab, nu)
+            n_site = 64
+            su = Su[:, :1, :n_site].cpu().numpy().astype(np.complex128)
+            sd = Sd[:, :1, :n_site].cpu().numpy().astype(np.complex128)
+            t0 = time.perf_counter()
+            DT.point_correlator(su, sd, None, None, nu, nd, sc, structure=stc)
+            dt = time.perf_counter() - t0
+            from oracle import oracle as O
+            res[name]["cpu_baseline"] = {"value": 1e3 * dt * L ** 3 / n_site, "unit": "ms/time slice",
+                                         "cores": O.num_threads(), "kind": "oracle",
+                                         "sample": f"{n_site} of {L ** 3} sites of one time slice, {dt:.1f} s"}
+        plan.free()
+    d = res["deuteron"]
+    print(json.dumps({"workload": "point", "metric": "2H point-sink correlator ms per time slice (24^3, FP64)",
+                      "value": d["ms_per_time_slice"], "unit": "ms/time slice", "higher_is_better": False,
+                      "steps": args.steps, "context_paper_a100_ms": 1e3 * PAPER_A100_2H_POINT_S,
+                      "nuclei": res, "gpu_launches_per_step": 2}), flush=True)
+
+
 def run_li7(args):
     """Li-7 = He-4 cluster x triton cluster, L=24, T=48, one source (one configuration per step)."""
     import torch
@@ -631,6 +707,8 @@ if __name__ == "__main__":
         run_profile_slab(a)
     elif a.impl == "ours" and a.workload == "li7":
         run_li7(a)
+    elif a.impl == "ours" and a.workload == "point":
+        run_point(a)
     elif a.impl == "ours" and a.workload == "batched":
         run_batched(a)
     elif a.impl == "reference":
