@@ -29,7 +29,8 @@
 // j <= 5 - (first slice in t), one MMA each (6 for the upper-spin tables,
 // 6+5+4+2 for the full-spin ones).  A CTA owns (block type, column tile of the
 // (c2, c3) columns, range of 512 sites, slice); the first two vary fastest in
-// the grid so that the CTAs reading the same rows of S run together.  Per chunk of 8 sites:
+// the grid so that the CTAs reading the same rows of S run together.  Per chunk
+// of 16 sites (upper tables; 8 for the full-spin ones, for shared memory):
 // the CTA builds the U and X slices of chunk c into one of two operand buffers
 // from S staged two chunks ahead (three staging buffers, cp.async), meets at one
 // barrier, and one thread of the least-loaded warp issues the chunk's MMAs and
@@ -51,11 +52,8 @@ constexpr int kThr = 512;                          // 16 warps
 constexpr int kSlices = 5;                         // slices of U
 constexpr int kSlicesX = 6;                        // slices of X
 constexpr int kMaxPair = 5;                        // kept slice pairs: i + j <= kMaxPair
-constexpr int kNX = 8;                             // sites per operand chunk
 constexpr int kKa = 3;                             // colour-term slots per site
-constexpr int kKc = kNX * kKa * 2;                 // K per chunk = 48
 constexpr int kRoundSites = 128;                   // sites per exact TMEM accumulation
-constexpr int kChunksPerRound = kRoundSites / kNX;
 constexpr int kRangeSites = 512;                   // sites per CTA (one grid, one partial)
 constexpr int kSpinLimit = 1 << 22;                // mbarrier polls before giving up
 constexpr int kStage = 3;                          // staging buffers
@@ -67,17 +65,19 @@ struct WeightExp {
 };
 
 // Compile-time shape of a table family: NC colours chi, NS spins, NT columns
-// per MMA (multiple of 16), NMT M tiles.
-template <int NC_, int NS_, int NT_, int NMT_> struct Shape {
-    static constexpr int NC = NC_, NS = NS_, NT = NT_, NMT = NMT_;
+// per MMA (multiple of 16), NMT M tiles, NX sites per operand chunk.
+template <int NC_, int NS_, int NT_, int NMT_, int NX_> struct Shape {
+    static constexpr int NC = NC_, NS = NS_, NT = NT_, NMT = NMT_, NX = NX_;
+    static constexpr int KC = NX * kKa * 2;                 // K per chunk
+    static constexpr int CHUNKS_PER_ROUND = kRoundSites / NX;
     static constexpr int NC2 = NC * NC;
     static constexpr int R = 2 * NS * NC;                   // real rows per U slice
     static constexpr int NCTA = NT >= NC2 ? NC2 : NT;       // (c2, c3) columns per CTA
     static constexpr int NCT = (NC2 + NT - 1) / NT;         // column tiles
     static constexpr int PER_TILE = 4 / NMT;                // warps of a lane quarter per M tile
     static constexpr int CW = NT / PER_TILE;                // readout columns per thread
-    static constexpr int NXJOB = kNX * kKa * NCTA;          // one X value each
-    static constexpr int NUJOB = kNX * kKa / 2 * NS * NC;   // two U values each
+    static constexpr int NXJOB = NX * kKa * NCTA;           // one X value each
+    static constexpr int NUJOB = NX * kKa / 2 * NS * NC;    // two U values each
     static constexpr int jmax(int t) {
         return kSlicesX < kMaxPair + 1 - t * 128 / R ? kSlicesX : kMaxPair + 1 - t * 128 / R;
     }
@@ -89,22 +89,22 @@ template <int NC_, int NS_, int NT_, int NMT_> struct Shape {
     static constexpr int TMEM_USED = toff(NMT - 1, 0) + jmax(NMT - 1) * NT;
     static constexpr int TMEM_COLS = TMEM_USED <= 32 ? 32 : TMEM_USED <= 64 ? 64 : TMEM_USED <= 128 ? 128
                                    : TMEM_USED <= 256 ? 256 : 512;
-    static constexpr int A_BYTES = NMT * 128 * kKc * 2;
-    static constexpr int B_BYTES = kSlicesX * NT * kKc * 2;
-    static constexpr int S_BYTES = kNX * kMaxRows * NC * 8;  // float2 staging
+    static constexpr int A_BYTES = NMT * 128 * KC * 2;
+    static constexpr int B_BYTES = kSlicesX * NT * KC * 2;
+    static constexpr int S_BYTES = NX * kMaxRows * NC * 8;  // float2 staging
     static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES + 4 * (16 + 256) + 32;
     static_assert(NMT * 128 >= kSlices * R && (NMT - 1) * 128 < kSlices * R, "M tiles");
     static_assert(NC2 <= NT || NC2 % NT == 0, "column tiles");
     static_assert(TMEM_USED <= 512 && CW % 4 == 0 && CW <= 32, "TMEM / readout");
     static_assert(NXJOB % 32 == 0, "X jobs fill whole warps");
-    static_assert(NXJOB + NUJOB <= 2 * kThr, "two jobs per thread");
+    static_assert((NXJOB + NUJOB) % 32 == 0, "U jobs fill whole warps");
     static_assert(R % 8 == 0, "U slices start on a core-matrix row group");
     static_assert(NCTA % 8 == 0 || NCTA % 8 == 4, "X job map");
     static_assert(kSlices * R * NT * 8 <= 2 * (A_BYTES + B_BYTES), "combine buffer");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
-using UpperShape = Shape<6, 2, 48, 1>;   // nucleon upper spin components: 2 x 216 per type
-using FullShape = Shape<12, 4, 16, 4>;   // all four spins: 4 x 1728 per type
+using UpperShape = Shape<6, 2, 48, 1, 16>;   // nucleon upper spin components: 2 x 216 per type
+using FullShape = Shape<12, 4, 16, 4, 8>;    // all four spins: 4 x 1728 per type
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -129,16 +129,16 @@ __host__ __device__ __forceinline__ int exponent_bound(float m) {
     return e < -100 ? -100 : e;
 }
 
-// K-major bf16 tile of 8x8 core matrices: element (row m, k) of a tile whose rows hold kKc values
-__device__ __forceinline__ int tile_off(int m, int k) {
-    return ((m >> 3) * (kKc / 8) + (k >> 3)) * 64 + (m & 7) * 8 + (k & 7);
+// K-major bf16 tile of 8x8 core matrices: element (row m, k) of a tile whose rows hold KC values
+template <int KC> __device__ __forceinline__ int tile_off(int m, int k) {
+    return ((m >> 3) * (KC / 8) + (k >> 3)) * 64 + (m & 7) * 8 + (k & 7);
 }
 
-// shared-memory matrix descriptor: no swizzle, core matrices 128 B apart along K, 8-row groups kKc/8*128 B apart
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+// shared-memory matrix descriptor: no swizzle, core matrices 128 B apart along K, 8-row groups KC/8*128 B apart
+template <int KC> __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
     d |= (uint64_t)(128 >> 4) << 16;
-    d |= (uint64_t)((kKc / 8 * 128) >> 4) << 32;
+    d |= (uint64_t)((KC / 8 * 128) >> 4) << 32;
     d |= (uint64_t)1 << 46;  // descriptor version of the sm_100 family
     return d;
 }
@@ -275,7 +275,7 @@ __device__ __forceinline__ pdf x_value(const BlockPlan &plan, const float2 *s1, 
 // 32 different banks (the leftover 4 columns of a 36-column tile: 4 x 8, two
 // ways).  Consecutive columns of one combo would meet only 8 banks.
 template <typename SH> __device__ __forceinline__ void x_map(int jb, int &n, int &gc) {
-    constexpr int NG = SH::NCTA / 8, GW = kNX * kKa / 4;
+    constexpr int NG = SH::NCTA / 8, GW = SH::NX * kKa / 4;
     const int w = jb >> 5, lane = jb & 31;
     if (w < NG * GW) {
         n = 8 * (w % NG) + (lane & 7);
@@ -304,9 +304,9 @@ __device__ __forceinline__ void x_job(const BlockPlan &plan, const float2 *S, in
 #pragma unroll
         for (int j = 0; j < kSlicesX; ++j) w[j] = 0u;
     }
-    __nv_bfloat16 *dst = B + tile_off(n, gc * 2);
+    __nv_bfloat16 *dst = B + tile_off<SH::KC>(n, gc * 2);
 #pragma unroll
-    for (int j = 0; j < kSlicesX; ++j) *reinterpret_cast<uint32_t *>(dst + j * NT * kKc) = w[j];
+    for (int j = 0; j < kSlicesX; ++j) *reinterpret_cast<uint32_t *>(dst + j * NT * SH::KC) = w[j];
 }
 
 // two X jobs with independent chains (both jA, jB < NXJOB)
@@ -328,11 +328,11 @@ __device__ __forceinline__ void x_job2(const BlockPlan &plan, const float2 *S, i
     uint32_t wA[kSlicesX], wB[kSlicesX];
     slice_x2(XA.h, XA.l, exp2i(7 - sF[nA]), wA);
     slice_x2(XB.h, XB.l, exp2i(7 - sF[nB]), wB);
-    __nv_bfloat16 *dA = B + tile_off(nA, gA * 2), *dB = B + tile_off(nB, gB * 2);
+    __nv_bfloat16 *dA = B + tile_off<SH::KC>(nA, gA * 2), *dB = B + tile_off<SH::KC>(nB, gB * 2);
 #pragma unroll
     for (int j = 0; j < kSlicesX; ++j) {
-        *reinterpret_cast<uint32_t *>(dA + j * NT * kKc) = wA[j];
-        *reinterpret_cast<uint32_t *>(dB + j * NT * kKc) = wB[j];
+        *reinterpret_cast<uint32_t *>(dA + j * NT * SH::KC) = wA[j];
+        *reinterpret_cast<uint32_t *>(dB + j * NT * SH::KC) = wB[j];
     }
 }
 
@@ -353,11 +353,11 @@ __device__ __forceinline__ void u_job(const BlockPlan &plan, const float2 *S, in
         slice_u2(u, scu, wre[h], wim[h]);
     }
     // re row: U_re X_re - U_im X_im ; im row: U_im X_re + U_re X_im
-    __nv_bfloat16 *dre = A + tile_off(s * NC + c1, gp * 4), *dim = A + tile_off(NS * NC + s * NC + c1, gp * 4);
+    __nv_bfloat16 *dre = A + tile_off<SH::KC>(s * NC + c1, gp * 4), *dim = A + tile_off<SH::KC>(NS * NC + s * NC + c1, gp * 4);
 #pragma unroll
     for (int i = 0; i < kSlices; ++i) {
-        *reinterpret_cast<uint2 *>(dre + tile_off(i * R, 0)) = make_uint2(wre[0][i], wre[1][i]);
-        *reinterpret_cast<uint2 *>(dim + tile_off(i * R, 0)) = make_uint2(wim[0][i], wim[1][i]);
+        *reinterpret_cast<uint2 *>(dre + tile_off<SH::KC>(i * R, 0)) = make_uint2(wre[0][i], wre[1][i]);
+        *reinterpret_cast<uint2 *>(dim + tile_off<SH::KC>(i * R, 0)) = make_uint2(wim[0][i], wim[1][i]);
     }
 }
 
@@ -410,14 +410,15 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
     }
 
     const int x_begin = rng * kRangeSites, x_end = min(V, x_begin + kRangeSites);
-    const int n_chunks = (x_end - x_begin + kNX - 1) / kNX;
+    constexpr int NX = SH::NX, KC = SH::KC;
+    const int n_chunks = (x_end - x_begin + NX - 1) / NX;
     const ST *su = Su + (size_t)slice * V * 144;
     const ST *sd = Sd + (size_t)slice * V * 144;
     // stage the rows of chunk c: sS[site][row][ic] as float2, flavour-0 rows first (zeros past the range)
     auto stage = [&](int c) {
         float2 *dst = sS0 + (c % kStage) * (SH::S_BYTES / 8);
-        const int xb = x_begin + c * kNX;
-        for (int e = tid; e < kNX * nr * NC; e += kThr) {
+        const int xb = x_begin + c * NX;
+        for (int e = tid; e < NX * nr * NC; e += kThr) {
             const int site = e / (nr * NC);
             const int rem = e - site * nr * NC;
             const int rc = rem / NC, ic = rem - rc * NC;
@@ -472,15 +473,18 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
             else bad = 1;
         }
         if (!bad) {
-            // jobs tid and tid + kThr: two X values are built side by side (independent chains)
-            const int jA = tid, jB = tid + kThr;
+            // jobs j0 and j0 + kThr per round: two X values are built side by side (independent chains);
+            // X jobs come first and fill whole warps, so every branch is warp-uniform
             constexpr int NJ = SH::NXJOB + SH::NUJOB;
-            if (jB < SH::NXJOB) {
-                x_job2<SH>(plan, S, nr, off1, off2, col0, t0, n_a, sF, B, jA, jB);
-            } else {
-                if (jA < SH::NXJOB) x_job<SH>(plan, S, nr, off1, off2, col0, t0, n_a, sF, B, jA);
-                else if (jA < NJ) u_job<SH>(plan, S, nr, off1, o, n_a, sEU, A, jA - SH::NXJOB);
-                if (jB < NJ) u_job<SH>(plan, S, nr, off1, o, n_a, sEU, A, jB - SH::NXJOB);
+            for (int j0 = tid; j0 < NJ; j0 += 2 * kThr) {
+                const int jA = j0, jB = j0 + kThr;
+                if (jB < SH::NXJOB) {
+                    x_job2<SH>(plan, S, nr, off1, off2, col0, t0, n_a, sF, B, jA, jB);
+                } else {
+                    if (jA < SH::NXJOB) x_job<SH>(plan, S, nr, off1, off2, col0, t0, n_a, sF, B, jA);
+                    else u_job<SH>(plan, S, nr, off1, o, n_a, sEU, A, jA - SH::NXJOB);
+                    if (jB < NJ) u_job<SH>(plan, S, nr, off1, o, n_a, sEU, A, jB - SH::NXJOB);
+                }
             }
         }
         // staged rows of chunk c + 1 complete (this thread's copies); operands of chunk c written
@@ -492,17 +496,17 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const bool fresh = c % kChunksPerRound == 0;
+        const bool fresh = c % SH::CHUNKS_PER_ROUND == 0;
         if (tid == kThr - 1) {  // the last warp has the fewest jobs
             const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
 #pragma unroll
-            for (int ks = 0; ks < kKc / 16; ++ks)
+            for (int ks = 0; ks < KC / 16; ++ks)
 #pragma unroll
                 for (int t = 0; t < SH::NMT; ++t) {
-                    const uint64_t da = smem_desc(a0 + (uint32_t)(t * 128 * kKc * 2 + ks * 256));
+                    const uint64_t da = smem_desc<KC>(a0 + (uint32_t)(t * 128 * KC * 2 + ks * 256));
 #pragma unroll
                     for (int j = 0; j < SH::jmax(t); ++j) {
-                        const uint64_t db = smem_desc(b0 + (uint32_t)(j * NT * kKc * 2 + ks * 256));
+                        const uint64_t db = smem_desc<KC>(b0 + (uint32_t)(j * NT * KC * 2 + ks * 256));
                         const uint32_t acc_in = (fresh && ks == 0) ? 0u : 1u;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -520,7 +524,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
         if (c + 2 < n_chunks) stage(c + 2);
 
         // end of a round: read the accumulators out of TMEM
-        if (c % kChunksPerRound == kChunksPerRound - 1 || c == n_chunks - 1) {
+        if (c % SH::CHUNKS_PER_ROUND == SH::CHUNKS_PER_ROUND - 1 || c == n_chunks - 1) {
             if (waited0 < issued0) {
                 if (poll_parity(&mbar[0], waited0 & 1)) ++waited0;
                 else bad = 1;
