@@ -547,6 +547,29 @@ def run_point(args):
             res[name]["cpu_baseline"] = {"value": 1e3 * dt * L ** 3 / n_site, "unit": "ms/time slice",
                                          "cores": O.num_threads(), "kind": "oracle",
                                          "sample": f"{n_site} of {L ** 3} sites of one time slice, {dt:.1f} s"}
+        if name == "deuteron":
+            # the 3 x 3 correlation matrix of three 2H operators (Eqs. E1-E3): shared determinants
+            # against nine separate pair evaluations
+            basis = operators.deuteron_basis()
+            t0 = time.perf_counter()
+            mp = wick.DetPlan(None, matrix=basis)
+            m_reduce = time.perf_counter() - t0
+            Cm = torch.empty((9, 1, T), dtype=torch.complex128, device="cuda")
+            ms_m = _timed(lambda: wick.wick_det_contract(Su, Sd, mp, Cm, L, T, 1, stream=stream), args.steps,
+                          max(1, args.warmup), stream)
+            sep = 0.0
+            for i in range(3):
+                for j in range(3):
+                    pp = wick.DetPlan(basis[i], basis[j])
+                    C1 = torch.empty((1, 1, T), dtype=torch.complex128, device="cuda")
+                    sep += _timed(lambda: wick.wick_det_contract(Su, Sd, pp, C1, L, T, 1, stream=stream),
+                                  max(1, args.steps // 2), 1, stream)
+                    pp.free()
+            ms_ = mp.stats()
+            res["gevp_2h_3x3"] = {"L": L, "T": T, "ms_per_time_slice": ms_m / T,
+                                  "nine_separate_ms_per_time_slice": sep / T, "reduce_seconds": m_reduce,
+                                  "zeta_u": ms_["zeta_u"], "zeta_d": ms_["zeta_d"], "theta": ms_["theta"]}
+            mp.free()
         plan.free()
     d = res["deuteron"]
     print(json.dumps({"workload": "point", "metric": "2H point-sink correlator ms per time slice (24^3, FP64)",

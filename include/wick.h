@@ -340,8 +340,20 @@ typedef struct {
 typedef struct wick_det_plan wick_det_plan;
 int wick_det_reduce(const wick_quark_operator *sink, const wick_quark_operator *source, uint64_t seed, int trials,
                     wick_det_plan **out);
-/* out[6]: sink terms, source terms (antisymmetrised), |zeta_u|, |zeta_d|, Theta non-zeros, n_u * 8 + n_d */
+/*
+ * wick_det_reduce_matrix: the N x N correlation matrix C_ij(t) = <O_i(t) Obar_j(0)>
+ * of N operators with the same quark content (Sec. "Application ... to the
+ * generalized eigenvalue problem", Eqs. E1-E3): one identity testing over the
+ * index sets of all operators, so the determinants are shared by every
+ * element, and one Theta per element (i, j), element index i * N + j.
+ * N * N <= 16.  Errors as wick_det_reduce.
+ */
+int wick_det_reduce_matrix(const wick_quark_operator *ops, int n_ops, uint64_t seed, int trials, wick_det_plan **out);
+/* out[7]: sink terms, source terms (antisymmetrised, summed over operators), |zeta_u|, |zeta_d|,
+ * Theta non-zeros (all elements), n_u * 8 + n_d, number of matrix elements */
 int wick_det_stats(const wick_det_plan *plan, int64_t *out);
+/* off[n_el + 1]: element e owns Theta entries [off[e], off[e + 1]) in wick_det_copy's order */
+int wick_det_element_offsets(const wick_det_plan *plan, int64_t *off);
 /* Copies Theta (k, l, weight) and the minimal sets to host arrays sized from
  * wick_det_stats (any pointer may be NULL): zu rows/cols [|zeta_u|][n_u],
  * zd rows/cols [|zeta_d|][n_d]. */
@@ -350,7 +362,8 @@ int wick_det_copy(const wick_det_plan *plan, int32_t *k, int32_t *l, int64_t *w,
 /*
  * wick_det_contract: G[src][t] for propagators Su, Sd (device, caller-owned,
  * complex64 or complex128; arithmetic in FP64) into C_out (device
- * complex128 [n_src][T]).  Asynchronous on `stream`; scratch from the
+ * complex128 [n_el][n_src][T], n_el = 1 for wick_det_reduce, N * N for a
+ * correlation matrix).  Asynchronous on `stream`; scratch from the
  * library's per-device workspace.  precision: WICK_FP64.
  * Errors: WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA.
  */

@@ -398,3 +398,19 @@ def antisymmetrised(table, n_u: int):
 def _perm_sign(x) -> int:
     inv = sum(1 for i in range(len(x)) for j in range(i + 1, len(x)) if x[i] > x[j])
     return -1 if inv % 2 else 1
+
+
+def deuteron_basis():
+    """Three 2H operators for a correlation matrix (Eqs. E1-E3): n^T (C g5 P+) p,
+    n^T (C g5 P-) p and n+^T (C g5 P+) p+ (nucleons projected with the paper's P+)."""
+    out = []
+    for gpar, npar in ((+1, 0), (-1, 0), (+1, +1)):
+        G = integer_matrix(cg5() @ paper_projector(gpar))
+        if npar:
+            tab = nucleon_table(cg5() @ paper_projector(npar), ALL_SPINS, ALL_SPINS)
+            nucs = [(U, tab), (D, tab)]
+        else:
+            nucs = plain_nucleons()
+        terms = [((NEUTRON, PROTON), (a, b), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b]]
+        out.append(grouped_operator(nucs, terms))
+    return out

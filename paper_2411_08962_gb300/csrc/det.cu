@@ -32,12 +32,14 @@
 struct wick_det_plan {
     int n_u = 0, n_d = 0, device = 0;
     int64_t n_snk = 0, n_src = 0, n_zu = 0, n_zd = 0, n_theta = 0;
+    int n_el = 1;                             // matrix elements (sink operator, source operator)
     int8_t *d_zu = nullptr, *d_zd = nullptr;  // [n][2][n_f]: rows (sink indices) then columns (source indices)
     int32_t *d_k = nullptr, *d_l = nullptr;
     double *d_w = nullptr;
+    int64_t *d_el_off = nullptr;              // Theta entries of element e: [el_off[e], el_off[e + 1])
     std::vector<int8_t> zu, zd;
     std::vector<int32_t> k, l;
-    std::vector<int64_t> w;
+    std::vector<int64_t> w, el_off;
 };
 
 namespace wick {
@@ -46,6 +48,7 @@ namespace {
 
 constexpr int kDetThreads = 256;
 constexpr int kDetChunk = 32;  // sites per work item
+constexpr int kMaxEl = 16;     // matrix elements (a 4 x 4 correlation matrix)
 constexpr uint64_t kP61 = (1ull << 61) - 1;
 
 // ---------------------------------------------------------------------------
@@ -210,14 +213,15 @@ __device__ __forceinline__ double2 det_small(const double2 *S, const int8_t *rc,
 }
 
 struct DetArgs {
-    int n_u, n_d;
-    int64_t n_zu, n_zd, n_theta;
+    int n_u, n_d, n_el;
+    int64_t n_zu, n_zd;
     const int8_t *zu, *zd;
     const int32_t *k, *l;
     const double *w;
+    const int64_t *el_off;
 };
 
-template <typename ST>
+template <typename ST, int MAXEL>
 __global__ void __launch_bounds__(kDetThreads)
 det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict__ Sd, int V, int n_slices,
                 int n_chunks, double2 *__restrict__ scratch, double2 *__restrict__ partials) {
@@ -230,7 +234,9 @@ det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int slice = (int)(it / n_chunks), chunk = (int)(it % n_chunks);
         const int x0 = chunk * kDetChunk, x1 = min(V, x0 + kDetChunk);
-        double2 acc = make_double2(0.0, 0.0);
+        double2 acc[MAXEL];
+#pragma unroll
+        for (int e = 0; e < MAXEL; ++e) acc[e] = make_double2(0.0, 0.0);
         for (int x = x0; x < x1; ++x) {
             __syncthreads();  // the previous site's determinants are consumed
             for (int e = tid; e < 288; e += kDetThreads) {
@@ -242,30 +248,42 @@ det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict
             for (int64_t q = tid; q < a.n_zu; q += kDetThreads) U[q] = det_small(sS[0], a.zu + q * 2 * a.n_u, a.n_u);
             for (int64_t q = tid; q < a.n_zd; q += kDetThreads) D[q] = det_small(sS[1], a.zd + q * 2 * a.n_d, a.n_d);
             __syncthreads();
-            for (int64_t e = tid; e < a.n_theta; e += kDetThreads) {
-                const double2 p = cmul(U[a.k[e]], D[a.l[e]]);
-                acc.x = fma(a.w[e], p.x, acc.x);
-                acc.y = fma(a.w[e], p.y, acc.y);
+            // the determinants are shared by every matrix element (Eq. E3)
+#pragma unroll
+            for (int el = 0; el < MAXEL; ++el) {
+                if (el >= a.n_el) break;
+                for (int64_t e = a.el_off[el] + tid; e < a.el_off[el + 1]; e += kDetThreads) {
+                    const double2 p = cmul(U[a.k[e]], D[a.l[e]]);
+                    acc[el].x = fma(a.w[e], p.x, acc[el].x);
+                    acc[el].y = fma(a.w[e], p.y, acc[el].y);
+                }
             }
         }
-        // fixed-order block reduction of the chunk's sum
-        red[tid] = acc;
-        __syncthreads();
-        for (int s = kDetThreads / 2; s > 0; s >>= 1) {
-            if (tid < s) red[tid] = cadd(red[tid], red[tid + s]);
+        // fixed-order block reduction of the chunk's sums
+#pragma unroll
+        for (int el = 0; el < MAXEL; ++el) {
+            if (el >= a.n_el) break;
+            red[tid] = acc[el];
+            __syncthreads();
+            for (int s = kDetThreads / 2; s > 0; s >>= 1) {
+                if (tid < s) red[tid] = cadd(red[tid], red[tid + s]);
+                __syncthreads();
+            }
+            if (tid == 0) partials[((size_t)slice * n_chunks + chunk) * a.n_el + el] = red[0];
             __syncthreads();
         }
-        if (tid == 0) partials[(size_t)slice * n_chunks + chunk] = red[0];
     }
 }
 
-__global__ void det_finish_kernel(const double2 *__restrict__ partials, int n_slices, int n_chunks, double scale,
-                                  double2 *__restrict__ out) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_slices) return;
+// out[el][slice] = scale * sum over chunks (fixed order)
+__global__ void det_finish_kernel(const double2 *__restrict__ partials, int n_slices, int n_chunks, int n_el,
+                                  double scale, double2 *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_slices * n_el) return;
+    const int el = i / n_slices, s = i % n_slices;
     double2 acc = make_double2(0.0, 0.0);
-    for (int c = 0; c < n_chunks; ++c) acc = cadd(acc, partials[(size_t)s * n_chunks + c]);
-    out[s] = make_double2(scale * acc.x, scale * acc.y);
+    for (int c = 0; c < n_chunks; ++c) acc = cadd(acc, partials[((size_t)s * n_chunks + c) * n_el + el]);
+    out[i] = make_double2(scale * acc.x, scale * acc.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -306,18 +324,6 @@ int antisymmetrise(const wick_quark_operator *op, Antisym &out) {
     for (auto it = out.terms.begin(); it != out.terms.end();)
         it = it->second == 0 ? out.terms.erase(it) : std::next(it);
     return WICK_OK;
-}
-
-// distinct index sets of one flavour, in increasing order, and the set id of every term
-void set_ids(const Antisym &A, bool d_part, std::vector<Key> &sets, std::vector<int> &ids) {
-    std::map<Key, int> idx;
-    for (auto &kv : A.terms) idx.emplace(d_part ? kv.first.second : kv.first.first, 0);
-    int i = 0;
-    for (auto &kv : idx) {
-        kv.second = i++;
-        sets.push_back(kv.first);
-    }
-    for (auto &kv : A.terms) ids.push_back(idx[d_part ? kv.first.second : kv.first.first]);
 }
 
 struct Classes {
@@ -419,6 +425,7 @@ void free_plan(wick_det_plan *p) {
     cudaFree(p->d_k);
     cudaFree(p->d_l);
     cudaFree(p->d_w);
+    cudaFree(p->d_el_off);
     delete p;
 }
 
@@ -442,75 +449,113 @@ using namespace wick;
 
 extern "C" {
 
-int wick_det_reduce(const wick_quark_operator *sink, const wick_quark_operator *source, uint64_t seed, int trials,
-                    wick_det_plan **out) {
-    if (!out || !sink || !source || trials < 1 || trials > 8) return WICK_EINVAL;
+}  // extern "C"
+
+namespace wick {
+namespace {
+
+// Minimal sets shared by the elements (i, j) of sinks x sources (Eq. E3) and one Theta per element.
+int reduce_matrix(const wick_quark_operator *const *snk, int n_snk_ops, const wick_quark_operator *const *src,
+                  int n_src_ops, uint64_t seed, int trials, wick_det_plan **out) {
+    if (!out || n_snk_ops < 1 || n_src_ops < 1 || n_snk_ops * n_src_ops > kMaxEl || trials < 1 || trials > 8)
+        return WICK_EINVAL;
     *out = nullptr;
-    if (sink->n_u != source->n_u || sink->n_d != source->n_d) return WICK_EINVAL;
-    Antisym As, Aq;
-    int err = antisymmetrise(sink, As);
-    if (!err) err = antisymmetrise(source, Aq);
+    for (int i = 0; i < n_snk_ops; ++i)
+        if (!snk[i]) return WICK_EINVAL;
+    for (int j = 0; j < n_src_ops; ++j)
+        if (!src[j]) return WICK_EINVAL;
+    const int nu = snk[0]->n_u, nd = snk[0]->n_d;
+    for (int i = 0; i < n_snk_ops; ++i)
+        if (snk[i]->n_u != nu || snk[i]->n_d != nd) return WICK_EINVAL;
+    for (int j = 0; j < n_src_ops; ++j)
+        if (src[j]->n_u != nu || src[j]->n_d != nd) return WICK_EINVAL;
+    std::vector<Antisym> As(n_snk_ops), Aq(n_src_ops);
+    int err = WICK_OK;
+    for (int i = 0; i < n_snk_ops && !err; ++i) err = antisymmetrise(snk[i], As[i]);
+    for (int j = 0; j < n_src_ops && !err; ++j) err = antisymmetrise(src[j], Aq[j]);
     if (err) return err;
-    const int nu = sink->n_u, nd = sink->n_d;
+    // distinct index sets over all sink operators and over all source operators
+    auto union_sets = [](const std::vector<Antisym> &ops, bool d_part, std::vector<Key> &sets,
+                         std::vector<std::vector<int>> &ids) {
+        std::map<Key, int> idx;
+        for (auto &A : ops)
+            for (auto &kv : A.terms) idx.emplace(d_part ? kv.first.second : kv.first.first, 0);
+        int i = 0;
+        for (auto &kv : idx) {
+            kv.second = i++;
+            sets.push_back(kv.first);
+        }
+        ids.resize(ops.size());
+        for (size_t o = 0; o < ops.size(); ++o)
+            for (auto &kv : ops[o].terms) ids[o].push_back(idx[d_part ? kv.first.second : kv.first.first]);
+    };
     std::vector<Key> su, sd, qu, qd;
-    std::vector<int> isu, isd, iqu, iqd;
-    set_ids(As, false, su, isu);
-    set_ids(As, true, sd, isd);
-    set_ids(Aq, false, qu, iqu);
-    set_ids(Aq, true, qd, iqd);
+    std::vector<std::vector<int>> isu, isd, iqu, iqd;
+    union_sets(As, false, su, isu);
+    union_sets(As, true, sd, isd);
+    union_sets(Aq, false, qu, iqu);
+    union_sets(Aq, true, qd, iqd);
     if ((int64_t)su.size() * (int64_t)qu.size() > (1ll << 30) || (int64_t)sd.size() * (int64_t)qd.size() > (1ll << 30))
         return WICK_EINVAL;
     Classes cu, cd;
     err = classify(su, qu, nu, seed, trials, 0, cu);
     if (!err) err = classify(sd, qd, nd, seed, trials, 1, cd);
     if (err) return err;
-    // Theta: every (M, M') -> (class_u, class_d), merged by sorting (key, weight)
-    std::vector<int64_t> ws, wq;
-    for (auto &kv : As.terms) ws.push_back(kv.second);
-    for (auto &kv : Aq.terms) wq.push_back(kv.second);
-    const int64_t n_cd = (int64_t)cd.rep.size();
-    std::vector<std::pair<int64_t, int64_t>> acc;
-    acc.reserve(ws.size() * wq.size());
-    for (size_t a = 0; a < ws.size(); ++a)
-        for (size_t b = 0; b < wq.size(); ++b) {
-            const int64_t ca = (int64_t)isu[a] * (int64_t)qu.size() + iqu[b];
-            const int64_t cb = (int64_t)isd[a] * (int64_t)qd.size() + iqd[b];
-            const int ku = cu.cls[ca], kd = cd.cls[cb];
-            if (ku < 0 || kd < 0) continue;
-            acc.push_back({(int64_t)ku * n_cd + kd, ws[a] * wq[b] * cu.sign[ca] * cd.sign[cb]});
-        }
-    std::sort(acc.begin(), acc.end(), [](const std::pair<int64_t, int64_t> &x, const std::pair<int64_t, int64_t> &y) {
-        return x.first < y.first;
-    });
     wick_det_plan *p = new (std::nothrow) wick_det_plan();
     if (!p) return WICK_ENOMEM;
     p->n_u = nu;
     p->n_d = nd;
-    p->n_snk = (int64_t)ws.size();
-    p->n_src = (int64_t)wq.size();
+    p->n_el = n_snk_ops * n_src_ops;
     cudaGetDevice(&p->device);
-    for (size_t i = 0; i < acc.size();) {
-        size_t j = i;
-        int64_t sum = 0;
-        for (; j < acc.size() && acc[j].first == acc[i].first; ++j) sum += acc[j].second;
-        if (sum != 0) {
-            if (sum >= (1ll << 53) || sum <= -(1ll << 53)) {
-                free_plan(p);
-                return WICK_EOVERFLOW;
+    for (auto &A : As) p->n_snk += (int64_t)A.terms.size();
+    for (auto &A : Aq) p->n_src += (int64_t)A.terms.size();
+    const int64_t n_cd = (int64_t)cd.rep.size();
+    p->el_off.push_back(0);
+    std::vector<std::pair<int64_t, int64_t>> acc;
+    for (int i = 0; i < n_snk_ops; ++i)
+        for (int j = 0; j < n_src_ops; ++j) {
+            // Theta of element (i, j): every (M, M') -> (class_u, class_d), merged by sorting
+            std::vector<int64_t> ws, wq;
+            for (auto &kv : As[i].terms) ws.push_back(kv.second);
+            for (auto &kv : Aq[j].terms) wq.push_back(kv.second);
+            acc.clear();
+            acc.reserve(ws.size() * wq.size());
+            for (size_t a = 0; a < ws.size(); ++a)
+                for (size_t b = 0; b < wq.size(); ++b) {
+                    const int64_t ca = (int64_t)isu[i][a] * (int64_t)qu.size() + iqu[j][b];
+                    const int64_t cb = (int64_t)isd[i][a] * (int64_t)qd.size() + iqd[j][b];
+                    const int ku = cu.cls[ca], kd = cd.cls[cb];
+                    if (ku < 0 || kd < 0) continue;
+                    acc.push_back({(int64_t)ku * n_cd + kd, ws[a] * wq[b] * cu.sign[ca] * cd.sign[cb]});
+                }
+            std::sort(acc.begin(), acc.end(),
+                      [](const std::pair<int64_t, int64_t> &x, const std::pair<int64_t, int64_t> &y) {
+                          return x.first < y.first;
+                      });
+            for (size_t a = 0; a < acc.size();) {
+                size_t b = a;
+                int64_t sum = 0;
+                for (; b < acc.size() && acc[b].first == acc[a].first; ++b) sum += acc[b].second;
+                if (sum != 0) {
+                    if (sum >= (1ll << 53) || sum <= -(1ll << 53)) {
+                        free_plan(p);
+                        return WICK_EOVERFLOW;
+                    }
+                    p->k.push_back((int32_t)(acc[a].first / n_cd));
+                    p->l.push_back((int32_t)(acc[a].first % n_cd));
+                    p->w.push_back(sum);
+                }
+                a = b;
             }
-            p->k.push_back((int32_t)(acc[i].first / n_cd));
-            p->l.push_back((int32_t)(acc[i].first % n_cd));
-            p->w.push_back(sum);
+            p->el_off.push_back((int64_t)p->w.size());
         }
-        i = j;
-    }
     // the minimal sets as (rows, columns) of each representative
-    auto pack = [](const Classes &c, const std::vector<Key> &snk, const std::vector<Key> &src, int n,
+    auto pack = [](const Classes &c, const std::vector<Key> &rs, const std::vector<Key> &cs, int n,
                    std::vector<int8_t> &dst) {
         for (int64_t r : c.rep) {
-            const int64_t i = src.empty() ? 0 : r / (int64_t)src.size(), j = src.empty() ? 0 : r % (int64_t)src.size();
-            for (int q = 0; q < n; ++q) dst.push_back(snk[i][q]);
-            for (int q = 0; q < n; ++q) dst.push_back(src[j][q]);
+            const int64_t i = cs.empty() ? 0 : r / (int64_t)cs.size(), j = cs.empty() ? 0 : r % (int64_t)cs.size();
+            for (int q = 0; q < n; ++q) dst.push_back(rs[i][q]);
+            for (int q = 0; q < n; ++q) dst.push_back(cs[j][q]);
         }
     };
     pack(cu, su, qu, nu, p->zu);
@@ -524,12 +569,31 @@ int wick_det_reduce(const wick_quark_operator *sink, const wick_quark_operator *
     if (!err) err = upload(&p->d_k, p->k);
     if (!err) err = upload(&p->d_l, p->l);
     if (!err) err = upload(&p->d_w, wd);
+    if (!err) err = upload(&p->d_el_off, p->el_off);
     if (err) {
         free_plan(p);
         return err;
     }
     *out = p;
     return WICK_OK;
+}
+
+}  // namespace
+}  // namespace wick
+
+extern "C" {
+
+int wick_det_reduce(const wick_quark_operator *sink, const wick_quark_operator *source, uint64_t seed, int trials,
+                    wick_det_plan **out) {
+    if (!sink || !source) return WICK_EINVAL;
+    return reduce_matrix(&sink, 1, &source, 1, seed, trials, out);
+}
+
+int wick_det_reduce_matrix(const wick_quark_operator *ops, int n_ops, uint64_t seed, int trials, wick_det_plan **out) {
+    if (!ops || n_ops < 1 || n_ops * n_ops > kMaxEl) return WICK_EINVAL;
+    std::vector<const wick_quark_operator *> v(n_ops);
+    for (int i = 0; i < n_ops; ++i) v[i] = &ops[i];
+    return reduce_matrix(v.data(), n_ops, v.data(), n_ops, seed, trials, out);
 }
 
 int wick_det_stats(const wick_det_plan *p, int64_t *out) {
@@ -540,6 +604,13 @@ int wick_det_stats(const wick_det_plan *p, int64_t *out) {
     out[3] = p->n_zd;
     out[4] = p->n_theta;
     out[5] = p->n_u * 8 + p->n_d;
+    out[6] = p->n_el;
+    return WICK_OK;
+}
+
+int wick_det_element_offsets(const wick_det_plan *p, int64_t *off) {
+    if (!p || !off) return WICK_EINVAL;
+    std::copy(p->el_off.begin(), p->el_off.end(), off);
     return WICK_OK;
 }
 
@@ -576,38 +647,43 @@ int wick_det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_det_p
     if (V > (1 << 24) || n_slices > (1 << 24)) return WICK_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     if (plan->n_theta == 0) {
-        WICK_CUDA_TRY(cudaMemsetAsync(C_out, 0, sizeof(double2) * n_slices, st));
+        WICK_CUDA_TRY(cudaMemsetAsync(C_out, 0, sizeof(double2) * n_slices * plan->n_el, st));
         return WICK_OK;
     }
     const int n_chunks = (int)((V + kDetChunk - 1) / kDetChunk);
     const int64_t items = n_slices * n_chunks;
     int n_sm = 0, occ = 0;
     WICK_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    if (Su->dtype == WICK_C64)
-        WICK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, det_eval_kernel<float2>, kDetThreads, 0));
-    else
-        WICK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, det_eval_kernel<double2>, kDetThreads, 0));
+    const bool one = plan->n_el == 1;
+    const bool c64 = Su->dtype == WICK_C64;
+    const void *kern = c64 ? (one ? (const void *)det_eval_kernel<float2, 1> : (const void *)det_eval_kernel<float2, kMaxEl>)
+                           : (one ? (const void *)det_eval_kernel<double2, 1> : (const void *)det_eval_kernel<double2, kMaxEl>);
+    WICK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDetThreads, 0));
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(occ, 1)));
     const size_t scratch_bytes = sizeof(double2) * (size_t)grid * (size_t)(plan->n_zu + plan->n_zd);
-    const size_t part_bytes = sizeof(double2) * (size_t)items;
+    const size_t part_bytes = sizeof(double2) * (size_t)items * plan->n_el;
     int err = WICK_OK;
     unsigned char *ws = (unsigned char *)workspace(2, scratch_bytes + part_bytes + 256, &err);
     if (err) return err;
     double2 *scratch = (double2 *)ws;
     double2 *partials = (double2 *)(ws + (scratch_bytes + 255) / 256 * 256);
-    DetArgs a{plan->n_u, plan->n_d, plan->n_zu, plan->n_zd, plan->n_theta, plan->d_zu, plan->d_zd,
-              plan->d_k, plan->d_l, plan->d_w};
-    if (Su->dtype == WICK_C64)
-        det_eval_kernel<float2><<<(unsigned)grid, kDetThreads, 0, st>>>(a, (const float2 *)Su->data,
-                                                                       (const float2 *)Sd->data, (int)V, (int)n_slices,
-                                                                       n_chunks, scratch, partials);
-    else
-        det_eval_kernel<double2><<<(unsigned)grid, kDetThreads, 0, st>>>(a, (const double2 *)Su->data,
-                                                                        (const double2 *)Sd->data, (int)V,
-                                                                        (int)n_slices, n_chunks, scratch, partials);
+    DetArgs a{plan->n_u, plan->n_d, plan->n_el, plan->n_zu, plan->n_zd, plan->d_zu, plan->d_zd,
+              plan->d_k, plan->d_l, plan->d_w, plan->d_el_off};
+    const unsigned g = (unsigned)grid;
+    const int iv = (int)V, is = (int)n_slices;
+    if (c64) {
+        const float2 *u = (const float2 *)Su->data, *d = (const float2 *)Sd->data;
+        if (one) det_eval_kernel<float2, 1><<<g, kDetThreads, 0, st>>>(a, u, d, iv, is, n_chunks, scratch, partials);
+        else det_eval_kernel<float2, kMaxEl><<<g, kDetThreads, 0, st>>>(a, u, d, iv, is, n_chunks, scratch, partials);
+    } else {
+        const double2 *u = (const double2 *)Su->data, *d = (const double2 *)Sd->data;
+        if (one) det_eval_kernel<double2, 1><<<g, kDetThreads, 0, st>>>(a, u, d, iv, is, n_chunks, scratch, partials);
+        else det_eval_kernel<double2, kMaxEl><<<g, kDetThreads, 0, st>>>(a, u, d, iv, is, n_chunks, scratch, partials);
+    }
     WICK_CUDA_TRY(cudaGetLastError());
-    det_finish_kernel<<<(unsigned)((n_slices + 127) / 128), 128, 0, st>>>(partials, (int)n_slices, n_chunks, scale,
-                                                                          (double2 *)C_out);
+    const int64_t n_out = n_slices * plan->n_el;
+    det_finish_kernel<<<(unsigned)((n_out + 127) / 128), 128, 0, st>>>(partials, (int)n_slices, n_chunks,
+                                                                       plan->n_el, scale, (double2 *)C_out);
     WICK_CUDA_TRY(cudaGetLastError());
     return WICK_OK;
 }

@@ -292,3 +292,21 @@ def point_operator(name: str) -> QuarkOperator:
     chi = np.array([c for c, _ in table], dtype=np.int8).reshape(len(table), len(flav))
     w = np.array([x for _, x in table], dtype=np.int64)
     return QuarkOperator(name, n_u, len(flav) - n_u, chi, w, scale)
+
+
+def deuteron_basis():
+    """[n^T (C g5 P+) p, n^T (C g5 P-) p, n+^T (C g5 P+) p+]: three 2H point operators
+    (the paper's P+-) for a correlation matrix (Eqs. E1-E3)."""
+    sp = (0, 1, 2, 3)
+    out = []
+    for name, gpar, npar in (("2H P+", -1, 0), ("2H P-", +1, 0), ("2H P+ projected", -1, -1)):
+        Gp = diquark_matrix(gpar)
+        nuc_gamma = diquark_matrix(npar) if npar else diquark_matrix()
+        ops = [nucleon_op(U, nuc_gamma, sp, sp), nucleon_op(D, nuc_gamma, sp, sp)]
+        terms = [((NEUTRON, PROTON), (a, b), int(Gp[a, b])) for a in range(4) for b in range(4) if Gp[a, b]]
+        table, flav = _flavour_grouped(ops, terms)
+        n_u = sum(1 for f in flav if f == U)
+        chi = np.array([c for c, _ in table], dtype=np.int8).reshape(len(table), len(flav))
+        w = np.array([x for _, x in table], dtype=np.int64)
+        out.append(QuarkOperator(name, n_u, len(flav) - n_u, chi, w, 1.0))
+    return out

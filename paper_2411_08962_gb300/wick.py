@@ -28,8 +28,8 @@ EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_reduce_terms", "wick_t
            "wick_terms_nucleons", "wick_terms_copy", "wick_terms_stats", "wick_terms_select",
            "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_contract_noalloc",
            "wick_status", "wick_batch_create", "wick_batch_run", "wick_batch_launches", "wick_batch_free",
-           "wick_synth_propagator", "wick_cluster_product", "wick_det_reduce", "wick_det_stats", "wick_det_copy",
-           "wick_det_contract", "wick_det_free", "wick_strerror", "wick_version")
+           "wick_synth_propagator", "wick_cluster_product", "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats",
+           "wick_det_element_offsets", "wick_det_copy", "wick_det_contract", "wick_det_free", "wick_strerror", "wick_version")
 
 
 class WickError(RuntimeError):
@@ -104,7 +104,9 @@ def load(path: str = LIB_PATH):
             L.wick_synth_propagator.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
             L.wick_cluster_product.argtypes = [vp, vp, C.c_int64, vp, vp]
             L.wick_det_reduce.argtypes = [P(wick_quark_operator), P(wick_quark_operator), C.c_uint64, C.c_int, P(vp)]
+            L.wick_det_reduce_matrix.argtypes = [P(wick_quark_operator), C.c_int, C.c_uint64, C.c_int, P(vp)]
             L.wick_det_stats.argtypes = [vp, P(C.c_int64)]
+            L.wick_det_element_offsets.argtypes = [vp, P(C.c_int64)]
             L.wick_det_copy.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
             L.wick_det_contract.argtypes = [P(wick_prop), P(wick_prop), vp, C.c_double, C.c_int, vp, vp]
             L.wick_det_free.argtypes = [vp]
@@ -116,7 +118,8 @@ def load(path: str = LIB_PATH):
                       "wick_terms_stats", "wick_terms_select", "wick_terms_save", "wick_terms_load",
                       "wick_contract", "wick_contract_noalloc", "wick_status", "wick_batch_create",
                       "wick_batch_run", "wick_batch_launches", "wick_synth_propagator", "wick_cluster_product",
-                      "wick_det_reduce", "wick_det_stats", "wick_det_copy", "wick_det_contract"):
+                      "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats", "wick_det_element_offsets",
+                      "wick_det_copy", "wick_det_contract"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -343,20 +346,33 @@ def _quark_op(q):
 class DetPlan:
     """Library-owned minimal sets zeta_u, zeta_d and Theta of a point-sink operator pair (wick_det_reduce)."""
 
-    def __init__(self, sink, source=None, seed: int = 0x2411D7, trials: int = 2):
-        source = sink if source is None else source
-        a, keep_a = _quark_op(sink)
-        b, keep_b = _quark_op(source)
+    def __init__(self, sink, source=None, seed: int = 0x2411D7, trials: int = 2, matrix=None):
+        """One correlator (sink, source), or with `matrix` = [O_1 .. O_N] the N x N correlation matrix."""
         h = C.c_void_p()
-        _check(load().wick_det_reduce(C.byref(a), C.byref(b), seed, trials, C.byref(h)), "wick_det_reduce")
+        if matrix is not None:
+            ops = [_quark_op(q) for q in matrix]
+            arr = (wick_quark_operator * len(ops))(*[o[0] for o in ops])
+            _check(load().wick_det_reduce_matrix(arr, len(ops), seed, trials, C.byref(h)), "wick_det_reduce_matrix")
+            self.scale = float(getattr(matrix[0], "scale", 1.0))
+        else:
+            source = sink if source is None else source
+            a, keep_a = _quark_op(sink)
+            b, keep_b = _quark_op(source)
+            _check(load().wick_det_reduce(C.byref(a), C.byref(b), seed, trials, C.byref(h)), "wick_det_reduce")
+            self.scale = float(getattr(sink, "scale", 1.0))
         self.h = h
-        self.scale = float(getattr(sink, "scale", 1.0))
 
     def stats(self) -> dict:
-        out = (C.c_int64 * 6)()
+        out = (C.c_int64 * 7)()
         _check(load().wick_det_stats(self.h, out), "wick_det_stats")
         return dict(n_sink=out[0], n_source=out[1], zeta_u=out[2], zeta_d=out[3], theta=out[4],
-                    n_u=out[5] // 8, n_d=out[5] % 8)
+                    n_u=out[5] // 8, n_d=out[5] % 8, n_el=out[6])
+
+    def element_offsets(self) -> np.ndarray:
+        off = np.zeros(self.stats()["n_el"] + 1, np.int64)
+        _check(load().wick_det_element_offsets(self.h, off.ctypes.data_as(C.POINTER(C.c_int64))),
+               "wick_det_element_offsets")
+        return off
 
     def copy(self) -> dict:
         st = self.stats()
@@ -386,7 +402,8 @@ class DetPlan:
 
 def wick_det_contract(Su, Sd, plan: DetPlan, C_out, L: int, T: int, n_src: int, scale=None,
                       precision: int = WICK_FP64, stream=None):
-    """C_out[src][t] (torch complex128 CUDA tensor) = point-sink correlator of the plan."""
+    """C_out[el][src][t] (torch complex128 CUDA tensor; el = i * N + j for a matrix plan, one element
+    otherwise) = point-sink correlators of the plan."""
     def prop(S):
         dt = WICK_C64 if str(S.dtype) == "torch.complex64" else WICK_C128
         return wick_prop(_ptr(S), L, T, n_src, dt)

@@ -94,3 +94,62 @@ def test_invalid_operator_rejected():
         wick.DetPlan(bad)
     with pytest.raises(wick.WickError):
         wick.DetPlan(q, operators.point_operator("he3"))   # different quark content
+
+
+def basis_plan():
+    if "basis" not in _PLANS:
+        _PLANS["basis"] = wick.DetPlan(None, matrix=operators.deuteron_basis())
+    return _PLANS["basis"]
+
+
+def gpu_matrix(Su, Sd):
+    n_src, T, V = Su.shape[:3]
+    L = round(V ** (1 / 3))
+    p = basis_plan()
+    n_el = p.stats()["n_el"]
+    out = torch.empty((n_el, n_src, T), dtype=torch.complex128, device="cuda")
+    wick.wick_det_contract(torch.from_numpy(np.ascontiguousarray(Su)).cuda(),
+                           torch.from_numpy(np.ascontiguousarray(Sd)).cuda(), p, out, L, T, n_src)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_correlation_matrix_matches_oracle():
+    """C_ij = <O_i(t) Obar_j(0)> for the three 2H operators (Eq. E3), every element."""
+    from oracle import operators as oops
+    basis = oops.deuteron_basis()
+    Su, Sd = props(2, 2, 1, seed=0xD39)
+    got = gpu_matrix(Su, Sd)
+    assert got.shape[0] == 9
+    for i, (ti, _) in enumerate(basis):
+        for j, (tj, _) in enumerate(basis):
+            ref = DT.point_correlator(Su, Sd, ti, tj, 3, 3)
+            assert np.max(np.abs(got[3 * i + j] - ref) / np.abs(ref)) < FP64_TOL
+
+
+def test_correlation_matrix_shares_determinants():
+    """One minimal set for all nine elements; each element's Theta is the pair's, bit-exact."""
+    from oracle import operators as oops
+    basis = oops.deuteron_basis()
+    p = basis_plan()
+    c, off = p.copy(), p.element_offsets()
+    gu = [(tuple(r), tuple(q)) for r, q in zip(c["zu_rows"].tolist(), c["zu_cols"].tolist())]
+    gd = [(tuple(r), tuple(q)) for r, q in zip(c["zd_rows"].tolist(), c["zd_cols"].tolist())]
+    union_u, union_d = set(), set()
+    for i, (ti, _) in enumerate(basis):
+        for j, (tj, _) in enumerate(basis):
+            zu, zd, th = DT.minimal_sets(ti, tj, 3)
+            union_u |= {zu[k] for k, _ in th}
+            union_d |= {zd[l] for _, l in th}
+            e0, e1 = off[3 * i + j], off[3 * i + j + 1]
+            got = {(gu[k], gd[l]): w for k, l, w in zip(c["k"][e0:e1].tolist(), c["l"][e0:e1].tolist(),
+                                                         c["w"][e0:e1].tolist())}
+            assert got == {(zu[k], zd[l]): w for (k, l), w in th.items()}
+    assert set(gu) == union_u and set(gd) == union_d
+
+
+def test_matrix_diagonal_equals_single_correlator():
+    Su, Sd = props(3, 1, 1, seed=0xD3A)
+    got = gpu_matrix(Su, Sd)
+    single = gpu_point("deuteron", Su, Sd)   # n^T (C g5 P+) p
+    assert np.max(np.abs(got[0] - single) / np.abs(single)) < 1e-13

@@ -174,3 +174,19 @@ def test_minimal_set_reduced_sum_equals_term_sum():
     reduced = sum(w * du[k] % P * dd[l] for (k, l), w in th.items()) % P
     terms = sum(int(w) * du[k] % P * dd[l] for k, l, w in zip(st["t_pu"], st["t_pd"], st["t_w"])) % P
     assert reduced == terms
+
+
+def test_cross_pair_point_sink_equals_plain_wick_sum_on_one_site():
+    """A correlation-matrix element with different sink and source operators (Eq. E3):
+    n^T (C g5 P+) p at the sink, n+^T (C g5 P+) p+ at the source, against the plane-wave
+    oracle's raw Wick sum with both nucleon kinds as block types, V = 1."""
+    (t1, fl1), _, (t3, fl3) = ops.deuteron_basis()
+    tab = ops.nucleon_table(ops.cg5() @ ops.paper_projector(+1), ops.ALL_SPINS, ops.ALL_SPINS)
+    o4 = ops.plain_nucleons() + [(ops.U, tab), (ops.D, tab)]     # p, n, p+, n+
+    G = ops.integer_matrix(ops.cg5() @ ops.paper_projector(+1))
+    sink = sorted(((ops.NEUTRON, ops.PROTON), (a, b), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b])
+    nuc = dict(A=2, ops=o4, n_spin=4, chi=list(range(12)), sink=sink, src=t3, src_flav=fl3, scale=1.0)
+    Su, Sd = props(1, 2, seed=17)
+    gp = DT.point_correlator(Su, Sd, t1, t3, 3, 3)
+    graw = O.correlator(Su, Sd, nuc)
+    assert np.max(np.abs(gp - graw) / np.abs(graw)) < 1e-13
