@@ -92,7 +92,7 @@ template <int NC_, int NS_, int NT_, int NMT_, int NX_> struct Shape {
     static constexpr int A_BYTES = NMT * 128 * KC * 2;
     static constexpr int B_BYTES = kSlicesX * NT * KC * 2;
     static constexpr int S_BYTES = NX * kMaxRows * NC * 8;  // float2 staging
-    static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES + 4 * (16 + 256) + 32;
+    static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES + 4 * (16 + 256) + 16 * kKa * 4 + 64 + 32;
     static_assert(NMT * 128 >= kSlices * R && (NMT - 1) * 128 < kSlices * R, "M tiles");
     static_assert(NC2 <= NT || NC2 % NT == 0, "column tiles");
     static_assert(TMEM_USED <= 512 && CW % 4 == 0 && CW <= 32, "TMEM / readout");
@@ -248,24 +248,29 @@ __device__ __forceinline__ void slice_x2(f2x h, f2x l, float sc, uint32_t *w) {
     }
 }
 
-constexpr int kListMax = 4;  // terms per diquark list the tensor-core path takes
+constexpr int kListLen = 4;  // terms per diquark list the tensor-core path takes (exactly)
 
-// double-FP32 list sum X_{o,a}[c23] of one staged site (lanes re, im)
-__device__ __forceinline__ pdf x_value(const BlockPlan &plan, const float2 *s1, const float2 *s2, int l, int nc) {
+// double-FP32 list sum X_{o,a}[c23] of one staged site (lanes re, im).  term[t] = (row2 * NC,
+// row3 * NC, weight bits): the list's terms, staged in shared memory; all loads first.
+__device__ __forceinline__ pdf x_value(const int4 *term, const float2 *s1, const float2 *s2) {
+    int4 tt[kListLen];
+#pragma unroll
+    for (int t = 0; t < kListLen; ++t) tt[t] = term[t];
+    float2 u[kListLen], d[kListLen];
+#pragma unroll
+    for (int t = 0; t < kListLen; ++t) {
+        u[t] = s1[tt[t].x];
+        d[t] = s2[tt[t].y];
+    }
     pdf va, vb;
     va.h = va.l = vb.h = vb.l = 0ull;
-    const int q0 = plan.x_off[l], len = plan.x_off[l + 1] - q0;
 #pragma unroll
-    for (int t = 0; t < kListMax; ++t) {
-        if (t < len) {
-            const float2 u = s1[plan.xt_r2[q0 + t] * nc];
-            const float2 d = s2[plan.xt_r3[q0 + t] * nc];
-            const float w = plan.xt_w[q0 + t];
-            const float ax = w * u.x, ay = w * u.y;  // exact: w is +-2^k
-            const f2x Bd = pk(d.x, d.y);
-            pacc_exact(va, pk(ax, ax), pk(-ax, -ax), Bd);
-            pacc_exact(vb, pk(ay, -ay), pk(-ay, ay), Bd);
-        }
+    for (int t = 0; t < kListLen; ++t) {
+        const float w = __int_as_float(tt[t].z);
+        const float ax = w * u[t].x, ay = w * u[t].y;  // exact: w is +-2^k
+        const f2x Bd = pk(d[t].x, d[t].y);
+        pacc_exact(va, pk(ax, ax), pk(-ax, -ax), Bd);
+        pacc_exact(vb, pk(ay, -ay), pk(-ay, ay), Bd);
     }
     return padd(va, pdf{swap2(vb.h), swap2(vb.l)});
 }
@@ -288,8 +293,8 @@ template <typename SH> __device__ __forceinline__ void x_map(int jb, int &n, int
 
 // X job jb: column n, combo gc = (site, a); 6 slices into B_j[n][(site, a, part)]
 template <typename SH>
-__device__ __forceinline__ void x_job(const BlockPlan &plan, const float2 *S, int nr, int off1, int off2, int col0,
-                                      int t0, int n_a, const int *sF, __nv_bfloat16 *B, int jb) {
+__device__ __forceinline__ void x_job(const int4 *sTerm, const float2 *S, int nr, int off1, int off2, int col0,
+                                      int n_a, const int *sF, __nv_bfloat16 *B, int jb) {
     constexpr int NC = SH::NC, NT = SH::NT;
     int n, gc;
     x_map<SH>(jb, n, gc);
@@ -297,8 +302,8 @@ __device__ __forceinline__ void x_job(const BlockPlan &plan, const float2 *S, in
     uint32_t w[kSlicesX];
     if (a < n_a) {
         const int c23 = col0 + n;
-        const pdf X = x_value(plan, S + site * nr * NC + off1 + c23 / NC, S + site * nr * NC + off2 + c23 % NC,
-                              plan.os_x[t0 + a], NC);
+        const pdf X = x_value(sTerm + a * kListLen, S + site * nr * NC + off1 + c23 / NC,
+                              S + site * nr * NC + off2 + c23 % NC);
         slice_x2(X.h, X.l, exp2i(7 - sF[n]), w);
     } else {
 #pragma unroll
@@ -311,8 +316,8 @@ __device__ __forceinline__ void x_job(const BlockPlan &plan, const float2 *S, in
 
 // two X jobs with independent chains (both jA, jB < NXJOB)
 template <typename SH>
-__device__ __forceinline__ void x_job2(const BlockPlan &plan, const float2 *S, int nr, int off1, int off2, int col0,
-                                       int t0, int n_a, const int *sF, __nv_bfloat16 *B, int jA, int jB) {
+__device__ __forceinline__ void x_job2(const int4 *sTerm, const float2 *S, int nr, int off1, int off2, int col0,
+                                       int n_a, const int *sF, __nv_bfloat16 *B, int jA, int jB) {
     constexpr int NC = SH::NC, NT = SH::NT;
     int nA, gA, nB, gB;
     x_map<SH>(jA, nA, gA);
@@ -320,9 +325,8 @@ __device__ __forceinline__ void x_job2(const BlockPlan &plan, const float2 *S, i
     const int aA = gA % kKa, aB = gB % kKa;
     const int cA = col0 + nA, cB = col0 + nB;
     const float2 *bA = S + (gA / kKa) * nr * NC, *bB = S + (gB / kKa) * nr * NC;
-    const int lA = plan.os_x[t0 + (aA < n_a ? aA : 0)], lB = plan.os_x[t0 + (aB < n_a ? aB : 0)];
-    pdf XA = x_value(plan, bA + off1 + cA / NC, bA + off2 + cA % NC, lA, NC);
-    pdf XB = x_value(plan, bB + off1 + cB / NC, bB + off2 + cB % NC, lB, NC);
+    pdf XA = x_value(sTerm + (aA < n_a ? aA : 0) * kListLen, bA + off1 + cA / NC, bA + off2 + cA % NC);
+    pdf XB = x_value(sTerm + (aB < n_a ? aB : 0) * kListLen, bB + off1 + cB / NC, bB + off2 + cB % NC);
     if (aA >= n_a) XA.h = XA.l = 0ull;
     if (aB >= n_a) XB.h = XB.l = 0ull;
     uint32_t wA[kSlicesX], wB[kSlicesX];
@@ -338,8 +342,8 @@ __device__ __forceinline__ void x_job2(const BlockPlan &plan, const float2 *S, i
 
 // U job ju: row (s, c1), combos 2 gp and 2 gp + 1; 5 slices into A[(i, part, s, c1)][(site, a, part')]
 template <typename SH>
-__device__ __forceinline__ void u_job(const BlockPlan &plan, const float2 *S, int nr, int off1, int o, int n_a,
-                                      const int *sEU, __nv_bfloat16 *A, int ju) {
+__device__ __forceinline__ void u_job(const int *sR1, const float2 *S, int nr, int n_a, const int *sEU,
+                                      __nv_bfloat16 *A, int ju) {
     constexpr int NC = SH::NC, NS = SH::NS, R = SH::R;
     const int sc1 = ju % (NS * NC), gp = ju / (NS * NC);
     const int s = sc1 / NC, c1 = sc1 % NC;
@@ -349,7 +353,7 @@ __device__ __forceinline__ void u_job(const BlockPlan &plan, const float2 *S, in
     for (int h = 0; h < 2; ++h) {
         const int gc = 2 * gp + h, site = gc / kKa, a = gc % kKa;
         float2 u = make_float2(0.f, 0.f);
-        if (a < n_a) u = S[site * nr * NC + off1 + plan.os_r1[plan.os_off[o * NS + s] + a] * NC + c1];
+        if (a < n_a) u = S[site * nr * NC + sR1[s * kKa + a] + c1];
         slice_u2(u, scu, wre[h], wim[h]);
     }
     // re row: U_re X_re - U_im X_im ; im row: U_im X_re + U_re X_im
@@ -384,7 +388,9 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
     float2 *sS0 = reinterpret_cast<float2 *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES));
     int *sEU = reinterpret_cast<int *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES) + kStage * SH::S_BYTES);
     int *sF = sEU + 16;                                       // [256] grid of X per column
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sF + 256);  // [2]
+    int4 *sTerm = reinterpret_cast<int4 *>(sF + 256);         // [kKa][kListLen] the op's diquark list terms
+    int *sR1 = reinterpret_cast<int *>(sTerm + kKa * kListLen);   // [NS][kKa] staged offset of U's row
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sR1 + 16);      // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
 
     // zero both operand buffers once: padding rows and unused colour terms stay zero
@@ -397,6 +403,19 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
     if (tid < NT) {
         const int c23 = col0 + tid;
         sF[tid] = tid < NCTA ? bnd[f1 * 24 + 12 + c23 / NC] + bnd[(1 - f1) * 24 + 12 + c23 % NC] + ew.e[o] : 0;
+    }
+    if (tid < kKa * kListLen) {
+        const int a = tid / kListLen, t = tid % kListLen;
+        int4 v = make_int4(0, 0, 0, 0);
+        if (a < n_a) {
+            const int q = plan.x_off[plan.os_x[t0 + a]] + t;
+            v = make_int4(plan.xt_r2[q] * NC, plan.xt_r3[q] * NC, __float_as_int(plan.xt_w[q]), 0);
+        }
+        sTerm[tid] = v;
+    }
+    if (tid >= 32 && tid < 32 + NS * kKa) {
+        const int s = (tid - 32) / kKa, a = (tid - 32) % kKa;
+        sR1[s * kKa + a] = a < n_a ? off1 + plan.os_r1[plan.os_off[o * NS + s] + a] * NC : 0;
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
@@ -479,11 +498,11 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
             for (int j0 = tid; j0 < NJ; j0 += 2 * kThr) {
                 const int jA = j0, jB = j0 + kThr;
                 if (jB < SH::NXJOB) {
-                    x_job2<SH>(plan, S, nr, off1, off2, col0, t0, n_a, sF, B, jA, jB);
+                    x_job2<SH>(sTerm, S, nr, off1, off2, col0, n_a, sF, B, jA, jB);
                 } else {
-                    if (jA < SH::NXJOB) x_job<SH>(plan, S, nr, off1, off2, col0, t0, n_a, sF, B, jA);
-                    else u_job<SH>(plan, S, nr, off1, o, n_a, sEU, A, jA - SH::NXJOB);
-                    if (jB < NJ) u_job<SH>(plan, S, nr, off1, o, n_a, sEU, A, jB - SH::NXJOB);
+                    if (jA < SH::NXJOB) x_job<SH>(sTerm, S, nr, off1, off2, col0, n_a, sF, B, jA);
+                    else u_job<SH>(sR1, S, nr, n_a, sEU, A, jA - SH::NXJOB);
+                    if (jB < NJ) u_job<SH>(sR1, S, nr, n_a, sEU, A, jB - SH::NXJOB);
                 }
             }
         }
@@ -622,7 +641,7 @@ __global__ void tc_reduce_kernel(const double2 *__restrict__ partials, int n_spl
 }
 
 // Which compiled shape a plan takes (0: none, 1: upper, 2: full): weights
-// +-2^k, at most 3 colour lists per block type of at most 4 terms each, the
+// +-2^k, at most 3 colour lists per block type of exactly 4 terms each, the
 // same lists for every spin, and at most 12 staged rows per flavour.
 int tc_family(const BlockPlan &plan) {
     if (!plan.pow2_w || plan.n_ops < 1 || plan.n_rows[0] + plan.n_rows[1] > kMaxRows) return 0;
@@ -633,7 +652,7 @@ int tc_family(const BlockPlan &plan) {
         if (n_a < 1 || n_a > kKa) return 0;
         for (int a = 0; a < n_a; ++a) {
             const int l = plan.os_x[b0 + a];
-            if (plan.x_off[l + 1] - plan.x_off[l] > kListMax) return 0;
+            if (plan.x_off[l + 1] - plan.x_off[l] != kListLen) return 0;
         }
         for (int s = 0; s < ns; ++s) {
             const int t0 = plan.os_off[o * ns + s];
