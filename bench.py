@@ -335,22 +335,41 @@ def run_ours(args):
     rel = (C_mixed - C64).abs() / C64.abs()
     rel_err = float(rel.max().item())
 
-    # end to end through the API with host buffers: H2D of the configuration, both calls, D2H of C
+    # end to end through the API with host buffers: every step copies its configuration from pinned
+    # host memory (a copy stream, two device buffers, so the next upload overlaps the current
+    # computation), runs both calls and reads C back to pinned host memory
     h2d = 2 * cfg_host[0][0].numel() * cfg_host[0][0].element_size()
     d2h = Cout.numel() * Cout.element_size()
-    ke = max(2, min(5, args.steps))
+    ke = max(4, min(10, args.steps))
     Cpin = torch.empty_like(Cout, device="cpu").pin_memory()
-    dbuf = (torch.empty_like(cfg_dev[0][0]), torch.empty_like(cfg_dev[0][1]))
+    dbufs = [(torch.empty_like(cfg_dev[0][0]), torch.empty_like(cfg_dev[0][1])) for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_step(i):
+        b = i % 2
+        hu, hd = cfg_host[i % len(cfg_host)]
+        with torch.cuda.stream(copy_stream):
+            if i >= 2:
+                copy_stream.wait_event(free[b])          # the buffer's previous step has finished
+            dbufs[b][0].copy_(hu, non_blocking=True)
+            dbufs[b][1].copy_(hd, non_blocking=True)
+            copied[b].record(copy_stream)
+        stream.wait_event(copied[b])
+        wick.wick_build_blocks(dbufs[b][0], dbufs[b][1], tabs, prec, blocks, L, T, n_src, stream)
+        wick.wick_contract(blocks, n_src, T, terms, prec, Cout, stream)
+        Cpin.copy_(Cout, non_blocking=True)
+        free[b].record(stream)
+
+    for i in range(4):                                   # warm-up: first DMA of each pinned buffer is slow
+        e2e_step(i)
     torch.cuda.synchronize()
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record(stream)
+    copy_stream.wait_event(g0)
     for i in range(ke):
-        hu, hd = cfg_host[i % 2]
-        dbuf[0].copy_(hu, non_blocking=True)
-        dbuf[1].copy_(hd, non_blocking=True)
-        wick.wick_build_blocks(dbuf[0], dbuf[1], tabs, prec, blocks, L, T, n_src, stream)
-        wick.wick_contract(blocks, n_src, T, terms, prec, Cout, stream)
-        Cpin.copy_(Cout, non_blocking=True)
+        e2e_step(i)
     g1.record(stream)
     torch.cuda.synchronize()
     e2e = sharding.max_over_ranks(g0.elapsed_time(g1) / ke, device="cuda") / world

@@ -262,17 +262,29 @@ __device__ __forceinline__ pdf x_value(const int4 *term, const float2 *s1, const
         u[t] = s1[tt[t].x];
         d[t] = s2[tt[t].y];
     }
-    pdf va, vb;
-    va.h = va.l = vb.h = vb.l = 0ull;
-#pragma unroll
-    for (int t = 0; t < kListLen; ++t) {
-        const float w = __int_as_float(tt[t].z);
-        const float ax = w * u[t].x, ay = w * u[t].y;  // exact: w is +-2^k
-        const f2x Bd = pk(d[t].x, d[t].y);
-        pacc_exact(va, pk(ax, ax), pk(-ax, -ax), Bd);
-        pacc_exact(vb, pk(ay, -ay), pk(-ay, ay), Bd);
+    // one packed accumulator with lanes (re, im): w u d = (ax dx - ay dy, ax dy + ay dx) is the sum of
+    // the lane products (ax, ax) (dx, dy) and (-ay, ay) (dy, dx), each exact as a TwoProd pair; the
+    // first product starts the accumulator without a TwoSum
+    pdf acc;
+    {
+        const float w = __int_as_float(tt[0].z);
+        const float ax = w * u[0].x, ay = w * u[0].y;  // exact: w is +-2^k
+        const f2x B1 = pk(d[0].x, d[0].y), B2 = pk(d[0].y, d[0].x);
+        const f2x nA1 = pk(-ax, -ax);
+        const f2x np = mul2(nA1, B1);                   // -RN(A1 B1)
+        acc.h = sub2(0ull, np);
+        acc.l = fma2(pk(ax, ax), B1, np);               // A1 B1 - RN(A1 B1)
+        pacc_exact(acc, pk(-ay, ay), pk(ay, -ay), B2);
     }
-    return padd(va, pdf{swap2(vb.h), swap2(vb.l)});
+#pragma unroll
+    for (int t = 1; t < kListLen; ++t) {
+        const float w = __int_as_float(tt[t].z);
+        const float ax = w * u[t].x, ay = w * u[t].y;
+        const f2x B1 = pk(d[t].x, d[t].y), B2 = pk(d[t].y, d[t].x);
+        pacc_exact(acc, pk(ax, ax), pk(-ax, -ax), B1);
+        pacc_exact(acc, pk(-ay, ay), pk(ay, -ay), B2);
+    }
+    return acc;
 }
 
 // X job jb -> (column n, combo gc = (site, a)).  A warp takes 8 columns x 4
