@@ -14,6 +14,12 @@ indices); M^f_ij = S_f(x, t)(chi_i, chi'_j).  The determinants are evaluated
 by their definition (Leibniz sum) in `det_oracle.c`, once per distinct
 (row set, column set) pair and site.
 
+Three-point functions (Sec. "Three-point functions", Eq. Proton3pt_seq): the
+current on flavour f through a sequential propagator Sigma_f replaces one
+f-quark line of every Wick term by Sigma_f, summed over the lines, i.e. each
+f determinant becomes the sum of the determinants with one row taken from
+Sigma_f (the derivative of Eq. 2.9 in the direction Sigma_f).
+
 The minimal set of App. A (Eq. a1): zeta_u, zeta_d = the distinct determinant
 index pairs, Theta(k, l) = sum of C[M] C'[M'] over the (M, M') whose u pair is
 k and d pair is l.  `minimal_sets` finds them by comparing index lists;
@@ -85,6 +91,28 @@ def point_correlator(Su, Sd, snk_table, src_table, n_u: int, n_d: int, scale: fl
         len(st["pu"]), _ptr(ur, i8), _ptr(uc, i8), len(st["pd"]), _ptr(dr, i8), _ptr(dc, i8),
         len(w), _ptr(st["t_pu"], i64), _ptr(st["t_pd"], i64), _ptr(w, dp),
         _ptr(out.view(np.float64), dp)), "point_correlator")
+    return scale * out.reshape(n_src, T)
+
+
+def point_3pt(Su, Sd, Sig, flavour: int, snk_table, src_table, n_u: int, n_d: int, scale: float = 1.0,
+              structure=None):
+    """Three-point function G3[src][t] with the current on `flavour` (0 = u, 1 = d) inserted through the
+    sequential propagator Sig (same layout as S): the derivative of Eq. 2.9 in the direction Sig."""
+    st = structure or pair_structure(snk_table, src_table, n_u)
+    Su = np.ascontiguousarray(Su, dtype=np.complex128)
+    Sd = np.ascontiguousarray(Sd, dtype=np.complex128)
+    Sg = np.ascontiguousarray(Sig, dtype=np.complex128)
+    n_src, T, V = Su.shape[:3]
+    ur, uc = _index_arrays(st["pu"], n_u)
+    dr, dc = _index_arrays(st["pd"], n_d)
+    w = st["t_w"].astype(np.float64)
+    out = np.zeros(n_src * T, dtype=np.complex128)
+    i8, i64, dp = C.c_int8, C.c_int64, C.c_double
+    _check(lib().oracle_point_3pt(
+        _ptr(Su.view(np.float64), dp), _ptr(Sd.view(np.float64), dp), _ptr(Sg.view(np.float64), dp), flavour, V,
+        n_src * T, n_u, n_d, len(st["pu"]), _ptr(ur, i8), _ptr(uc, i8), len(st["pd"]), _ptr(dr, i8), _ptr(dc, i8),
+        len(w), _ptr(st["t_pu"], i64), _ptr(st["t_pd"], i64), _ptr(w, dp),
+        _ptr(out.view(np.float64), dp)), "point_3pt")
     return scale * out.reshape(n_src, T)
 
 

@@ -12,6 +12,12 @@
  * over permutations.  Sums are Neumaier-compensated; the sum over sites is
  * taken per thread and the thread sums are added in a fixed order.
  *
+ * Three-point functions (Sec. "Three-point functions", Eq. Proton3pt_seq,
+ * generalised to nuclei): the current on flavour f through a sequential
+ * propagator Sig replaces, in every Wick term, one f-quark line by Sig, summed
+ * over the lines -- each f determinant becomes the sum over its rows of the
+ * determinant with that row taken from Sig.
+ *
  * Also: determinants modulo p = 2^61 - 1 of a random integer matrix (the
  * identity testing of App. C applied to determinants, Sec. III.B).
  */
@@ -71,6 +77,27 @@ static cplx det_leibniz(const cplx *S, const int8_t *rows, const int8_t *cols, i
     return (sr + cr) + I * (si + ci);
 }
 
+/* derivative of det S[rows][cols] in the direction Sig (Jacobi's formula written as a sum over the row
+ * replaced): sum_i det(S with row i taken from Sig), each by the Leibniz sum */
+static cplx det_leibniz_deriv(const cplx *S, const cplx *Sig, const int8_t *rows, const int8_t *cols, int n,
+                              const int8_t *perm, const int8_t *sign, int np) {
+    double sr = 0, cr = 0, si = 0, ci = 0;
+    for (int k = 0; k < np; ++k)
+        for (int rep = 0; rep < n; ++rep) {
+            cplx p = sign[k];
+            for (int i = 0; i < n; ++i) p *= (i == rep ? Sig : S)[rows[i] * 12 + cols[perm[(size_t)k * n + i]]];
+            double v[2] = {creal(p), cimag(p)};
+            double *acc[2] = {&sr, &si}, *cmp[2] = {&cr, &ci};
+            for (int q = 0; q < 2; ++q) {
+                double t = *acc[q] + v[q];
+                if (fabs(*acc[q]) >= fabs(v[q])) *cmp[q] += (*acc[q] - t) + v[q];
+                else *cmp[q] += (v[q] - t) + *acc[q];
+                *acc[q] = t;
+            }
+        }
+    return (sr + cr) + I * (si + ci);
+}
+
 static void neumaier(double *s, double *c, double v) {
     double t = *s + v;
     if (fabs(*s) >= fabs(v)) *c += (*s - t) + v;
@@ -79,10 +106,35 @@ static void neumaier(double *s, double *c, double v) {
 }
 
 /* S_f[slice][x][a][alpha][b][beta] complex128 (interleaved doubles); out[slice] complex. */
+static int point_sum(const double *Su, const double *Sd, const double *Sig, int sig_flavour, int V, int n_slices,
+                     int n_u, int n_d, int64_t n_pu, const int8_t *pu_rows, const int8_t *pu_cols, int64_t n_pd,
+                     const int8_t *pd_rows, const int8_t *pd_cols, int64_t n_terms, const int64_t *t_pu,
+                     const int64_t *t_pd, const double *t_w, double *out);
+
 int oracle_point_correlator(const double *Su, const double *Sd, int V, int n_slices, int n_u, int n_d,
                             int64_t n_pu, const int8_t *pu_rows, const int8_t *pu_cols, int64_t n_pd,
                             const int8_t *pd_rows, const int8_t *pd_cols, int64_t n_terms, const int64_t *t_pu,
                             const int64_t *t_pd, const double *t_w, double *out) {
+    return point_sum(Su, Sd, NULL, -1, V, n_slices, n_u, n_d, n_pu, pu_rows, pu_cols, n_pd, pd_rows, pd_cols,
+                     n_terms, t_pu, t_pd, t_w, out);
+}
+
+/* Three-point function with the current on flavour sig_flavour (0 = u, 1 = d) through the sequential
+ * propagator Sig (same layout as S): every determinant of that flavour becomes the sum over the row
+ * whose propagator line is replaced by Sig (the derivative of Eq. 2.9 in the direction Sig). */
+int oracle_point_3pt(const double *Su, const double *Sd, const double *Sig, int sig_flavour, int V, int n_slices,
+                     int n_u, int n_d, int64_t n_pu, const int8_t *pu_rows, const int8_t *pu_cols, int64_t n_pd,
+                     const int8_t *pd_rows, const int8_t *pd_cols, int64_t n_terms, const int64_t *t_pu,
+                     const int64_t *t_pd, const double *t_w, double *out) {
+    if (!Sig || (sig_flavour != 0 && sig_flavour != 1)) return -1;
+    return point_sum(Su, Sd, Sig, sig_flavour, V, n_slices, n_u, n_d, n_pu, pu_rows, pu_cols, n_pd, pd_rows,
+                     pd_cols, n_terms, t_pu, t_pd, t_w, out);
+}
+
+static int point_sum(const double *Su, const double *Sd, const double *Sig, int sig_flavour, int V, int n_slices,
+                     int n_u, int n_d, int64_t n_pu, const int8_t *pu_rows, const int8_t *pu_cols, int64_t n_pd,
+                     const int8_t *pd_rows, const int8_t *pd_cols, int64_t n_terms, const int64_t *t_pu,
+                     const int64_t *t_pd, const double *t_w, double *out) {
     if (n_u < 0 || n_u > 7 || n_d < 0 || n_d > 7) return -1;
     int8_t *pmu, *smu, *pmd, *smd;
     const int npu = det_perms(n_u, &pmu, &smu), npd = det_perms(n_d, &pmd, &smd);
@@ -106,10 +158,15 @@ int oracle_point_correlator(const double *Su, const double *Sd, int V, int n_sli
             for (int x = 0; x < V; ++x) {
                 const cplx *su = (const cplx *)(Su + ((size_t)sl * V + x) * 288);
                 const cplx *sd = (const cplx *)(Sd + ((size_t)sl * V + x) * 288);
+                const cplx *sg = Sig ? (const cplx *)(Sig + ((size_t)sl * V + x) * 288) : NULL;
                 for (int64_t k = 0; k < n_pu; ++k)
-                    U[k] = det_leibniz(su, pu_rows + k * n_u, pu_cols + k * n_u, n_u, pmu, smu, npu);
+                    U[k] = sig_flavour == 0
+                               ? det_leibniz_deriv(su, sg, pu_rows + k * n_u, pu_cols + k * n_u, n_u, pmu, smu, npu)
+                               : det_leibniz(su, pu_rows + k * n_u, pu_cols + k * n_u, n_u, pmu, smu, npu);
                 for (int64_t k = 0; k < n_pd; ++k)
-                    Dt[k] = det_leibniz(sd, pd_rows + k * n_d, pd_cols + k * n_d, n_d, pmd, smd, npd);
+                    Dt[k] = sig_flavour == 1
+                                ? det_leibniz_deriv(sd, sg, pd_rows + k * n_d, pd_cols + k * n_d, n_d, pmd, smd, npd)
+                                : det_leibniz(sd, pd_rows + k * n_d, pd_cols + k * n_d, n_d, pmd, smd, npd);
                 for (int64_t t = 0; t < n_terms; ++t) {
                     const cplx v = t_w[t] * U[t_pu[t]] * Dt[t_pd[t]];
                     neumaier(&sr, &cr, creal(v));

@@ -69,8 +69,10 @@ def lib():
             L.oracle_source_multisets.argtypes = [P, C.c_int64, i8p, i8p, i64p, i64p]
             L.oracle_point_correlator.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, i8p, i8p,
                                                   C.c_int64, i8p, i8p, C.c_int64, i64p, i64p, dp, dp]
+            L.oracle_point_3pt.argtypes = [dp, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, i8p,
+                                           i8p, C.c_int64, i8p, i8p, C.c_int64, i64p, i64p, dp, dp]
             L.oracle_det_modp.argtypes = [u64p, C.c_int, C.c_int64, i8p, i8p, u64p]
-            for f in ("oracle_point_correlator", "oracle_det_modp",
+            for f in ("oracle_point_correlator", "oracle_point_3pt", "oracle_det_modp",
                       "oracle_blocks", "oracle_raw_correlator", "oracle_table_correlator", "oracle_dedup",
                       "oracle_modp_raw", "oracle_modp_table", "oracle_num_threads", "oracle_source_multisets"):
                 getattr(L, f).restype = C.c_int

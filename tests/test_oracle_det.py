@@ -190,3 +190,47 @@ def test_cross_pair_point_sink_equals_plain_wick_sum_on_one_site():
     gp = DT.point_correlator(Su, Sd, t1, t3, 3, 3)
     graw = O.correlator(Su, Sd, nuc)
     assert np.max(np.abs(gp - graw) / np.abs(graw)) < 1e-13
+
+
+@pytest.mark.parametrize("name,flavour", [("deuteron", 0), ("deuteron", 1), ("he3", 1)])
+def test_three_point_is_derivative_of_two_point(name, flavour):
+    """The current through a sequential propagator Sigma_f: G3 = d/de G(S_f + e Sigma_f) at e = 0.
+    G is a polynomial of degree n_f in e; its linear coefficient comes from n_f + 1 evaluations
+    of the two-point oracle (exact interpolation)."""
+    tab, nu, nd, scale = DT.operator(name)
+    L = 2 if name == "deuteron" else 1
+    Su, Sd = props(L, 1, seed=21)
+    Sig = synth.propagator(22, 0, L, 1, 1)
+    n_f = nu if flavour == 0 else nd
+    eps = np.linspace(-1.0, 1.0, n_f + 1)
+    vals = []
+    for e in eps:
+        a, b = (Su + e * Sig, Sd) if flavour == 0 else (Su, Sd + e * Sig)
+        vals.append(DT.point_correlator(a, b, tab, tab, nu, nd, scale)[0, 0])
+    coef = np.linalg.solve(np.vander(eps, n_f + 1, increasing=True).astype(complex), np.array(vals))
+    g3 = DT.point_3pt(Su, Sd, Sig, flavour, tab, tab, nu, nd, scale)[0, 0]
+    assert abs(g3 - coef[1]) < 1e-9 * np.max(np.abs(vals))
+
+
+def test_three_point_euler_identity():
+    """With Sigma_f = S_f the derivative is n_f times the two-point function (homogeneity)."""
+    tab, nu, nd, scale = DT.operator("deuteron")
+    Su, Sd = props(2, 2, seed=23)
+    g = DT.point_correlator(Su, Sd, tab, tab, nu, nd, scale)
+    assert np.max(np.abs(DT.point_3pt(Su, Sd, Su, 0, tab, tab, nu, nd, scale) - nu * g) / np.abs(g)) < 1e-13
+    assert np.max(np.abs(DT.point_3pt(Su, Sd, Sd, 1, tab, tab, nu, nd, scale) - nd * g) / np.abs(g)) < 1e-13
+
+
+def test_proton_three_point_point_equals_plane_wave_derivative():
+    """One nucleon (the paper's proton example): the point-sink three-point function is the
+    derivative of the plane-wave two-point function in the direction Sigma_u, on any lattice."""
+    nuc = ops.nucleus("proton", "full")
+    tab, fl = ops.grouped_operator(nuc["ops"], [((ops.PROTON,), (0,), 1), ((ops.PROTON,), (1,), 1)])
+    pw = ops._cluster(nuc["ops"], [((ops.PROTON,), (0,), 1), ((ops.PROTON,), (1,), 1)], 1.0)
+    Su, Sd = props(2, 1, seed=24)
+    Sig = synth.propagator(25, 0, 2, 1, 1)
+    eps = np.array([-1.0, 0.0, 1.0])
+    vals = [O.correlator(Su + e * Sig, Sd, pw)[0, 0] for e in eps]
+    coef = np.linalg.solve(np.vander(eps, 3, increasing=True).astype(complex), np.array(vals))
+    g3 = DT.point_3pt(Su, Sd, Sig, 0, tab, tab, 2, 1)[0, 0]
+    assert abs(g3 - coef[1]) < 1e-11 * np.max(np.abs(vals))
