@@ -567,6 +567,14 @@ def run_point(args):
                                          "cores": O.num_threads(), "kind": "oracle",
                                          "sample": f"{n_site} of {L ** 3} sites of one time slice, {dt:.1f} s"}
         if name == "deuteron":
+            # three-point function, current on u through a sequential propagator (synthetic, same layout)
+            Sig = torch.empty_like(Su)
+            wick.wick_synth_propagator(seed + 7, 0, 0, L, T, Sig[0])
+            C3 = torch.empty((1, T), dtype=torch.complex128, device="cuda")
+            ms3 = _timed(lambda: wick.wick_det_contract_3pt(Su, Sd, Sig, wick.WICK_U, plan, C3, L, T, 1,
+                                                            stream=stream), args.steps, 1, stream)
+            res["three_point_2h_u"] = {"L": L, "T": T, "ms_per_time_slice": ms3 / T}
+            del Sig
             # the 3 x 3 correlation matrix of three 2H operators (Eqs. E1-E3): shared determinants
             # against nine separate pair evaluations
             basis = operators.deuteron_basis()

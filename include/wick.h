@@ -369,6 +369,20 @@ int wick_det_copy(const wick_det_plan *plan, int32_t *k, int32_t *l, int64_t *w,
  */
 int wick_det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_det_plan *plan, double scale,
                       int precision, void *C_out, wick_stream_t stream);
+/*
+ * wick_det_contract_3pt: three-point function (Sec. "Three-point functions",
+ * Eq. Proton3pt_seq, generalised to nuclei) with the current on `flavour`
+ * (WICK_U or WICK_D) inserted through the sequential propagator Sig (device,
+ * same L, T, n_src, dtype and layout as S; obtained by inverting the Dirac
+ * operator on the current's source, an input here).  The connected
+ * contribution replaces one quark line of that flavour in every Wick term by
+ * Sig, summed over the lines: each determinant of that flavour becomes the
+ * sum of the determinants with one row taken from Sig (the derivative of
+ * Eq. 2.9 in the direction Sig).  Same plan, output layout and errors as
+ * wick_det_contract.
+ */
+int wick_det_contract_3pt(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig, int flavour,
+                          const wick_det_plan *plan, double scale, int precision, void *C_out, wick_stream_t stream);
 void wick_det_free(wick_det_plan *plan);
 
 /* Synchronises `stream` and returns (then clears) the device status word. */

@@ -135,13 +135,15 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
+// determinant of the n x n matrix row[i][cols[j]] (rows given as pointers into 12 x 12 matrices, so
+// that a row can come from another propagator)
 template <int N>
-__device__ __forceinline__ double2 det_lu(const double2 *S, const int8_t *rc) {
+__device__ __forceinline__ double2 det_lu(const double2 *const *row, const int8_t *cols) {
     double2 a[N][N];
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll
-        for (int j = 0; j < N; ++j) a[i][j] = S[rc[i] * 12 + rc[N + j]];
+        for (int j = 0; j < N; ++j) a[i][j] = row[i][cols[j]];
     double2 det = make_double2(1.0, 0.0);
 #pragma unroll
     for (int c = 0; c < N; ++c) {
@@ -183,37 +185,54 @@ __device__ __forceinline__ double2 det_lu(const double2 *S, const int8_t *rc) {
     return det;
 }
 
-// rc: n row indices then n column indices
-__device__ __forceinline__ double2 det_small(const double2 *S, const int8_t *rc, int n) {
+__device__ __forceinline__ double2 det_rows(const double2 *const *row, const int8_t *cols, int n) {
     switch (n) {
     case 1:
-        return S[rc[0] * 12 + rc[1]];
-    case 2: {
-        const double2 a = S[rc[0] * 12 + rc[2]], b = S[rc[0] * 12 + rc[3]];
-        const double2 c = S[rc[1] * 12 + rc[2]], d = S[rc[1] * 12 + rc[3]];
-        return csub(cmul(a, d), cmul(b, c));
-    }
+        return row[0][cols[0]];
+    case 2:
+        return csub(cmul(row[0][cols[0]], row[1][cols[1]]), cmul(row[0][cols[1]], row[1][cols[0]]));
     case 3: {
-        const double2 *r0 = S + rc[0] * 12, *r1 = S + rc[1] * 12, *r2 = S + rc[2] * 12;
-        const int c0 = rc[3], c1 = rc[4], c2 = rc[5];
+        const double2 *r0 = row[0], *r1 = row[1], *r2 = row[2];
+        const int c0 = cols[0], c1 = cols[1], c2 = cols[2];
         const double2 m0 = csub(cmul(r1[c1], r2[c2]), cmul(r1[c2], r2[c1]));
         const double2 m1 = csub(cmul(r1[c0], r2[c2]), cmul(r1[c2], r2[c0]));
         const double2 m2 = csub(cmul(r1[c0], r2[c1]), cmul(r1[c1], r2[c0]));
         return cadd(csub(cmul(r0[c0], m0), cmul(r0[c1], m1)), cmul(r0[c2], m2));
     }
     case 4:
-        return det_lu<4>(S, rc);
+        return det_lu<4>(row, cols);
     case 5:
-        return det_lu<5>(S, rc);
+        return det_lu<5>(row, cols);
     case 6:
-        return det_lu<6>(S, rc);
+        return det_lu<6>(row, cols);
     default:
         return make_double2(1.0, 0.0);  // no quark of this flavour
     }
 }
 
+// rc: n row indices (sink) then n column indices (source) of S
+__device__ __forceinline__ double2 det_small(const double2 *S, const int8_t *rc, int n) {
+    const double2 *row[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) row[i] = S + (i < n ? rc[i] : 0) * 12;
+    return det_rows(row, rc + n, n);
+}
+
+// the derivative of det S[rows][cols] in the direction Sig: the sum over the row taken from Sig
+__device__ __forceinline__ double2 det_deriv(const double2 *S, const double2 *Sig, const int8_t *rc, int n) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int rep = 0; rep < n; ++rep) {
+        const double2 *row[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) row[i] = (i == rep ? Sig : S) + (i < n ? rc[i] : 0) * 12;
+        acc = cadd(acc, det_rows(row, rc + n, n));
+    }
+    return acc;
+}
+
 struct DetArgs {
     int n_u, n_d, n_el;
+    int seq_flavour;          // -1: two-point function; 0 / 1: current on u / d through Sig
     int64_t n_zu, n_zd;
     const int8_t *zu, *zd;
     const int32_t *k, *l;
@@ -223,9 +242,9 @@ struct DetArgs {
 
 template <typename ST, int MAXEL>
 __global__ void __launch_bounds__(kDetThreads)
-det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict__ Sd, int V, int n_slices,
-                int n_chunks, double2 *__restrict__ scratch, double2 *__restrict__ partials) {
-    __shared__ double2 sS[2][144];
+det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict__ Sd, const ST *__restrict__ Sig,
+                int V, int n_slices, int n_chunks, double2 *__restrict__ scratch, double2 *__restrict__ partials) {
+    __shared__ double2 sS[3][144];
     __shared__ double2 red[kDetThreads];
     double2 *U = scratch + (size_t)blockIdx.x * (a.n_zu + a.n_zd);
     double2 *D = U + a.n_zu;
@@ -239,14 +258,19 @@ det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict
         for (int e = 0; e < MAXEL; ++e) acc[e] = make_double2(0.0, 0.0);
         for (int x = x0; x < x1; ++x) {
             __syncthreads();  // the previous site's determinants are consumed
-            for (int e = tid; e < 288; e += kDetThreads) {
-                const ST *src = (e < 144 ? Su : Sd) + ((size_t)slice * V + x) * 144 + (e % 144);
-                const ST v = *src;
+            const int n_mat = a.seq_flavour < 0 ? 2 : 3;
+            for (int e = tid; e < 144 * n_mat; e += kDetThreads) {
+                const ST *base = e < 144 ? Su : (e < 288 ? Sd : Sig);
+                const ST v = base[((size_t)slice * V + x) * 144 + (e % 144)];
                 sS[e / 144][e % 144] = make_double2((double)v.x, (double)v.y);
             }
             __syncthreads();
-            for (int64_t q = tid; q < a.n_zu; q += kDetThreads) U[q] = det_small(sS[0], a.zu + q * 2 * a.n_u, a.n_u);
-            for (int64_t q = tid; q < a.n_zd; q += kDetThreads) D[q] = det_small(sS[1], a.zd + q * 2 * a.n_d, a.n_d);
+            for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
+                U[q] = a.seq_flavour == 0 ? det_deriv(sS[0], sS[2], a.zu + q * 2 * a.n_u, a.n_u)
+                                          : det_small(sS[0], a.zu + q * 2 * a.n_u, a.n_u);
+            for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
+                D[q] = a.seq_flavour == 1 ? det_deriv(sS[1], sS[2], a.zd + q * 2 * a.n_d, a.n_d)
+                                          : det_small(sS[1], a.zd + q * 2 * a.n_d, a.n_d);
             __syncthreads();
             // the determinants are shared by every matrix element (Eq. E3)
 #pragma unroll
@@ -633,12 +657,21 @@ int wick_det_copy(const wick_det_plan *p, int32_t *k, int32_t *l, int64_t *w, in
     return WICK_OK;
 }
 
-int wick_det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_det_plan *plan, double scale,
-                      int precision, void *C_out, wick_stream_t stream) {
-    if (!Su || !Sd || !plan || !C_out || precision != WICK_FP64) return WICK_EINVAL;
-    if (!Su->data || !Sd->data || Su->L != Sd->L || Su->T != Sd->T || Su->n_src != Sd->n_src ||
-        Su->dtype != Sd->dtype || Su->L < 1 || Su->T < 1 || Su->n_src < 1 ||
-        (Su->dtype != WICK_C64 && Su->dtype != WICK_C128))
+}  // extern "C"
+
+namespace wick {
+namespace {
+
+bool props_match(const wick_prop *a, const wick_prop *b) {
+    return a && b && a->data && b->data && a->L == b->L && a->T == b->T && a->n_src == b->n_src &&
+           a->dtype == b->dtype;
+}
+
+int det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig, int seq_flavour,
+                 const wick_det_plan *plan, double scale, int precision, void *C_out, wick_stream_t stream) {
+    if (!plan || !C_out || precision != WICK_FP64 || !props_match(Su, Sd)) return WICK_EINVAL;
+    if (seq_flavour >= 0 && !props_match(Su, Sig)) return WICK_EINVAL;
+    if (Su->L < 1 || Su->T < 1 || Su->n_src < 1 || (Su->dtype != WICK_C64 && Su->dtype != WICK_C128))
         return WICK_EINVAL;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -667,18 +700,20 @@ int wick_det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_det_p
     if (err) return err;
     double2 *scratch = (double2 *)ws;
     double2 *partials = (double2 *)(ws + (scratch_bytes + 255) / 256 * 256);
-    DetArgs a{plan->n_u, plan->n_d, plan->n_el, plan->n_zu, plan->n_zd, plan->d_zu, plan->d_zd,
+    DetArgs a{plan->n_u, plan->n_d, plan->n_el, seq_flavour, plan->n_zu, plan->n_zd, plan->d_zu, plan->d_zd,
               plan->d_k, plan->d_l, plan->d_w, plan->d_el_off};
     const unsigned g = (unsigned)grid;
     const int iv = (int)V, is = (int)n_slices;
     if (c64) {
         const float2 *u = (const float2 *)Su->data, *d = (const float2 *)Sd->data;
-        if (one) det_eval_kernel<float2, 1><<<g, kDetThreads, 0, st>>>(a, u, d, iv, is, n_chunks, scratch, partials);
-        else det_eval_kernel<float2, kMaxEl><<<g, kDetThreads, 0, st>>>(a, u, d, iv, is, n_chunks, scratch, partials);
+        const float2 *q = seq_flavour >= 0 ? (const float2 *)Sig->data : u;
+        if (one) det_eval_kernel<float2, 1><<<g, kDetThreads, 0, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
+        else det_eval_kernel<float2, kMaxEl><<<g, kDetThreads, 0, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
     } else {
         const double2 *u = (const double2 *)Su->data, *d = (const double2 *)Sd->data;
-        if (one) det_eval_kernel<double2, 1><<<g, kDetThreads, 0, st>>>(a, u, d, iv, is, n_chunks, scratch, partials);
-        else det_eval_kernel<double2, kMaxEl><<<g, kDetThreads, 0, st>>>(a, u, d, iv, is, n_chunks, scratch, partials);
+        const double2 *q = seq_flavour >= 0 ? (const double2 *)Sig->data : u;
+        if (one) det_eval_kernel<double2, 1><<<g, kDetThreads, 0, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
+        else det_eval_kernel<double2, kMaxEl><<<g, kDetThreads, 0, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
     }
     WICK_CUDA_TRY(cudaGetLastError());
     const int64_t n_out = n_slices * plan->n_el;
@@ -686,6 +721,22 @@ int wick_det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_det_p
                                                                        plan->n_el, scale, (double2 *)C_out);
     WICK_CUDA_TRY(cudaGetLastError());
     return WICK_OK;
+}
+
+}  // namespace
+}  // namespace wick
+
+extern "C" {
+
+int wick_det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_det_plan *plan, double scale,
+                      int precision, void *C_out, wick_stream_t stream) {
+    return det_contract(Su, Sd, nullptr, -1, plan, scale, precision, C_out, stream);
+}
+
+int wick_det_contract_3pt(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig, int flavour,
+                          const wick_det_plan *plan, double scale, int precision, void *C_out, wick_stream_t stream) {
+    if (flavour != WICK_U && flavour != WICK_D) return WICK_EINVAL;
+    return det_contract(Su, Sd, Sig, flavour, plan, scale, precision, C_out, stream);
 }
 
 void wick_det_free(wick_det_plan *plan) { free_plan(plan); }

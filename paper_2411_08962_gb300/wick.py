@@ -29,7 +29,7 @@ EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_reduce_terms", "wick_t
            "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_contract_noalloc",
            "wick_status", "wick_batch_create", "wick_batch_run", "wick_batch_launches", "wick_batch_free",
            "wick_synth_propagator", "wick_cluster_product", "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats",
-           "wick_det_element_offsets", "wick_det_copy", "wick_det_contract", "wick_det_free", "wick_strerror", "wick_version")
+           "wick_det_element_offsets", "wick_det_copy", "wick_det_contract", "wick_det_contract_3pt", "wick_det_free", "wick_strerror", "wick_version")
 
 
 class WickError(RuntimeError):
@@ -109,6 +109,8 @@ def load(path: str = LIB_PATH):
             L.wick_det_element_offsets.argtypes = [vp, P(C.c_int64)]
             L.wick_det_copy.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
             L.wick_det_contract.argtypes = [P(wick_prop), P(wick_prop), vp, C.c_double, C.c_int, vp, vp]
+            L.wick_det_contract_3pt.argtypes = [P(wick_prop), P(wick_prop), P(wick_prop), C.c_int, vp, C.c_double,
+                                                C.c_int, vp, vp]
             L.wick_det_free.argtypes = [vp]
             L.wick_det_free.restype = None
             L.wick_strerror.argtypes = [C.c_int]
@@ -119,7 +121,7 @@ def load(path: str = LIB_PATH):
                       "wick_contract", "wick_contract_noalloc", "wick_status", "wick_batch_create",
                       "wick_batch_run", "wick_batch_launches", "wick_synth_propagator", "wick_cluster_product",
                       "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats", "wick_det_element_offsets",
-                      "wick_det_copy", "wick_det_contract"):
+                      "wick_det_copy", "wick_det_contract", "wick_det_contract_3pt"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -411,3 +413,15 @@ def wick_det_contract(Su, Sd, plan: DetPlan, C_out, L: int, T: int, n_src: int, 
     sc = plan.scale if scale is None else float(scale)
     _check(load().wick_det_contract(C.byref(pu), C.byref(pd), plan.h, sc, precision, _ptr(C_out), _stream(stream)),
            "wick_det_contract")
+
+
+def wick_det_contract_3pt(Su, Sd, Sig, flavour: int, plan: DetPlan, C_out, L: int, T: int, n_src: int, scale=None,
+                          precision: int = WICK_FP64, stream=None):
+    """Three-point function: the current on `flavour` (WICK_U / WICK_D) through the sequential propagator Sig."""
+    def prop(S):
+        dt = WICK_C64 if str(S.dtype) == "torch.complex64" else WICK_C128
+        return wick_prop(_ptr(S), L, T, n_src, dt)
+    pu, pd, pq = prop(Su), prop(Sd), prop(Sig)
+    sc = plan.scale if scale is None else float(scale)
+    _check(load().wick_det_contract_3pt(C.byref(pu), C.byref(pd), C.byref(pq), flavour, plan.h, sc, precision,
+                                        _ptr(C_out), _stream(stream)), "wick_det_contract_3pt")

@@ -153,3 +153,29 @@ def test_matrix_diagonal_equals_single_correlator():
     got = gpu_matrix(Su, Sd)
     single = gpu_point("deuteron", Su, Sd)   # n^T (C g5 P+) p
     assert np.max(np.abs(got[0] - single) / np.abs(single)) < 1e-13
+
+
+@pytest.mark.parametrize("name,flavour,L", [("deuteron", wick.WICK_U, 2), ("deuteron", wick.WICK_D, 3),
+                                           ("he3", wick.WICK_D, 1)])
+def test_three_point_matches_oracle(name, flavour, L):
+    """Current on u or d through a sequential propagator: the derivative of Eq. 2.9 (FP64, 1e-12)."""
+    T, n_src = 2, 1
+    Su, Sd = props(L, T, n_src, seed=0xD3B + L)
+    Sig = synth.propagator(0xD3C, 0, L, T, n_src)
+    tab, nu, nd, scale = DT.operator(name)
+    ref = DT.point_3pt(Su, Sd, Sig, flavour, tab, tab, nu, nd, scale)
+    out = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
+    dev_ = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (Su, Sd, Sig)]
+    wick.wick_det_contract_3pt(dev_[0], dev_[1], dev_[2], flavour, plan(name), out, L, T, n_src)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(out.cpu().numpy() - ref) / np.abs(ref)) < FP64_TOL
+
+
+def test_three_point_euler_identity_on_gpu():
+    """Sigma_u = S_u gives n_u times the two-point function."""
+    Su, Sd = props(3, 1, 1, seed=0xD3D)
+    out = torch.empty((1, 1), dtype=torch.complex128, device="cuda")
+    su, sd = torch.from_numpy(Su).cuda(), torch.from_numpy(Sd).cuda()
+    wick.wick_det_contract_3pt(su, sd, su, wick.WICK_U, plan("deuteron"), out, 3, 1, 1)
+    two = gpu_point("deuteron", Su, Sd)
+    assert np.max(np.abs(out.cpu().numpy() - 3 * two) / np.abs(two)) < 1e-13
