@@ -498,14 +498,23 @@ def _timed(fn, steps, warmup, stream):
     return a.elapsed_time(b) / steps
 
 
-# FP64 flops of one determinant as evaluated on the device: explicit forms up
-# to 3 x 3 (2 x 2: two complex products and a difference; 3 x 3: three 2 x 2
-# minors and three products), pivoted LU above (per column: the pivot product
-# and reciprocal, 14; per lower row: the multiplier, 6, and 8 per updated
-# entry); a Theta term: one complex product and two FMAs (10).
-def det_flops(n: int) -> int:
+# FP64 flops of one determinant as evaluated on the device (complex product
+# 6, complex add 2).  Two-point functions with at most 5 quarks per flavour
+# read a per-site table of all 66 x 66 2 x 2 minors of each S (14 flops each):
+# 2 x 2 a lookup, 3 x 3 three products and two adds (22), 4 x 4 six products
+# of complementary minors and five adds (46), 5 x 5 five 4 x 4 along the first
+# row (268).  Otherwise explicit forms up to 3 x 3 (64 for 3 x 3) and pivoted
+# LU above (per column: pivot product and reciprocal 14; per lower row the
+# multiplier 6 and 8 per updated entry).  A Theta term: one complex product
+# and two FMAs (10).
+MINOR_TABLE_FLOPS = 2 * 66 * 66 * 14
+
+
+def det_flops(n: int, minors: bool = True) -> int:
     if n <= 1:
         return 0
+    if minors and n <= 5:
+        return {2: 0, 3: 22, 4: 46, 5: 5 * (46 + 6) + 8}[n]
     if n == 2:
         return 14
     if n == 3:
@@ -543,8 +552,9 @@ def run_point(args):
         ms = _timed(lambda: wick.wick_det_contract(Su, Sd, plan, C, L, T, 1, stream=stream), args.steps,
                     max(1, args.warmup), stream)
         sites = L ** 3 * T
-        flops = sites * (st["zeta_u"] * det_flops(st["n_u"]) + st["zeta_d"] * det_flops(st["n_d"])
-                         + st["theta"] * THETA_FLOPS)
+        minors = st["n_u"] <= 5 and st["n_d"] <= 5
+        flops = sites * (st["zeta_u"] * det_flops(st["n_u"], minors) + st["zeta_d"] * det_flops(st["n_d"], minors)
+                         + st["theta"] * THETA_FLOPS + (MINOR_TABLE_FLOPS if minors else 0))
         tf = flops / (ms / 1e3) / 1e12
         res[name] = {"L": L, "T": T, "ms_per_time_slice": ms / T, "reduce_seconds": reduce_s,
                      "zeta_u": st["zeta_u"], "zeta_d": st["zeta_d"], "theta": st["theta"],

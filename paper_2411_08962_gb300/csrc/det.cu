@@ -230,6 +230,65 @@ __device__ __forceinline__ double2 det_deriv(const double2 *S, const double2 *Si
     return acc;
 }
 
+// ---------------------------------------------------------------------------
+// determinants from a per-site table of all 2 x 2 minors of a 12 x 12 matrix:
+// M2[pair(r0, r1)][pair(c0, c1)] = S[r0][c0] S[r1][c1] - S[r0][c1] S[r1][c0], pair(i < j) in 0..65
+// ---------------------------------------------------------------------------
+constexpr int kPairs = 66;
+__host__ __device__ constexpr int pair_index(int i, int j) { return i * (23 - i) / 2 + (j - i - 1); }
+
+__device__ __forceinline__ double2 m2(const double2 *M, int r0, int r1, int c0, int c1) {
+    return M[pair_index(r0, r1) * kPairs + pair_index(c0, c1)];
+}
+
+// 4 x 4 by Laplace expansion along rows (r0, r1): sum over column pairs of the signed products of
+// complementary 2 x 2 minors
+__device__ __forceinline__ double2 det4_m2(const double2 *M, int r0, int r1, int r2, int r3, const int *c) {
+    double2 d = cmul(m2(M, r0, r1, c[0], c[1]), m2(M, r2, r3, c[2], c[3]));
+    d = csub(d, cmul(m2(M, r0, r1, c[0], c[2]), m2(M, r2, r3, c[1], c[3])));
+    d = cadd(d, cmul(m2(M, r0, r1, c[0], c[3]), m2(M, r2, r3, c[1], c[2])));
+    d = cadd(d, cmul(m2(M, r0, r1, c[1], c[2]), m2(M, r2, r3, c[0], c[3])));
+    d = csub(d, cmul(m2(M, r0, r1, c[1], c[3]), m2(M, r2, r3, c[0], c[2])));
+    return cadd(d, cmul(m2(M, r0, r1, c[2], c[3]), m2(M, r2, r3, c[0], c[1])));
+}
+
+// det of S[rc[0..n)][rc[n..2n)] for n <= 5 from the minor table (n = 6 falls back to LU)
+__device__ __forceinline__ double2 det_minors(const double2 *S, const double2 *M, const int8_t *rc, int n) {
+    switch (n) {
+    case 1:
+        return S[rc[0] * 12 + rc[1]];
+    case 2:
+        return m2(M, rc[0], rc[1], rc[2], rc[3]);
+    case 3: {
+        const double2 *r0 = S + rc[0] * 12;
+        const int a = rc[1], b = rc[2], c0 = rc[3], c1 = rc[4], c2 = rc[5];
+        return cadd(csub(cmul(r0[c0], m2(M, a, b, c1, c2)), cmul(r0[c1], m2(M, a, b, c0, c2))),
+                    cmul(r0[c2], m2(M, a, b, c0, c1)));
+    }
+    case 4: {
+        const int c[4] = {rc[4], rc[5], rc[6], rc[7]};
+        return det4_m2(M, rc[0], rc[1], rc[2], rc[3], c);
+    }
+    case 5: {
+        // along the first row: sum_j (-1)^j S[r0][c_j] det4(rows r1..r4, columns without c_j)
+        const double2 *r0 = S + rc[0] * 12;
+        double2 d = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            int c[4], q = 0;
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                if (k != j) c[q++] = rc[5 + k];
+            const double2 t = cmul(r0[rc[5 + j]], det4_m2(M, rc[1], rc[2], rc[3], rc[4], c));
+            d = (j & 1) ? csub(d, t) : cadd(d, t);
+        }
+        return d;
+    }
+    default:
+        return det_small(S, rc, n);
+    }
+}
+
 struct DetArgs {
     int n_u, n_d, n_el;
     int seq_flavour;          // -1: two-point function; 0 / 1: current on u / d through Sig
@@ -240,12 +299,13 @@ struct DetArgs {
     const int64_t *el_off;
 };
 
-template <typename ST, int MAXEL>
+template <typename ST, int MAXEL, bool MINORS>
 __global__ void __launch_bounds__(kDetThreads)
 det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict__ Sd, const ST *__restrict__ Sig,
                 int V, int n_slices, int n_chunks, double2 *__restrict__ scratch, double2 *__restrict__ partials) {
     __shared__ double2 sS[3][144];
     __shared__ double2 red[kDetThreads];
+    extern __shared__ double2 sM[];   // MINORS: [2][kPairs * kPairs] 2 x 2 minor tables of S_u, S_d
     double2 *U = scratch + (size_t)blockIdx.x * (a.n_zu + a.n_zd);
     double2 *D = U + a.n_zu;
     const int tid = threadIdx.x;
@@ -265,12 +325,29 @@ det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict
                 sS[e / 144][e % 144] = make_double2((double)v.x, (double)v.y);
             }
             __syncthreads();
-            for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
-                U[q] = a.seq_flavour == 0 ? det_deriv(sS[0], sS[2], a.zu + q * 2 * a.n_u, a.n_u)
-                                          : det_small(sS[0], a.zu + q * 2 * a.n_u, a.n_u);
-            for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
-                D[q] = a.seq_flavour == 1 ? det_deriv(sS[1], sS[2], a.zd + q * 2 * a.n_d, a.n_d)
-                                          : det_small(sS[1], a.zd + q * 2 * a.n_d, a.n_d);
+            if constexpr (MINORS) {
+                for (int e = tid; e < 2 * kPairs * kPairs; e += kDetThreads) {
+                    const int f = e / (kPairs * kPairs), rp = (e / kPairs) % kPairs, cp = e % kPairs;
+                    int r0 = 0, c0 = 0;
+                    while (pair_index(r0, 11) < rp) ++r0;      // first index of the pair
+                    while (pair_index(c0, 11) < cp) ++c0;
+                    const int r1 = rp - pair_index(r0, r0 + 1) + r0 + 1, c1 = cp - pair_index(c0, c0 + 1) + c0 + 1;
+                    const double2 *S = sS[f];
+                    sM[e] = csub(cmul(S[r0 * 12 + c0], S[r1 * 12 + c1]), cmul(S[r0 * 12 + c1], S[r1 * 12 + c0]));
+                }
+                __syncthreads();
+                for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
+                    U[q] = det_minors(sS[0], sM, a.zu + q * 2 * a.n_u, a.n_u);
+                for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
+                    D[q] = det_minors(sS[1], sM + kPairs * kPairs, a.zd + q * 2 * a.n_d, a.n_d);
+            } else {
+                for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
+                    U[q] = a.seq_flavour == 0 ? det_deriv(sS[0], sS[2], a.zu + q * 2 * a.n_u, a.n_u)
+                                              : det_small(sS[0], a.zu + q * 2 * a.n_u, a.n_u);
+                for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
+                    D[q] = a.seq_flavour == 1 ? det_deriv(sS[1], sS[2], a.zd + q * 2 * a.n_d, a.n_d)
+                                              : det_small(sS[1], a.zd + q * 2 * a.n_d, a.n_d);
+            }
             __syncthreads();
             // the determinants are shared by every matrix element (Eq. E3)
 #pragma unroll
@@ -689,9 +766,20 @@ int det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig,
     WICK_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const bool one = plan->n_el == 1;
     const bool c64 = Su->dtype == WICK_C64;
-    const void *kern = c64 ? (one ? (const void *)det_eval_kernel<float2, 1> : (const void *)det_eval_kernel<float2, kMaxEl>)
-                           : (one ? (const void *)det_eval_kernel<double2, 1> : (const void *)det_eval_kernel<double2, kMaxEl>);
-    WICK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDetThreads, 0));
+    // two-point functions with at most 5 quarks of each flavour use the 2 x 2 minor tables
+    const bool minors = seq_flavour < 0 && plan->n_u <= 5 && plan->n_d <= 5;
+    const size_t dyn = minors ? sizeof(double2) * 2 * kPairs * kPairs : 0;
+    using KF = void (*)(const DetArgs, const float2 *, const float2 *, const float2 *, int, int, int, double2 *,
+                        double2 *);
+    using KD = void (*)(const DetArgs, const double2 *, const double2 *, const double2 *, int, int, int, double2 *,
+                        double2 *);
+    KF kf = one ? (minors ? det_eval_kernel<float2, 1, true> : det_eval_kernel<float2, 1, false>)
+                : (minors ? det_eval_kernel<float2, kMaxEl, true> : det_eval_kernel<float2, kMaxEl, false>);
+    KD kd = one ? (minors ? det_eval_kernel<double2, 1, true> : det_eval_kernel<double2, 1, false>)
+                : (minors ? det_eval_kernel<double2, kMaxEl, true> : det_eval_kernel<double2, kMaxEl, false>);
+    const void *kern = c64 ? (const void *)kf : (const void *)kd;
+    if (dyn) WICK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    WICK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDetThreads, dyn));
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(occ, 1)));
     const size_t scratch_bytes = sizeof(double2) * (size_t)grid * (size_t)(plan->n_zu + plan->n_zd);
     const size_t part_bytes = sizeof(double2) * (size_t)items * plan->n_el;
@@ -707,13 +795,11 @@ int det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig,
     if (c64) {
         const float2 *u = (const float2 *)Su->data, *d = (const float2 *)Sd->data;
         const float2 *q = seq_flavour >= 0 ? (const float2 *)Sig->data : u;
-        if (one) det_eval_kernel<float2, 1><<<g, kDetThreads, 0, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
-        else det_eval_kernel<float2, kMaxEl><<<g, kDetThreads, 0, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
+        kf<<<g, kDetThreads, dyn, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
     } else {
         const double2 *u = (const double2 *)Su->data, *d = (const double2 *)Sd->data;
         const double2 *q = seq_flavour >= 0 ? (const double2 *)Sig->data : u;
-        if (one) det_eval_kernel<double2, 1><<<g, kDetThreads, 0, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
-        else det_eval_kernel<double2, kMaxEl><<<g, kDetThreads, 0, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
+        kd<<<g, kDetThreads, dyn, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
     }
     WICK_CUDA_TRY(cudaGetLastError());
     const int64_t n_out = n_slices * plan->n_el;
