@@ -11,18 +11,19 @@
 // 5 slices on a fixed-point grid 2^E (E bounds the |components| of its colour
 // c1 over the CTA's sites), every X value -- a double-FP32 number -- into 6
 // slices on a grid 2^F of its column (2^F >= sum|w| max|u| max|d|):
-//     v = 2^E * sum_i q_i 2^(-7-8i),   |q_i| <= 128   (39 / 47 bits)
-// A slice is an integer of at most 128 in magnitude, exact in bf16; a slice
-// product is at most 2^14 in magnitude, and a sum of K <= 768 of them (128
-// sites) below 2^24, so the FP32 accumulation in TMEM is exact for a whole
-// round of 128 sites.  The pair (i, j) carries the weight 2^(E+F-14-8(i+j));
-// pairs with i + j <= 5 are kept.  The grids bound the largest values of a
+//     v = 2^(E-7) * sum_i q_i 2^(-8i),   |q_i| <= 128   (39 / 47 bits)
+// Slice i is stored at its own weight, q_i 2^(-8i): at most 8 significant
+// bits, exact in bf16.  The products of the pair (i, j) are multiples of
+// 2^(-8(i+j)) of magnitude at most 2^(14-8(i+j)), and a sum of K <= 768 of
+// them (128 sites) stays below 2^(24-8(i+j)), so the FP32 accumulation in TMEM
+// is exact for a whole round of 128 sites, and every accumulator is read with
+// the one factor 2^(E+F-14).  Pairs with i + j <= 5 are kept.  The grids bound the largest values of a
 // 512-site range, so typical X values sit ~6 bits below 2^F: with 5 x 5 slices
 // and i + j <= 4 the blocks came out ~1e-9 relative, with 5 x 6 and i + j <= 5
 // ~5e-12 (the same class as the double-FP32 CUDA-core kernel).
-// Each round's accumulators are scaled by that exact power of two and added in
-// double-FP32 relative to 2^(E+F); the five U-slice rows of an output are
-// combined at the end and converted to FP64.
+// Each round's accumulators are added in double-FP32 relative to 2^(E+F-14);
+// the five U-slice rows of an output are combined at the end and converted to
+// FP64.
 //
 // Layout.  The U slices are stacked along M (row i*R + r, R = 2 n_spin n_chi)
 // and cut into M tiles of 128 rows; tile t meets only the X slices
@@ -58,6 +59,7 @@ constexpr int kRangeSites = 512;                   // sites per CTA (one grid, o
 constexpr int kSpinLimit = 1 << 22;                // mbarrier polls before giving up
 constexpr int kStage = 3;                          // staging buffers
 constexpr int kMaxRows = 24;                       // staged S rows (both flavours)
+constexpr int kListLen = 4;                        // terms per diquark list the tensor-core path takes (exactly)
 
 // exponent bound of the largest colour-list weight sum, per block type
 struct WeightExp {
@@ -76,8 +78,15 @@ template <int NC_, int NS_, int NT_, int NMT_, int NX_> struct Shape {
     static constexpr int NCT = (NC2 + NT - 1) / NT;         // column tiles
     static constexpr int PER_TILE = 4 / NMT;                // warps of a lane quarter per M tile
     static constexpr int CW = NT / PER_TILE;                // readout columns per thread
-    static constexpr int NXJOB = NX * kKa * NCTA;           // one X value each
-    static constexpr int NUJOB = NX * kKa / 2 * NS * NC;    // two U values each
+    static constexpr int NSP = NX / 2;                      // site pairs per chunk
+    static constexpr int PS = kMaxRows * NC * NX;           // floats per staged plane (re or im)
+    static constexpr int NXJOB = NCTA * kKa * NSP;          // two X values (a site pair) each
+    static constexpr int NUJOB = NS * NC * kKa * NSP;       // two U values (a site pair) each
+    // rotation of the thread -> job map in round r: the last round goes to the threads whose earlier
+    // jobs were U jobs (the cheaper ones)
+    static constexpr int rot(int r) {
+        return (r + 1) * kThr < NXJOB + NUJOB ? 0 : NXJOB % kThr;
+    }
     static constexpr int jmax(int t) {
         return kSlicesX < kMaxPair + 1 - t * 128 / R ? kSlicesX : kMaxPair + 1 - t * 128 / R;
     }
@@ -91,15 +100,15 @@ template <int NC_, int NS_, int NT_, int NMT_, int NX_> struct Shape {
                                    : TMEM_USED <= 256 ? 256 : 512;
     static constexpr int A_BYTES = NMT * 128 * KC * 2;
     static constexpr int B_BYTES = kSlicesX * NT * KC * 2;
-    static constexpr int S_BYTES = NX * kMaxRows * NC * 8;  // float2 staging
-    static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES + 4 * (16 + 256) + 16 * kKa * 4 + 64 + 32;
+    static constexpr int S_BYTES = 2 * PS * 4;              // two float planes
+    static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES + 4 * (16 + 256) +
+                                (16 + 8) * kKa * kListLen + 4 * 16 + 4 * kMaxRows * 12 + 32;
     static_assert(NMT * 128 >= kSlices * R && (NMT - 1) * 128 < kSlices * R, "M tiles");
     static_assert(NC2 <= NT || NC2 % NT == 0, "column tiles");
     static_assert(TMEM_USED <= 512 && CW % 4 == 0 && CW <= 32, "TMEM / readout");
-    static_assert(NXJOB % 32 == 0, "X jobs fill whole warps");
-    static_assert((NXJOB + NUJOB) % 32 == 0, "U jobs fill whole warps");
+    static_assert(NXJOB % 32 == 0 && NUJOB % 32 == 0, "jobs fill whole warps");
+    static_assert(NX % 8 == 0, "site pairs in groups of 4 per warp");
     static_assert(R % 8 == 0, "U slices start on a core-matrix row group");
-    static_assert(NCTA % 8 == 0 || NCTA % 8 == 4, "X job map");
     static_assert(kSlices * R * NT * 8 <= 2 * (A_BYTES + B_BYTES), "combine buffer");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -147,8 +156,8 @@ template <int KC> __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 __device__ __forceinline__ float2 to_f2(float2 v) { return v; }
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -207,173 +216,174 @@ tc_bounds_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ 
 }
 
 // Packed slicing: lanes (re, im) of a complex value at once on the f32x2
-// instructions.  Rounding to the nearest integer adds and subtracts 1.5 * 2^23
-// (exact for |t| < 2^22); a slice, an integer of at most 128 in magnitude, is
-// exact in bf16, whose bits are the upper half of the float's.
-// U: v = 2^E sum_i q_i 2^(-7-8i); returns the re-row word (q_re, -q_im) and the
-// im-row word (q_im, q_re) of every slice as bf16x2.
+// instructions.  A slice is kept at its own weight: slice i of r (|r| <= 128)
+// is r rounded to the grid 2^(-8i), i.e. q_i 2^(-8i) with an integer
+// |q_i| <= 128 -- at most 8 significant bits, exact in bf16, whose bits are
+// the upper half of the float's.  Rounding to the grid 2^(-8i) adds and
+// subtracts M_i = 1.5 * 2^(23-8i) (exact for |r| < 2^(22-8i)), and r minus
+// its rounding is exact, so no rescaling between slices is needed.
+__device__ __forceinline__ f2x round_grid(f2x r, int i) {
+    const float m = 12582912.f * exp2i(-8 * i);   // 1.5 * 2^(23-8i); i is a compile-time constant
+    const f2x M = pk(m, m);
+    return sub2(add2(r, M), M);
+}
+
+// U: lanes = two sites, v = 2^(E-7) sum_i q_i 2^(-8i) + O(2^(E-40)); one bf16x2 word per slice.
 // sc = 2^(7-E), a power of two (clamped to the float range; zero rows stay zero)
-__device__ __forceinline__ void slice_u2(float2 v, float sc, uint32_t *wre, uint32_t *wim) {
-    const f2x magic = pk(12582912.f, 12582912.f), k256 = pk(256.f, 256.f);
-    f2x r = mul2(pk(v.x, v.y), pk(sc, sc));  // exact: power-of-two scale
+__device__ __forceinline__ void slice_u2(f2x v, float sc, uint32_t *w) {
+    f2x r = mul2(v, pk(sc, sc));  // exact: power-of-two scale
 #pragma unroll
     for (int i = 0; i < kSlices; ++i) {
-        const f2x q = sub2(add2(r, magic), magic);
+        const f2x q = round_grid(r, i);
         uint32_t lo, hi;
         asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(q));
-        wre[i] = __byte_perm(lo, hi, 0x7632) ^ 0x80000000u;  // (q_re, -q_im)
-        wim[i] = __byte_perm(hi, lo, 0x7632);                // (q_im, q_re)
-        r = mul2(sub2(r, q), k256);
+        w[i] = __byte_perm(lo, hi, 0x7632);
+        if (i + 1 < kSlices) r = sub2(r, q);
     }
 }
 
-// X = (h + l) lane-wise: 2^F sum_j q_j 2^(-7-8j) + O(2^(F-48)); words (q_re, q_im) per slice;
-// sc = 2^(7-F)
+// X = (h + l) lane-wise (two sites): r = X 2^(7-F) = sum_j q_j 2^(-8j) + e, |e| <= 2^-40; one bf16x2 word per
+// slice; sc = 2^(7-F).  |r| <= 128 and the low part |l 2^(7-F)| <= 2^-13 (the list's rounding
+// errors).  The low part joins the remainder after the first slice by a TwoSum (t, e0): then
+// |t| <= 1/2 + 2^-13 (slice 1 still within 128) and |e0| <= 2^-25.  Slices 1 and 2 take t alone
+// (exact remainders, the second within 2^-17); e0 joins after slice 2 with one rounding of at most
+// 2^-41, below slice 3's grid 2^-24; slices 3 to 5 round that single float.
 __device__ __forceinline__ void slice_x2(f2x h, f2x l, float sc, uint32_t *w) {
-    const f2x magic = pk(12582912.f, 12582912.f), k256 = pk(256.f, 256.f), s2 = pk(sc, sc);
-    f2x rh = mul2(h, s2), rl = mul2(l, s2);
-#pragma unroll
-    for (int j = 0; j < kSlicesX; ++j) {
-        const f2x q = sub2(add2(rh, magic), magic);
+    const f2x s2 = pk(sc, sc);
+    const f2x rh = mul2(h, s2), rl = mul2(l, s2);
+    auto word = [](f2x q) {
         uint32_t lo, hi;
         asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(q));
-        w[j] = __byte_perm(lo, hi, 0x7632);
-        // (rh - q) + rl exactly as a pair (TwoSum), then the next 8 bits up
-        const f2x d = sub2(rh, q);
-        const f2x t = add2(d, rl);
-        const f2x bb = sub2(t, d);
-        const f2x e = add2(sub2(d, sub2(t, bb)), sub2(rl, bb));
-        rh = mul2(t, k256);
-        rl = mul2(e, k256);
+        return __byte_perm(lo, hi, 0x7632);
+    };
+    f2x q = round_grid(rh, 0);
+    w[0] = word(q);
+    const f2x d0 = sub2(rh, q);
+    const f2x t = add2(d0, rl), bb = sub2(t, d0);
+    const f2x e0 = add2(sub2(d0, sub2(t, bb)), sub2(rl, bb));
+    q = round_grid(t, 1);
+    w[1] = word(q);
+    const f2x d1 = sub2(t, q);
+    q = round_grid(d1, 2);
+    w[2] = word(q);
+    f2x r = add2(sub2(d1, q), e0);
+#pragma unroll
+    for (int j = 3; j < kSlicesX; ++j) {
+        q = round_grid(r, j);
+        w[j] = word(q);
+        if (j + 1 < kSlicesX) r = sub2(r, q);
     }
 }
 
-constexpr int kListLen = 4;  // terms per diquark list the tensor-core path takes (exactly)
+__device__ __forceinline__ f2x lds2(const float *p) { return *reinterpret_cast<const f2x *>(p); }
 
-// double-FP32 list sum X_{o,a}[c23] of one staged site (lanes re, im).  term[t] = (row2 * NC,
-// row3 * NC, weight bits): the list's terms, staged in shared memory; all loads first.
-__device__ __forceinline__ pdf x_value(const int4 *term, const float2 *s1, const float2 *s2) {
-    int4 tt[kListLen];
-#pragma unroll
-    for (int t = 0; t < kListLen; ++t) tt[t] = term[t];
-    float2 u[kListLen], d[kListLen];
+// The pair of sites (s, s + 1) of one column of the X_{o,a} list in double-FP32, lanes = sites:
+// re += w (ur dr - ui di), im += w (ur di + ui dr) per term, every product exact (TwoProd) and
+// summed by TwoSum.  term[t] = (float offset of the u row, of the d row, w, w), wn[t] = (-w, -w);
+// the re / im planes are PS floats apart.  All loads first.
+template <int PS>
+__device__ __forceinline__ void x_pair(const int4 *term, const f2x *wn, const float *bu, const float *bd, pdf &re,
+                                       pdf &im) {
+    f2x ur[kListLen], ui[kListLen], dr[kListLen], di[kListLen], ww[kListLen], nw[kListLen];
 #pragma unroll
     for (int t = 0; t < kListLen; ++t) {
-        u[t] = s1[tt[t].x];
-        d[t] = s2[tt[t].y];
+        const int4 tt = term[t];
+        ur[t] = lds2(bu + tt.x);
+        ui[t] = lds2(bu + tt.x + PS);
+        dr[t] = lds2(bd + tt.y);
+        di[t] = lds2(bd + tt.y + PS);
+        asm("mov.b64 %0, {%1, %2};" : "=l"(ww[t]) : "r"(tt.z), "r"(tt.w));
+        nw[t] = wn[t];
     }
-    // one packed accumulator with lanes (re, im): w u d = (ax dx - ay dy, ax dy + ay dx) is the sum of
-    // the lane products (ax, ax) (dx, dy) and (-ay, ay) (dy, dx), each exact as a TwoProd pair; the
-    // first product starts the accumulator without a TwoSum
-    pdf acc;
-    {
-        const float w = __int_as_float(tt[0].z);
-        const float ax = w * u[0].x, ay = w * u[0].y;  // exact: w is +-2^k
-        const f2x B1 = pk(d[0].x, d[0].y), B2 = pk(d[0].y, d[0].x);
-        const f2x nA1 = pk(-ax, -ax);
-        const f2x np = mul2(nA1, B1);                   // -RN(A1 B1)
-        acc.h = sub2(0ull, np);
-        acc.l = fma2(pk(ax, ax), B1, np);               // A1 B1 - RN(A1 B1)
-        pacc_exact(acc, pk(-ay, ay), pk(ay, -ay), B2);
+    {   // the first products start the accumulators without a TwoSum
+        const f2x a = mul2(ur[0], ww[0]), na = mul2(ur[0], nw[0]);
+        f2x np = mul2(na, dr[0]);
+        re.h = sub2(0ull, np);
+        re.l = fma2(a, dr[0], np);
+        np = mul2(na, di[0]);
+        im.h = sub2(0ull, np);
+        im.l = fma2(a, di[0], np);
+        const f2x b = mul2(ui[0], ww[0]), nb = mul2(ui[0], nw[0]);
+        pacc_exact(re, nb, b, di[0]);   // - w ui di
+        pacc_exact(im, b, nb, dr[0]);
     }
 #pragma unroll
     for (int t = 1; t < kListLen; ++t) {
-        const float w = __int_as_float(tt[t].z);
-        const float ax = w * u[t].x, ay = w * u[t].y;
-        const f2x B1 = pk(d[t].x, d[t].y), B2 = pk(d[t].y, d[t].x);
-        pacc_exact(acc, pk(ax, ax), pk(-ax, -ax), B1);
-        pacc_exact(acc, pk(-ay, ay), pk(ay, -ay), B2);
+        const f2x a = mul2(ur[t], ww[t]), na = mul2(ur[t], nw[t]);   // exact: w = +-2^k
+        const f2x b = mul2(ui[t], ww[t]), nb = mul2(ui[t], nw[t]);
+        pacc_exact(re, a, na, dr[t]);
+        pacc_exact(re, nb, b, di[t]);
+        pacc_exact(im, a, na, di[t]);
+        pacc_exact(im, b, nb, dr[t]);
     }
-    return acc;
 }
 
-// X job jb -> (column n, combo gc = (site, a)).  A warp takes 8 columns x 4
-// combos: its 32-bit stores then fall on 8 rows x 4 words of a core matrix,
-// 32 different banks (the leftover 4 columns of a 36-column tile: 4 x 8, two
-// ways).  Consecutive columns of one combo would meet only 8 banks.
-template <typename SH> __device__ __forceinline__ void x_map(int jb, int &n, int &gc) {
-    constexpr int NG = SH::NCTA / 8, GW = SH::NX * kKa / 4;
+// Job jb over (row or column n < NN, colour term a < kKa, site pair sp < NSP) -> (n, a, sp).  A
+// warp takes one a and 8 n x 4 site pairs: its 32-bit operand stores then fall on 8 rows x 4 words
+// of a core matrix, 32 different banks; a leftover group of 4 n takes 4 n x 8 site pairs.
+template <int NN, int NSP> __device__ __forceinline__ void job_map(int jb, int &n, int &a, int &sp) {
+    constexpr int NG = NN / 8, FW = NG * (NSP / 4), GA = FW + (NN % 8 ? 1 : 0);
+    static_assert(NN % 8 == 0 || (NN % 8 == 4 && NSP == 8), "job map");
     const int w = jb >> 5, lane = jb & 31;
-    if (w < NG * GW) {
-        n = 8 * (w % NG) + (lane & 7);
-        gc = 4 * (w / NG) + (lane >> 3);
+    a = w / GA;
+    const int wa = w - a * GA;
+    if (wa < FW) {
+        n = 8 * (wa % NG) + (lane >> 2);
+        sp = 4 * (wa / NG) + (lane & 3);
     } else {
-        n = 8 * NG + (lane & 3);
-        gc = 8 * (w - NG * GW) + (lane >> 2);
+        n = 8 * NG + (lane >> 3);
+        sp = lane & 7;
     }
 }
 
-// X job jb: column n, combo gc = (site, a); 6 slices into B_j[n][(site, a, part)]
+// X job: column n, colour term a, sites (2 sp, 2 sp + 1); 6 slices into B_j[n][k], k = (a, part, site)
 template <typename SH>
-__device__ __forceinline__ void x_job(const int4 *sTerm, const float2 *S, int nr, int off1, int off2, int col0,
-                                      int n_a, const int *sF, __nv_bfloat16 *B, int jb) {
-    constexpr int NC = SH::NC, NT = SH::NT;
-    int n, gc;
-    x_map<SH>(jb, n, gc);
-    const int site = gc / kKa, a = gc % kKa;
-    uint32_t w[kSlicesX];
-    if (a < n_a) {
-        const int c23 = col0 + n;
-        const pdf X = x_value(sTerm + a * kListLen, S + site * nr * NC + off1 + c23 / NC,
-                              S + site * nr * NC + off2 + c23 % NC);
-        slice_x2(X.h, X.l, exp2i(7 - sF[n]), w);
-    } else {
-#pragma unroll
-        for (int j = 0; j < kSlicesX; ++j) w[j] = 0u;
-    }
-    __nv_bfloat16 *dst = B + tile_off<SH::KC>(n, gc * 2);
-#pragma unroll
-    for (int j = 0; j < kSlicesX; ++j) *reinterpret_cast<uint32_t *>(dst + j * NT * SH::KC) = w[j];
-}
-
-// two X jobs with independent chains (both jA, jB < NXJOB)
-template <typename SH>
-__device__ __forceinline__ void x_job2(const int4 *sTerm, const float2 *S, int nr, int off1, int off2, int col0,
-                                       int n_a, const int *sF, __nv_bfloat16 *B, int jA, int jB) {
-    constexpr int NC = SH::NC, NT = SH::NT;
-    int nA, gA, nB, gB;
-    x_map<SH>(jA, nA, gA);
-    x_map<SH>(jB, nB, gB);
-    const int aA = gA % kKa, aB = gB % kKa;
-    const int cA = col0 + nA, cB = col0 + nB;
-    const float2 *bA = S + (gA / kKa) * nr * NC, *bB = S + (gB / kKa) * nr * NC;
-    pdf XA = x_value(sTerm + (aA < n_a ? aA : 0) * kListLen, bA + off1 + cA / NC, bA + off2 + cA % NC);
-    pdf XB = x_value(sTerm + (aB < n_a ? aB : 0) * kListLen, bB + off1 + cB / NC, bB + off2 + cB % NC);
-    if (aA >= n_a) XA.h = XA.l = 0ull;
-    if (aB >= n_a) XB.h = XB.l = 0ull;
-    uint32_t wA[kSlicesX], wB[kSlicesX];
-    slice_x2(XA.h, XA.l, exp2i(7 - sF[nA]), wA);
-    slice_x2(XB.h, XB.l, exp2i(7 - sF[nB]), wB);
-    __nv_bfloat16 *dA = B + tile_off<SH::KC>(nA, gA * 2), *dB = B + tile_off<SH::KC>(nB, gB * 2);
+__device__ __forceinline__ void x_job(const int4 *sTerm, const f2x *sTermN, const float *S, int col0, int n_a,
+                                      const int *sF, __nv_bfloat16 *B, int jb) {
+    constexpr int NC = SH::NC, NT = SH::NT, NX = SH::NX, KC = SH::KC;
+    int n, a, sp;
+    job_map<SH::NCTA, SH::NSP>(jb, n, a, sp);
+    if (a >= n_a) return;  // warp-uniform; those K rows stay zero
+    const int c23 = col0 + n;
+    pdf re, im;
+    x_pair<SH::PS>(sTerm + a * kListLen, sTermN + a * kListLen, S + (c23 / NC) * NX + 2 * sp,
+                   S + (c23 % NC) * NX + 2 * sp, re, im);
+    uint32_t wr[kSlicesX], wi[kSlicesX];
+    const float sc = exp2i(7 - sF[n]);
+    slice_x2(re.h, re.l, sc, wr);
+    slice_x2(im.h, im.l, sc, wi);
+    __nv_bfloat16 *dst = B + tile_off<KC>(n, a * 2 * NX + 2 * sp);
 #pragma unroll
     for (int j = 0; j < kSlicesX; ++j) {
-        *reinterpret_cast<uint32_t *>(dA + j * NT * SH::KC) = wA[j];
-        *reinterpret_cast<uint32_t *>(dB + j * NT * SH::KC) = wB[j];
+        *reinterpret_cast<uint32_t *>(dst + j * NT * KC) = wr[j];
+        *reinterpret_cast<uint32_t *>(dst + j * NT * KC + NX * 8) = wi[j];  // part 1: k + NX
     }
 }
 
-// U job ju: row (s, c1), combos 2 gp and 2 gp + 1; 5 slices into A[(i, part, s, c1)][(site, a, part')]
+// U job: row (s, c1), colour term a, sites (2 sp, 2 sp + 1); 5 slices into A[(i, part, s, c1)][k]:
+// the re row takes (U_re, -U_im) against (X_re, X_im), the im row (U_im, U_re)
 template <typename SH>
-__device__ __forceinline__ void u_job(const int *sR1, const float2 *S, int nr, int n_a, const int *sEU,
-                                      __nv_bfloat16 *A, int ju) {
-    constexpr int NC = SH::NC, NS = SH::NS, R = SH::R;
-    const int sc1 = ju % (NS * NC), gp = ju / (NS * NC);
-    const int s = sc1 / NC, c1 = sc1 % NC;
-    const float scu = exp2i(7 - sEU[c1]);
-    uint32_t wre[2][kSlices], wim[2][kSlices];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int gc = 2 * gp + h, site = gc / kKa, a = gc % kKa;
-        float2 u = make_float2(0.f, 0.f);
-        if (a < n_a) u = S[site * nr * NC + sR1[s * kKa + a] + c1];
-        slice_u2(u, scu, wre[h], wim[h]);
-    }
-    // re row: U_re X_re - U_im X_im ; im row: U_im X_re + U_re X_im
-    __nv_bfloat16 *dre = A + tile_off<SH::KC>(s * NC + c1, gp * 4), *dim = A + tile_off<SH::KC>(NS * NC + s * NC + c1, gp * 4);
+__device__ __forceinline__ void u_job(const int *sR1, const float *S, int n_a, const int *sEU, __nv_bfloat16 *A,
+                                      int ju) {
+    constexpr int NC = SH::NC, NS = SH::NS, NX = SH::NX, R = SH::R, KC = SH::KC;
+    int m, a, sp;
+    job_map<NS * NC, SH::NSP>(ju, m, a, sp);
+    if (a >= n_a) return;
+    const int s = m / NC, c1 = m % NC;
+    const float *p = S + sR1[s * kKa + a] + c1 * NX + 2 * sp;
+    uint32_t qr[kSlices], qi[kSlices];
+    const float sc = exp2i(7 - sEU[c1]);
+    slice_u2(lds2(p), sc, qr);
+    slice_u2(lds2(p + SH::PS), sc, qi);
+    __nv_bfloat16 *dre = A + tile_off<KC>(m, a * 2 * NX + 2 * sp);
+    __nv_bfloat16 *dim = A + tile_off<KC>(NS * NC + m, a * 2 * NX + 2 * sp);
 #pragma unroll
     for (int i = 0; i < kSlices; ++i) {
-        *reinterpret_cast<uint2 *>(dre + tile_off<SH::KC>(i * R, 0)) = make_uint2(wre[0][i], wre[1][i]);
-        *reinterpret_cast<uint2 *>(dim + tile_off<SH::KC>(i * R, 0)) = make_uint2(wim[0][i], wim[1][i]);
+        const int o = tile_off<KC>(i * R, 0);
+        *reinterpret_cast<uint32_t *>(dre + o) = qr[i];
+        *reinterpret_cast<uint32_t *>(dre + o + NX * 8) = qi[i] ^ 0x80008000u;
+        *reinterpret_cast<uint32_t *>(dim + o) = qi[i];
+        *reinterpret_cast<uint32_t *>(dim + o + NX * 8) = qr[i];
     }
 }
 
@@ -393,16 +403,19 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
     const int col0 = ct * NT;
     const int t0 = plan.os_off[o * NS];
     const int n_a = plan.os_off[o * NS + 1] - t0;
-    const int off1 = f1 == 0 ? 0 : nr0 * NC, off2 = f1 == 0 ? nr0 * NC : 0;  // flavour rows in a staged site
+    constexpr int NX = SH::NX, KC = SH::KC, PS = SH::PS;
+    const int rc1 = f1 == 0 ? 0 : nr0, rc2 = f1 == 0 ? nr0 : 0;  // first staged row of either flavour
 
     __nv_bfloat16 *sA0 = reinterpret_cast<__nv_bfloat16 *>(smem);
     __nv_bfloat16 *sB0 = reinterpret_cast<__nv_bfloat16 *>(smem + 2 * SH::A_BYTES);
-    float2 *sS0 = reinterpret_cast<float2 *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES));
+    float *sS0 = reinterpret_cast<float *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES));
     int *sEU = reinterpret_cast<int *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES) + kStage * SH::S_BYTES);
     int *sF = sEU + 16;                                       // [256] grid of X per column
     int4 *sTerm = reinterpret_cast<int4 *>(sF + 256);         // [kKa][kListLen] the op's diquark list terms
-    int *sR1 = reinterpret_cast<int *>(sTerm + kKa * kListLen);   // [NS][kKa] staged offset of U's row
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sR1 + 16);      // [2]
+    f2x *sTermN = reinterpret_cast<f2x *>(sTerm + kKa * kListLen);  // [kKa][kListLen] (-w, -w)
+    int *sR1 = reinterpret_cast<int *>(sTermN + kKa * kListLen);    // [NS][kKa] staged offset of U's row
+    int *sSrc = sR1 + 16;                                     // [kMaxRows * NC] flavour << 16 | row * 12 + chi
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sSrc + kMaxRows * 12);   // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
 
     // zero both operand buffers once: padding rows and unused colour terms stay zero
@@ -419,15 +432,25 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
     if (tid < kKa * kListLen) {
         const int a = tid / kListLen, t = tid % kListLen;
         int4 v = make_int4(0, 0, 0, 0);
+        float w = 0.f;
         if (a < n_a) {
             const int q = plan.x_off[plan.os_x[t0 + a]] + t;
-            v = make_int4(plan.xt_r2[q] * NC, plan.xt_r3[q] * NC, __float_as_int(plan.xt_w[q]), 0);
+            w = plan.xt_w[q];
+            v = make_int4((rc1 + plan.xt_r2[q]) * NC * NX, (rc2 + plan.xt_r3[q]) * NC * NX, __float_as_int(w),
+                          __float_as_int(w));
         }
         sTerm[tid] = v;
+        sTermN[tid] = pk(-w, -w);
     }
     if (tid >= 32 && tid < 32 + NS * kKa) {
         const int s = (tid - 32) / kKa, a = (tid - 32) % kKa;
-        sR1[s * kKa + a] = a < n_a ? off1 + plan.os_r1[plan.os_off[o * NS + s] + a] * NC : 0;
+        sR1[s * kKa + a] = a < n_a ? (rc1 + plan.os_r1[plan.os_off[o * NS + s] + a]) * NC * NX : 0;
+    }
+    for (int e = tid; e < nr * NC; e += kThr) {
+        const int rc = e / NC, ic = e - rc * NC;
+        const int f = rc < nr0 ? 0 : 1;
+        const int row = f == 0 ? plan.rows[0][rc] : plan.rows[1][rc - nr0];
+        sSrc[e] = f << 16 | (row * 12 + plan.chi[ic]);
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
@@ -441,24 +464,31 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
     }
 
     const int x_begin = rng * kRangeSites, x_end = min(V, x_begin + kRangeSites);
-    constexpr int NX = SH::NX, KC = SH::KC;
     const int n_chunks = (x_end - x_begin + NX - 1) / NX;
     const ST *su = Su + (size_t)slice * V * 144;
     const ST *sd = Sd + (size_t)slice * V * 144;
-    // stage the rows of chunk c: sS[site][row][ic] as float2, flavour-0 rows first (zeros past the range)
+    __syncthreads();   // sSrc
+    // stage the rows of chunk c as two planes (re, im) of [row][ic][site], flavour-0 rows first, sites
+    // innermost (zeros past the range)
     auto stage = [&](int c) {
-        float2 *dst = sS0 + (c % kStage) * (SH::S_BYTES / 8);
+        float *dst = sS0 + (c % kStage) * (2 * PS);
         const int xb = x_begin + c * NX;
         for (int e = tid; e < NX * nr * NC; e += kThr) {
-            const int site = e / (nr * NC);
-            const int rem = e - site * nr * NC;
-            const int rc = rem / NC, ic = rem - rc * NC;
-            const int f = rc < nr0 ? 0 : 1;
-            const int row = f == 0 ? plan.rows[0][rc] : plan.rows[1][rc - nr0];
-            const ST *src = (f == 0 ? su : sd) + (size_t)(xb + site) * 144 + row * 12 + plan.chi[ic];
-            if (xb + site >= x_end) dst[e] = make_float2(0.f, 0.f);
-            else if constexpr (sizeof(ST) == 8) cp_async8(dst + e, src);
-            else dst[e] = to_f2(*src);
+            const int site = e % NX, rcc = e / NX;
+            const int src_off = sSrc[rcc];
+            const ST *src = ((src_off >> 16) ? sd : su) + (size_t)(xb + site) * 144 + (src_off & 0xFFFF);
+            float *d0 = dst + e;   // = rcc * NX + site
+            if (xb + site >= x_end) {
+                d0[0] = 0.f;
+                d0[PS] = 0.f;
+            } else if constexpr (sizeof(ST) == 8) {
+                cp_async4(d0, reinterpret_cast<const float *>(src));
+                cp_async4(d0 + PS, reinterpret_cast<const float *>(src) + 1);
+            } else {
+                const float2 v = to_f2(*src);
+                d0[0] = v.x;
+                d0[PS] = v.y;
+            }
         }
         cp_async_commit();
     };
@@ -494,7 +524,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
         const int buf = c & 1;
         __nv_bfloat16 *A = sA0 + buf * (SH::A_BYTES / 2);
         __nv_bfloat16 *B = sB0 + buf * (SH::B_BYTES / 2);
-        const float2 *S = sS0 + (c % kStage) * (SH::S_BYTES / 8);
+        const float *S = sS0 + (c % kStage) * (2 * PS);
         // the MMAs of chunk c - 2 read this operand buffer
         if (buf == 0 && waited0 < issued0) {
             if (poll_parity(&mbar[0], waited0 & 1)) ++waited0;
@@ -504,18 +534,14 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
             else bad = 1;
         }
         if (!bad) {
-            // jobs j0 and j0 + kThr per round: two X values are built side by side (independent chains);
-            // X jobs come first and fill whole warps, so every branch is warp-uniform
+            // one job per thread and round: X jobs first, then U jobs; both fill whole warps, so every
+            // branch is warp-uniform.  The last round goes to the threads that took U jobs before.
             constexpr int NJ = SH::NXJOB + SH::NUJOB;
-            for (int j0 = tid; j0 < NJ; j0 += 2 * kThr) {
-                const int jA = j0, jB = j0 + kThr;
-                if (jB < SH::NXJOB) {
-                    x_job2<SH>(sTerm, S, nr, off1, off2, col0, n_a, sF, B, jA, jB);
-                } else {
-                    if (jA < SH::NXJOB) x_job<SH>(sTerm, S, nr, off1, off2, col0, n_a, sF, B, jA);
-                    else u_job<SH>(sR1, S, nr, n_a, sEU, A, jA - SH::NXJOB);
-                    if (jB < NJ) u_job<SH>(sR1, S, nr, n_a, sEU, A, jB - SH::NXJOB);
-                }
+#pragma unroll 1
+            for (int r = 0; r * kThr < NJ; ++r) {
+                const int jb = r * kThr + (tid + kThr - SH::rot(r)) % kThr;
+                if (jb < SH::NXJOB) x_job<SH>(sTerm, sTermN, S, col0, n_a, sF, B, jb);
+                else if (jb < NJ) u_job<SH>(sR1, S, n_a, sEU, A, jb - SH::NXJOB);
             }
         }
         // staged rows of chunk c + 1 complete (this thread's copies); operands of chunk c written
@@ -583,9 +609,8 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
                                  : "r"(taddr + (uint32_t)c4));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
                 if (row_ok && my_i + j <= kMaxPair) {
-                    const float scale = exp2i(-14 - 8 * (my_i + j));
 #pragma unroll
-                    for (int n = 0; n < SH::CW; ++n) acc_add(acc[n], df{__fmul_rn(__uint_as_float(r[n]), scale), 0.f});
+                    for (int n = 0; n < SH::CW; ++n) acc_add(acc[n], df{__uint_as_float(r[n]), 0.f});
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -624,7 +649,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
         }
         const int pp = rr / (NS * NC), sc1 = rr % (NS * NC);   // part, (s, c1)
         const int s_ = sc1 / NC, c1 = sc1 % NC;
-        const double v = ((double)s.h + (double)s.l) * exp2d(sEU[c1] + sF[n]);
+        const double v = ((double)s.h + (double)s.l) * exp2d(sEU[c1] + sF[n] - 14);
         const size_t out = ((size_t)(o * NS + s_) * NC + c1) * SH::NC2 + col0 + n;
         part[2 * out + pp] = v;
     }
