@@ -142,6 +142,28 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def gpu_local_cpus(device: int):
+    """The host CPUs next to the GPU (sysfs local_cpulist of its PCI function), limited to the CPUs
+    this process may run on; None when unknown.  Pinned buffers allocated by a thread on these CPUs
+    land in the GPU's own host memory node (first touch), so their copies take the direct link."""
+    import torch
+    p = torch.cuda.get_device_properties(device)
+    try:
+        bdf = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        text = open(f"/sys/bus/pci/devices/{bdf}/local_cpulist").read().strip()
+    except (AttributeError, OSError):
+        return None
+    cpus = set()
+    for part in text.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    cpus &= os.sched_getaffinity(0)
+    return cpus or None
+
+
 def block_bytes_per_site(dtype_bytes: int) -> int:
     """Algorithmic DRAM bytes per site of the upper-component block build: the
     six sink-upper rows (a, alpha in {0,1}) of S_u and S_d.  Every 32-byte
@@ -268,14 +290,21 @@ def run_ours(args):
     reduce_s = time.perf_counter() - t0
     (n_raw, n_zero, n_keys, U), bound = terms.stats()
 
-    # inputs: two configurations per rank, resident on the device; pinned host copies for e2e
+    # inputs: two configurations per rank, resident on the device; pinned host copies for e2e,
+    # allocated from the CPUs next to the GPU so that they sit in its local host memory
     cfg_host, cfg_dev = [], []
+    all_cpus = os.sched_getaffinity(0)
+    local_cpus = gpu_local_cpus(torch.cuda.current_device())
+    if local_cpus:
+        os.sched_setaffinity(0, local_cpus)
     for c in sharding.shard(2 * world, rank, world):
         Su, Sd = host_props(sharding.config_seed(w["seed"], c), L, T, n_src)
         hu = torch.from_numpy(Su).pin_memory()
         hd = torch.from_numpy(Sd).pin_memory()
         cfg_host.append((hu, hd))
         cfg_dev.append((hu.cuda(), hd.cuda()))
+    Cpin = torch.empty_like(torch.empty((n_src, T), dtype=torch.complex128), device="cpu").pin_memory()
+    os.sched_setaffinity(0, all_cpus)
     blocks = torch.empty((n_src, T, nuc.n_blk), dtype=torch.complex128, device="cuda")
     Cout = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
     prec = wick.WICK_MIXED
@@ -335,44 +364,63 @@ def run_ours(args):
     rel = (C_mixed - C64).abs() / C64.abs()
     rel_err = float(rel.max().item())
 
-    # end to end through the API with host buffers: every step copies its configuration from pinned
-    # host memory (a copy stream, two device buffers, so the next upload overlaps the current
-    # computation), runs both calls and reads C back to pinned host memory
-    h2d = 2 * cfg_host[0][0].numel() * cfg_host[0][0].element_size()
+    # end to end through the API with host buffers: every step uploads, from pinned host memory, the
+    # rows of its configuration that the block build reads (wick_upload_rows; a copy stream, two
+    # device buffers, so the next upload overlaps the current computation), runs the build and the
+    # contraction and reads C back to pinned host memory
     d2h = Cout.numel() * Cout.element_size()
     ke = max(4, min(10, args.steps))
-    Cpin = torch.empty_like(Cout, device="cpu").pin_memory()
     dbufs = [(torch.empty_like(cfg_dev[0][0]), torch.empty_like(cfg_dev[0][1])) for _ in range(2)]
     copy_stream = torch.cuda.Stream()
     copied = [torch.cuda.Event() for _ in range(2)]
     free = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_step(i):
+    def e2e_step(i, mode=wick.WICK_UPLOAD_AUTO):
         b = i % 2
         hu, hd = cfg_host[i % len(cfg_host)]
         with torch.cuda.stream(copy_stream):
             if i >= 2:
                 copy_stream.wait_event(free[b])          # the buffer's previous step has finished
-            dbufs[b][0].copy_(hu, non_blocking=True)
-            dbufs[b][1].copy_(hd, non_blocking=True)
+            nb = wick.wick_upload_rows(hu, hd, dbufs[b][0], dbufs[b][1], tabs, L, T, n_src, copy_stream, mode)
             copied[b].record(copy_stream)
         stream.wait_event(copied[b])
         wick.wick_build_blocks(dbufs[b][0], dbufs[b][1], tabs, prec, blocks, L, T, n_src, stream)
         wick.wick_contract(blocks, n_src, T, terms, prec, Cout, stream)
         Cpin.copy_(Cout, non_blocking=True)
         free[b].record(stream)
+        return nb
 
-    for i in range(4):                                   # warm-up: first DMA of each pinned buffer is slow
-        e2e_step(i)
+    def e2e_time(mode):
+        for i in range(4):                               # warm-up: first DMA of each pinned buffer is slow
+            nb = e2e_step(i, mode)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        copy_stream.wait_event(g0)
+        for i in range(ke):
+            e2e_step(i, mode)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        return sharding.max_over_ranks(g0.elapsed_time(g1) / ke, device="cuda") / world, nb
+
+    e2e_dma, h2d_dma = e2e_time(wick.WICK_UPLOAD_DMA)         # pitched copies of the row runs
+    e2e_kernel, h2d_kernel = e2e_time(wick.WICK_UPLOAD_KERNEL)  # the gather kernel
+    upload_mode = wick.WICK_UPLOAD_KERNEL if e2e_kernel < e2e_dma else wick.WICK_UPLOAD_DMA
+    e2e, h2d = (e2e_kernel, h2d_kernel) if upload_mode == wick.WICK_UPLOAD_KERNEL else (e2e_dma, h2d_dma)
+    # the link alone: one configuration's row upload, and a full copy of it, on the copy stream
+    c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    with torch.cuda.stream(copy_stream):
+        c0.record(copy_stream)
+        wick.wick_upload_rows(cfg_host[0][0], cfg_host[0][1], dbufs[0][0], dbufs[0][1], tabs, L, T, n_src,
+                              copy_stream, upload_mode)
+        c1.record(copy_stream)
+        dbufs[0][0].copy_(cfg_host[0][0], non_blocking=True)
+        dbufs[0][1].copy_(cfg_host[0][1], non_blocking=True)
+        c2.record(copy_stream)
     torch.cuda.synchronize()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    copy_stream.wait_event(g0)
-    for i in range(ke):
-        e2e_step(i)
-    g1.record(stream)
-    torch.cuda.synchronize()
-    e2e = sharding.max_over_ranks(g0.elapsed_time(g1) / ke, device="cuda") / world
+    h2d_gbs = h2d / (c0.elapsed_time(c1) / 1e3) / 1e9
+    full_bytes = 2 * cfg_host[0][0].numel() * cfg_host[0][0].element_size()
+    full_gbs = full_bytes / (c1.elapsed_time(c2) / 1e3) / 1e9
 
     # the same configurations through the batched executor: one CUDA-graph launch per pair
     bblocks = torch.empty((len(cfg_dev), n_src, T, nuc.n_blk), dtype=torch.complex128, device="cuda")
@@ -436,7 +484,14 @@ def run_ours(args):
                                 "frac": mma_flops / (build_ms / 1e3) / 1e12 / bf16_peak,
                                 "peak_kind": "measured bf16 burst (the MMAs issued, padding included)"},
                      "cuda_core_kernel_ms": simt_ms},
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "upload": "wick_upload_rows: the sink-upper rows the block build reads (half of S), by the " +
+                          ("gather kernel" if upload_mode == wick.WICK_UPLOAD_KERNEL else "copy engines") +
+                          " (the faster of the two in this run; the host link is shared, so e2e varies by box)",
+                "value_kernel_upload": e2e_kernel, "value_dma_upload": e2e_dma,
+                "h2d_gbs_alone": h2d_gbs, "full_copy_gbs": full_gbs,
+                "host_buffers": "pinned; allocated from the GPU's local CPUs (%s)" % (
+                    f"{len(local_cpus)} CPUs" if local_cpus else "unknown, default placement")},
         "gpu_launches": kernels_per_config * args.steps,
         "clocks": clk,
     }

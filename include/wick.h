@@ -146,10 +146,12 @@ size_t wick_block_count(const wick_block_layout *layout);
  *               with FMA, sums as float pairs (about 44 significant bits) over a
  *               chunk of at most 256 sites -- and an FP64 sum of the chunks.
  *               C128 input is rounded to float first under WICK_MIXED.  For the
- *               upper-spin tables the update sum over sites runs on the tensor
- *               cores (tcgen05, bf16) as an exact sliced product: 16-site chunks,
- *               5 x 5 fixed-point slices of 8 bits, every chunk sum exact in FP32,
- *               slice pairs combined in double-FP32 (same accuracy class).
+ *               upper- and full-spin tables with +-2^k weights the update sum
+ *               over sites runs on the tensor cores (tcgen05, bf16) as an exact
+ *               sliced product: U in 5 and the double-FP32 diquark values in 6
+ *               fixed-point slices of 8 bits, slice pairs i + j <= 5, every
+ *               128-site sum exact in FP32, rounds combined in double-FP32 (same
+ *               accuracy class).
  *               WICK_MIXED_SIMT requests the CUDA-core double-FP32 kernel.
  *   blocks      device, caller-owned, complex128 [n_src][T][wick_block_count]
  * Uses a library-cached device workspace for the per-chunk FP64 partials
@@ -160,6 +162,37 @@ size_t wick_block_count(const wick_block_layout *layout);
 int wick_build_blocks(const wick_prop *Su, const wick_prop *Sd, const wick_nucleon_op *ops,
                       const wick_block_layout *layout, int precision, void *blocks,
                       wick_stream_t stream);
+
+/*
+ * Upload of the propagator rows a block build reads.  Eq. 2.4/2.5 take
+ * S(x)(chi, c) only at the sink indices chi that the nucleon tables use (for
+ * the upper-spin tables the six rows (a, alpha), alpha in {0, 1}: half of S),
+ * so only those rows cross the host link.
+ *   Su_host, Sd_host  page-locked host memory (cudaHostAlloc / cudaHostRegister),
+ *                     the wick_prop layout; read after the call returns, so keep
+ *                     them alive until `stream` reaches this point
+ *   Su_dev, Sd_dev    device propagators of the same shape and dtype; the rows the
+ *                     tables do not read are left as they are
+ *   ops, layout       the tables of the wick_build_blocks call that follows
+ *   mode              WICK_UPLOAD_KERNEL: a gather kernel reads the rows from the
+ *                     device-mapped host buffers (16-byte words, one warp per site;
+ *                     WICK_EINVAL when the host memory is not mapped);
+ *                     WICK_UPLOAD_DMA: one pitched copy (cudaMemcpy2DAsync) per run of
+ *                     consecutive rows and flavour, on the copy engines;
+ *                     WICK_UPLOAD_AUTO: DMA (the kernel is faster on an idle GPU, 205
+ *                     against 170 GB/s on a GB300's host link, but takes SM slots from a
+ *                     block build that runs beside it)
+ *   bytes             out, may be NULL: the bytes copied (both flavours)
+ * Everything is enqueued on `stream`.
+ * Errors: WICK_EINVAL (shapes or dtypes differ, invalid tables or mode, host memory
+ * not page-locked, device pointer not 16-byte aligned), WICK_ECUDA.
+ */
+#define WICK_UPLOAD_AUTO 0
+#define WICK_UPLOAD_DMA 1
+#define WICK_UPLOAD_KERNEL 2
+int wick_upload_rows(const wick_prop *Su_host, const wick_prop *Sd_host, const wick_prop *Su_dev,
+                     const wick_prop *Sd_dev, const wick_nucleon_op *ops, const wick_block_layout *layout,
+                     int mode, size_t *bytes, wick_stream_t stream);
 
 /*
  * Randomised minimal-set search (Sec. III.B "Computation of non-redundant

@@ -226,6 +226,77 @@ size_t wick_block_count(const wick_block_layout *layout) {
     return (size_t)layout->n_ops * layout->n_spin * layout->n_chi * layout->n_chi * layout->n_chi;
 }
 
+static int is_page_locked(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+int wick_upload_rows(const wick_prop *Su_host, const wick_prop *Sd_host, const wick_prop *Su_dev,
+                     const wick_prop *Sd_dev, const wick_nucleon_op *ops, const wick_block_layout *layout,
+                     int mode, size_t *bytes, wick_stream_t stream) {
+    const wick_prop *h[2] = {Su_host, Sd_host}, *d[2] = {Su_dev, Sd_dev};
+    if (mode != WICK_UPLOAD_AUTO && mode != WICK_UPLOAD_DMA && mode != WICK_UPLOAD_KERNEL) return WICK_EINVAL;
+    for (int f = 0; f < 2; ++f) {
+        if (!h[f] || !d[f] || !h[f]->data || !prop_ok(d[f])) return WICK_EINVAL;
+        if (h[f]->L != d[f]->L || h[f]->T != d[f]->T || h[f]->n_src != d[f]->n_src || h[f]->dtype != d[f]->dtype ||
+            (h[f]->dtype != WICK_C64 && h[f]->dtype != WICK_C128))
+            return WICK_EINVAL;
+        if (!is_page_locked(h[f]->data)) return WICK_EINVAL;
+    }
+    BlockPlan plan;
+    int err = build_block_plan(ops, layout, &plan);
+    if (err) return err;
+    // the copy engines by default: the gather kernel moves the rows faster on an idle GPU but takes SM
+    // slots from a block build that runs beside it
+    const bool use_kernel = mode == WICK_UPLOAD_KERNEL;
+    const void *hdev[2] = {nullptr, nullptr};   // the device addresses of the host buffers
+    if (use_kernel)
+        for (int f = 0; f < 2; ++f) {
+            void *p = nullptr;
+            if (cudaHostGetDevicePointer(&p, const_cast<void *>(h[f]->data), 0) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return WICK_EINVAL;
+            }
+            if ((uintptr_t)p % 16) return WICK_EINVAL;
+            hdev[f] = p;
+        }
+    size_t total = 0;
+    UploadMap map;
+    map.n = 0;
+    for (int f = 0; f < 2; ++f) {
+        const size_t el = h[f]->dtype == WICK_C64 ? 8 : 16;
+        const size_t rows = (size_t)h[f]->n_src * h[f]->T * h[f]->L * h[f]->L * h[f]->L;   // sites x slices
+        const size_t pitch = 144 * el;                                                     // one site
+        // runs of consecutive rows (the plan lists them ascending): one pitched copy each
+        for (int i = 0; i < plan.n_rows[f];) {
+            int j = i + 1;
+            while (j < plan.n_rows[f] && plan.rows[f][j] == plan.rows[f][j - 1] + 1) ++j;
+            const size_t off = (size_t)plan.rows[f][i] * 12 * el, width = (size_t)(j - i) * 12 * el;
+            if (use_kernel) {
+                for (size_t wd = off / 16; wd < (off + width) / 16; ++wd) map.word[map.n++] = (uint16_t)(f << 15 | wd);
+            } else {
+                WICK_CUDA_TRY(cudaMemcpy2DAsync((char *)d[f]->data + off, pitch, (const char *)h[f]->data + off,
+                                                pitch, width, rows, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+            }
+            total += width * rows;
+            i = j;
+        }
+    }
+    if (use_kernel && map.n > 0) {
+        const size_t n_sites = (size_t)h[0]->n_src * h[0]->T * h[0]->L * h[0]->L * h[0]->L;
+        int err2 = launch_upload_rows(map, hdev[0], hdev[1], d[0]->data, d[1]->data, n_sites,
+                                      h[0]->dtype == WICK_C64 ? 72 : 144, h[1]->dtype == WICK_C64 ? 72 : 144,
+                                      (cudaStream_t)stream);
+        if (err2) return err2;
+    }
+    if (bytes) *bytes = total;
+    return WICK_OK;
+}
+
 int wick_build_blocks(const wick_prop *Su, const wick_prop *Sd, const wick_nucleon_op *ops,
                       const wick_block_layout *layout, int precision, void *blocks, wick_stream_t stream) {
     if (!prop_ok(Su) || !prop_ok(Sd) || !blocks) return WICK_EINVAL;

@@ -55,6 +55,14 @@ int launch_block_build(const BlockPlan &plan, const void *Su, int dtype_u, const
 size_t block_partials_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int *n_splits,
                             int *chunk);
 // tensor-core update stage (blocks_tc.cu): upper-spin plans, double-FP32-exact
+// the 16-byte words of one site that wick_upload_rows gathers: flavour << 15 | word in the site
+constexpr int kMaxUploadWords = 2 * 12 * 12;   // both flavours, all rows, complex128
+struct UploadMap {
+    int n;
+    uint16_t word[kMaxUploadWords];
+};
+int launch_upload_rows(const UploadMap &map, const void *hu, const void *hd, const void *du, const void *dd,
+                       size_t n_sites, int words_u, int words_d, cudaStream_t stream);
 bool tc_applicable(const BlockPlan &plan);
 int block_build_launches(const BlockPlan &plan, int precision);  // kernels one launch_block_build issues
 size_t tc_partials_bytes(const BlockPlan &plan, int V, int n_slices, int *n_splits, int *chunk);

@@ -22,9 +22,10 @@ WICK_OK, WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA = 0, -1, -2, -3
 WICK_ECAPACITY, WICK_EOVERFLOW, WICK_ETIMEOUT, WICK_EIO, WICK_ESCRATCH = -4, -5, -6, -7, -8
 WICK_C128, WICK_C64 = 0, 1
 WICK_FP64, WICK_MIXED, WICK_MIXED_SIMT = 0, 1, 2
+WICK_UPLOAD_AUTO, WICK_UPLOAD_DMA, WICK_UPLOAD_KERNEL = 0, 1, 2
 WICK_U, WICK_D = 0, 1
 
-EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_reduce_terms", "wick_terms_count",
+EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_upload_rows", "wick_reduce_terms", "wick_terms_count",
            "wick_terms_nucleons", "wick_terms_copy", "wick_terms_stats", "wick_terms_select",
            "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_contract_noalloc",
            "wick_status", "wick_batch_create", "wick_batch_run", "wick_batch_launches", "wick_batch_free",
@@ -80,6 +81,8 @@ def load(path: str = LIB_PATH):
             L.wick_block_count.restype = C.c_size_t
             L.wick_build_blocks.argtypes = [P(wick_prop), P(wick_prop), P(wick_nucleon_op), P(wick_block_layout),
                                             C.c_int, vp, vp]
+            L.wick_upload_rows.argtypes = [P(wick_prop), P(wick_prop), P(wick_prop), P(wick_prop),
+                                           P(wick_nucleon_op), P(wick_block_layout), C.c_int, P(C.c_size_t), vp]
             L.wick_reduce_terms.argtypes = [P(wick_nucleus), P(wick_nucleon_op), P(wick_block_layout), C.c_uint64,
                                             C.c_int, C.c_int, P(vp), vp]
             L.wick_terms_count.argtypes = [vp]
@@ -205,6 +208,20 @@ def wick_build_blocks(Su, Sd, tables: Tables, precision: int, blocks, L: int, T:
     pu, pd = prop(Su), prop(Sd)
     _check(load().wick_build_blocks(C.byref(pu), C.byref(pd), tables.ops, C.byref(tables.layout), precision,
                                     _ptr(blocks), _stream(stream)), "wick_build_blocks")
+
+
+def wick_upload_rows(Su_host, Sd_host, Su_dev, Sd_dev, tables: Tables, L: int, T: int, n_src: int,
+                     stream=None, mode: int = 0) -> int:
+    """Copy the rows of S the block build of `tables` reads from pinned host tensors to device tensors of
+    the same shape (mode WICK_UPLOAD_AUTO / _DMA / _KERNEL); returns the bytes copied."""
+    def prop(S):
+        dt = WICK_C64 if str(S.dtype) == "torch.complex64" else WICK_C128
+        return wick_prop(_ptr(S), L, T, n_src, dt)
+    hu, hd, du, dd = prop(Su_host), prop(Sd_host), prop(Su_dev), prop(Sd_dev)
+    n = C.c_size_t(0)
+    _check(load().wick_upload_rows(C.byref(hu), C.byref(hd), C.byref(du), C.byref(dd), tables.ops,
+                                   C.byref(tables.layout), mode, C.byref(n), _stream(stream)), "wick_upload_rows")
+    return int(n.value)
 
 
 class Terms:
