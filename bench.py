@@ -81,15 +81,18 @@ CMAC_PER_SITE = 2 * 3 * 36 * 4 + 2 * 2 * 216 * 3
 DF32_OPS_PER_MAC = 11
 
 # The tensor-core block build (WICK_MIXED) per site, both block types: the
-# FP32-pipe work of preparing the operands, in lane operations --
-#   216 diquark values (2 types x 3 lists x 36 entries): 4 terms x 2 exact
-#   packed product-accumulations (9 f32x2 ops = 18 lane ops), one packed
-#   renormalising add (18), 6 packed slices (11 f32x2 ops = 22 lane ops each);
-#   72 propagator values (2 types x 2 spins x 6 x 3 terms): 5 packed slices
-#   (4 f32x2 ops = 8 lane ops each)
+# FP32-pipe work of preparing the operands, in lane operations (an f32x2
+# instruction is two) --
+#   216 diquark values (2 types x 3 lists x 36 entries), two sites per packed
+#   instruction: 4 terms x (4 weight products + 4 exact product-accumulations
+#   of 10 f32x2 ops each), less 14 f32x2 ops for the first term, = 162 f32x2
+#   ops per value; 6 slices at their own weight, 26 f32x2 ops per real part
+#   pair = 52 -> 214 f32x2 ops = 428 lane ops per site pair, 214 per value;
+#   72 propagator values (2 types x 2 spins x 6 x 3 terms): 5 slices, 15 f32x2
+#   ops per real part pair = 30 lane ops per value
 # -- and the MMA work: per type 6 MMAs of M=128 (5 stacked slices x 24 rows,
 # padded), N=48 (36 columns, padded), over K = 6 per site.
-TC_LANE_OPS_PER_SITE = 216 * (4 * 2 * 18 + 18 + 6 * 22) + 72 * 5 * 8
+TC_LANE_OPS_PER_SITE = 216 * 214 + 72 * 30
 TC_MMA_FLOPS_PER_SITE = 2 * 6 * 2 * 128 * 48 * 6
 
 
