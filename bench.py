@@ -568,11 +568,16 @@ def _timed(fn, steps, warmup, stream):
 MINOR_TABLE_FLOPS = 2 * 66 * 66 * 14
 
 
+# 3 x 3 minor table, per flavour with 5 or 6 quarks: 220 x 220 entries of 3 complex products
+# and 2 complex adds
+M3_TABLE_FLOPS = 220 * 220 * 22
+
+
 def det_flops(n: int, minors: bool = True) -> int:
     if n <= 1:
         return 0
-    if minors and n <= 5:
-        return {2: 0, 3: 22, 4: 46, 5: 5 * (46 + 6) + 8}[n]
+    if minors:   # 5 x 5: 10 products of a 2 x 2 and a 3 x 3 minor; 6 x 6: 20 of two 3 x 3 minors
+        return {2: 0, 3: 22, 4: 46, 5: 10 * 8, 6: 20 * 8}[n]
     if n == 2:
         return 14
     if n == 3:
@@ -587,8 +592,8 @@ PAPER_A100_2H_POINT_S = 0.15
 
 def run_point(args):
     """Point-sink correlators by the determinant algorithm (FP64): 2H on the
-    paper's 24^3 lattice, 3He on 8^3; one configuration, one source; the
-    metric is ms per time slice."""
+    paper's 24^3 lattice, 3He on 8^3, 4He on 4^3; one configuration, one
+    source; the metric is ms per time slice."""
     import torch
 
     from paper_2411_08962_gb300 import build, operators, wick
@@ -596,7 +601,7 @@ def run_point(args):
     wick.load()
     stream = torch.cuda.current_stream()
     res = {}
-    for name, L, T, seed in (("deuteron", 24, 4, 0x2411D2), ("he3", 8, 4, 0x2411D3)):
+    for name, L, T, seed in (("deuteron", 24, 4, 0x2411D2), ("he3", 8, 4, 0x2411D3), ("he4", 4, 2, 0x2411D4)):
         q = operators.point_operator(name)
         t0 = time.perf_counter()
         plan = wick.DetPlan(q)
@@ -610,9 +615,10 @@ def run_point(args):
         ms = _timed(lambda: wick.wick_det_contract(Su, Sd, plan, C, L, T, 1, stream=stream), args.steps,
                     max(1, args.warmup), stream)
         sites = L ** 3 * T
-        minors = st["n_u"] <= 5 and st["n_d"] <= 5
+        minors = True   # two-point functions always take the minor tables
+        n_m3 = (st["n_u"] >= 5) + (st["n_d"] >= 5) if minors else 0
         flops = sites * (st["zeta_u"] * det_flops(st["n_u"], minors) + st["zeta_d"] * det_flops(st["n_d"], minors)
-                         + st["theta"] * THETA_FLOPS + (MINOR_TABLE_FLOPS if minors else 0))
+                         + st["theta"] * THETA_FLOPS + (MINOR_TABLE_FLOPS if minors else 0) + n_m3 * M3_TABLE_FLOPS)
         tf = flops / (ms / 1e3) / 1e12
         res[name] = {"L": L, "T": T, "ms_per_time_slice": ms / T, "reduce_seconds": reduce_s,
                      "zeta_u": st["zeta_u"], "zeta_d": st["zeta_d"], "theta": st["theta"],

@@ -47,7 +47,7 @@ namespace wick {
 namespace {
 
 constexpr int kDetThreads = 256;
-constexpr int kDetChunk = 32;  // sites per work item
+constexpr int kDetChunk = 32;  // sites per work item at most (fewer when that leaves SMs idle)
 constexpr int kMaxEl = 16;     // matrix elements (a 4 x 4 correlation matrix)
 constexpr uint64_t kP61 = (1ull << 61) - 1;
 
@@ -289,9 +289,89 @@ __device__ __forceinline__ double2 det_minors(const double2 *S, const double2 *M
     }
 }
 
+// ---------------------------------------------------------------------------
+// 5 x 5 and 6 x 6 determinants from a per-site table of all 3 x 3 minors (in global scratch):
+// M3[tri(r0, r1, r2)][tri(c0, c1, c2)], tri(i < j < k) = C(k, 3) + C(j, 2) + i in 0..219, built
+// from the 2 x 2 minors by the first row.  5 x 5: Laplace expansion along the first two rows over
+// the 10 column pairs; 6 x 6: along the first three rows over the 20 column triples.
+// ---------------------------------------------------------------------------
+constexpr int kTriples = 220;
+__host__ __device__ constexpr int tri_index(int i, int j, int k) {
+    return k * (k - 1) * (k - 2) / 6 + j * (j - 1) / 2 + i;
+}
+
+__device__ __forceinline__ double2 m3(const double2 *__restrict__ T3, int r0, int r1, int r2, int c0, int c1, int c2) {
+    return T3[tri_index(r0, r1, r2) * kTriples + tri_index(c0, c1, c2)];
+}
+
+__device__ __forceinline__ double2 det_m3(const double2 *M, const double2 *__restrict__ T3, const int8_t *rc, int n) {
+    const int8_t *r = rc, *c = rc + n;
+    double2 d = make_double2(0.0, 0.0);
+    if (n == 5) {
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+#pragma unroll
+            for (int b = a + 1; b < 5; ++b) {
+                int q[3], k = 0;
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+                    if (j != a && j != b) q[k++] = c[j];
+                const double2 t = cmul(m2(M, r[0], r[1], c[a], c[b]), m3(T3, r[2], r[3], r[4], q[0], q[1], q[2]));
+                d = ((a + b) & 1) ? cadd(d, t) : csub(d, t);   // (-1)^(1 + a + b)
+            }
+    } else {   // n == 6
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int b = a + 1; b < 6; ++b)
+#pragma unroll
+                for (int e = b + 1; e < 6; ++e) {
+                    int q[3], k = 0;
+#pragma unroll
+                    for (int j = 0; j < 6; ++j)
+                        if (j != a && j != b && j != e) q[k++] = c[j];
+                    const double2 t = cmul(m3(T3, r[0], r[1], r[2], c[a], c[b], c[e]),
+                                           m3(T3, r[3], r[4], r[5], q[0], q[1], q[2]));
+                    d = ((a + b + e) & 1) ? cadd(d, t) : csub(d, t);   // (-1)^(3 + a + b + e)
+                }
+    }
+    return d;
+}
+
+// Derivative of det S[r][c] in the direction Sig (the three-point insertion) for n <= 3, by the
+// cofactor expansion of each row-replaced determinant: sum_{i,j} (-1)^(i+j) Sig[r_i][c_j] times the
+// minor of S without row r_i and column c_j (from the 2 x 2 minor table for n = 3).
+__device__ __forceinline__ double2 det_deriv_m2(const double2 *S, const double2 *Sig, const double2 *M,
+                                                const int8_t *rc, int n) {
+    const int8_t *r = rc, *c = rc + n;
+    if (n == 1) return Sig[r[0] * 12 + c[0]];
+    double2 d = make_double2(0.0, 0.0);
+    if (n == 2) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const double2 t = cmul(Sig[r[i] * 12 + c[j]], S[r[1 - i] * 12 + c[1 - j]]);
+                d = ((i + j) & 1) ? csub(d, t) : cadd(d, t);
+            }
+        return d;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int ra = r[i == 0 ? 1 : 0], rb = r[i == 2 ? 1 : 2];
+            const int ca = c[j == 0 ? 1 : 0], cb = c[j == 2 ? 1 : 2];
+            const double2 t = cmul(Sig[r[i] * 12 + c[j]], m2(M, ra, rb, ca, cb));
+            d = ((i + j) & 1) ? csub(d, t) : cadd(d, t);
+        }
+    return d;
+}
+
 struct DetArgs {
     int n_u, n_d, n_el;
     int seq_flavour;          // -1: two-point function; 0 / 1: current on u / d through Sig
+    int m3_mask;              // bit f: flavour f (n_f = 5 or 6) takes the 3 x 3 minor table
     int64_t n_zu, n_zd;
     const int8_t *zu, *zd;
     const int32_t *k, *l;
@@ -302,17 +382,33 @@ struct DetArgs {
 template <typename ST, int MAXEL, bool MINORS>
 __global__ void __launch_bounds__(kDetThreads)
 det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict__ Sd, const ST *__restrict__ Sig,
-                int V, int n_slices, int n_chunks, double2 *__restrict__ scratch, double2 *__restrict__ partials) {
+                int V, int n_slices, int n_chunks, int chunk_sites, double2 *__restrict__ scratch,
+                double2 *__restrict__ partials) {
     __shared__ double2 sS[3][144];
     __shared__ double2 red[kDetThreads];
     extern __shared__ double2 sM[];   // MINORS: [2][kPairs * kPairs] 2 x 2 minor tables of S_u, S_d
-    double2 *U = scratch + (size_t)blockIdx.x * (a.n_zu + a.n_zd);
+    const int n_m3 = (a.m3_mask & 1) + (a.m3_mask >> 1 & 1);
+    double2 *U = scratch + (size_t)blockIdx.x * (a.n_zu + a.n_zd + (size_t)n_m3 * kTriples * kTriples);
     double2 *D = U + a.n_zu;
+    double2 *T3[2];   // this CTA's 3 x 3 minor tables
+    T3[0] = D + a.n_zd;
+    T3[1] = T3[0] + ((a.m3_mask & 1) ? kTriples * kTriples : 0);
+    __shared__ int8_t sTri[kTriples][3];
     const int tid = threadIdx.x;
+    if (MINORS && a.m3_mask)
+        for (int t = tid; t < kTriples; t += kDetThreads) {
+            int k = 2;
+            while (tri_index(0, 1, k + 1) <= t) ++k;   // C(k + 1, 3) <= t
+            int j = 1;
+            while (tri_index(0, j + 1, k) <= t) ++j;
+            sTri[t][0] = (int8_t)(t - tri_index(0, j, k));
+            sTri[t][1] = (int8_t)j;
+            sTri[t][2] = (int8_t)k;
+        }
     const int64_t items = (int64_t)n_slices * n_chunks;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int slice = (int)(it / n_chunks), chunk = (int)(it % n_chunks);
-        const int x0 = chunk * kDetChunk, x1 = min(V, x0 + kDetChunk);
+        const int x0 = chunk * chunk_sites, x1 = min(V, x0 + chunk_sites);
         double2 acc[MAXEL];
 #pragma unroll
         for (int e = 0; e < MAXEL; ++e) acc[e] = make_double2(0.0, 0.0);
@@ -336,10 +432,43 @@ det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict
                     sM[e] = csub(cmul(S[r0 * 12 + c0], S[r1 * 12 + c1]), cmul(S[r0 * 12 + c1], S[r1 * 12 + c0]));
                 }
                 __syncthreads();
-                for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
-                    U[q] = det_minors(sS[0], sM, a.zu + q * 2 * a.n_u, a.n_u);
-                for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
-                    D[q] = det_minors(sS[1], sM + kPairs * kPairs, a.zd + q * 2 * a.n_d, a.n_d);
+                if (a.m3_mask) {
+                    for (int f = 0; f < 2; ++f) {
+                        if (!(a.m3_mask >> f & 1)) continue;
+                        const double2 *S = sS[f], *M = sM + f * kPairs * kPairs;
+                        for (int e = tid; e < kTriples * kTriples; e += kDetThreads) {
+                            const int rt = e / kTriples, ct = e - rt * kTriples;
+                            const int r0 = sTri[rt][0], r1 = sTri[rt][1], r2 = sTri[rt][2];
+                            const int c0 = sTri[ct][0], c1 = sTri[ct][1], c2 = sTri[ct][2];
+                            const double2 *s0 = S + r0 * 12;
+                            T3[f][e] = cadd(csub(cmul(s0[c0], m2(M, r1, r2, c1, c2)), cmul(s0[c1], m2(M, r1, r2, c0, c2))),
+                                            cmul(s0[c2], m2(M, r1, r2, c0, c1)));
+                        }
+                    }
+                    __syncthreads();
+                }
+                // the flavour carrying the current (three-point functions): cofactor expansion for n <= 3,
+                // pivoted LU of the row-replaced matrices above
+                if (a.seq_flavour == 0)
+                    for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
+                        U[q] = a.n_u <= 3 ? det_deriv_m2(sS[0], sS[2], sM, a.zu + q * 2 * a.n_u, a.n_u)
+                                          : det_deriv(sS[0], sS[2], a.zu + q * 2 * a.n_u, a.n_u);
+                else if (a.m3_mask & 1)
+                    for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
+                        U[q] = det_m3(sM, T3[0], a.zu + q * 2 * a.n_u, a.n_u);
+                else
+                    for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
+                        U[q] = det_minors(sS[0], sM, a.zu + q * 2 * a.n_u, a.n_u);
+                if (a.seq_flavour == 1)
+                    for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
+                        D[q] = a.n_d <= 3 ? det_deriv_m2(sS[1], sS[2], sM + kPairs * kPairs, a.zd + q * 2 * a.n_d, a.n_d)
+                                          : det_deriv(sS[1], sS[2], a.zd + q * 2 * a.n_d, a.n_d);
+                else if (a.m3_mask & 2)
+                    for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
+                        D[q] = det_m3(sM + kPairs * kPairs, T3[1], a.zd + q * 2 * a.n_d, a.n_d);
+                else
+                    for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
+                        D[q] = det_minors(sS[1], sM + kPairs * kPairs, a.zd + q * 2 * a.n_d, a.n_d);
             } else {
                 for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
                     U[q] = a.seq_flavour == 0 ? det_deriv(sS[0], sS[2], a.zu + q * 2 * a.n_u, a.n_u)
@@ -760,19 +889,20 @@ int det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig,
         WICK_CUDA_TRY(cudaMemsetAsync(C_out, 0, sizeof(double2) * n_slices * plan->n_el, st));
         return WICK_OK;
     }
-    const int n_chunks = (int)((V + kDetChunk - 1) / kDetChunk);
-    const int64_t items = n_slices * n_chunks;
     int n_sm = 0, occ = 0;
     WICK_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const bool one = plan->n_el == 1;
     const bool c64 = Su->dtype == WICK_C64;
-    // two-point functions with at most 5 quarks of each flavour use the 2 x 2 minor tables
-    const bool minors = seq_flavour < 0 && plan->n_u <= 5 && plan->n_d <= 5;
+    // the 2 x 2 minor tables always; flavours with 5 or 6 quarks also the 3 x 3 ones (except the one
+    // carrying a three-point current)
+    const bool minors = true;
+    const int m3_mask = (plan->n_u >= 5 && seq_flavour != 0 ? 1 : 0) | (plan->n_d >= 5 && seq_flavour != 1 ? 2 : 0);
+    const int n_m3 = (m3_mask & 1) + (m3_mask >> 1 & 1);
     const size_t dyn = minors ? sizeof(double2) * 2 * kPairs * kPairs : 0;
-    using KF = void (*)(const DetArgs, const float2 *, const float2 *, const float2 *, int, int, int, double2 *,
-                        double2 *);
-    using KD = void (*)(const DetArgs, const double2 *, const double2 *, const double2 *, int, int, int, double2 *,
-                        double2 *);
+    using KF = void (*)(const DetArgs, const float2 *, const float2 *, const float2 *, int, int, int, int,
+                        double2 *, double2 *);
+    using KD = void (*)(const DetArgs, const double2 *, const double2 *, const double2 *, int, int, int, int,
+                        double2 *, double2 *);
     KF kf = one ? (minors ? det_eval_kernel<float2, 1, true> : det_eval_kernel<float2, 1, false>)
                 : (minors ? det_eval_kernel<float2, kMaxEl, true> : det_eval_kernel<float2, kMaxEl, false>);
     KD kd = one ? (minors ? det_eval_kernel<double2, 1, true> : det_eval_kernel<double2, 1, false>)
@@ -780,26 +910,33 @@ int det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig,
     const void *kern = c64 ? (const void *)kf : (const void *)kd;
     if (dyn) WICK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     WICK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDetThreads, dyn));
+    // sites per work item: 32, halved while that leaves fewer than two items per resident CTA
+    const int64_t capacity = (int64_t)n_sm * std::max(occ, 1);
+    int chunk_sites = kDetChunk;
+    while (chunk_sites > 1 && n_slices * ((V + chunk_sites - 1) / chunk_sites) < 2 * capacity) chunk_sites /= 2;
+    const int n_chunks = (int)((V + chunk_sites - 1) / chunk_sites);
+    const int64_t items = n_slices * n_chunks;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)n_sm * std::max(occ, 1)));
-    const size_t scratch_bytes = sizeof(double2) * (size_t)grid * (size_t)(plan->n_zu + plan->n_zd);
+    const size_t scratch_bytes =
+        sizeof(double2) * (size_t)grid * (size_t)(plan->n_zu + plan->n_zd + (int64_t)n_m3 * kTriples * kTriples);
     const size_t part_bytes = sizeof(double2) * (size_t)items * plan->n_el;
     int err = WICK_OK;
     unsigned char *ws = (unsigned char *)workspace(2, scratch_bytes + part_bytes + 256, &err);
     if (err) return err;
     double2 *scratch = (double2 *)ws;
     double2 *partials = (double2 *)(ws + (scratch_bytes + 255) / 256 * 256);
-    DetArgs a{plan->n_u, plan->n_d, plan->n_el, seq_flavour, plan->n_zu, plan->n_zd, plan->d_zu, plan->d_zd,
-              plan->d_k, plan->d_l, plan->d_w, plan->d_el_off};
+    DetArgs a{plan->n_u, plan->n_d, plan->n_el, seq_flavour, m3_mask, plan->n_zu, plan->n_zd, plan->d_zu,
+              plan->d_zd, plan->d_k, plan->d_l, plan->d_w, plan->d_el_off};
     const unsigned g = (unsigned)grid;
     const int iv = (int)V, is = (int)n_slices;
     if (c64) {
         const float2 *u = (const float2 *)Su->data, *d = (const float2 *)Sd->data;
         const float2 *q = seq_flavour >= 0 ? (const float2 *)Sig->data : u;
-        kf<<<g, kDetThreads, dyn, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
+        kf<<<g, kDetThreads, dyn, st>>>(a, u, d, q, iv, is, n_chunks, chunk_sites, scratch, partials);
     } else {
         const double2 *u = (const double2 *)Su->data, *d = (const double2 *)Sd->data;
         const double2 *q = seq_flavour >= 0 ? (const double2 *)Sig->data : u;
-        kd<<<g, kDetThreads, dyn, st>>>(a, u, d, q, iv, is, n_chunks, scratch, partials);
+        kd<<<g, kDetThreads, dyn, st>>>(a, u, d, q, iv, is, n_chunks, chunk_sites, scratch, partials);
     }
     WICK_CUDA_TRY(cudaGetLastError());
     const int64_t n_out = n_slices * plan->n_el;
