@@ -620,7 +620,16 @@ def run_point(args):
         flops = sites * (st["zeta_u"] * det_flops(st["n_u"], minors) + st["zeta_d"] * det_flops(st["n_d"], minors)
                          + st["theta"] * THETA_FLOPS + (MINOR_TABLE_FLOPS if minors else 0) + n_m3 * M3_TABLE_FLOPS)
         tf = flops / (ms / 1e3) / 1e12
+        # the same in double-FP32 on the float pipes, and its deviation from FP64
+        C64 = C.clone()
+        Cm = torch.empty_like(C)
+        ms_mixed = _timed(lambda: wick.wick_det_contract(Su, Sd, plan, Cm, L, T, 1, precision=wick.WICK_MIXED,
+                                                         stream=stream), args.steps, max(1, args.warmup), stream)
+        torch.cuda.synchronize()
+        rel_mixed = float(((Cm - C64).abs() / C64.abs()).max().item())
         res[name] = {"L": L, "T": T, "ms_per_time_slice": ms / T, "reduce_seconds": reduce_s,
+                     "mixed": {"ms_per_time_slice": ms_mixed / T, "rel_err_vs_fp64_max_per_t": rel_mixed,
+                               "arithmetic": "double-FP32 minors, determinants and Theta sum; FP64 chunk sums"},
                      "zeta_u": st["zeta_u"], "zeta_d": st["zeta_d"], "theta": st["theta"],
                      "operator_terms": st["n_sink"],
                      "roofline": {"bound": "fp64", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",

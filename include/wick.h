@@ -394,10 +394,16 @@ int wick_det_copy(const wick_det_plan *plan, int32_t *k, int32_t *l, int64_t *w,
                   int8_t *zd_rows, int8_t *zd_cols);
 /*
  * wick_det_contract: G[src][t] for propagators Su, Sd (device, caller-owned,
- * complex64 or complex128; arithmetic in FP64) into C_out (device
- * complex128 [n_el][n_src][T], n_el = 1 for wick_det_reduce, N * N for a
- * correlation matrix).  Asynchronous on `stream`; scratch from the
- * library's per-device workspace.  precision: WICK_FP64.
+ * complex64 or complex128) into C_out (device complex128 [n_el][n_src][T],
+ * n_el = 1 for wick_det_reduce, N * N for a correlation matrix).
+ * Asynchronous on `stream`; scratch from the library's per-device workspace.
+ * Per site the kernel builds the table of all 2 x 2 minors of S_u(x), S_d(x)
+ * and, for a flavour with 5 or 6 quarks, of all 3 x 3 minors, and expands
+ * every determinant of the minimal sets over them (Laplace expansion).
+ *   precision  WICK_FP64: FP64 throughout.  WICK_MIXED: the minor tables, the
+ *              determinants and the Theta sum in double-FP32 on the float
+ *              pipes (about 44 significant bits per operation; complex128
+ *              input split into float pairs), the per-chunk sums in FP64.
  * Errors: WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA.
  */
 int wick_det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_det_plan *plan, double scale,
@@ -412,7 +418,8 @@ int wick_det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_det_p
  * Sig, summed over the lines: each determinant of that flavour becomes the
  * sum of the determinants with one row taken from Sig (the derivative of
  * Eq. 2.9 in the direction Sig).  Same plan, output layout and errors as
- * wick_det_contract.
+ * wick_det_contract; WICK_MIXED needs at most 3 quarks of `flavour` (the
+ * cofactor form of the derivative), else WICK_EINVAL.
  */
 int wick_det_contract_3pt(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig, int flavour,
                           const wick_det_plan *plan, double scale, int precision, void *C_out, wick_stream_t stream);

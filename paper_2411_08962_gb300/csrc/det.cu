@@ -28,6 +28,9 @@
 #include <vector>
 
 #include "common.cuh"
+#include "df32.cuh"
+
+#include <type_traits>
 
 struct wick_det_plan {
     int n_u = 0, n_d = 0, device = 0;
@@ -49,6 +52,7 @@ namespace {
 constexpr int kDetThreads = 256;
 constexpr int kDetChunk = 32;  // sites per work item at most (fewer when that leaves SMs idle)
 constexpr int kMaxEl = 16;     // matrix elements (a 4 x 4 correlation matrix)
+constexpr int kTheta = 8;      // Theta entries per thread in flight (double-FP32; FP64 is bound by its pipe)
 constexpr uint64_t kP61 = (1ull << 61) - 1;
 
 // ---------------------------------------------------------------------------
@@ -134,6 +138,30 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+// the same on double-FP32 complex values (the WICK_MIXED evaluation)
+__device__ __forceinline__ cdf cmul(const cdf &a, const cdf &b) { return cdf_mul(a, b); }
+__device__ __forceinline__ cdf cadd(const cdf &a, const cdf &b) { return {df_add(a.x, b.x), df_add(a.y, b.y)}; }
+__device__ __forceinline__ cdf csub(const cdf &a, const cdf &b) {
+    return {df_add(a.x, df_neg(b.x)), df_add(a.y, df_neg(b.y))};
+}
+template <typename C> __device__ __forceinline__ C to_c(float2 v);
+template <> __device__ __forceinline__ double2 to_c<double2>(float2 v) { return make_double2(v.x, v.y); }
+template <> __device__ __forceinline__ cdf to_c<cdf>(float2 v) { return {{v.x, 0.f}, {v.y, 0.f}}; }
+template <typename C> __device__ __forceinline__ C to_c(double2 v);
+template <> __device__ __forceinline__ double2 to_c<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ cdf to_c<cdf>(double2 v) { return {split_double(v.x), split_double(v.y)}; }
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(const cdf &v) { return make_double2(to_double(v.x), to_double(v.y)); }
+// acc += w p with an integer weight w
+__device__ __forceinline__ void theta_acc(double2 &acc, double w, double2 p) {
+    acc.x = fma(w, p.x, acc.x);
+    acc.y = fma(w, p.y, acc.y);
+}
+__device__ __forceinline__ void theta_acc(cdf &acc, double w, const cdf &p) {
+    const df wd = split_double(w);
+    acc.x = df_add(acc.x, df_mul(wd, p.x));
+    acc.y = df_add(acc.y, df_mul(wd, p.y));
+}
 
 // determinant of the n x n matrix row[i][cols[j]] (rows given as pointers into 12 x 12 matrices, so
 // that a row can come from another propagator)
@@ -237,14 +265,15 @@ __device__ __forceinline__ double2 det_deriv(const double2 *S, const double2 *Si
 constexpr int kPairs = 66;
 __host__ __device__ constexpr int pair_index(int i, int j) { return i * (23 - i) / 2 + (j - i - 1); }
 
-__device__ __forceinline__ double2 m2(const double2 *M, int r0, int r1, int c0, int c1) {
+template <typename C> __device__ __forceinline__ C m2(const C *M, int r0, int r1, int c0, int c1) {
     return M[pair_index(r0, r1) * kPairs + pair_index(c0, c1)];
 }
 
 // 4 x 4 by Laplace expansion along rows (r0, r1): sum over column pairs of the signed products of
 // complementary 2 x 2 minors
-__device__ __forceinline__ double2 det4_m2(const double2 *M, int r0, int r1, int r2, int r3, const int *c) {
-    double2 d = cmul(m2(M, r0, r1, c[0], c[1]), m2(M, r2, r3, c[2], c[3]));
+template <typename C>
+__device__ __forceinline__ C det4_m2(const C *M, int r0, int r1, int r2, int r3, const int *c) {
+    C d = cmul(m2(M, r0, r1, c[0], c[1]), m2(M, r2, r3, c[2], c[3]));
     d = csub(d, cmul(m2(M, r0, r1, c[0], c[2]), m2(M, r2, r3, c[1], c[3])));
     d = cadd(d, cmul(m2(M, r0, r1, c[0], c[3]), m2(M, r2, r3, c[1], c[2])));
     d = cadd(d, cmul(m2(M, r0, r1, c[1], c[2]), m2(M, r2, r3, c[0], c[3])));
@@ -253,14 +282,14 @@ __device__ __forceinline__ double2 det4_m2(const double2 *M, int r0, int r1, int
 }
 
 // det of S[rc[0..n)][rc[n..2n)] for n <= 5 from the minor table (n = 6 falls back to LU)
-__device__ __forceinline__ double2 det_minors(const double2 *S, const double2 *M, const int8_t *rc, int n) {
+template <typename C> __device__ __forceinline__ C det_minors(const C *S, const C *M, const int8_t *rc, int n) {
     switch (n) {
     case 1:
         return S[rc[0] * 12 + rc[1]];
     case 2:
         return m2(M, rc[0], rc[1], rc[2], rc[3]);
     case 3: {
-        const double2 *r0 = S + rc[0] * 12;
+        const C *r0 = S + rc[0] * 12;
         const int a = rc[1], b = rc[2], c0 = rc[3], c1 = rc[4], c2 = rc[5];
         return cadd(csub(cmul(r0[c0], m2(M, a, b, c1, c2)), cmul(r0[c1], m2(M, a, b, c0, c2))),
                     cmul(r0[c2], m2(M, a, b, c0, c1)));
@@ -271,21 +300,22 @@ __device__ __forceinline__ double2 det_minors(const double2 *S, const double2 *M
     }
     case 5: {
         // along the first row: sum_j (-1)^j S[r0][c_j] det4(rows r1..r4, columns without c_j)
-        const double2 *r0 = S + rc[0] * 12;
-        double2 d = make_double2(0.0, 0.0);
+        const C *r0 = S + rc[0] * 12;
+        C d = C{};
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
             int c[4], q = 0;
 #pragma unroll
             for (int k = 0; k < 5; ++k)
                 if (k != j) c[q++] = rc[5 + k];
-            const double2 t = cmul(r0[rc[5 + j]], det4_m2(M, rc[1], rc[2], rc[3], rc[4], c));
+            const C t = cmul(r0[rc[5 + j]], det4_m2(M, rc[1], rc[2], rc[3], rc[4], c));
             d = (j & 1) ? csub(d, t) : cadd(d, t);
         }
         return d;
     }
     default:
-        return det_small(S, rc, n);
+        if constexpr (std::is_same<C, double2>::value) return det_small(S, rc, n);
+        else return C{};
     }
 }
 
@@ -300,13 +330,15 @@ __host__ __device__ constexpr int tri_index(int i, int j, int k) {
     return k * (k - 1) * (k - 2) / 6 + j * (j - 1) / 2 + i;
 }
 
-__device__ __forceinline__ double2 m3(const double2 *__restrict__ T3, int r0, int r1, int r2, int c0, int c1, int c2) {
+template <typename C>
+__device__ __forceinline__ C m3(const C *__restrict__ T3, int r0, int r1, int r2, int c0, int c1, int c2) {
     return T3[tri_index(r0, r1, r2) * kTriples + tri_index(c0, c1, c2)];
 }
 
-__device__ __forceinline__ double2 det_m3(const double2 *M, const double2 *__restrict__ T3, const int8_t *rc, int n) {
+template <typename C>
+__device__ __forceinline__ C det_m3(const C *M, const C *__restrict__ T3, const int8_t *rc, int n) {
     const int8_t *r = rc, *c = rc + n;
-    double2 d = make_double2(0.0, 0.0);
+    C d = C{};
     if (n == 5) {
 #pragma unroll
         for (int a = 0; a < 5; ++a)
@@ -316,7 +348,7 @@ __device__ __forceinline__ double2 det_m3(const double2 *M, const double2 *__res
 #pragma unroll
                 for (int j = 0; j < 5; ++j)
                     if (j != a && j != b) q[k++] = c[j];
-                const double2 t = cmul(m2(M, r[0], r[1], c[a], c[b]), m3(T3, r[2], r[3], r[4], q[0], q[1], q[2]));
+                const C t = cmul(m2(M, r[0], r[1], c[a], c[b]), m3(T3, r[2], r[3], r[4], q[0], q[1], q[2]));
                 d = ((a + b) & 1) ? cadd(d, t) : csub(d, t);   // (-1)^(1 + a + b)
             }
     } else {   // n == 6
@@ -330,7 +362,7 @@ __device__ __forceinline__ double2 det_m3(const double2 *M, const double2 *__res
 #pragma unroll
                     for (int j = 0; j < 6; ++j)
                         if (j != a && j != b && j != e) q[k++] = c[j];
-                    const double2 t = cmul(m3(T3, r[0], r[1], r[2], c[a], c[b], c[e]),
+                    const C t = cmul(m3(T3, r[0], r[1], r[2], c[a], c[b], c[e]),
                                            m3(T3, r[3], r[4], r[5], q[0], q[1], q[2]));
                     d = ((a + b + e) & 1) ? cadd(d, t) : csub(d, t);   // (-1)^(3 + a + b + e)
                 }
@@ -341,17 +373,17 @@ __device__ __forceinline__ double2 det_m3(const double2 *M, const double2 *__res
 // Derivative of det S[r][c] in the direction Sig (the three-point insertion) for n <= 3, by the
 // cofactor expansion of each row-replaced determinant: sum_{i,j} (-1)^(i+j) Sig[r_i][c_j] times the
 // minor of S without row r_i and column c_j (from the 2 x 2 minor table for n = 3).
-__device__ __forceinline__ double2 det_deriv_m2(const double2 *S, const double2 *Sig, const double2 *M,
-                                                const int8_t *rc, int n) {
+template <typename C>
+__device__ __forceinline__ C det_deriv_m2(const C *S, const C *Sig, const C *M, const int8_t *rc, int n) {
     const int8_t *r = rc, *c = rc + n;
     if (n == 1) return Sig[r[0] * 12 + c[0]];
-    double2 d = make_double2(0.0, 0.0);
+    C d = C{};
     if (n == 2) {
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const double2 t = cmul(Sig[r[i] * 12 + c[j]], S[r[1 - i] * 12 + c[1 - j]]);
+                const C t = cmul(Sig[r[i] * 12 + c[j]], S[r[1 - i] * 12 + c[1 - j]]);
                 d = ((i + j) & 1) ? csub(d, t) : cadd(d, t);
             }
         return d;
@@ -362,7 +394,7 @@ __device__ __forceinline__ double2 det_deriv_m2(const double2 *S, const double2 
         for (int j = 0; j < 3; ++j) {
             const int ra = r[i == 0 ? 1 : 0], rb = r[i == 2 ? 1 : 2];
             const int ca = c[j == 0 ? 1 : 0], cb = c[j == 2 ? 1 : 2];
-            const double2 t = cmul(Sig[r[i] * 12 + c[j]], m2(M, ra, rb, ca, cb));
+            const C t = cmul(Sig[r[i] * 12 + c[j]], m2(M, ra, rb, ca, cb));
             d = ((i + j) & 1) ? csub(d, t) : cadd(d, t);
         }
     return d;
@@ -379,23 +411,27 @@ struct DetArgs {
     const int64_t *el_off;
 };
 
-template <typename ST, int MAXEL, bool MINORS>
+// C = double2: FP64 throughout; C = cdf: double-FP32 (the float pipes) for the minor tables,
+// determinants and the Theta sum, FP64 for the per-chunk reduction.
+template <typename ST, typename C, int MAXEL>
 __global__ void __launch_bounds__(kDetThreads)
 det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict__ Sd, const ST *__restrict__ Sig,
                 int V, int n_slices, int n_chunks, int chunk_sites, double2 *__restrict__ scratch,
                 double2 *__restrict__ partials) {
-    __shared__ double2 sS[3][144];
+    static_assert(sizeof(C) == sizeof(double2), "one 16-byte complex value");
+    __shared__ C sS[3][144];
     __shared__ double2 red[kDetThreads];
-    extern __shared__ double2 sM[];   // MINORS: [2][kPairs * kPairs] 2 x 2 minor tables of S_u, S_d
+    extern __shared__ double2 sM_raw[];   // [2][kPairs * kPairs] 2 x 2 minor tables of S_u, S_d
+    C *sM = reinterpret_cast<C *>(sM_raw);
     const int n_m3 = (a.m3_mask & 1) + (a.m3_mask >> 1 & 1);
-    double2 *U = scratch + (size_t)blockIdx.x * (a.n_zu + a.n_zd + (size_t)n_m3 * kTriples * kTriples);
-    double2 *D = U + a.n_zu;
-    double2 *T3[2];   // this CTA's 3 x 3 minor tables
+    C *U = reinterpret_cast<C *>(scratch) + (size_t)blockIdx.x * (a.n_zu + a.n_zd + (size_t)n_m3 * kTriples * kTriples);
+    C *D = U + a.n_zu;
+    C *T3[2];   // this CTA's 3 x 3 minor tables
     T3[0] = D + a.n_zd;
     T3[1] = T3[0] + ((a.m3_mask & 1) ? kTriples * kTriples : 0);
     __shared__ int8_t sTri[kTriples][3];
     const int tid = threadIdx.x;
-    if (MINORS && a.m3_mask)
+    if (a.m3_mask)
         for (int t = tid; t < kTriples; t += kDetThreads) {
             int k = 2;
             while (tri_index(0, 1, k + 1) <= t) ++k;   // C(k + 1, 3) <= t
@@ -409,91 +445,97 @@ det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int slice = (int)(it / n_chunks), chunk = (int)(it % n_chunks);
         const int x0 = chunk * chunk_sites, x1 = min(V, x0 + chunk_sites);
-        double2 acc[MAXEL];
+        C acc[MAXEL];
 #pragma unroll
-        for (int e = 0; e < MAXEL; ++e) acc[e] = make_double2(0.0, 0.0);
+        for (int e = 0; e < MAXEL; ++e) acc[e] = C{};
         for (int x = x0; x < x1; ++x) {
             __syncthreads();  // the previous site's determinants are consumed
             const int n_mat = a.seq_flavour < 0 ? 2 : 3;
             for (int e = tid; e < 144 * n_mat; e += kDetThreads) {
                 const ST *base = e < 144 ? Su : (e < 288 ? Sd : Sig);
-                const ST v = base[((size_t)slice * V + x) * 144 + (e % 144)];
-                sS[e / 144][e % 144] = make_double2((double)v.x, (double)v.y);
+                sS[e / 144][e % 144] = to_c<C>(base[((size_t)slice * V + x) * 144 + (e % 144)]);
             }
             __syncthreads();
-            if constexpr (MINORS) {
-                for (int e = tid; e < 2 * kPairs * kPairs; e += kDetThreads) {
-                    const int f = e / (kPairs * kPairs), rp = (e / kPairs) % kPairs, cp = e % kPairs;
-                    int r0 = 0, c0 = 0;
-                    while (pair_index(r0, 11) < rp) ++r0;      // first index of the pair
-                    while (pair_index(c0, 11) < cp) ++c0;
-                    const int r1 = rp - pair_index(r0, r0 + 1) + r0 + 1, c1 = cp - pair_index(c0, c0 + 1) + c0 + 1;
-                    const double2 *S = sS[f];
-                    sM[e] = csub(cmul(S[r0 * 12 + c0], S[r1 * 12 + c1]), cmul(S[r0 * 12 + c1], S[r1 * 12 + c0]));
+            for (int e = tid; e < 2 * kPairs * kPairs; e += kDetThreads) {
+                const int f = e / (kPairs * kPairs), rp = (e / kPairs) % kPairs, cp = e % kPairs;
+                int r0 = 0, c0 = 0;
+                while (pair_index(r0, 11) < rp) ++r0;      // first index of the pair
+                while (pair_index(c0, 11) < cp) ++c0;
+                const int r1 = rp - pair_index(r0, r0 + 1) + r0 + 1, c1 = cp - pair_index(c0, c0 + 1) + c0 + 1;
+                const C *S = sS[f];
+                sM[e] = csub(cmul(S[r0 * 12 + c0], S[r1 * 12 + c1]), cmul(S[r0 * 12 + c1], S[r1 * 12 + c0]));
+            }
+            __syncthreads();
+            if (a.m3_mask) {
+                for (int f = 0; f < 2; ++f) {
+                    if (!(a.m3_mask >> f & 1)) continue;
+                    const C *S = sS[f], *M = sM + f * kPairs * kPairs;
+                    for (int e = tid; e < kTriples * kTriples; e += kDetThreads) {
+                        const int rt = e / kTriples, ct = e - rt * kTriples;
+                        const int r0 = sTri[rt][0], r1 = sTri[rt][1], r2 = sTri[rt][2];
+                        const int c0 = sTri[ct][0], c1 = sTri[ct][1], c2 = sTri[ct][2];
+                        const C *s0 = S + r0 * 12;
+                        T3[f][e] = cadd(csub(cmul(s0[c0], m2(M, r1, r2, c1, c2)), cmul(s0[c1], m2(M, r1, r2, c0, c2))),
+                                        cmul(s0[c2], m2(M, r1, r2, c0, c1)));
+                    }
                 }
                 __syncthreads();
-                if (a.m3_mask) {
-                    for (int f = 0; f < 2; ++f) {
-                        if (!(a.m3_mask >> f & 1)) continue;
-                        const double2 *S = sS[f], *M = sM + f * kPairs * kPairs;
-                        for (int e = tid; e < kTriples * kTriples; e += kDetThreads) {
-                            const int rt = e / kTriples, ct = e - rt * kTriples;
-                            const int r0 = sTri[rt][0], r1 = sTri[rt][1], r2 = sTri[rt][2];
-                            const int c0 = sTri[ct][0], c1 = sTri[ct][1], c2 = sTri[ct][2];
-                            const double2 *s0 = S + r0 * 12;
-                            T3[f][e] = cadd(csub(cmul(s0[c0], m2(M, r1, r2, c1, c2)), cmul(s0[c1], m2(M, r1, r2, c0, c2))),
-                                            cmul(s0[c2], m2(M, r1, r2, c0, c1)));
-                        }
+            }
+            // the flavour carrying the current (three-point functions): cofactor expansion for n <= 3,
+            // pivoted LU of the row-replaced matrices above (FP64 only)
+            for (int f = 0; f < 2; ++f) {
+                const int n = f == 0 ? a.n_u : a.n_d;
+                const int64_t nz = f == 0 ? a.n_zu : a.n_zd;
+                const int8_t *z = f == 0 ? a.zu : a.zd;
+                C *out = f == 0 ? U : D;
+                const C *M = sM + f * kPairs * kPairs;
+                if (a.seq_flavour == f) {
+                    for (int64_t q = tid; q < nz; q += kDetThreads) {
+                        if (n <= 3) out[q] = det_deriv_m2(sS[f], sS[2], M, z + q * 2 * n, n);
+                        else if constexpr (std::is_same<C, double2>::value)
+                            out[q] = det_deriv(sS[f], sS[2], z + q * 2 * n, n);
                     }
-                    __syncthreads();
+                } else if (a.m3_mask >> f & 1) {
+                    for (int64_t q = tid; q < nz; q += kDetThreads) out[q] = det_m3(M, T3[f], z + q * 2 * n, n);
+                } else {
+                    for (int64_t q = tid; q < nz; q += kDetThreads) out[q] = det_minors(sS[f], M, z + q * 2 * n, n);
                 }
-                // the flavour carrying the current (three-point functions): cofactor expansion for n <= 3,
-                // pivoted LU of the row-replaced matrices above
-                if (a.seq_flavour == 0)
-                    for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
-                        U[q] = a.n_u <= 3 ? det_deriv_m2(sS[0], sS[2], sM, a.zu + q * 2 * a.n_u, a.n_u)
-                                          : det_deriv(sS[0], sS[2], a.zu + q * 2 * a.n_u, a.n_u);
-                else if (a.m3_mask & 1)
-                    for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
-                        U[q] = det_m3(sM, T3[0], a.zu + q * 2 * a.n_u, a.n_u);
-                else
-                    for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
-                        U[q] = det_minors(sS[0], sM, a.zu + q * 2 * a.n_u, a.n_u);
-                if (a.seq_flavour == 1)
-                    for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
-                        D[q] = a.n_d <= 3 ? det_deriv_m2(sS[1], sS[2], sM + kPairs * kPairs, a.zd + q * 2 * a.n_d, a.n_d)
-                                          : det_deriv(sS[1], sS[2], a.zd + q * 2 * a.n_d, a.n_d);
-                else if (a.m3_mask & 2)
-                    for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
-                        D[q] = det_m3(sM + kPairs * kPairs, T3[1], a.zd + q * 2 * a.n_d, a.n_d);
-                else
-                    for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
-                        D[q] = det_minors(sS[1], sM + kPairs * kPairs, a.zd + q * 2 * a.n_d, a.n_d);
-            } else {
-                for (int64_t q = tid; q < a.n_zu; q += kDetThreads)
-                    U[q] = a.seq_flavour == 0 ? det_deriv(sS[0], sS[2], a.zu + q * 2 * a.n_u, a.n_u)
-                                              : det_small(sS[0], a.zu + q * 2 * a.n_u, a.n_u);
-                for (int64_t q = tid; q < a.n_zd; q += kDetThreads)
-                    D[q] = a.seq_flavour == 1 ? det_deriv(sS[1], sS[2], a.zd + q * 2 * a.n_d, a.n_d)
-                                              : det_small(sS[1], a.zd + q * 2 * a.n_d, a.n_d);
             }
             __syncthreads();
-            // the determinants are shared by every matrix element (Eq. E3)
+            // the determinants are shared by every matrix element (Eq. E3).  The gathers of U[k] and
+            // D[l] come from L2: in double-FP32 each thread keeps kTheta of them in flight.
+            constexpr int KT = std::is_same<C, cdf>::value ? kTheta : 1;
 #pragma unroll
             for (int el = 0; el < MAXEL; ++el) {
                 if (el >= a.n_el) break;
-                for (int64_t e = a.el_off[el] + tid; e < a.el_off[el + 1]; e += kDetThreads) {
-                    const double2 p = cmul(U[a.k[e]], D[a.l[e]]);
-                    acc[el].x = fma(a.w[e], p.x, acc[el].x);
-                    acc[el].y = fma(a.w[e], p.y, acc[el].y);
+                const int64_t end = a.el_off[el + 1];
+                for (int64_t e0 = a.el_off[el] + tid; e0 < end; e0 += KT * kDetThreads) {
+                    int kk[KT], ll[KT];
+                    double ww[KT];
+#pragma unroll
+                    for (int u = 0; u < KT; ++u) {
+                        const int64_t e = e0 + u * kDetThreads;
+                        const bool ok = e < end;
+                        kk[u] = ok ? a.k[e] : 0;
+                        ll[u] = ok ? a.l[e] : 0;
+                        ww[u] = ok ? a.w[e] : 0.0;   // a zero weight adds nothing
+                    }
+                    C uu[KT], dd[KT];
+#pragma unroll
+                    for (int u = 0; u < KT; ++u) {
+                        uu[u] = U[kk[u]];
+                        dd[u] = D[ll[u]];
+                    }
+#pragma unroll
+                    for (int u = 0; u < KT; ++u) theta_acc(acc[el], ww[u], cmul(uu[u], dd[u]));
                 }
             }
         }
-        // fixed-order block reduction of the chunk's sums
+        // fixed-order block reduction of the chunk's sums (FP64)
 #pragma unroll
         for (int el = 0; el < MAXEL; ++el) {
             if (el >= a.n_el) break;
-            red[tid] = acc[el];
+            red[tid] = to_d2(acc[el]);
             __syncthreads();
             for (int s = kDetThreads / 2; s > 0; s >>= 1) {
                 if (tid < s) red[tid] = cadd(red[tid], red[tid + s]);
@@ -875,7 +917,11 @@ bool props_match(const wick_prop *a, const wick_prop *b) {
 
 int det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig, int seq_flavour,
                  const wick_det_plan *plan, double scale, int precision, void *C_out, wick_stream_t stream) {
-    if (!plan || !C_out || precision != WICK_FP64 || !props_match(Su, Sd)) return WICK_EINVAL;
+    if (!plan || !C_out || (precision != WICK_FP64 && precision != WICK_MIXED) || !props_match(Su, Sd))
+        return WICK_EINVAL;
+    // double-FP32 derivatives exist for the cofactor form only
+    if (precision == WICK_MIXED && seq_flavour >= 0 && (seq_flavour == 0 ? plan->n_u : plan->n_d) > 3)
+        return WICK_EINVAL;
     if (seq_flavour >= 0 && !props_match(Su, Sig)) return WICK_EINVAL;
     if (Su->L < 1 || Su->T < 1 || Su->n_src < 1 || (Su->dtype != WICK_C64 && Su->dtype != WICK_C128))
         return WICK_EINVAL;
@@ -893,22 +939,22 @@ int det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig,
     WICK_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const bool one = plan->n_el == 1;
     const bool c64 = Su->dtype == WICK_C64;
+    const bool mixed = precision == WICK_MIXED;
     // the 2 x 2 minor tables always; flavours with 5 or 6 quarks also the 3 x 3 ones (except the one
     // carrying a three-point current)
-    const bool minors = true;
     const int m3_mask = (plan->n_u >= 5 && seq_flavour != 0 ? 1 : 0) | (plan->n_d >= 5 && seq_flavour != 1 ? 2 : 0);
     const int n_m3 = (m3_mask & 1) + (m3_mask >> 1 & 1);
-    const size_t dyn = minors ? sizeof(double2) * 2 * kPairs * kPairs : 0;
+    const size_t dyn = sizeof(double2) * 2 * kPairs * kPairs;
     using KF = void (*)(const DetArgs, const float2 *, const float2 *, const float2 *, int, int, int, int,
                         double2 *, double2 *);
     using KD = void (*)(const DetArgs, const double2 *, const double2 *, const double2 *, int, int, int, int,
                         double2 *, double2 *);
-    KF kf = one ? (minors ? det_eval_kernel<float2, 1, true> : det_eval_kernel<float2, 1, false>)
-                : (minors ? det_eval_kernel<float2, kMaxEl, true> : det_eval_kernel<float2, kMaxEl, false>);
-    KD kd = one ? (minors ? det_eval_kernel<double2, 1, true> : det_eval_kernel<double2, 1, false>)
-                : (minors ? det_eval_kernel<double2, kMaxEl, true> : det_eval_kernel<double2, kMaxEl, false>);
+    KF kf = mixed ? (one ? det_eval_kernel<float2, cdf, 1> : det_eval_kernel<float2, cdf, kMaxEl>)
+                  : (one ? det_eval_kernel<float2, double2, 1> : det_eval_kernel<float2, double2, kMaxEl>);
+    KD kd = mixed ? (one ? det_eval_kernel<double2, cdf, 1> : det_eval_kernel<double2, cdf, kMaxEl>)
+                  : (one ? det_eval_kernel<double2, double2, 1> : det_eval_kernel<double2, double2, kMaxEl>);
     const void *kern = c64 ? (const void *)kf : (const void *)kd;
-    if (dyn) WICK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    WICK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     WICK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDetThreads, dyn));
     // sites per work item: 32, halved while that leaves fewer than two items per resident CTA
     const int64_t capacity = (int64_t)n_sm * std::max(occ, 1);

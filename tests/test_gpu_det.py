@@ -179,3 +179,73 @@ def test_three_point_euler_identity_on_gpu():
     wick.wick_det_contract_3pt(su, sd, su, wick.WICK_U, plan("deuteron"), out, 3, 1, 1)
     two = gpu_point("deuteron", Su, Sd)
     assert np.max(np.abs(out.cpu().numpy() - 3 * two) / np.abs(two)) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# WICK_MIXED: minor tables, determinants and the Theta sum in double-FP32 on the float pipes
+# ---------------------------------------------------------------------------
+MIXED_TOL = 1e-9
+
+
+def gpu_point_mixed(name, Su, Sd):
+    n_src, T, V = Su.shape[:3]
+    L = round(V ** (1 / 3))
+    out = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
+    wick.wick_det_contract(torch.from_numpy(np.ascontiguousarray(Su)).cuda(),
+                           torch.from_numpy(np.ascontiguousarray(Sd)).cuda(), plan(name), out, L, T, n_src,
+                           precision=wick.WICK_MIXED)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,L,T,n_src,dtype", [
+    ("deuteron", 3, 1, 2, np.complex64),    # 27 sites: ragged chunks
+    ("deuteron", 2, 2, 1, np.complex128),   # complex128 input split into float pairs
+    ("he3", 2, 1, 1, np.complex64),         # 5 x 5 through the 3 x 3 minor table
+    ("he4", 1, 1, 1, np.complex64),         # 6 x 6 through the 3 x 3 minor table
+])
+def test_point_correlator_mixed_matches_oracle(name, L, T, n_src, dtype):
+    Su, Sd = props(L, T, n_src, seed=0xD40 + L, dtype=dtype)
+    tab, nu, nd, scale = DT.operator(name)
+    ref = DT.point_correlator(Su.astype(np.complex128), Sd.astype(np.complex128), tab, tab, nu, nd, scale)
+    got = gpu_point_mixed(name, Su, Sd)
+    assert np.max(np.abs(got - ref) / np.abs(ref)) < MIXED_TOL
+
+
+def test_matrix_mixed_matches_fp64():
+    Su, Sd = props(2, 1, 1, seed=0xD41, dtype=np.complex64)
+    p = basis_plan()
+    n_el = p.stats()["n_el"]
+    su, sd = torch.from_numpy(Su).cuda(), torch.from_numpy(Sd).cuda()
+    outs = []
+    for prec in (wick.WICK_FP64, wick.WICK_MIXED):
+        out = torch.empty((n_el, 1, 1), dtype=torch.complex128, device="cuda")
+        wick.wick_det_contract(su, sd, p, out, 2, 1, 1, precision=prec)
+        torch.cuda.synchronize()
+        outs.append(out.cpu().numpy())
+    assert np.max(np.abs(outs[1] - outs[0]) / np.abs(outs[0])) < MIXED_TOL
+
+
+@pytest.mark.parametrize("flavour", [wick.WICK_U, wick.WICK_D])
+def test_three_point_mixed_matches_oracle(flavour):
+    L, T, n_src = 2, 1, 1
+    Su, Sd = props(L, T, n_src, seed=0xD42, dtype=np.complex64)
+    Sig = synth.propagator(0xD43, 0, L, T, n_src, dtype=np.complex64)
+    tab, nu, nd, scale = DT.operator("deuteron")
+    ref = DT.point_3pt(Su.astype(np.complex128), Sd.astype(np.complex128), Sig.astype(np.complex128), flavour,
+                       tab, tab, nu, nd, scale)
+    out = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
+    dev_ = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (Su, Sd, Sig)]
+    wick.wick_det_contract_3pt(dev_[0], dev_[1], dev_[2], flavour, plan("deuteron"), out, L, T, n_src,
+                               precision=wick.WICK_MIXED)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(out.cpu().numpy() - ref) / np.abs(ref)) < MIXED_TOL
+
+
+def test_three_point_mixed_rejects_large_flavour():
+    """The double-FP32 derivative exists in the cofactor form (n_f <= 3) only: 3He's d quarks (4) refuse."""
+    Su, Sd = props(1, 1, 1, seed=0xD44, dtype=np.complex64)
+    out = torch.empty((1, 1), dtype=torch.complex128, device="cuda")
+    su, sd = torch.from_numpy(Su).cuda(), torch.from_numpy(Sd).cuda()
+    with pytest.raises(wick.WickError):
+        wick.wick_det_contract_3pt(su, sd, su, wick.WICK_D, plan("he3"), out, 1, 1, 1, precision=wick.WICK_MIXED)
