@@ -49,7 +49,11 @@ namespace wick {
 
 namespace {
 
-constexpr int kDetThreads = 256;
+// threads per CTA: 512 for the double-FP32 single-element kernel (its Theta gathers are latency-bound
+// and it fits 128 registers), else 256
+template <typename C, int MAXEL> __host__ __device__ constexpr int det_threads() {
+    return std::is_same<C, cdf>::value && MAXEL == 1 ? 512 : 256;
+}
 constexpr int kDetChunk = 32;  // sites per work item at most (fewer when that leaves SMs idle)
 constexpr int kMaxEl = 16;     // matrix elements (a 4 x 4 correlation matrix)
 constexpr int kTheta = 8;      // Theta entries per thread in flight (double-FP32; FP64 is bound by its pipe)
@@ -414,11 +418,12 @@ struct DetArgs {
 // C = double2: FP64 throughout; C = cdf: double-FP32 (the float pipes) for the minor tables,
 // determinants and the Theta sum, FP64 for the per-chunk reduction.
 template <typename ST, typename C, int MAXEL>
-__global__ void __launch_bounds__(kDetThreads)
+__global__ void __launch_bounds__(det_threads<C, MAXEL>())
 det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict__ Sd, const ST *__restrict__ Sig,
                 int V, int n_slices, int n_chunks, int chunk_sites, double2 *__restrict__ scratch,
                 double2 *__restrict__ partials) {
     static_assert(sizeof(C) == sizeof(double2), "one 16-byte complex value");
+    constexpr int kDetThreads = det_threads<C, MAXEL>();
     __shared__ C sS[3][144];
     __shared__ double2 red[kDetThreads];
     extern __shared__ double2 sM_raw[];   // [2][kPairs * kPairs] 2 x 2 minor tables of S_u, S_d
@@ -955,7 +960,8 @@ int det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig,
                   : (one ? det_eval_kernel<double2, double2, 1> : det_eval_kernel<double2, double2, kMaxEl>);
     const void *kern = c64 ? (const void *)kf : (const void *)kd;
     WICK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    WICK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDetThreads, dyn));
+    const int threads = mixed && one ? det_threads<cdf, 1>() : det_threads<double2, 1>();
+    WICK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, dyn));
     // sites per work item: 32, halved while that leaves fewer than two items per resident CTA
     const int64_t capacity = (int64_t)n_sm * std::max(occ, 1);
     int chunk_sites = kDetChunk;
@@ -978,11 +984,11 @@ int det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig,
     if (c64) {
         const float2 *u = (const float2 *)Su->data, *d = (const float2 *)Sd->data;
         const float2 *q = seq_flavour >= 0 ? (const float2 *)Sig->data : u;
-        kf<<<g, kDetThreads, dyn, st>>>(a, u, d, q, iv, is, n_chunks, chunk_sites, scratch, partials);
+        kf<<<g, threads, dyn, st>>>(a, u, d, q, iv, is, n_chunks, chunk_sites, scratch, partials);
     } else {
         const double2 *u = (const double2 *)Su->data, *d = (const double2 *)Sd->data;
         const double2 *q = seq_flavour >= 0 ? (const double2 *)Sig->data : u;
-        kd<<<g, kDetThreads, dyn, st>>>(a, u, d, q, iv, is, n_chunks, chunk_sites, scratch, partials);
+        kd<<<g, threads, dyn, st>>>(a, u, d, q, iv, is, n_chunks, chunk_sites, scratch, partials);
     }
     WICK_CUDA_TRY(cudaGetLastError());
     const int64_t n_out = n_slices * plan->n_el;
