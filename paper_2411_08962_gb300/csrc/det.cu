@@ -39,6 +39,7 @@ struct wick_det_plan {
     int8_t *d_zu = nullptr, *d_zd = nullptr;  // [n][2][n_f]: rows (sink indices) then columns (source indices)
     int32_t *d_k = nullptr, *d_l = nullptr;
     double *d_w = nullptr;
+    float2 *d_wf = nullptr;   // the same weights as float pairs (hi, lo), for the double-FP32 kernel
     int64_t *d_el_off = nullptr;              // Theta entries of element e: [el_off[e], el_off[e + 1])
     std::vector<int8_t> zu, zd;
     std::vector<int32_t> k, l;
@@ -161,8 +162,8 @@ __device__ __forceinline__ void theta_acc(double2 &acc, double w, double2 p) {
     acc.x = fma(w, p.x, acc.x);
     acc.y = fma(w, p.y, acc.y);
 }
-__device__ __forceinline__ void theta_acc(cdf &acc, double w, const cdf &p) {
-    const df wd = split_double(w);
+__device__ __forceinline__ void theta_acc(cdf &acc, float2 w, const cdf &p) {
+    const df wd = {w.x, w.y};
     acc.x = df_add(acc.x, df_mul(wd, p.x));
     acc.y = df_add(acc.y, df_mul(wd, p.y));
 }
@@ -412,6 +413,7 @@ struct DetArgs {
     const int8_t *zu, *zd;
     const int32_t *k, *l;
     const double *w;
+    const float2 *wf;
     const int64_t *el_off;
 };
 
@@ -515,15 +517,17 @@ det_eval_kernel(const DetArgs a, const ST *__restrict__ Su, const ST *__restrict
                 if (el >= a.n_el) break;
                 const int64_t end = a.el_off[el + 1];
                 for (int64_t e0 = a.el_off[el] + tid; e0 < end; e0 += KT * kDetThreads) {
+                    using W = typename std::conditional<std::is_same<C, cdf>::value, float2, double>::type;
                     int kk[KT], ll[KT];
-                    double ww[KT];
+                    W ww[KT];
 #pragma unroll
                     for (int u = 0; u < KT; ++u) {
                         const int64_t e = e0 + u * kDetThreads;
                         const bool ok = e < end;
                         kk[u] = ok ? a.k[e] : 0;
                         ll[u] = ok ? a.l[e] : 0;
-                        ww[u] = ok ? a.w[e] : 0.0;   // a zero weight adds nothing
+                        if constexpr (std::is_same<C, cdf>::value) ww[u] = ok ? a.wf[e] : make_float2(0.f, 0.f);
+                        else ww[u] = ok ? a.w[e] : 0.0;   // a zero weight adds nothing
                     }
                     C uu[KT], dd[KT];
 #pragma unroll
@@ -702,6 +706,7 @@ void free_plan(wick_det_plan *p) {
     cudaFree(p->d_k);
     cudaFree(p->d_l);
     cudaFree(p->d_w);
+    cudaFree(p->d_wf);
     cudaFree(p->d_el_off);
     delete p;
 }
@@ -841,11 +846,17 @@ int reduce_matrix(const wick_quark_operator *const *snk, int n_snk_ops, const wi
     p->n_zd = (int64_t)cd.rep.size();
     p->n_theta = (int64_t)p->w.size();
     std::vector<double> wd(p->w.begin(), p->w.end());
+    std::vector<float2> wf(wd.size());
+    for (size_t i = 0; i < wd.size(); ++i) {   // exact for |w| < 2^48
+        const float h = (float)wd[i];
+        wf[i] = make_float2(h, (float)(wd[i] - (double)h));
+    }
     err = upload(&p->d_zu, p->zu);
     if (!err) err = upload(&p->d_zd, p->zd);
     if (!err) err = upload(&p->d_k, p->k);
     if (!err) err = upload(&p->d_l, p->l);
     if (!err) err = upload(&p->d_w, wd);
+    if (!err) err = upload(&p->d_wf, wf);
     if (!err) err = upload(&p->d_el_off, p->el_off);
     if (err) {
         free_plan(p);
@@ -978,7 +989,7 @@ int det_contract(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig,
     double2 *scratch = (double2 *)ws;
     double2 *partials = (double2 *)(ws + (scratch_bytes + 255) / 256 * 256);
     DetArgs a{plan->n_u, plan->n_d, plan->n_el, seq_flavour, m3_mask, plan->n_zu, plan->n_zd, plan->d_zu,
-              plan->d_zd, plan->d_k, plan->d_l, plan->d_w, plan->d_el_off};
+              plan->d_zd, plan->d_k, plan->d_l, plan->d_w, plan->d_wf, plan->d_el_off};
     const unsigned g = (unsigned)grid;
     const int iv = (int)V, is = (int)n_slices;
     if (c64) {
