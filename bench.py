@@ -728,13 +728,29 @@ def run_li7(args):
                                                                         Cs[n], stream), args.steps, 1, stream)
     ms64 = _timed(lambda: step(wick.WICK_FP64), max(1, min(3, args.steps)), 1, stream)
     rel = float(((c_mixed - Cli).abs() / Cli.abs()).max().item())
+    # roofline of the full-spin tensor-core block build: the operand preparation per site (4 block
+    # types x 144 columns x 3 lists diquark values at 214 lane ops, 4 x 48 rows x 3 lists propagator
+    # values at 30, each counted once although the kernel rebuilds the U slices and restages S for
+    # each of its 9 column tiles) against the FP32 lanes, and the useful complex MACs of the update
+    # (4 types x 4 spins x 1728 entries x 3 lists per site)
+    _, sm_mhz, _ = peaks()
+    sites = n_src * T * L ** 3
+    ops = sites * (4 * 144 * 3 * 214 + 4 * 48 * 3 * 30)
+    alu_peak = N_SM * FP32_LANES * sm_mhz * 1e6 / 1e12
+    achieved = ops / (phases["blocks"] / 1e3) / 1e12
+    useful_tflops = sites * 4 * 4 * 1728 * 3 * 8 / (phases["blocks"] / 1e3) / 1e12
+    roofline = {"kernel": "block_tc_kernel<float2, Shape<12,4,16,4,8>> (full spin)", "bound": "alu",
+                "achieved": achieved, "peak": alu_peak, "unit": "Top/s", "frac": achieved / alu_peak,
+                "useful_update_tflops": useful_tflops, "tensor_peak_tflops": bf16_peak_tflops(),
+                "note": "U slices and staged rows are rebuilt by each of the 9 column tiles (TMEM holds 16 "
+                        "columns x 17 slice-pair blocks per CTA)"}
     print(json.dumps({"workload": "li7", "metric": "Li-7 correlator ms/config (He-4 cluster x triton)",
                       "value": ms, "unit": UNIT, "higher_is_better": False, "steps": args.steps,
                       "config": {"L": L, "T": T, "n_src": n_src, "block_types": 4, "spins": 4,
                                  "terms": {n: t.count for n, t in terms.items()}},
                       "fp64_plain": {"value": ms64, "unit": UNIT},
                       "rel_err_mixed_vs_fp64_max_per_t": rel, "reduce_seconds": reduce_s,
-                      "mixed_phases_ms": phases,
+                      "mixed_phases_ms": phases, "roofline": roofline,
                       "gpu_launches_per_step": 2 + 2 * len(tabs) + 1}), flush=True)
 
 

@@ -80,6 +80,7 @@ template <int NC_, int NS_, int NT_, int NMT_, int NX_> struct Shape {
     static constexpr int CW = NT / PER_TILE;                // readout columns per thread
     static constexpr int NSP = NX / 2;                      // site pairs per chunk
     static constexpr int PS = kMaxRows * NC * NX;           // floats per staged plane (re or im)
+    static constexpr int STAGERS = kMaxRows * NC * NX / 8;   // staging threads: one (row, colour), 8 sites each
     static constexpr int NXJOB = NCTA * kKa * NSP;          // two X values (a site pair) each
     static constexpr int NUJOB = NS * NC * kKa * NSP;       // two U values (a site pair) each
     // rotation of the thread -> job map in round r: the last round goes to the threads whose earlier
@@ -108,6 +109,7 @@ template <int NC_, int NS_, int NT_, int NMT_, int NX_> struct Shape {
     static_assert(TMEM_USED <= 512 && CW % 4 == 0 && CW <= 32, "TMEM / readout");
     static_assert(NXJOB % 32 == 0 && NUJOB % 32 == 0, "jobs fill whole warps");
     static_assert(NX % 8 == 0, "site pairs in groups of 4 per warp");
+    static_assert(STAGERS <= kThr, "staging threads");
     static_assert(R % 8 == 0, "U slices start on a core-matrix row group");
     static_assert(kSlices * R * NT * 8 <= 2 * (A_BYTES + B_BYTES), "combine buffer");
     static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -156,8 +158,10 @@ template <int KC> __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 __device__ __forceinline__ float2 to_f2(float2 v) { return v; }
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+// 4-byte copy; src_bytes 0 writes a zero
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -469,25 +473,32 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
     const ST *sd = Sd + (size_t)slice * V * 144;
     __syncthreads();   // sSrc
     // stage the rows of chunk c as two planes (re, im) of [row][ic][site], flavour-0 rows first, sites
-    // innermost (zeros past the range)
+    // innermost (zeros past the range).  The last STAGERS threads (the warps with the lightest jobs)
+    // each copy one (row, colour) for 8 consecutive sites, from offsets computed once.
+    const int st_t = tid - (kThr - SH::STAGERS);
+    const int st_rcc = st_t >= 0 ? st_t / (NX / 8) : 0, st_part = st_t >= 0 ? st_t % (NX / 8) : 0;
+    const bool stager = st_t >= 0 && st_rcc < nr * NC;
+    const ST *st_src = su;
+    if (stager) {
+        const int src_off = sSrc[st_rcc];
+        st_src = ((src_off >> 16) ? sd : su) + (src_off & 0xFFFF);
+    }
     auto stage = [&](int c) {
-        float *dst = sS0 + (c % kStage) * (2 * PS);
-        const int xb = x_begin + c * NX;
-        for (int e = tid; e < NX * nr * NC; e += kThr) {
-            const int site = e % NX, rcc = e / NX;
-            const int src_off = sSrc[rcc];
-            const ST *src = ((src_off >> 16) ? sd : su) + (size_t)(xb + site) * 144 + (src_off & 0xFFFF);
-            float *d0 = dst + e;   // = rcc * NX + site
-            if (xb + site >= x_end) {
-                d0[0] = 0.f;
-                d0[PS] = 0.f;
-            } else if constexpr (sizeof(ST) == 8) {
-                cp_async4(d0, reinterpret_cast<const float *>(src));
-                cp_async4(d0 + PS, reinterpret_cast<const float *>(src) + 1);
-            } else {
-                const float2 v = to_f2(*src);
-                d0[0] = v.x;
-                d0[PS] = v.y;
+        if (stager) {
+            float *dst = sS0 + (c % kStage) * (2 * PS) + st_rcc * NX + st_part * 8;
+            const int xb = x_begin + c * NX + st_part * 8;
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8) {
+                const bool in = xb + s8 < x_end;
+                const ST *src = st_src + (size_t)(in ? xb + s8 : x_begin) * 144;
+                if constexpr (sizeof(ST) == 8) {
+                    cp_async4(dst + s8, reinterpret_cast<const float *>(src), in ? 4 : 0);
+                    cp_async4(dst + s8 + PS, reinterpret_cast<const float *>(src) + 1, in ? 4 : 0);
+                } else {
+                    const float2 v = in ? to_f2(*src) : make_float2(0.f, 0.f);
+                    dst[s8] = v.x;
+                    dst[s8 + PS] = v.y;
+                }
             }
         }
         cp_async_commit();
