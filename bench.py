@@ -176,10 +176,19 @@ def block_bytes_per_site(dtype_bytes: int) -> int:
     return 2 * rows * cols * dtype_bytes
 
 
+def code_tokens(text: str) -> str:
+    """C++ source without comments and blank space: two sources that differ only there compile to
+    the same kernel."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("blocks_tc.cu", "common.cuh", "df32.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2411_08962_gb300", "csrc", f), "rb").read())
+        h.update(code_tokens(open(os.path.join(ROOT, "paper_2411_08962_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -33,11 +33,13 @@
 // the grid so that the CTAs reading the same rows of S run together.  Per chunk
 // of 16 sites (upper tables; 8 for the full-spin ones, for shared memory):
 // the CTA builds the U and X slices of chunk c into one of two operand buffers
-// from S staged two chunks ahead (three staging buffers, cp.async), meets at one
-// barrier, and one thread of the least-loaded warp issues the chunk's MMAs and
-// commits them to the buffer's mbarrier while the others go on to chunk c + 1.  The work of a chunk
-// is a list of jobs -- one X value, or two U values -- ordered so that every
-// warp does one kind.  Every wait on an mbarrier is bounded.
+// from S staged two chunks ahead (three staging buffers, 4-byte cp.async into
+// re / im planes with sites innermost), meets at one barrier, and one thread of
+// the least-loaded warp issues the chunk's MMAs and commits them to the
+// buffer's mbarrier while the others go on to chunk c + 1.  The work of a
+// chunk is a list of jobs -- two X values (a site pair) of one column, or two
+// U values of one row -- ordered so that every warp does one kind and one
+// colour term.  Every wait on an mbarrier is bounded.
 #include <cuda_bf16.h>
 
 #include <cstring>
