@@ -249,3 +249,14 @@ def test_three_point_mixed_rejects_large_flavour():
     su, sd = torch.from_numpy(Su).cuda(), torch.from_numpy(Sd).cuda()
     with pytest.raises(wick.WickError):
         wick.wick_det_contract_3pt(su, sd, su, wick.WICK_D, plan("he3"), out, 1, 1, 1, precision=wick.WICK_MIXED)
+
+
+def test_deuteron_benchmark_size_matches_oracle():
+    """2H on the 24^3 lattice of the point-sink benchmark (one time slice, complex64 storage, the
+    benchmark's launch configuration): FP64 within 1e-12 and double-FP32 within 1e-9 of the oracle."""
+    L, T, n_src = 24, 1, 1
+    Su, Sd = props(L, T, n_src, seed=0xD45, dtype=np.complex64)
+    tab, nu, nd, scale = DT.operator("deuteron")
+    ref = DT.point_correlator(Su.astype(np.complex128), Sd.astype(np.complex128), tab, tab, nu, nd, scale)
+    assert np.max(np.abs(gpu_point("deuteron", Su, Sd) - ref) / np.abs(ref)) < FP64_TOL
+    assert np.max(np.abs(gpu_point_mixed("deuteron", Su, Sd) - ref) / np.abs(ref)) < MIXED_TOL
