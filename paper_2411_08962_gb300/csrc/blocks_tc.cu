@@ -342,47 +342,67 @@ template <int NN, int NSP> __device__ __forceinline__ void job_map(int jb, int &
     }
 }
 
-// X job: column n, colour term a, sites (2 sp, 2 sp + 1); 6 slices into B_j[n][k], k = (a, part, site)
+// A thread's jobs are the same in every chunk; only the staging and operand buffers change.  Their
+// offsets are decoded once: kind 1 = X job (column n, colour term a, sites 2 sp, 2 sp + 1), kind 2 =
+// U job (row (s, c1), colour term a, sites 2 sp, 2 sp + 1), 0 = nothing (a colour term beyond the
+// operator's, whose K rows stay zero).
+struct Job {
+    int kind, a;
+    int s1, s2;      // X: staged offsets of the u-side and d-side columns; U: the U value, -
+    int d1, d2;      // X: B offset of slice 0; U: A offsets of the re and im rows of slice 0
+    float sc;        // 2^(7 - grid exponent)
+};
+
 template <typename SH>
-__device__ __forceinline__ void x_job(const int4 *sTerm, const f2x *sTermN, const float *S, int col0, int n_a,
-                                      const int *sF, __nv_bfloat16 *B, int jb) {
-    constexpr int NC = SH::NC, NT = SH::NT, NX = SH::NX, KC = SH::KC;
-    int n, a, sp;
-    job_map<SH::NCTA, SH::NSP>(jb, n, a, sp);
-    if (a >= n_a) return;  // warp-uniform; those K rows stay zero
-    const int c23 = col0 + n;
+__device__ __forceinline__ Job make_job(int jb, int col0, int n_a, const int *sF, const int *sR1, const int *sEU) {
+    constexpr int NC = SH::NC, NS = SH::NS, NX = SH::NX, KC = SH::KC;
+    Job j{0, 0, 0, 0, 0, 0, 0.f};
+    if (jb < SH::NXJOB) {
+        int n, a, sp;
+        job_map<SH::NCTA, SH::NSP>(jb, n, a, sp);
+        if (a >= n_a) return j;
+        const int c23 = col0 + n;
+        j = {1, a, (c23 / NC) * NX + 2 * sp, (c23 % NC) * NX + 2 * sp, tile_off<KC>(n, a * 2 * NX + 2 * sp), 0,
+             exp2i(7 - sF[n])};
+    } else if (jb < SH::NXJOB + SH::NUJOB) {
+        int m, a, sp;
+        job_map<NS * NC, SH::NSP>(jb - SH::NXJOB, m, a, sp);
+        if (a >= n_a) return j;
+        const int s = m / NC, c1 = m % NC;
+        j = {2, a, sR1[s * kKa + a] + c1 * NX + 2 * sp, 0, tile_off<KC>(m, a * 2 * NX + 2 * sp),
+             tile_off<KC>(NS * NC + m, a * 2 * NX + 2 * sp), exp2i(7 - sEU[c1])};
+    }
+    return j;
+}
+
+// X job: 6 slices of the site pair's re and im parts into B_j[n][k], k = (a, part, site)
+template <typename SH>
+__device__ __forceinline__ void x_job(const Job &j, const int4 *sTerm, const f2x *sTermN, const float *S,
+                                      __nv_bfloat16 *B) {
+    constexpr int NT = SH::NT, NX = SH::NX, KC = SH::KC;
     pdf re, im;
-    x_pair<SH::PS>(sTerm + a * kListLen, sTermN + a * kListLen, S + (c23 / NC) * NX + 2 * sp,
-                   S + (c23 % NC) * NX + 2 * sp, re, im);
+    x_pair<SH::PS>(sTerm + j.a * kListLen, sTermN + j.a * kListLen, S + j.s1, S + j.s2, re, im);
     uint32_t wr[kSlicesX], wi[kSlicesX];
-    const float sc = exp2i(7 - sF[n]);
-    slice_x2(re.h, re.l, sc, wr);
-    slice_x2(im.h, im.l, sc, wi);
-    __nv_bfloat16 *dst = B + tile_off<KC>(n, a * 2 * NX + 2 * sp);
+    slice_x2(re.h, re.l, j.sc, wr);
+    slice_x2(im.h, im.l, j.sc, wi);
+    __nv_bfloat16 *dst = B + j.d1;
 #pragma unroll
-    for (int j = 0; j < kSlicesX; ++j) {
-        *reinterpret_cast<uint32_t *>(dst + j * NT * KC) = wr[j];
-        *reinterpret_cast<uint32_t *>(dst + j * NT * KC + NX * 8) = wi[j];  // part 1: k + NX
+    for (int i = 0; i < kSlicesX; ++i) {
+        *reinterpret_cast<uint32_t *>(dst + i * NT * KC) = wr[i];
+        *reinterpret_cast<uint32_t *>(dst + i * NT * KC + NX * 8) = wi[i];  // part 1: k + NX
     }
 }
 
-// U job: row (s, c1), colour term a, sites (2 sp, 2 sp + 1); 5 slices into A[(i, part, s, c1)][k]:
-// the re row takes (U_re, -U_im) against (X_re, X_im), the im row (U_im, U_re)
+// U job: 5 slices into A[(i, part, s, c1)][k]: the re row takes (U_re, -U_im) against (X_re, X_im),
+// the im row (U_im, U_re)
 template <typename SH>
-__device__ __forceinline__ void u_job(const int *sR1, const float *S, int n_a, const int *sEU, __nv_bfloat16 *A,
-                                      int ju) {
-    constexpr int NC = SH::NC, NS = SH::NS, NX = SH::NX, R = SH::R, KC = SH::KC;
-    int m, a, sp;
-    job_map<NS * NC, SH::NSP>(ju, m, a, sp);
-    if (a >= n_a) return;
-    const int s = m / NC, c1 = m % NC;
-    const float *p = S + sR1[s * kKa + a] + c1 * NX + 2 * sp;
+__device__ __forceinline__ void u_job(const Job &j, const float *S, __nv_bfloat16 *A) {
+    constexpr int NX = SH::NX, R = SH::R, KC = SH::KC;
+    const float *p = S + j.s1;
     uint32_t qr[kSlices], qi[kSlices];
-    const float sc = exp2i(7 - sEU[c1]);
-    slice_u2(lds2(p), sc, qr);
-    slice_u2(lds2(p + SH::PS), sc, qi);
-    __nv_bfloat16 *dre = A + tile_off<KC>(m, a * 2 * NX + 2 * sp);
-    __nv_bfloat16 *dim = A + tile_off<KC>(NS * NC + m, a * 2 * NX + 2 * sp);
+    slice_u2(lds2(p), j.sc, qr);
+    slice_u2(lds2(p + SH::PS), j.sc, qi);
+    __nv_bfloat16 *dre = A + j.d1, *dim = A + j.d2;
 #pragma unroll
     for (int i = 0; i < kSlices; ++i) {
         const int o = tile_off<KC>(i * R, 0);
@@ -529,6 +549,14 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
 #pragma unroll
     for (int n = 0; n < SH::CW; ++n) acc[n] = {0.f, 0.f};
 
+    // one job per thread and round: X jobs first, then U jobs; both fill whole warps, so every branch
+    // is warp-uniform.  The last round goes to the threads that took U jobs before.
+    constexpr int NR = (SH::NXJOB + SH::NUJOB + kThr - 1) / kThr;
+    Job job[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+        job[r] = make_job<SH>(r * kThr + (tid + kThr - SH::rot(r)) % kThr, col0, n_a, sF, sR1, sEU);
+
     constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
     int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0, bad = 0;
@@ -547,14 +575,10 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
             else bad = 1;
         }
         if (!bad) {
-            // one job per thread and round: X jobs first, then U jobs; both fill whole warps, so every
-            // branch is warp-uniform.  The last round goes to the threads that took U jobs before.
-            constexpr int NJ = SH::NXJOB + SH::NUJOB;
-#pragma unroll 1
-            for (int r = 0; r * kThr < NJ; ++r) {
-                const int jb = r * kThr + (tid + kThr - SH::rot(r)) % kThr;
-                if (jb < SH::NXJOB) x_job<SH>(sTerm, sTermN, S, col0, n_a, sF, B, jb);
-                else if (jb < NJ) u_job<SH>(sR1, S, n_a, sEU, A, jb - SH::NXJOB);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (job[r].kind == 1) x_job<SH>(job[r], sTerm, sTermN, S, B);
+                else if (job[r].kind == 2) u_job<SH>(job[r], S, A);
             }
         }
         // staged rows of chunk c + 1 complete (this thread's copies); operands of chunk c written
