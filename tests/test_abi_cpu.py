@@ -70,6 +70,28 @@ def test_null_arguments_are_rejected(lib):
     assert lib.wick_reduce_terms(None, None, None, 0, 2, 1, C.byref(h), None) == wick.WICK_EINVAL
     assert lib.wick_build_blocks(None, None, None, None, 0, None, None) == wick.WICK_EINVAL
     assert lib.wick_contract(None, 1, 1, None, 0, None, None) == wick.WICK_EINVAL
+    n = C.c_size_t(0)
+    assert lib.wick_upload_rows(None, None, None, None, None, None, wick.WICK_UPLOAD_AUTO, C.byref(n),
+                                None) == wick.WICK_EINVAL
+    assert lib.wick_det_contract(None, None, None, 1.0, wick.WICK_FP64, None, None) == wick.WICK_EINVAL
+
+
+def test_upload_rows_rejects_bad_mode_and_host_memory(lib):
+    """Argument checks that run before any device work: an unknown mode, and host memory that is not
+    page-locked (no CUDA device here, so no host buffer can be)."""
+    tabs = wick.Tables(operators.nucleus("he4"))
+    host = np.zeros(2 * 1 * 8 * 144, dtype=np.complex64)
+    dev = np.zeros(2 * 1 * 8 * 144 + 2, dtype=np.complex64)   # stands in for a device pointer: only checked
+    dptr = dev.ctypes.data + (-dev.ctypes.data) % 16           # for 16-byte alignment before the mode / host
+    hp = wick.wick_prop(host.ctypes.data, 2, 1, 1, wick.WICK_C64)
+    dp = wick.wick_prop(dptr, 2, 1, 1, wick.WICK_C64)
+    n = C.c_size_t(0)
+    for mode in (7, -1):
+        assert lib.wick_upload_rows(C.byref(hp), C.byref(hp), C.byref(dp), C.byref(dp), tabs.ops,
+                                    C.byref(tabs.layout), mode, C.byref(n), None) == wick.WICK_EINVAL
+    assert lib.wick_upload_rows(C.byref(hp), C.byref(hp), C.byref(dp), C.byref(dp), tabs.ops,
+                                C.byref(tabs.layout), wick.WICK_UPLOAD_DMA, C.byref(n), None) == wick.WICK_EINVAL
+    assert n.value == 0
 
 
 def test_product_dirac_algebra():
