@@ -233,6 +233,9 @@ int wick_reduce_terms(const wick_nucleus *nucleus, const wick_nucleon_op *ops,
 /* Accessors of a reduced table. */
 int64_t wick_terms_count(const wick_terms *terms);     /* U, or a negative error */
 int wick_terms_nucleons(const wick_terms *terms);      /* A */
+/* Block entries per (src, t) of the layout the table was reduced for
+ * (wick_block_count of that layout), or a negative error. */
+int64_t wick_terms_block_count(const wick_terms *terms);
 /* Copy to host arrays: ids [U][A] uint16, w [U] int64, rep [U] int64 (any may be NULL). */
 int wick_terms_copy(const wick_terms *terms, uint16_t *ids, int64_t *w, int64_t *rep);
 /* stats[0] raw terms, [1] identically zero, [2] distinct keys, [3] kept terms;
@@ -268,18 +271,21 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *terms,
  * device memory it is allowed to use, or a runtime that forbids driver-level
  * allocations (and the implicit device synchronisation of cudaMalloc/cudaFree)
  * once its set-up phase is over.  wick_contract itself allocates its scratch
- * on first use; this variant never does.
+ * on first use; this variant calls no cudaMalloc, cudaFree or allocating
+ * library routine.
  *
  * Same arguments, result and errors as wick_contract.  Its scratch (the FP64
  * partial sums, one complex128 per (term chunk, slice)) is a fixed array of
  * 65,536 complex128 values (1 MiB) that every GPU loading the library holds
- * until the process exits.  At most 65,536 slices (n_src * T) per call; larger
- * requests fail with WICK_ESCRATCH.  When the usual chunking would not fit,
- * fewer term chunks are used (the sum order then differs from wick_contract's
- * within rounding).
- *   - The first call on a device looks up the array's device address for that
- *     device (cudaGetSymbolAddress, with that device current); make that first
- *     call before any stream capture.
+ * until the process exits.  A call takes at most 65,536 slices (n_src * T);
+ * larger requests fail with WICK_ESCRATCH before anything is enqueued.  When
+ * the usual chunking would not fit, fewer term chunks are used (the sum order
+ * then differs from wick_contract's within rounding).
+ *   - Every call looks up the array's device address for the current device
+ *     (cudaGetSymbolAddress).  Under lazy module loading the first call on a
+ *     device may make the driver load the library's device code, which
+ *     reserves the array and the kernels in device memory: make that first
+ *     call in the caller's set-up phase, before any stream capture.
  *   - Every call shares the one array and it keeps the last call's contents;
  *     each call writes every partial it reads, so nothing needs clearing, but
  *     calls that overlap on the GPU (concurrent streams, other host threads)

@@ -469,6 +469,7 @@ int wick_reduce_terms(const wick_nucleus *nuc, const wick_nucleon_op *ops, const
 
 int64_t wick_terms_count(const wick_terms *t) { return t ? t->U : WICK_EINVAL; }
 int wick_terms_nucleons(const wick_terms *t) { return t ? t->A : WICK_EINVAL; }
+int64_t wick_terms_block_count(const wick_terms *t) { return t ? (int64_t)t->n_blk : WICK_EINVAL; }
 
 int wick_terms_copy(const wick_terms *t, uint16_t *ids, int64_t *w, int64_t *rep) {
     if (!t) return WICK_EINVAL;
@@ -618,7 +619,7 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *t, int
     if (precision != WICK_FP64 && precision != WICK_MIXED) return WICK_EINVAL;
     if ((uintptr_t)blocks % 16 || (uintptr_t)C_out % 16) return WICK_EINVAL;
     const int64_t n_slices = (int64_t)n_src * T;
-    if (n_slices > 65535) return WICK_EINVAL;
+    if (n_slices > 2147483647) return WICK_EINVAL;   // slices run on grid.x
     int n_chunks = 1;
     const size_t bytes = contract_partials_bytes((int)n_slices, t->U, t->A, t->n_blk, &n_chunks);
     int err = WICK_OK;
@@ -634,7 +635,6 @@ int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms
     if (precision != WICK_FP64 && precision != WICK_MIXED) return WICK_EINVAL;
     if ((uintptr_t)blocks % 16 || (uintptr_t)C_out % 16) return WICK_EINVAL;
     const int64_t n_slices = (int64_t)n_src * T;
-    if (n_slices > 65535) return WICK_EINVAL;
     double2 *scratch = nullptr;
     size_t cap = 0;
     int err = noalloc_partials(&scratch, &cap);

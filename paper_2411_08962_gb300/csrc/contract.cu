@@ -10,7 +10,6 @@
 // so the float pipes do the products and only the term sum is FP64.  The CTA reduces in a fixed tree; a second kernel sums
 // the chunk partials in chunk order.  Both orders are fixed: the result is
 // bitwise reproducible.
-#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -152,33 +151,19 @@ int launch_p(int A, const double2 *blocks, int n_slices, int n_blk, int64_t U, c
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) double2 g_noalloc_partials[kNoAllocPartials];
 
-namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[kMaxDevices] = {};
-}  // namespace
-
 int noalloc_partials(double2 **ptr, size_t *capacity) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    // In host code the array's name is only a host-side stand-in; its device
+    // address comes from the runtime for the device that is current now.  It
+    // is looked up on every call (no allocation, a table lookup once the
+    // module is loaded), so a context that was reset or replaced never sees a
+    // stale address.
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess || !p) {
         (void)cudaGetLastError();
         return WICK_ECUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) return WICK_EINVAL;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        // In host code the array's name is only a host-side stand-in; the
-        // device address comes from the runtime, once per device, with that
-        // device current.
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e != cudaSuccess || !p) {
-            (void)cudaGetLastError();
-            return WICK_ECUDA;
-        }
-        g_noalloc_addr[dev] = p;
-    }
-    *ptr = static_cast<double2 *>(g_noalloc_addr[dev]);
+    *ptr = static_cast<double2 *>(p);
     *capacity = kNoAllocPartials;
     return WICK_OK;
 }

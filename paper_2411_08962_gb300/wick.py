@@ -26,7 +26,7 @@ WICK_UPLOAD_AUTO, WICK_UPLOAD_DMA, WICK_UPLOAD_KERNEL = 0, 1, 2
 WICK_U, WICK_D = 0, 1
 
 EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_upload_rows", "wick_reduce_terms", "wick_terms_count",
-           "wick_terms_nucleons", "wick_terms_copy", "wick_terms_stats", "wick_terms_select",
+           "wick_terms_nucleons", "wick_terms_block_count", "wick_terms_copy", "wick_terms_stats", "wick_terms_select",
            "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_contract_noalloc",
            "wick_status", "wick_batch_create", "wick_batch_run", "wick_batch_launches", "wick_batch_free",
            "wick_synth_propagator", "wick_cluster_product", "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats",
@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
             L.wick_terms_count.argtypes = [vp]
             L.wick_terms_count.restype = C.c_int64
             L.wick_terms_nucleons.argtypes = [vp]
+            L.wick_terms_block_count.argtypes = [vp]
+            L.wick_terms_block_count.restype = C.c_int64
             L.wick_terms_copy.argtypes = [vp, vp, vp, vp]
             L.wick_terms_stats.argtypes = [vp, P(C.c_int64), P(C.c_double)]
             L.wick_terms_select.argtypes = [vp, P(C.c_int64), C.c_int64]
@@ -119,7 +121,7 @@ def load(path: str = LIB_PATH):
             L.wick_strerror.argtypes = [C.c_int]
             L.wick_strerror.restype = C.c_char_p
             L.wick_version.restype = C.c_char_p
-            for f in ("wick_build_blocks", "wick_reduce_terms", "wick_terms_nucleons", "wick_terms_copy",
+            for f in ("wick_build_blocks", "wick_reduce_terms", "wick_terms_nucleons", "wick_terms_block_count", "wick_terms_copy",
                       "wick_terms_stats", "wick_terms_select", "wick_terms_save", "wick_terms_load",
                       "wick_contract", "wick_contract_noalloc", "wick_status", "wick_batch_create",
                       "wick_batch_run", "wick_batch_launches", "wick_synth_propagator", "wick_cluster_product",
@@ -142,13 +144,40 @@ def _check(rc, what):
         raise WickError(rc, what)
 
 
-def _ptr(x):
-    """Device pointer of a torch tensor (or an int)."""
-    if x is None:
-        return None
+_C128 = ("torch.complex128",)
+_CPLX = ("torch.complex64", "torch.complex128")
+
+
+def _buf(x, what: str, dtypes, numel: int, where: str = "cuda", exact: bool = False):
+    """Pointer of a torch tensor that the library will read or write, after the checks the C side
+    cannot make: dtype, contiguity, size (at least `numel` elements, exactly with `exact`) and
+    placement ("cuda": device memory; "pinned": page-locked host memory).  Raw integer pointers pass
+    through unchecked.  A bad tensor raises ValueError before anything reaches libwick."""
     if isinstance(x, int):
         return x
+    if x is None:
+        raise ValueError(f"{what}: a tensor is required")
+    if str(x.dtype) not in dtypes:
+        raise ValueError(f"{what}: dtype {x.dtype}, expected {' or '.join(dtypes)}")
+    if not x.is_contiguous():
+        raise ValueError(f"{what}: tensor is not contiguous")
+    if x.numel() < numel or (exact and x.numel() != numel):
+        raise ValueError(f"{what}: {x.numel()} elements, {'exactly' if exact else 'at least'} {numel} needed")
+    if where == "cuda" and not x.is_cuda:
+        raise ValueError(f"{what}: tensor is not in CUDA device memory")
+    if where == "pinned" and (x.is_cuda or not x.is_pinned()):
+        raise ValueError(f"{what}: tensor is not in page-locked host memory")
     return x.data_ptr()
+
+
+def _dtype_code(S) -> int:
+    return WICK_C64 if str(getattr(S, "dtype", "")) == "torch.complex64" else WICK_C128
+
+
+def _prop(S, L: int, T: int, n_src: int, what: str, where: str = "cuda") -> "wick_prop":
+    """wick_prop of a propagator tensor [n_src][T][L^3][3][4][3][4] (complex64 or complex128)."""
+    n = n_src * T * L ** 3 * 144
+    return wick_prop(_buf(S, what, _CPLX, n, where, exact=True), L, T, n_src, _dtype_code(S))
 
 
 def _stream(stream):
@@ -202,22 +231,18 @@ def wick_block_count(tables: Tables) -> int:
 
 def wick_build_blocks(Su, Sd, tables: Tables, precision: int, blocks, L: int, T: int, n_src: int, stream=None):
     """Blocks[src][t][n_blk] complex128 (torch.complex128 CUDA tensor) from Su, Sd."""
-    def prop(S):
-        dt = WICK_C64 if str(S.dtype) == "torch.complex64" else WICK_C128
-        return wick_prop(_ptr(S), L, T, n_src, dt)
-    pu, pd = prop(Su), prop(Sd)
+    pu, pd = _prop(Su, L, T, n_src, "Su"), _prop(Sd, L, T, n_src, "Sd")
+    pb = _buf(blocks, "blocks", _C128, n_src * T * tables.nuc.n_blk)
     _check(load().wick_build_blocks(C.byref(pu), C.byref(pd), tables.ops, C.byref(tables.layout), precision,
-                                    _ptr(blocks), _stream(stream)), "wick_build_blocks")
+                                    pb, _stream(stream)), "wick_build_blocks")
 
 
 def wick_upload_rows(Su_host, Sd_host, Su_dev, Sd_dev, tables: Tables, L: int, T: int, n_src: int,
                      stream=None, mode: int = 0) -> int:
     """Copy the rows of S the block build of `tables` reads from pinned host tensors to device tensors of
     the same shape (mode WICK_UPLOAD_AUTO / _DMA / _KERNEL); returns the bytes copied."""
-    def prop(S):
-        dt = WICK_C64 if str(S.dtype) == "torch.complex64" else WICK_C128
-        return wick_prop(_ptr(S), L, T, n_src, dt)
-    hu, hd, du, dd = prop(Su_host), prop(Sd_host), prop(Su_dev), prop(Sd_dev)
+    hu, hd = _prop(Su_host, L, T, n_src, "Su_host", "pinned"), _prop(Sd_host, L, T, n_src, "Sd_host", "pinned")
+    du, dd = _prop(Su_dev, L, T, n_src, "Su_dev"), _prop(Sd_dev, L, T, n_src, "Sd_dev")
     n = C.c_size_t(0)
     _check(load().wick_upload_rows(C.byref(hu), C.byref(hd), C.byref(du), C.byref(dd), tables.ops,
                                    C.byref(tables.layout), mode, C.byref(n), _stream(stream)), "wick_upload_rows")
@@ -245,6 +270,14 @@ class Terms:
     @property
     def nucleons(self) -> int:
         return int(load().wick_terms_nucleons(self.h))
+
+    @property
+    def block_count(self) -> int:
+        """Block entries per (source, time slice) of the layout the table was reduced for."""
+        n = int(load().wick_terms_block_count(self.h))
+        if n < 0:
+            raise WickError(n, "wick_terms_block_count")
+        return n
 
     def copy(self):
         U, A = self.count, self.nucleons
@@ -281,15 +314,21 @@ def wick_reduce_terms(tables: Tables, seed: int = 0x2411, trials: int = 2, sites
     return Terms(h.value)
 
 
+def _contract_args(blocks, n_src, T, terms, C_out):
+    nb = terms.block_count
+    return (_buf(blocks, "blocks", _C128, n_src * T * nb), _buf(C_out, "C_out", _C128, n_src * T))
+
+
 def wick_contract(blocks, n_src: int, T: int, terms: Terms, precision: int, C_out, stream=None):
-    _check(load().wick_contract(_ptr(blocks), n_src, T, terms.h, precision, _ptr(C_out), _stream(stream)),
-           "wick_contract")
+    pb, pc = _contract_args(blocks, n_src, T, terms, C_out)
+    _check(load().wick_contract(pb, n_src, T, terms.h, precision, pc, _stream(stream)), "wick_contract")
 
 
 def wick_contract_noalloc(blocks, n_src: int, T: int, terms: Terms, precision: int, C_out, stream=None):
     """wick_contract for callers that cannot allocate device memory: its scratch
     is a fixed 1 MiB device array inside the library (see include/wick.h)."""
-    _check(load().wick_contract_noalloc(_ptr(blocks), n_src, T, terms.h, precision, _ptr(C_out), _stream(stream)),
+    pb, pc = _contract_args(blocks, n_src, T, terms, C_out)
+    _check(load().wick_contract_noalloc(pb, n_src, T, terms.h, precision, pc, _stream(stream)),
            "wick_contract_noalloc")
 
 
@@ -299,18 +338,21 @@ class Batch:
     def __init__(self, Su_list, Sd_list, tables: Tables, terms_list, precision, blocks, C_out, L, T, n_src):
         n = len(Su_list)
 
-        def props(lst):
+        def props(lst, what):
             arr = (wick_prop * n)()
             for i, S in enumerate(lst):
-                dt = WICK_C64 if str(S.dtype) == "torch.complex64" else WICK_C128
-                arr[i] = wick_prop(_ptr(S), L, T, n_src, dt)
+                arr[i] = _prop(S, L, T, n_src, f"{what}[{i}]")
             return arr
         self._keep = (Su_list, Sd_list, tables, terms_list, blocks, C_out)
-        self.su, self.sd = props(Su_list), props(Sd_list)
+        if len(Sd_list) != n:
+            raise ValueError("Su_list and Sd_list differ in length")
+        self.su, self.sd = props(Su_list, "Su_list"), props(Sd_list, "Sd_list")
+        pb = _buf(blocks, "blocks", _C128, n * n_src * T * tables.nuc.n_blk)
+        pc = _buf(C_out, "C_out", _C128, n * len(terms_list) * n_src * T)
         handles = (C.c_void_p * len(terms_list))(*[t.h.value for t in terms_list])
         h = C.c_void_p(None)
         _check(load().wick_batch_create(self.su, self.sd, n, tables.ops, C.byref(tables.layout), handles,
-                                        len(terms_list), precision, _ptr(blocks), _ptr(C_out), C.byref(h)),
+                                        len(terms_list), precision, pb, pc, C.byref(h)),
                "wick_batch_create")
         self.h = h
 
@@ -332,14 +374,17 @@ class Batch:
 
 def wick_synth_propagator(seed: int, flavour: int, src: int, L: int, T: int, out, stream=None):
     """Device-generated synthetic propagator of one (flavour, source) into `out`."""
-    dt = WICK_C64 if str(out.dtype) == "torch.complex64" else WICK_C128
-    _check(load().wick_synth_propagator(seed, flavour, src, L, T, dt, _ptr(out), _stream(stream)),
+    po = _buf(out, "out", _CPLX, T * L ** 3 * 144, exact=True)
+    _check(load().wick_synth_propagator(seed, flavour, src, L, T, _dtype_code(out), po, _stream(stream)),
            "wick_synth_propagator")
 
 
 def wick_cluster_product(Ca, Cb, out, stream=None):
     """out = Ca * Cb elementwise (complex128 device tensors of equal size)."""
-    _check(load().wick_cluster_product(_ptr(Ca), _ptr(Cb), Ca.numel(), _ptr(out), _stream(stream)),
+    n = Ca.numel()
+    pa, pb = _buf(Ca, "Ca", _C128, n, exact=True), _buf(Cb, "Cb", _C128, n, exact=True)
+    po = _buf(out, "out", _C128, n, exact=True)
+    _check(load().wick_cluster_product(pa, pb, n, po, _stream(stream)),
            "wick_cluster_product")
 
 
@@ -423,22 +468,19 @@ def wick_det_contract(Su, Sd, plan: DetPlan, C_out, L: int, T: int, n_src: int, 
                       precision: int = WICK_FP64, stream=None):
     """C_out[el][src][t] (torch complex128 CUDA tensor; el = i * N + j for a matrix plan, one element
     otherwise) = point-sink correlators of the plan."""
-    def prop(S):
-        dt = WICK_C64 if str(S.dtype) == "torch.complex64" else WICK_C128
-        return wick_prop(_ptr(S), L, T, n_src, dt)
-    pu, pd = prop(Su), prop(Sd)
+    pu, pd = _prop(Su, L, T, n_src, "Su"), _prop(Sd, L, T, n_src, "Sd")
+    pc = _buf(C_out, "C_out", _C128, plan.stats()["n_el"] * n_src * T)
     sc = plan.scale if scale is None else float(scale)
-    _check(load().wick_det_contract(C.byref(pu), C.byref(pd), plan.h, sc, precision, _ptr(C_out), _stream(stream)),
+    _check(load().wick_det_contract(C.byref(pu), C.byref(pd), plan.h, sc, precision, pc, _stream(stream)),
            "wick_det_contract")
 
 
 def wick_det_contract_3pt(Su, Sd, Sig, flavour: int, plan: DetPlan, C_out, L: int, T: int, n_src: int, scale=None,
                           precision: int = WICK_FP64, stream=None):
     """Three-point function: the current on `flavour` (WICK_U / WICK_D) through the sequential propagator Sig."""
-    def prop(S):
-        dt = WICK_C64 if str(S.dtype) == "torch.complex64" else WICK_C128
-        return wick_prop(_ptr(S), L, T, n_src, dt)
-    pu, pd, pq = prop(Su), prop(Sd), prop(Sig)
+    pu, pd = _prop(Su, L, T, n_src, "Su"), _prop(Sd, L, T, n_src, "Sd")
+    pq = _prop(Sig, L, T, n_src, "Sig")
+    pc = _buf(C_out, "C_out", _C128, plan.stats()["n_el"] * n_src * T)
     sc = plan.scale if scale is None else float(scale)
     _check(load().wick_det_contract_3pt(C.byref(pu), C.byref(pd), C.byref(pq), flavour, plan.h, sc, precision,
-                                        _ptr(C_out), _stream(stream)), "wick_det_contract_3pt")
+                                        pc, _stream(stream)), "wick_det_contract_3pt")

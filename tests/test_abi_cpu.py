@@ -118,3 +118,45 @@ def test_product_tables_equal_oracle_tables(name, form):
     assert a.src == b["src"]
     assert list(a.src_flav) == list(b["src_flav"])
     assert a.n_raw == oops.n_raw_terms(b)
+
+
+def test_binding_rejects_bad_tensors_before_the_library(lib):
+    """The C side cannot see the size, dtype or placement of a buffer; the binding checks them and
+    raises ValueError before anything reaches libwick (a bad buffer would otherwise be read or
+    written out of bounds on the device)."""
+    import types
+
+    torch = pytest.importorskip("torch")
+    tabs = wick.Tables(operators.nucleus("deuteron"))
+    L, T, n_src = 2, 2, 1
+    n_prop = n_src * T * L ** 3 * 144
+    nb = tabs.nuc.n_blk
+    good_s = torch.zeros(n_prop, dtype=torch.complex64)
+    good_b = torch.zeros(n_src * T * nb, dtype=torch.complex128)
+    cases = {
+        "wrong propagator dtype": (torch.zeros(n_prop, dtype=torch.float64), good_b),
+        "non-contiguous propagator": (torch.zeros(2 * n_prop, dtype=torch.complex64)[::2], good_b),
+        "short propagator": (torch.zeros(n_prop - 1, dtype=torch.complex64), good_b),
+        "host propagator": (good_s, good_b),
+        "complex64 blocks": (good_s, torch.zeros(n_src * T * nb, dtype=torch.complex64)),
+        "short blocks": (good_s, torch.zeros(n_src * T * nb - 1, dtype=torch.complex128)),
+    }
+    for what, (S, B) in cases.items():
+        with pytest.raises(ValueError):
+            wick.wick_build_blocks(S, S, tabs, wick.WICK_FP64, B, L, T, n_src)
+    fake_terms = types.SimpleNamespace(block_count=nb, h=None)
+    with pytest.raises(ValueError):   # output too small
+        wick.wick_contract(good_b, n_src, T, fake_terms, wick.WICK_FP64,
+                           torch.zeros(n_src * T - 1, dtype=torch.complex128))
+    with pytest.raises(ValueError):   # blocks of another layout (too few entries per slice)
+        wick.wick_contract_noalloc(torch.zeros(n_src * T * (nb - 1), dtype=torch.complex128), n_src, T,
+                                   fake_terms, wick.WICK_FP64, torch.zeros(n_src * T, dtype=torch.complex128))
+    with pytest.raises(ValueError):   # host tensors
+        wick.wick_contract(good_b, n_src, T, fake_terms, wick.WICK_FP64, torch.zeros(n_src * T, dtype=torch.complex128))
+    with pytest.raises(ValueError):   # upload source not page-locked
+        wick.wick_upload_rows(good_s, good_s, good_s, good_s, tabs, L, T, n_src)
+    with pytest.raises(ValueError):
+        wick.wick_cluster_product(torch.zeros(4, dtype=torch.complex128), torch.zeros(3, dtype=torch.complex128),
+                                  torch.zeros(4, dtype=torch.complex128))
+    with pytest.raises(ValueError):
+        wick.wick_synth_propagator(1, 0, 0, L, T, torch.zeros(n_prop // n_src - 1, dtype=torch.complex64))
