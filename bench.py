@@ -3,12 +3,12 @@
 
 Workload: He-4 (p up, p down, n up, n down; upper Dirac components), L=16,
 T=32, 4 sources, complex64 propagators (synthetic i.i.d. Gaussian; the paper's
-HISQ/overlap ensembles are not available).  One step = one configuration:
-wick_build_blocks + wick_contract in MIXED precision for all 4 sources x 32
-time slices, inputs resident in HBM (1.2 GB per configuration, larger than
-L2; two configurations alternate).  The reduced term table is the one-time
-per-nucleus preprocessing (Sec. III.B): it is built once before the timed
-region and its time is reported separately ("reduce").
+HISQ/overlap ensembles are not available).  One step = one batched launch
+(mixed precision) over 32 configurations resident in HBM (1.2 GB each, far
+larger than L2): the block build of every configuration and the contraction
+of the reduced He-4 table for all 4 sources x 32 time slices.  The reduced
+term table is the one-time per-nucleus preprocessing (Sec. III.B): it is built
+once before the timed region and its time is reported separately ("reduce").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the Li-7 and batched sub-records")
     ap.add_argument("--workload", choices=["he4", "li7", "batched", "point"], default="he4",
                     help="he4: the metric's workload (default); li7 / batched: the other scope rows")
     ap.add_argument("--profile-slab", choices=["mixed", "fp64"], default=None,
@@ -59,6 +60,34 @@ def bf16_peak_tflops():
     return FALLBACK_BF16_TFLOPS
 
 
+_FP64_PEAK = None
+
+
+def fp64_peak_tflops():
+    """FP64 roof of this GPU, measured: the FP64 GEMM rate of cuBLAS (through torch.matmul on 8192^2
+    float64 operands, CUDA events, best of 5 after warm-up).  MEASURED_PEAKS has no FP64 entry."""
+    global _FP64_PEAK
+    if _FP64_PEAK is None:
+        import torch
+        n = 8192
+        a = torch.randn((n, n), dtype=torch.float64, device="cuda")
+        b = torch.randn((n, n), dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            torch.matmul(a, b)
+        best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        _FP64_PEAK = 2.0 * n ** 3 / (best / 1e3) / 1e12
+        del a, b
+        torch.cuda.empty_cache()
+    return _FP64_PEAK
+
+
 def peaks():
     """(HBM GB/s, SM max MHz, kind) from the measured-peaks file, else the fallback."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -70,15 +99,15 @@ def peaks():
 
 N_SM = 152
 FP32_LANES = 128          # FP32 pipe lanes per SM
-FP64_NOMINAL_TFLOPS = 1.25
+
+# Algorithmic DRAM bytes per site of the upper-spin block build: the 6 x 6 complex64 entries per flavour
+# that the tables use (sink rows a, alpha in {0, 1}; source columns b, beta in {0, 1}).
+BLOCK_ALG_BYTES_PER_SITE = 2 * 6 * 6 * 8
 
 # Complex multiply-adds per site of the upper-spin block build (both block
 # types): the diquark lists 2 ops x 3 lists x 36 entries x 4 terms and the
 # update 2 ops x 2 spins x 216 entries x 3 terms.
 CMAC_PER_SITE = 2 * 3 * 36 * 4 + 2 * 2 * 216 * 3
-# FP32-pipe operations per real multiply-add in double-FP32: TwoProd (2), the
-# low-part FMA (1), TwoSum (6) and the two low-part adds (2).
-DF32_OPS_PER_MAC = 11
 
 # The tensor-core block build (WICK_MIXED) per site, both block types: the
 # FP32-pipe work of preparing the operands, in lane operations (an f32x2
@@ -167,15 +196,6 @@ def gpu_local_cpus(device: int):
     return cpus or None
 
 
-def block_bytes_per_site(dtype_bytes: int) -> int:
-    """Algorithmic DRAM bytes per site of the upper-component block build: the
-    six sink-upper rows (a, alpha in {0,1}) of S_u and S_d.  Every 32-byte
-    sector of those rows holds a needed (beta in {0,1}) pair, so the rows are
-    the minimum traffic in the paper's propagator layout."""
-    rows, cols = 6, 12
-    return 2 * rows * cols * dtype_bytes
-
-
 def code_tokens(text: str) -> str:
     """C++ source without comments and blank space: two sources that differ only there compile to
     the same kernel."""
@@ -211,21 +231,26 @@ def recorded_traffic():
 # ---------------------------------------------------------------------------
 # CPU reference timing (the oracle as it stands, on this host's cores)
 # ---------------------------------------------------------------------------
-def oracle_ms_per_config(Su, Sd, slices, tab):
-    """Time the CPU reference on `slices` (src, t) of one configuration (one
-    call, so its OpenMP loop spans every host core) and scale to the whole
-    configuration."""
+NB_CONFIGS = 32          # He-4 configurations per step (one batched launch)
+
+
+def config_dict(U):
+    """The workload description both arms print (identical keys and values)."""
+    return {"workload": WORKLOAD, "L": 16, "T": 32, "n_src": 4, "reduced_terms": U,
+            "l2": "inputs larger than L2 (1.2 GB per configuration; consecutive configurations are distinct)"}
+
+
+def oracle_config(Su, Sd, tab):
+    """The CPU reference on one whole configuration (one call, so its OpenMP
+    loop spans every host core): blocks and the reduced-table correlator for
+    every (source, time slice).  Returns (C[src][t], seconds, threads)."""
     from oracle import operators as oops
     from oracle import oracle as O
     onuc = oops.nucleus("he4")
-    n_src, T = Su.shape[:2]
-    su = np.stack([Su[s, t] for s, t in slices])[None].astype(np.complex128)
-    sd = np.stack([Sd[s, t] for s, t in slices])[None].astype(np.complex128)
     t0 = time.perf_counter()
-    Bh = O.blocks_single(su, sd, onuc)
-    O.table_correlator(onuc, Bh, tab)
-    dt = time.perf_counter() - t0
-    return 1e3 * dt * (n_src * T) / len(slices), O.num_threads(), dt
+    Bh = O.blocks_single(Su.astype(np.complex128), Sd.astype(np.complex128), onuc)
+    Cref = O.table_correlator(onuc, Bh, tab)
+    return Cref, time.perf_counter() - t0, O.num_threads()
 
 
 def he4_oracle_table():
@@ -242,28 +267,29 @@ def host_props(seed, L, T, n_src):
 
 
 def run_reference(args):
+    """The oracle arm: every step evaluates one whole configuration (all 4
+    sources x 32 time slices: blocks and the reduced-table sum) on the host
+    cores; two configurations alternate."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_2411_08962_gb300 import synth
+    from paper_2411_08962_gb300 import sharding, synth
     w = synth.WORKLOADS["he4"]
     L, T, n_src = w["L"], w["T"], w["n_src"]
-    Su, Sd = host_props(w["seed"], L, T, n_src)
+    cfgs = [host_props(sharding.config_seed(w["seed"], c), L, T, n_src) for c in range(2)]
     tab = he4_oracle_table()
-    rng = np.random.default_rng(0)
-    per_step = 4
-    times = []
+    times, cores = [], 1
     for i in range(args.warmup + args.steps):
-        sl = [(int(rng.integers(n_src)), int(rng.integers(T))) for _ in range(per_step)]
-        ms, cores, _ = oracle_ms_per_config(Su, Sd, sl, tab)
+        Su, Sd = cfgs[i % 2]
+        _, dt, cores = oracle_config(Su, Sd, tab)
         if i >= args.warmup:
-            times.append(ms)
+            times.append(1e3 * dt)
     v = float(np.mean(times))
-    sample = f"{per_step} random (source, time-slice) pairs per step, scaled by {n_src * T}/{per_step}"
+    sample = f"one whole configuration ({n_src} sources x {T} time slices) per step, two alternating"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "L": L, "T": T, "n_src": n_src},
+            "config": config_dict(len(tab["w"])),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -295,129 +321,139 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     # one-time preprocessing: the reduced term table
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     terms = wick.wick_reduce_terms(tabs)
     reduce_s = time.perf_counter() - t0
     (n_raw, n_zero, n_keys, U), bound = terms.stats()
 
-    # inputs: two configurations per rank, resident on the device; pinned host copies for e2e,
-    # allocated from the CPUs next to the GPU so that they sit in its local host memory
+    # inputs: NB_CONFIGS configurations per rank, resident on the device.  The first two come from the
+    # host generator (pinned host copies serve the end-to-end leg and the CPU reference); the others are
+    # generated on the device (the same definition; last bits may differ).
+    mine = list(sharding.shard(NB_CONFIGS * world, rank, world))
     cfg_host, cfg_dev = [], []
     all_cpus = os.sched_getaffinity(0)
     local_cpus = gpu_local_cpus(torch.cuda.current_device())
     if local_cpus:
         os.sched_setaffinity(0, local_cpus)
-    for c in sharding.shard(2 * world, rank, world):
+    host_np = []
+    for c in mine[:2]:
         Su, Sd = host_props(sharding.config_seed(w["seed"], c), L, T, n_src)
+        host_np.append((Su, Sd))
         hu = torch.from_numpy(Su).pin_memory()
         hd = torch.from_numpy(Sd).pin_memory()
         cfg_host.append((hu, hd))
         cfg_dev.append((hu.cuda(), hd.cuda()))
-    Cpin = torch.empty_like(torch.empty((n_src, T), dtype=torch.complex128), device="cpu").pin_memory()
+    Cpin = torch.empty((n_src, T), dtype=torch.complex128).pin_memory()
     os.sched_setaffinity(0, all_cpus)
+    shape = (n_src, T, V, 3, 4, 3, 4)
+    for c in mine[2:]:
+        pair = (torch.empty(shape, dtype=torch.complex64, device="cuda"),
+                torch.empty(shape, dtype=torch.complex64, device="cuda"))
+        for f in (0, 1):
+            for s in range(n_src):
+                wick.wick_synth_propagator(sharding.config_seed(w["seed"], c), f, s, L, T, pair[f][s], stream)
+        cfg_dev.append(pair)
+    nb = len(cfg_dev)
     blocks = torch.empty((n_src, T, nuc.n_blk), dtype=torch.complex128, device="cuda")
     Cout = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
     prec = wick.WICK_MIXED
 
-    def step(i, p=prec, b_ev=None):
-        Su_d, Sd_d = cfg_dev[i % 2]
-        if b_ev is not None:
-            b_ev[0].record(stream)
-        wick.wick_build_blocks(Su_d, Sd_d, tabs, p, blocks, L, T, n_src, stream)
-        if b_ev is not None:
-            b_ev[1].record(stream)
-        wick.wick_contract(blocks, n_src, T, terms, p, Cout, stream)
-
-    for i in range(args.warmup):
-        step(i)
+    # the step: one batched launch over the rank's configurations
+    bblocks = torch.empty((nb, n_src, T, nuc.n_blk), dtype=torch.complex128, device="cuda")
+    bC = torch.empty((nb, 1, n_src, T), dtype=torch.complex128, device="cuda")
+    batch = wick.Batch([c[0] for c in cfg_dev], [c[1] for c in cfg_dev], tabs, [terms], prec, bblocks, bC,
+                       L, T, n_src)
+    launches_per_step = batch.launches
+    for _ in range(args.warmup):
+        batch.run(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
-    bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     e0.record(stream)
-    for i in range(args.steps):
-        step(i, b_ev=bev[i])
+    for _ in range(args.steps):
+        batch.run(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop() if clocks else None
     elapsed = sharding.max_over_ranks(e0.elapsed_time(e1), device="cuda")
-    build_ms = float(np.mean([a.elapsed_time(b) for a, b in bev]))
-    configs = args.steps * world
+    configs = args.steps * nb * world
     value = elapsed / configs
     terms_per_s = U * n_src * T * configs / (elapsed / 1e3)
-    C_mixed = Cout.clone()
+    C_mixed0 = bC[0, 0].clone()          # configuration mine[0]
+    batch.free()
 
+    # the dominant kernel alone (the block build of one configuration), CUDA events on its stream
+    kb = max(5, min(20, args.steps))
+    build_ms = _timed(lambda i=[0]: (wick.wick_build_blocks(*cfg_dev[i[0] % 2], tabs, prec, blocks, L, T, n_src,
+                                                             stream), i.__setitem__(0, i[0] + 1)), kb, 2, stream)
+    contract_ms = _timed(lambda: wick.wick_contract(blocks, n_src, T, terms, prec, Cout, stream), kb, 2, stream)
+
+    def single(i, p):
+        wick.wick_build_blocks(*cfg_dev[i % 2], tabs, p, blocks, L, T, n_src, stream)
+        wick.wick_contract(blocks, n_src, T, terms, p, Cout, stream)
+
+    single_ms = _timed(lambda i=[0]: (single(i[0], prec), i.__setitem__(0, i[0] + 1)), kb, 2, stream)
     # FP64 plain path on the same inputs (fewer steps)
     k64 = max(2, min(5, args.steps))
-    step(0, wick.WICK_FP64)
+    fp64_ms = _timed(lambda i=[0]: (single(i[0], wick.WICK_FP64), i.__setitem__(0, i[0] + 1)), k64, 1, stream)
+    single(0, wick.WICK_FP64)
     torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for i in range(k64):
-        step(i, wick.WICK_FP64)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    fp64_ms = f0.elapsed_time(f1) / k64
-    # precision: mixed vs FP64 GPU path on the last configuration of the timed loop
-    last = (args.steps - 1) % 2
-    step(last, wick.WICK_FP64)
-    torch.cuda.synchronize()
-    C64 = Cout.clone()
-    rel = (C_mixed - C64).abs() / C64.abs()
-    rel_err = float(rel.max().item())
+    C64_0 = Cout.clone()
+    rel_err = float(((C_mixed0 - C64_0).abs() / C64_0.abs()).max().item())
 
-    # end to end through the API with host buffers: every step uploads, from pinned host memory, the
-    # rows of its configuration that the block build reads (wick_upload_rows; a copy stream, two
-    # device buffers, so the next upload overlaps the current computation), runs the build and the
-    # contraction and reads C back to pinned host memory
+    # end to end through the API with host buffers: every configuration of a step uploads, from pinned host
+    # memory, the rows the block build reads (wick_upload_rows; a copy stream, two device buffers, so the
+    # next upload overlaps the current computation), runs the build and the contraction and reads C back
     d2h = Cout.numel() * Cout.element_size()
-    ke = max(4, min(10, args.steps))
     dbufs = [(torch.empty_like(cfg_dev[0][0]), torch.empty_like(cfg_dev[0][1])) for _ in range(2)]
     copy_stream = torch.cuda.Stream()
     copied = [torch.cuda.Event() for _ in range(2)]
     free = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_step(i, mode=wick.WICK_UPLOAD_AUTO):
+    def e2e_config(i, mode):
         b = i % 2
         hu, hd = cfg_host[i % len(cfg_host)]
         with torch.cuda.stream(copy_stream):
             if i >= 2:
-                copy_stream.wait_event(free[b])          # the buffer's previous step has finished
-            nb = wick.wick_upload_rows(hu, hd, dbufs[b][0], dbufs[b][1], tabs, L, T, n_src, copy_stream, mode)
+                copy_stream.wait_event(free[b])          # the buffer's previous configuration has finished
+            nb_ = wick.wick_upload_rows(hu, hd, dbufs[b][0], dbufs[b][1], tabs, L, T, n_src, copy_stream, mode)
             copied[b].record(copy_stream)
         stream.wait_event(copied[b])
         wick.wick_build_blocks(dbufs[b][0], dbufs[b][1], tabs, prec, blocks, L, T, n_src, stream)
         wick.wick_contract(blocks, n_src, T, terms, prec, Cout, stream)
         Cpin.copy_(Cout, non_blocking=True)
         free[b].record(stream)
-        return nb
+        return nb_
 
-    def e2e_time(mode):
+    def e2e_time(mode, n_cfg):
         for i in range(4):                               # warm-up: first DMA of each pinned buffer is slow
-            nb = e2e_step(i, mode)
+            nb_ = e2e_config(i, mode)
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         copy_stream.wait_event(g0)
-        for i in range(ke):
-            e2e_step(i, mode)
+        for i in range(n_cfg):
+            e2e_config(i, mode)
         g1.record(stream)
         torch.cuda.synchronize()
-        return sharding.max_over_ranks(g0.elapsed_time(g1) / ke, device="cuda") / world, nb
+        return sharding.max_over_ranks(g0.elapsed_time(g1) / n_cfg, device="cuda") / world, nb_
 
-    e2e_dma, h2d_dma = e2e_time(wick.WICK_UPLOAD_DMA)         # pitched copies of the row runs
-    e2e_kernel, h2d_kernel = e2e_time(wick.WICK_UPLOAD_KERNEL)  # the gather kernel
+    ke = max(2, min(4, args.steps)) * nb                 # whole steps of nb configurations
+    e2e_dma, h2d_dma = e2e_time(wick.WICK_UPLOAD_DMA, ke)
+    e2e_kernel, h2d_kernel = e2e_time(wick.WICK_UPLOAD_KERNEL, 8)
     upload_mode = wick.WICK_UPLOAD_KERNEL if e2e_kernel < e2e_dma else wick.WICK_UPLOAD_DMA
+    if upload_mode == wick.WICK_UPLOAD_KERNEL:
+        e2e_kernel, h2d_kernel = e2e_time(wick.WICK_UPLOAD_KERNEL, ke)
     e2e, h2d = (e2e_kernel, h2d_kernel) if upload_mode == wick.WICK_UPLOAD_KERNEL else (e2e_dma, h2d_dma)
     # the link alone: one configuration's row upload, and a full copy of it, on the copy stream
     c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -434,69 +470,64 @@ def run_ours(args):
     full_bytes = 2 * cfg_host[0][0].numel() * cfg_host[0][0].element_size()
     full_gbs = full_bytes / (c1.elapsed_time(c2) / 1e3) / 1e9
 
-    # the same configurations through the batched executor: one CUDA-graph launch per pair
-    bblocks = torch.empty((len(cfg_dev), n_src, T, nuc.n_blk), dtype=torch.complex128, device="cuda")
-    bC = torch.empty((len(cfg_dev), 1, n_src, T), dtype=torch.complex128, device="cuda")
-    batch = wick.Batch([c[0] for c in cfg_dev], [c[1] for c in cfg_dev], tabs, [terms], prec, bblocks, bC,
-                       L, T, n_src)
-    for _ in range(2):
-        batch.run(stream)
-    torch.cuda.synchronize()
-    kb = max(2, min(10, args.steps))
-    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    h0.record(stream)
-    for _ in range(kb):
-        batch.run(stream)
-    h1.record(stream)
-    torch.cuda.synchronize()
-    batched_ms = h0.elapsed_time(h1) / (kb * len(cfg_dev))
-    batch_launches = batch.launches
-    kernels_per_config = batch_launches // len(cfg_dev)   # the library's own count of its launches
-    batch.free()
-
     # the CUDA-core double-FP32 block kernel on the same input, for comparison
     simt_ms = _timed(lambda: wick.wick_build_blocks(cfg_dev[0][0], cfg_dev[0][1], tabs, wick.WICK_MIXED_SIMT, blocks,
                                                     L, T, n_src, stream), max(2, min(5, args.steps)), 1, stream)
+    del cfg_dev, dbufs, bblocks
+    torch.cuda.empty_cache()
 
     hbm_peak, sm_mhz, peak_kind = peaks()
     bf16_peak = bf16_peak_tflops()
-    bytes_launch = n_src * T * V * block_bytes_per_site(8)
     sites = n_src * T * V
-    ops_launch = sites * TC_LANE_OPS_PER_SITE
-    mma_flops = sites * TC_MMA_FLOPS_PER_SITE
+    bytes_alg = sites * BLOCK_ALG_BYTES_PER_SITE
+    achieved_gbs = bytes_alg / (build_ms / 1e3) / 1e9
     alu_peak = N_SM * FP32_LANES * sm_mhz * 1e6 / 1e12      # Top/s, one op per lane per clock
-    achieved = ops_launch / (build_ms / 1e3) / 1e12
-    fp64_block_ms = fp64_ms  # the FP64 step is dominated by its block build
-    fp64_tflops = sites * CMAC_PER_SITE * 8 / (fp64_block_ms / 1e3) / 1e12
+    lane_tops = sites * TC_LANE_OPS_PER_SITE / (build_ms / 1e3) / 1e12
+    mma_tflops = sites * TC_MMA_FLOPS_PER_SITE / (build_ms / 1e3) / 1e12
+    method_tflops = sites * CMAC_PER_SITE * 8 / (build_ms / 1e3) / 1e12
+    fp64_tflops = sites * CMAC_PER_SITE * 8 / (fp64_ms / 1e3) / 1e12
+    # the contraction (c1): per term, slice: A block entries gathered (16 B each) + the table entry
+    c1_bytes = U * n_src * T * (4 * 16) + U * (4 * 2 + 8)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "L": L, "T": T, "n_src": n_src, "precision": "mixed (double-FP32)",
-                   "reduced_terms": U, "l2": "inputs larger than L2 (1.2 GB per configuration; 2 alternate)",
-                   "parallelism": f"{world} independent rank(s), configurations sharded"},
+        "config": config_dict(U),
+        "precision": "mixed: double-FP32 products on the float pipes, exact sliced bf16 update on the tensor "
+                     "cores, FP64 sums over site ranges and terms",
+        "parallelism": f"{world} independent rank(s), configurations sharded",
+        "configs_per_step": nb * world,
         "wick_terms_per_s": terms_per_s,
-        "fp64_plain": {"value": fp64_ms, "unit": UNIT, "speedup_mixed": fp64_ms / value * world,
-                       "fp64_tflops_vs_nominal": fp64_tflops / FP64_NOMINAL_TFLOPS},
+        "single_config": {"value": single_ms, "unit": UNIT,
+                          "note": "wick_build_blocks + wick_contract of one configuration, not batched"},
+        "fp64_plain": {"value": fp64_ms, "unit": UNIT, "speedup_mixed_batched": fp64_ms / value * world,
+                       "method_tflops": fp64_tflops, "fp64_peak_tflops": fp64_peak_tflops(),
+                       "frac": fp64_tflops / fp64_peak_tflops(),
+                       "peak_kind": "measured FP64 GEMM rate (cuBLAS via torch.matmul, 8192^2)"},
         "rel_err_mixed_vs_fp64_max_per_t": rel_err,
-        "batched_graph": {"value": batched_ms, "unit": UNIT, "configs_per_launch": len(cfg_dev),
-                          "kernels_per_launch": batch_launches},
         "reduce": {"seconds": reduce_s, "raw_terms": n_raw, "zero_terms": n_zero, "distinct_keys": n_keys,
                    "kept_terms": U, "raw_terms_per_s": n_raw / reduce_s, "false_merge_bound": bound},
-        "roofline": {"kernel": "block build on the tensor cores (tc_bounds_kernel + block_tc_kernel + "
-                               "tc_reduce_kernel; block_tc_kernel dominates)",
-                     "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
-                     "frac": achieved / alu_peak, "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES} FP32 lanes x "
-                                                              f"{sm_mhz:.0f} MHz ({peak_kind} clock)",
-                     "ops_per_launch": ops_launch, "traffic": recorded_traffic(),
-                     "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": build_ms,
-                     "hbm": {"achieved_gbs": bytes_launch / (build_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
-                             "frac": bytes_launch / (build_ms / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind},
-                     "tensor": {"achieved_tflops": mma_flops / (build_ms / 1e3) / 1e12, "peak_tflops": bf16_peak,
-                                "frac": mma_flops / (build_ms / 1e3) / 1e12 / bf16_peak,
+        "roofline": {"kernel": "block build (tc_bounds_kernel + block_tc_kernel + tc_reduce_kernel; "
+                               "block_tc_kernel dominates)",
+                     "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved_gbs / hbm_peak, "traffic": recorded_traffic(),
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                     "algorithmic_bytes_per_site": BLOCK_ALG_BYTES_PER_SITE, "sites_per_launch": sites,
+                     "launch_ms": build_ms,
+                     "binding_unit": "FP32 pipe: the double-FP32 diquark products and the slicing of the operands",
+                     "method_tflops": method_tflops,
+                     "fp32_lanes": {"achieved_tops": lane_tops, "peak_tops": alu_peak, "frac": lane_tops / alu_peak,
+                                    "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz",
+                                    "ops_per_site": TC_LANE_OPS_PER_SITE},
+                     "tensor": {"achieved_tflops": mma_tflops, "peak_tflops": bf16_peak,
+                                "frac": mma_tflops / bf16_peak,
                                 "peak_kind": "measured bf16 burst (the MMAs issued, padding included)"},
                      "cuda_core_kernel_ms": simt_ms},
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        "contraction": {"launch_ms": contract_ms, "term_slices_per_s": U * n_src * T / (contract_ms / 1e3),
+                        "gather_gbs": c1_bytes / (contract_ms / 1e3) / 1e9,
+                        "note": "algorithmic bytes: 4 gathered complex128 block entries per term and slice "
+                                "(from shared memory after one staging of the slice's blocks) plus the table"},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d * nb, "d2h_bytes_per_step": d2h * nb,
                 "upload": "wick_upload_rows: the sink-upper rows the block build reads (half of S), by the " +
                           ("gather kernel" if upload_mode == wick.WICK_UPLOAD_KERNEL else "copy engines") +
                           " (the faster of the two in this run; the host link is shared, so e2e varies by box)",
@@ -504,17 +535,24 @@ def run_ours(args):
                 "h2d_gbs_alone": h2d_gbs, "full_copy_gbs": full_gbs,
                 "host_buffers": "pinned; allocated from the GPU's local CPUs (%s)" % (
                     f"{len(local_cpus)} CPUs" if local_cpus else "unknown, default placement")},
-        "gpu_launches": kernels_per_config * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
+    if world == 1 and not args.no_extras:
+        line["li7"] = li7_record(max(2, min(5, args.steps)))
+        torch.cuda.empty_cache()
+        line["batched"] = batched_record(2)
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         tab = he4_oracle_table()
-        Su, Sd = (cfg_host[0][0].numpy(), cfg_host[0][1].numpy())
-        sl = [(s, t) for s in range(n_src) for t in range(T)]   # the whole configuration
-        ms, cores, dt = oracle_ms_per_config(Su, Sd, sl, tab)
-        line["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{len(sl)} of {n_src * T} (source, time-slice) pairs, "
-                                          f"{dt:.1f} s, scaled to one configuration"}
+        Su, Sd = host_np[0]
+        Cref, dt, cores = oracle_config(Su, Sd, tab)
+        cm, c64 = C_mixed0.cpu().numpy(), C64_0.cpu().numpy()
+        line["rel_err_vs_oracle_max_per_t"] = float(np.max(np.abs(cm - Cref) / np.abs(Cref)))
+        line["rel_err_fp64_vs_oracle_max_per_t"] = float(np.max(np.abs(c64 - Cref) / np.abs(Cref)))
+        line["cpu_baseline"] = {"value": 1e3 * dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"one whole configuration ({n_src} sources x {T} time slices), "
+                                          f"{dt:.1f} s; its C(t) is the reference of rel_err_vs_oracle"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -641,8 +679,9 @@ def run_point(args):
                                "arithmetic": "double-FP32 minors, determinants and Theta sum; FP64 chunk sums"},
                      "zeta_u": st["zeta_u"], "zeta_d": st["zeta_d"], "theta": st["theta"],
                      "operator_terms": st["n_sink"],
-                     "roofline": {"bound": "fp64", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                                  "frac": tf / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal FP64",
+                     "roofline": {"bound": "fp64", "achieved": tf, "peak": fp64_peak_tflops(), "unit": "TFLOP/s",
+                                  "frac": tf / fp64_peak_tflops(),
+                                  "peak_kind": "measured FP64 GEMM rate (cuBLAS via torch.matmul, 8192^2)",
                                   "flops_per_site": flops // sites}}
         if name == "deuteron" and not args.no_cpu_baseline:
             from oracle import det as DT
@@ -697,13 +736,16 @@ def run_point(args):
                       "nuclei": res, "gpu_launches_per_step": 2}), flush=True)
 
 
-def run_li7(args):
-    """Li-7 = He-4 cluster x triton cluster, L=24, T=48, one source (one configuration per step)."""
+def li7_record(steps: int) -> dict:
+    """Li-7 = He-4 cluster x triton cluster, L=24, T=48, one source (one configuration per step):
+    mixed and FP64 times, the error of the mixed result against FP64, where the mixed step's time goes
+    and the roofline of the full-spin block build."""
     import torch
 
     from paper_2411_08962_gb300 import build, operators, synth, wick
     build.build()
     wick.load()
+    warmup = 1
     w = synth.WORKLOADS["li7"]
     L, T, n_src = w["L"], w["T"], w["n_src"]
     stream = torch.cuda.current_stream()
@@ -727,15 +769,15 @@ def run_li7(args):
             wick.wick_contract(B, n_src, T, terms[n], prec, Cs[n], stream)
         wick.wick_cluster_product(Cs["he4_cluster"], Cs["triton"], Cli, stream)
 
-    ms = _timed(lambda: step(wick.WICK_MIXED), args.steps, args.warmup, stream)
+    ms = _timed(lambda: step(wick.WICK_MIXED), steps, warmup, stream)
     c_mixed = Cli.clone()
     # where the mixed step's time goes: the block build and each table's contraction alone
     phases = {"blocks": _timed(lambda: wick.wick_build_blocks(Su, Sd, tb, wick.WICK_MIXED, B, L, T, n_src, stream),
-                               args.steps, 1, stream)}
+                               steps, 1, stream)}
     for n in tabs:
         phases["contract_" + n] = _timed(lambda n=n: wick.wick_contract(B, n_src, T, terms[n], wick.WICK_MIXED,
-                                                                        Cs[n], stream), args.steps, 1, stream)
-    ms64 = _timed(lambda: step(wick.WICK_FP64), max(1, min(3, args.steps)), 1, stream)
+                                                                        Cs[n], stream), steps, 1, stream)
+    ms64 = _timed(lambda: step(wick.WICK_FP64), max(1, min(3, steps)), 1, stream)
     rel = float(((c_mixed - Cli).abs() / Cli.abs()).max().item())
     # roofline of the full-spin tensor-core block build: the operand preparation per site (4 block
     # types x 144 columns x 3 lists diquark values at 214 lane ops, 4 x 48 rows x 3 lists propagator
@@ -753,17 +795,21 @@ def run_li7(args):
                 "useful_update_tflops": useful_tflops, "tensor_peak_tflops": bf16_peak_tflops(),
                 "note": "U slices and staged rows are rebuilt by each of the 9 column tiles (TMEM holds 16 "
                         "columns x 17 slice-pair blocks per CTA)"}
-    print(json.dumps({"workload": "li7", "metric": "Li-7 correlator ms/config (He-4 cluster x triton)",
-                      "value": ms, "unit": UNIT, "higher_is_better": False, "steps": args.steps,
+    return {"workload": "li7", "metric": "Li-7 correlator ms/config (He-4 cluster x triton)",
+                      "value": ms, "unit": UNIT, "higher_is_better": False, "steps": steps,
                       "config": {"L": L, "T": T, "n_src": n_src, "block_types": 4, "spins": 4,
                                  "terms": {n: t.count for n, t in terms.items()}},
                       "fp64_plain": {"value": ms64, "unit": UNIT},
                       "rel_err_mixed_vs_fp64_max_per_t": rel, "reduce_seconds": reduce_s,
                       "mixed_phases_ms": phases, "roofline": roofline,
-                      "gpu_launches_per_step": 2 + 2 * len(tabs) + 1}), flush=True)
+                      "gpu_launches_per_step": 2 + 2 * len(tabs) + 1}
 
 
-def run_batched(args):
+def run_li7(args):
+    print(json.dumps(li7_record(args.steps)), flush=True)
+
+
+def batched_record(steps: int, warmup: int = 1) -> dict:
     """64 configurations x {deuteron, He-3, He-4} x 2 sources, L=32, T=64,
     complex64, generated on the device and streamed through two buffers
     (generation of the next configuration overlaps the current one)."""
@@ -773,7 +819,7 @@ def run_batched(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    if world > 1:
+    if world > 1 and not (torch.distributed.is_available() and torch.distributed.is_initialized()):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     build.build()
@@ -834,7 +880,7 @@ def run_batched(args):
             wick.wick_build_blocks(bufs[slot][0], bufs[slot][1], tabs, prec, B, L, T, n_src, comp)
             for k, t in enumerate(terms):
                 wick.wick_contract(B, n_src, T, t, prec, C[i, k], comp)
-    ms = _timed(lambda: compute(wick.WICK_MIXED), args.steps, min(args.warmup, 1), comp)
+    ms = _timed(lambda: compute(wick.WICK_MIXED), steps, min(warmup, 1), comp)
     ms = sharding.max_over_ranks(ms, device="cuda")
     cm = C[0].clone()
 
@@ -846,8 +892,10 @@ def run_batched(args):
     t64 = _timed(one64, 1, 0, comp)
     rel = float(((cm - C[0]).abs() / C[0].abs()).max().item())
     n_corr = n_cfg * len(nuclei) * n_src
-    if rank == 0:
-        print(json.dumps({"workload": "batched", "metric": "correlators/s (C(t) vectors over all T)",
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return {"workload": "batched", "metric": "correlators/s (C(t) vectors over all T)",
                           "value": n_corr / (ms / 1e3), "unit": "correlators/s", "higher_is_better": True,
                           "ms_per_step": ms, "ms_per_config": ms / n_cfg * world, "n_gpus": world,
                           "scaling": "weak" if world > 1 else None,
@@ -856,7 +904,13 @@ def run_batched(args):
                           "streamed": {"ms_per_step": streamed, "generation_ms_per_config": gen_ms,
                                        "note": "device generation (FP64 Box-Muller) overlapped with compute"},
                           "fp64_plain_one_config_ms": t64, "rel_err_mixed_vs_fp64_max_per_t": rel,
-                          "gpu_launches_per_step": len(mine) * (2 + 2 * len(nuclei))}), flush=True)
+                          "gpu_launches_per_step": len(mine) * (2 + 2 * len(nuclei))}
+
+
+def run_batched(args):
+    rec = batched_record(args.steps, args.warmup)
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(rec), flush=True)
 
 
 if __name__ == "__main__":
