@@ -254,15 +254,46 @@ void wick_terms_free(wick_terms *terms);
  * Correlator from the reduced table, Eq. 2.6 / App. D in reduced form:
  *   C[src][t] = scale * sum_u w_u prod_k B[src][t][id_{u,k}]
  *   blocks     device complex128 [n_src][T][n_blk], from wick_build_blocks with
- *              the layout the table was reduced for (n_blk is checked)
+ *              the layout the table was reduced for (n_blk = wick_terms_block_count)
  *   precision  WICK_FP64: FP64 products and sums.  WICK_MIXED: block entries
  *              split into float pairs, products in double-FP32 on the float
  *              pipes, FP64 sum over terms.
  *   C_out      device complex128 [n_src][T], caller-owned, overwritten.
- * Deterministic (fixed reduction order).  Errors: WICK_EINVAL, WICK_ECUDA.
+ * One persistent kernel launch: CTAs take (slice, chunk of terms) work items
+ * from a device counter; each slice's blocks are staged in shared memory; the
+ * chunk sums are added in chunk order by the last chunk of a slice to finish.
+ * Deterministic (fixed reduction order, whatever CTA takes which item).
+ * Uses a library-cached device workspace (allocated and zeroed on first use
+ * and when it grows: make the first call, with the largest shape, before any
+ * stream capture); calls that overlap on the GPU share it and must be ordered.
+ * Errors: WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA.
  */
 int wick_contract(const void *blocks, int n_src, int T, const wick_terms *terms, int precision,
                   void *C_out, wick_stream_t stream);
+
+/*
+ * Launch tuning, process-wide: read by every later call when it plans its
+ * launches (wick_build_blocks, wick_contract, wick_batch_create); a batch keeps
+ * the tuning it was created with.  0 in a field means the default.  The
+ * package's autotuner (paper_2411_08962_gb300.autotune) times candidates on a
+ * workload and records its choice as JSON.
+ *   range_sites            tensor-core block build: sites per CTA and per FP64 partial,
+ *                          a multiple of 128 up to 4096 (default 512)
+ *   contract_threads       contraction CTA size, a multiple of 32 up to 512 (default 256)
+ *   contract_ctas_per_sm   resident contraction CTAs per SM (default: as many as fit)
+ *   contract_chunk_terms   terms per contraction work item, about (64 or more; default 4096);
+ *                          the chunking depends on a table's size and this value only, so a
+ *                          batch reproduces the single calls of its configurations bit for bit
+ * NULL restores the defaults.  Errors: WICK_EINVAL (a field out of range).
+ */
+typedef struct wick_tuning {
+    int range_sites;
+    int contract_threads;
+    int contract_ctas_per_sm;
+    int contract_chunk_terms;
+} wick_tuning;
+int wick_set_tuning(const wick_tuning *tuning);
+int wick_get_tuning(wick_tuning *tuning);
 
 /*
  * wick_contract without any device allocation.  The paper has no counterpart:
@@ -274,13 +305,15 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *terms,
  * on first use; this variant calls no cudaMalloc, cudaFree or allocating
  * library routine.
  *
- * Same arguments, result and errors as wick_contract.  Its scratch (the FP64
- * partial sums, one complex128 per (term chunk, slice)) is a fixed array of
- * 65,536 complex128 values (1 MiB) that every GPU loading the library holds
- * until the process exits.  A call takes at most 65,536 slices (n_src * T);
- * larger requests fail with WICK_ESCRATCH before anything is enqueued.  When
- * the usual chunking would not fit, fewer term chunks are used (the sum order
- * then differs from wick_contract's within rounding).
+ * Same arguments, result and errors as wick_contract.  Its scratch (the work
+ * counters and the FP64 partial sums, one complex128 per work item) is a fixed
+ * array of 1,310,976 bytes (65,536 counters and 65,536 partials) that every GPU
+ * loading the library holds until the process exits.  A call takes at most
+ * 65,536 slices (n_src * T); larger requests fail with WICK_ESCRATCH before
+ * anything is enqueued.  When the usual chunking would need more than 65,536
+ * work items, longer term chunks are used (the sum order then differs from
+ * wick_contract's within rounding).  Each call clears the counters it starts
+ * from (cudaMemsetAsync on `stream`, no allocation) before its launch.
  *   - Every call looks up the array's device address for the current device
  *     (cudaGetSymbolAddress).  Under lazy module loading the first call on a
  *     device may make the driver load the library's device code, which

@@ -25,6 +25,8 @@ struct wick_terms {
     std::vector<int64_t> w, rep;
     uint16_t *d_ids = nullptr;  // device copies (on the device current at creation)
     int64_t *d_w = nullptr, *d_rep = nullptr;
+    uint16_t *d_ids_pad = nullptr;  // the contraction's copies: ids padded to 4 or 8, weights as doubles
+    double *d_wd = nullptr;
     int device = 0;
 };
 
@@ -35,8 +37,9 @@ namespace wick {
 // ---------------------------------------------------------------------------
 namespace {
 struct DevState {
-    void *ws[3] = {nullptr, nullptr, nullptr};   // block partials, contraction partials, determinant scratch
-    size_t ws_bytes[3] = {0, 0, 0};
+    // block partials (FP64 / CUDA-core paths), contraction scratch, determinant scratch, tensor-core block scratch
+    void *ws[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t ws_bytes[4] = {0, 0, 0, 0};
     int *status = nullptr;
 };
 std::mutex g_mu;
@@ -57,6 +60,14 @@ void *workspace(int slot, size_t bytes, int *err) {
         if (cudaMalloc(&d.ws[slot], want) != cudaSuccess) {
             (void)cudaGetLastError();
             *err = WICK_ENOMEM;
+            return nullptr;
+        }
+        // zero once: the kernels' work counters start at zero and reset themselves after every launch
+        if (cudaMemset(d.ws[slot], 0, want) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaFree(d.ws[slot]);
+            d.ws[slot] = nullptr;
+            *err = WICK_ECUDA;
             return nullptr;
         }
         d.ws_bytes[slot] = want;
@@ -96,15 +107,31 @@ int status_read_clear(cudaStream_t stream) {
 // ---------------------------------------------------------------------------
 // layouts and plans
 // ---------------------------------------------------------------------------
-int terms_view(const wick_terms *t, int *A, int64_t *U, int *n_blk, const uint16_t **ids, const int64_t **w,
-               double *scale) {
+int terms_table(const wick_terms *t, ContractTable *tab, int *n_blk) {
     if (!t) return WICK_EINVAL;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != t->device) return WICK_EINVAL;  // the device copies live on another GPU
-    *A = t->A; *U = t->U; *n_blk = t->n_blk; *ids = t->d_ids; *w = t->d_w; *scale = t->scale;
+    if (t->U > 0 && (!t->d_ids_pad || !t->d_wd)) return WICK_EINVAL;
+    *tab = {t->d_ids_pad, t->d_wd, t->U, t->A, t->scale};
+    *n_blk = t->n_blk;
     return WICK_OK;
 }
+
+// ---------------------------------------------------------------------------
+// process-wide tuning (set by wick_set_tuning, read when a call plans its launches)
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+wick_tuning g_tuning = {0, 0, 0, 0};
+}  // namespace
+
+wick_tuning current_tuning() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tuning;
+}
+
+ContractTune contract_tune(const wick_tuning &t) { return {t.contract_threads, t.contract_ctas_per_sm, t.contract_chunk_terms}; }
 
 static bool layout_ok(const wick_block_layout *l) {
     if (!l || l->n_ops < 1 || l->n_ops > kMaxOps || l->n_spin < 1 || l->n_spin > kMaxSpin || l->n_chi < 1 ||
@@ -219,6 +246,27 @@ static int prop_ok(const wick_prop *p) {
 
 using namespace wick;
 
+// the contraction's copies of a table (padded ids, FP64 weights), from its device ids and weights
+static int make_contract_copies(wick_terms *t) {
+    cudaFree(t->d_ids_pad);
+    cudaFree(t->d_wd);
+    t->d_ids_pad = nullptr;
+    t->d_wd = nullptr;
+    const size_t U = (size_t)(t->U ? t->U : 1);
+    const int AP = t->A <= 4 ? 4 : 8;
+    if (cudaMalloc(&t->d_ids_pad, sizeof(uint16_t) * U * AP) != cudaSuccess ||
+        cudaMalloc(&t->d_wd, sizeof(double) * U) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return WICK_ENOMEM;
+    }
+    for (int64_t u = 0; u < t->U; ++u)
+        if (t->w[(size_t)u] >= (1ll << 53) || t->w[(size_t)u] <= -(1ll << 53)) return WICK_EOVERFLOW;
+    int err = pad_table(t->d_ids, t->d_w, t->U, t->A, t->d_ids_pad, t->d_wd, nullptr);
+    if (err) return err;
+    WICK_CUDA_TRY(cudaDeviceSynchronize());
+    return WICK_OK;
+}
+
 extern "C" {
 
 size_t wick_block_count(const wick_block_layout *layout) {
@@ -309,13 +357,13 @@ int wick_build_blocks(const wick_prop *Su, const wick_prop *Sd, const wick_nucle
     const int64_t V = (int64_t)Su->L * Su->L * Su->L;
     const int64_t n_slices = (int64_t)Su->n_src * Su->T;
     if (V > (1 << 24) || n_slices > 65535) return WICK_EINVAL;
-    int n_splits = 0, chunk = 0;
-    const size_t bytes = block_partials_bytes(plan, (int)V, (int)n_slices, precision, &n_splits, &chunk);
-    if (n_splits > 65535) return WICK_EINVAL;
-    void *ws = workspace(0, bytes, &err);
+    const int rs = current_tuning().range_sites;
+    const size_t bytes = block_scratch_bytes(plan, (int)V, (int)n_slices, precision, rs);
+    // the tensor-core path keeps its counters in its scratch: a slot of its own, never written by the others
+    void *ws = workspace(precision == WICK_MIXED && tc_applicable(plan) ? 3 : 0, bytes, &err);
     if (err) return err;
-    return launch_block_build(plan, Su->data, Su->dtype, Sd->data, Sd->dtype, (int)V, (int)n_slices, precision,
-                              (double *)ws, n_splits, chunk, (double2 *)blocks, (cudaStream_t)stream);
+    return launch_block_build(plan, Su->data, Su->dtype, Sd->data, Sd->dtype, (int)V, (int)n_slices, precision, rs,
+                              ws, bytes, (double2 *)blocks, (cudaStream_t)stream);
 }
 
 int wick_reduce_terms(const wick_nucleus *nuc, const wick_nucleon_op *ops, const wick_block_layout *layout,
@@ -463,6 +511,11 @@ int wick_reduce_terms(const wick_nucleus *nuc, const wick_nucleon_op *ops, const
         wick_terms_free(t);
         return WICK_ECUDA;
     }
+    err = make_contract_copies(t);
+    if (err) {
+        wick_terms_free(t);
+        return err;
+    }
     *out = t;
     return WICK_OK;
 }
@@ -502,7 +555,7 @@ static int upload_terms(wick_terms *t) {
          cudaMemcpy(t->d_rep, t->rep.data(), sizeof(int64_t) * t->U, cudaMemcpyHostToDevice) != cudaSuccess))
         return WICK_ECUDA;
     cudaGetDevice(&t->device);
-    return WICK_OK;
+    return make_contract_copies(t);
 }
 
 int wick_terms_select(wick_terms *t, const int64_t *perm, int64_t n) {
@@ -610,41 +663,75 @@ void wick_terms_free(wick_terms *t) {
     cudaFree(t->d_ids);
     cudaFree(t->d_w);
     cudaFree(t->d_rep);
+    cudaFree(t->d_ids_pad);
+    cudaFree(t->d_wd);
     delete t;
+}
+
+static int contract_args(const void *blocks, int n_src, int T, const wick_terms *t, int precision, void *C_out,
+                         ContractTable *tab, int *n_blk) {
+    if (!blocks || !t || !C_out || n_src < 1 || T < 1) return WICK_EINVAL;
+    if (precision != WICK_FP64 && precision != WICK_MIXED) return WICK_EINVAL;
+    if ((uintptr_t)blocks % 16 || (uintptr_t)C_out % 16) return WICK_EINVAL;
+    if ((int64_t)n_src * T > 2147483647) return WICK_EINVAL;
+    return terms_table(t, tab, n_blk);
 }
 
 int wick_contract(const void *blocks, int n_src, int T, const wick_terms *t, int precision, void *C_out,
                   wick_stream_t stream) {
-    if (!blocks || !t || !C_out || n_src < 1 || T < 1) return WICK_EINVAL;
-    if (precision != WICK_FP64 && precision != WICK_MIXED) return WICK_EINVAL;
-    if ((uintptr_t)blocks % 16 || (uintptr_t)C_out % 16) return WICK_EINVAL;
-    const int64_t n_slices = (int64_t)n_src * T;
-    if (n_slices > 2147483647) return WICK_EINVAL;   // slices run on grid.x
-    int n_chunks = 1;
-    const size_t bytes = contract_partials_bytes((int)n_slices, t->U, t->A, t->n_blk, &n_chunks);
-    int err = WICK_OK;
-    void *ws = workspace(1, bytes, &err);
+    ContractTable tab;
+    int n_blk = 0;
+    int err = contract_args(blocks, n_src, T, t, precision, C_out, &tab, &n_blk);
     if (err) return err;
-    return launch_contract((const double2 *)blocks, (int)n_slices, t->n_blk, t->A, t->U, t->d_ids, t->d_w, t->scale,
-                           precision, (double2 *)C_out, (double *)ws, n_chunks, (cudaStream_t)stream);
+    const int n_slices = n_src * T;
+    ContractPlan plan;
+    err = contract_plan(n_blk, 1, n_slices, &tab, 1, precision, contract_tune(current_tuning()), INT64_MAX, &plan);
+    if (err) return err;
+    void *ws = workspace(1, plan.bytes, &err);
+    if (err) return err;
+    return launch_contract((const double2 *)blocks, n_blk, 1, n_slices, &tab, 1, precision, plan, ws,
+                           (double2 *)C_out, (cudaStream_t)stream);
 }
 
 int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms *t, int precision, void *C_out,
                           wick_stream_t stream) {
-    if (!blocks || !t || !C_out || n_src < 1 || T < 1) return WICK_EINVAL;
-    if (precision != WICK_FP64 && precision != WICK_MIXED) return WICK_EINVAL;
-    if ((uintptr_t)blocks % 16 || (uintptr_t)C_out % 16) return WICK_EINVAL;
-    const int64_t n_slices = (int64_t)n_src * T;
-    double2 *scratch = nullptr;
-    size_t cap = 0;
-    int err = noalloc_partials(&scratch, &cap);
+    ContractTable tab;
+    int n_blk = 0;
+    int err = contract_args(blocks, n_src, T, t, precision, C_out, &tab, &n_blk);
     if (err) return err;
-    if ((size_t)n_slices > cap) return WICK_ESCRATCH;
-    int n_chunks = 1;
-    contract_partials_bytes((int)n_slices, t->U, t->A, t->n_blk, &n_chunks);
-    if ((size_t)n_chunks * (size_t)n_slices > cap) n_chunks = (int)(cap / (size_t)n_slices);
-    return launch_contract((const double2 *)blocks, (int)n_slices, t->n_blk, t->A, t->U, t->d_ids, t->d_w, t->scale,
-                           precision, (double2 *)C_out, (double *)scratch, n_chunks, (cudaStream_t)stream);
+    const int64_t n_slices = (int64_t)n_src * T;
+    if (n_slices > kNoAllocItems) return WICK_ESCRATCH;
+    void *scratch = nullptr;
+    size_t cap = 0;
+    err = noalloc_scratch(&scratch, &cap);
+    if (err) return err;
+    ContractPlan plan;
+    err = contract_plan(n_blk, 1, (int)n_slices, &tab, 1, precision, contract_tune(current_tuning()), kNoAllocItems,
+                        &plan);
+    if (err) return err;
+    if (plan.bytes > cap || plan.counters > (size_t)kNoAllocItems) return WICK_ESCRATCH;
+    // the array keeps the last call's contents: clear the counters this launch starts from
+    WICK_CUDA_TRY(cudaMemsetAsync(scratch, 0, contract_counter_bytes(plan), (cudaStream_t)stream));
+    return launch_contract((const double2 *)blocks, n_blk, 1, (int)n_slices, &tab, 1, precision, plan, scratch,
+                           (double2 *)C_out, (cudaStream_t)stream);
+}
+
+int wick_set_tuning(const wick_tuning *t) {
+    wick_tuning v = {0, 0, 0, 0};
+    if (t) v = *t;
+    if (v.range_sites < 0 || v.range_sites % 128 || v.range_sites > 4096) return WICK_EINVAL;
+    if (v.contract_threads < 0 || v.contract_threads % 32 || v.contract_threads > 512) return WICK_EINVAL;
+    if (v.contract_ctas_per_sm < 0 || v.contract_ctas_per_sm > 32) return WICK_EINVAL;
+    if (v.contract_chunk_terms < 0 || (v.contract_chunk_terms > 0 && v.contract_chunk_terms < 64)) return WICK_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuning = v;
+    return WICK_OK;
+}
+
+int wick_get_tuning(wick_tuning *t) {
+    if (!t) return WICK_EINVAL;
+    *t = current_tuning();
+    return WICK_OK;
 }
 
 int wick_status(wick_stream_t stream) { return status_read_clear((cudaStream_t)stream); }

@@ -1,13 +1,19 @@
-// Batched executor: many configurations x many nuclei in one CUDA graph.
+// Batched executor: many configurations x many nuclei in one CUDA graph of
+// few launches.
 //
 // wick_batch_create records, for fixed device buffers, the block build of
-// every configuration (Eq. 2.4/2.5) followed by the contraction of every
-// reduced table against those blocks (Eq. 2.6 / App. D), captured on a
-// private stream and instantiated once.  Nuclei built from the same nucleon
-// operators share one block build per configuration.  The batch owns its
-// scratch (block partials, contraction partials), so the graph never depends
-// on the library's shared workspace.  wick_batch_run launches the graph on a
-// stream: one host call per batch, every kernel in stream order on the device.
+// every configuration (Eq. 2.4/2.5) and the contraction of every reduced table
+// against those blocks (Eq. 2.6 / App. D), captured on a private stream and
+// instantiated once.  Nuclei built from the same nucleon operators share one
+// block build per configuration.  With the tensor-core block build
+// (WICK_MIXED) one launch covers up to 64 configurations (more launches only
+// for larger batches or when their partial sums would pass kGroupBytes); one
+// persistent launch then evaluates every (configuration, table, slice, chunk
+// of terms) work item.  He-4-sized batches of up to 64 configurations are
+// therefore two kernel launches.  The batch owns its scratch, zeroed at
+// creation (the kernels' counters reset themselves after every launch), so
+// the graph never depends on the library's shared workspace.  wick_batch_run
+// launches the graph on a stream: one host call per batch.
 #include <vector>
 
 #include "common.cuh"
@@ -15,14 +21,13 @@
 struct wick_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    void *block_partials = nullptr;
-    void *contract_partials = nullptr;
+    void *block_scratch = nullptr;
+    void *contract_scratch = nullptr;
     int n_launches = 0;
 };
 
-namespace wick {
-int terms_view(const wick_terms *t, int *A, int64_t *U, int *n_blk, const uint16_t **ids, const int64_t **w,
-               double *scale);
+namespace {
+constexpr size_t kGroupBytes = size_t(4) << 30;   // partial sums of one block-build launch, at most
 }
 
 extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n_cfg, const wick_nucleon_op *ops,
@@ -31,7 +36,8 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
     using namespace wick;
     if (!out) return WICK_EINVAL;
     *out = nullptr;
-    if (!Su || !Sd || n_cfg < 1 || !tables || n_tables < 1 || !blocks || !C_out) return WICK_EINVAL;
+    if (!Su || !Sd || n_cfg < 1 || !tables || n_tables < 1 || n_tables > kMaxTables || !blocks || !C_out)
+        return WICK_EINVAL;
     if (precision != WICK_FP64 && precision != WICK_MIXED) return WICK_EINVAL;
     if ((uintptr_t)blocks % 16 || (uintptr_t)C_out % 16) return WICK_EINVAL;
     BlockPlan plan;
@@ -47,38 +53,49 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
     }
     const int64_t V = (int64_t)L * L * L, n_slices = (int64_t)n_src * T;
     if (V > (1 << 24) || n_slices > 65535 || L < 1 || T < 1 || n_src < 1) return WICK_EINVAL;
-    struct TV { int A, n_blk; int64_t U; const uint16_t *ids; const int64_t *w; double scale; };
-    std::vector<TV> tv(n_tables);
+    std::vector<ContractTable> tabs(n_tables);
     for (int k = 0; k < n_tables; ++k) {
+        int n_blk = 0;
         if (!tables[k]) return WICK_EINVAL;
-        err = terms_view(tables[k], &tv[k].A, &tv[k].U, &tv[k].n_blk, &tv[k].ids, &tv[k].w, &tv[k].scale);
+        err = terms_table(tables[k], &tabs[k], &n_blk);
         if (err) return err;
-        if (tv[k].n_blk != plan.n_out) return WICK_EINVAL;  // reduced for another layout
+        if (n_blk != plan.n_out) return WICK_EINVAL;  // reduced for another layout
     }
-    int n_splits = 0, chunk = 0;
-    const size_t pbytes = block_partials_bytes(plan, (int)V, (int)n_slices, precision, &n_splits, &chunk);
-    size_t cbytes = 16;
-    std::vector<int> n_chunks(n_tables);
-    for (int k = 0; k < n_tables; ++k) {
-        const size_t b = contract_partials_bytes((int)n_slices, tv[k].U, tv[k].A, tv[k].n_blk, &n_chunks[k]);
-        cbytes = b > cbytes ? b : cbytes;
+    const wick_tuning tune = current_tuning();
+    const int rs = tune.range_sites;
+    const bool tc = precision == WICK_MIXED && tc_applicable(plan);
+    int group = 1;
+    size_t bbytes = block_scratch_bytes(plan, (int)V, (int)n_slices, precision, rs);
+    if (tc) {
+        const size_t per_cfg = tc_scratch_bytes(plan, (int)V, (int)n_slices, 1, rs);
+        group = (int)std::max<size_t>(1, std::min<size_t>(kGroupBytes / per_cfg, (size_t)tc_max_configs()));
+        group = std::min(group, n_cfg);
+        while ((int64_t)group * n_slices > 65535) --group;
+        bbytes = tc_scratch_bytes(plan, (int)V, (int)n_slices, group, rs);
     }
+    ContractPlan cplan;
+    err = contract_plan(plan.n_out, n_cfg, (int)n_slices, tabs.data(), n_tables, precision, contract_tune(tune),
+                        INT64_MAX, &cplan);
+    if (err) return err;
     wick_batch *bt = new (std::nothrow) wick_batch();
     if (!bt) return WICK_ENOMEM;
     auto fail = [&](int e) {
         if (bt->exec) cudaGraphExecDestroy(bt->exec);
         if (bt->graph) cudaGraphDestroy(bt->graph);
-        cudaFree(bt->block_partials);
-        cudaFree(bt->contract_partials);
+        cudaFree(bt->block_scratch);
+        cudaFree(bt->contract_scratch);
         delete bt;
         (void)cudaGetLastError();
         return e;
     };
-    if (cudaMalloc(&bt->block_partials, pbytes) != cudaSuccess ||
-        cudaMalloc(&bt->contract_partials, cbytes) != cudaSuccess)
+    if (cudaMalloc(&bt->block_scratch, bbytes) != cudaSuccess ||
+        cudaMalloc(&bt->contract_scratch, cplan.bytes) != cudaSuccess)
         return fail(WICK_ENOMEM);
+    if (cudaMemset(bt->block_scratch, 0, bbytes) != cudaSuccess ||
+        cudaMemset(bt->contract_scratch, 0, cplan.bytes) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return fail(WICK_ECUDA);
     int serr = WICK_OK;
-    (void)status_word(&serr);  // the device status word exists before capture (kernels report timeouts there)
+    int *status = status_word(&serr);  // the device status word exists before capture (kernels report timeouts there)
     if (serr) return fail(serr);
     cudaStream_t cap;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return fail(WICK_ECUDA);
@@ -88,17 +105,31 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
     }
     const size_t blk_stride = (size_t)n_slices * plan.n_out;
     int launch_err = WICK_OK;
-    for (int c = 0; c < n_cfg && !launch_err; ++c) {
-        double2 *bc = (double2 *)blocks + (size_t)c * blk_stride;
-        launch_err = launch_block_build(plan, Su[c].data, dtype, Sd[c].data, dtype, (int)V, (int)n_slices, precision,
-                                        (double *)bt->block_partials, n_splits, chunk, bc, cap);
-        bt->n_launches += block_build_launches(plan, precision);
-        for (int k = 0; k < n_tables && !launch_err; ++k) {
-            double2 *co = (double2 *)C_out + ((size_t)c * n_tables + k) * n_slices;
-            launch_err = launch_contract(bc, (int)n_slices, tv[k].n_blk, tv[k].A, tv[k].U, tv[k].ids, tv[k].w,
-                                         tv[k].scale, precision, co, (double *)bt->contract_partials, n_chunks[k], cap);
-            bt->n_launches += 2;
+    if (tc) {
+        std::vector<const void *> su(n_cfg), sd(n_cfg);
+        for (int c = 0; c < n_cfg; ++c) {
+            su[c] = Su[c].data;
+            sd[c] = Sd[c].data;
         }
+        for (int c0 = 0; c0 < n_cfg && !launch_err; c0 += group) {
+            const int gn = std::min(group, n_cfg - c0);
+            launch_err = launch_block_tc(plan, su.data() + c0, sd.data() + c0, gn, dtype, (int)V, (int)n_slices, rs,
+                                         bt->block_scratch, bbytes, (double2 *)blocks + (size_t)c0 * blk_stride,
+                                         status, cap);
+            bt->n_launches += 1;
+        }
+    } else {
+        for (int c = 0; c < n_cfg && !launch_err; ++c) {
+            launch_err = launch_block_build(plan, Su[c].data, dtype, Sd[c].data, dtype, (int)V, (int)n_slices,
+                                            precision, rs, bt->block_scratch, bbytes,
+                                            (double2 *)blocks + (size_t)c * blk_stride, cap);
+            bt->n_launches += block_build_launches(plan, precision);
+        }
+    }
+    if (!launch_err) {
+        launch_err = launch_contract((const double2 *)blocks, plan.n_out, n_cfg, (int)n_slices, tabs.data(), n_tables,
+                                     precision, cplan, bt->contract_scratch, (double2 *)C_out, cap);
+        bt->n_launches += 1;
     }
     const cudaError_t ec = cudaStreamEndCapture(cap, &bt->graph);
     cudaStreamDestroy(cap);
@@ -121,7 +152,7 @@ extern "C" void wick_batch_free(wick_batch *b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    cudaFree(b->block_partials);
-    cudaFree(b->contract_partials);
+    cudaFree(b->block_scratch);
+    cudaFree(b->contract_scratch);
     delete b;
 }

@@ -294,28 +294,30 @@ int launch_typed(const BlockPlan &plan, const void *Su, const void *Sd, int V, i
 
 }  // namespace
 
-size_t block_partials_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int *n_splits, int *chunk) {
-    if (precision == WICK_MIXED && tc_applicable(plan)) return tc_partials_bytes(plan, V, n_slices, n_splits, chunk);
-    *chunk = kChunk;
-    *n_splits = (V + kChunk - 1) / kChunk;
-    return sizeof(double2) * (size_t)(*n_splits) * n_slices * plan.n_out;
+size_t block_scratch_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int range_sites) {
+    if (precision == WICK_MIXED && tc_applicable(plan)) return tc_scratch_bytes(plan, V, n_slices, 1, range_sites);
+    const int n_splits = (V + kChunk - 1) / kChunk;
+    return sizeof(double2) * (size_t)n_splits * n_slices * plan.n_out;
 }
 
 int block_build_launches(const BlockPlan &plan, int precision) {
-    return precision == WICK_MIXED && tc_applicable(plan) ? 3 : 2;
+    return precision == WICK_MIXED && tc_applicable(plan) ? 1 : 2;
 }
 
 int launch_block_build(const BlockPlan &plan, const void *Su, int dtype_u, const void *Sd, int dtype_d, int V,
-                       int n_slices, int precision, double *partials, int n_splits, int chunk, double2 *blocks,
-                       cudaStream_t stream) {
+                       int n_slices, int precision, int range_sites, void *scratch, size_t scratch_bytes,
+                       double2 *blocks, cudaStream_t stream) {
     if (dtype_u != dtype_d) return WICK_EINVAL;
-    double2 *part = reinterpret_cast<double2 *>(partials);
+    if (scratch_bytes < block_scratch_bytes(plan, V, n_slices, precision, range_sites)) return WICK_EINVAL;
     if (precision == WICK_MIXED && tc_applicable(plan)) {
         int err = WICK_OK;
         int *status = status_word(&err);
         if (err) return err;
-        return launch_block_tc(plan, Su, Sd, dtype_u, V, n_slices, partials, n_splits, blocks, status, stream);
+        return launch_block_tc(plan, &Su, &Sd, 1, dtype_u, V, n_slices, range_sites, scratch, scratch_bytes, blocks,
+                               status, stream);
     }
+    double2 *part = static_cast<double2 *>(scratch);
+    const int chunk = kChunk, n_splits = (V + kChunk - 1) / kChunk;
     if (precision == WICK_MIXED || precision == WICK_MIXED_SIMT) {
         if (plan.pow2_w) {
             if (dtype_u == WICK_C64)

@@ -40,6 +40,15 @@
 // chunk is a list of jobs -- two X values (a site pair) of one column, or two
 // U values of one row -- ordered so that every warp does one kind and one
 // colour term.  Every wait on an mbarrier is bounded.
+//
+// One launch covers up to kMaxCfg configurations (grid.z = configuration x
+// slice).  A CTA first scans its range of sites for the grid exponents (the
+// largest |re|, |im| and |re| + |im| per flavour and source column), builds
+// its FP64 partial sums, and arrives on a counter of its (configuration,
+// slice, block type); the last CTA to arrive -- no CTA waits for another --
+// adds the partials of every range in range order and writes the blocks,
+// antisymmetrised in the like-flavour pair, B = P(c1,c2,c3) - P(c2,c1,c3),
+// then clears the counter for the next launch.
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -57,7 +66,8 @@ constexpr int kSlicesX = 6;                        // slices of X
 constexpr int kMaxPair = 5;                        // kept slice pairs: i + j <= kMaxPair
 constexpr int kKa = 3;                             // colour-term slots per site
 constexpr int kRoundSites = 128;                   // sites per exact TMEM accumulation
-constexpr int kRangeSites = 512;                   // sites per CTA (one grid, one partial)
+constexpr int kRangeSitesDefault = 512;            // sites per CTA (one grid, one partial) unless tuned
+constexpr int kMaxCfg = 64;                        // configurations per launch
 constexpr int kSpinLimit = 1 << 22;                // mbarrier polls before giving up
 constexpr int kStage = 3;                          // staging buffers
 constexpr int kMaxRows = 24;                       // staged S rows (both flavours)
@@ -66,6 +76,12 @@ constexpr int kListLen = 4;                        // terms per diquark list the
 // exponent bound of the largest colour-list weight sum, per block type
 struct WeightExp {
     int e[kMaxOps];
+};
+
+// the propagators of the configurations of one launch
+struct CfgPtrs {
+    const void *su[kMaxCfg];
+    const void *sd[kMaxCfg];
 };
 
 // Compile-time shape of a table family: NC colours chi, NS spins, NT columns
@@ -178,47 +194,6 @@ __device__ __forceinline__ bool poll_parity(uint64_t *mbar, int parity) {
             : "r"(smem_u32(mbar)), "r"(parity)
             : "memory");
     return done != 0;
-}
-
-// Grids of one (slice, range of kRangeSites sites): for flavour f and colour
-// column ic over the rows the tables use, E = bound of max(|re|, |im|) and
-// G = bound of max(|re| + |im|).  bounds[(slice * n_ranges + range) * 48 + f * 24 + kind * 12 + ic].
-template <typename ST>
-__global__ void __launch_bounds__(256)
-tc_bounds_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ Su, const ST *__restrict__ Sd,
-                 int V, int n_ranges, int *__restrict__ bounds) {
-    __shared__ unsigned smax[48];  // [f][kind][ic]
-    const int tid = threadIdx.x;
-    if (tid < 48) smax[tid] = 0u;
-    __syncthreads();
-    const int rng = blockIdx.x, slice = blockIdx.y;
-    const int nc = plan.n_chi, nr0 = plan.n_rows[0], nr = nr0 + plan.n_rows[1];
-    const int cols = nr * nc;
-    const int parts = max(1, (int)blockDim.x / cols);
-    const int x_begin = rng * kRangeSites, x_end = min(V, x_begin + kRangeSites);
-    for (int e = tid; e < cols * parts; e += blockDim.x) {
-        const int col = e % cols, part = e / cols;
-        const int rc = col / nc, ic = col % nc;
-        const int f = rc < nr0 ? 0 : 1;
-        const int row = f == 0 ? plan.rows[0][rc] : plan.rows[1][rc - nr0];
-        const ST *src = (f == 0 ? Su : Sd) + (size_t)slice * V * 144 + row * 12 + plan.chi[ic];
-        float m1 = 0.f, m2 = 0.f;
-#pragma unroll 8
-        for (int x = x_begin + part; x < x_end; x += parts) {
-            const float2 v = to_f2(src[(size_t)x * 144]);
-            const float ax = fabsf(v.x), ay = fabsf(v.y);
-            m1 = fmaxf(m1, fmaxf(ax, ay));
-            m2 = fmaxf(m2, __fadd_ru(ax, ay));  // rounded up: still a bound of |re| + |im|
-        }
-        atomicMax(&smax[f * 24 + ic], __float_as_uint(m1));
-        atomicMax(&smax[f * 24 + 12 + ic], __float_as_uint(m2));
-    }
-    __syncthreads();
-    if (tid < 48) {
-        const int ic = tid % 12;
-        int *out = bounds + ((size_t)slice * n_ranges + rng) * 48;
-        out[tid] = ic < nc ? exponent_bound(__uint_as_float(smax[tid])) : -100;
-    }
 }
 
 // Packed slicing: lanes (re, im) of a complex value at once on the f32x2
@@ -413,17 +388,96 @@ __device__ __forceinline__ void u_job(const Job &j, const float *S, __nv_bfloat1
     }
 }
 
+// The grid exponents of one range of sites (this CTA's): for flavour f and source column ic over the
+// rows the tables use, E = bound of max(|re|, |im|) and G = bound of max(|re| + |im|); out[f * 24 +
+// kind * 12 + ic].  Every thread of the CTA takes part; ends with the CTA's barrier.
+template <typename ST>
+__device__ __forceinline__ void range_bounds(const BlockPlan &plan, const ST *su, const ST *sd, int x_begin,
+                                             int x_end, unsigned *smax, int *out) {
+    const int tid = threadIdx.x;
+    if (tid < 48) smax[tid] = 0u;
+    __syncthreads();
+    const int nc = plan.n_chi, nr0 = plan.n_rows[0], nr = nr0 + plan.n_rows[1];
+    const int cols = nr * nc;
+    const int parts = max(1, (int)blockDim.x / cols);
+    if (tid < cols * parts) {
+        const int col = tid % cols, part = tid / cols;
+        const int rc = col / nc, ic = col % nc;
+        const int f = rc < nr0 ? 0 : 1;
+        const int row = f == 0 ? plan.rows[0][rc] : plan.rows[1][rc - nr0];
+        const ST *src = (f == 0 ? su : sd) + row * 12 + plan.chi[ic];
+        float m1 = 0.f, m2 = 0.f;
+#pragma unroll 8
+        for (int x = x_begin + part; x < x_end; x += parts) {
+            const float2 v = to_f2(src[(size_t)x * 144]);
+            const float ax = fabsf(v.x), ay = fabsf(v.y);
+            m1 = fmaxf(m1, fmaxf(ax, ay));
+            m2 = fmaxf(m2, __fadd_ru(ax, ay));  // rounded up: still a bound of |re| + |im|
+        }
+        atomicMax(&smax[f * 24 + ic], __float_as_uint(m1));
+        atomicMax(&smax[f * 24 + 12 + ic], __float_as_uint(m2));
+    }
+    __syncthreads();
+    if (tid < 48) {
+        const int ic = tid % 12;
+        out[tid] = ic < nc ? exponent_bound(__uint_as_float(smax[tid])) : -100;
+    }
+    __syncthreads();
+}
+
+// The CTA's partials of (configuration x slice cs, block type o) are written; count it in.  The last
+// of the n_ranges x NCT CTAs of (cs, o) sums the partials of every range in range order and writes
+// B = P(c1,c2,c3) - P(c2,c1,c3) for the type's entries, then clears the counter.
+template <typename SH>
+__device__ __forceinline__ void arrive_and_reduce(const BlockPlan &plan, int cs, int o, int n_ranges,
+                                                  const double2 *partials, int *counters, double2 *blocks,
+                                                  int *s_last) {
+    constexpr int NC = SH::NC, NS = SH::NS, NC2 = NC * NC, NC3 = NC2 * NC;
+    const int tid = threadIdx.x;
+    int *cnt = counters + (size_t)cs * plan.n_ops + o;
+    __syncthreads();   // every partial of this CTA is written
+    if (tid == 0) {
+        __threadfence();
+        *s_last = atomicAdd(cnt, 1) == n_ranges * SH::NCT - 1;
+    }
+    __syncthreads();
+    if (!*s_last) return;
+    __threadfence();
+    const size_t n_out = (size_t)plan.n_out;
+    const double2 *P = partials + (size_t)cs * n_ranges * n_out;
+    double2 *Bo = blocks + (size_t)cs * n_out;
+    for (int e = tid; e < NS * NC3; e += blockDim.x) {
+        const int out = o * NS * NC3 + e;
+        const int os = out / NC3, i1 = (out / NC2) % NC, i2 = (out / NC) % NC, i3 = out % NC;
+        const int sw = os * NC3 + i2 * NC2 + i1 * NC + i3;
+        double ax = 0, ay = 0, bx = 0, by = 0;
+        for (int r = 0; r < n_ranges; ++r) {
+            const double2 a = __ldcg(P + (size_t)r * n_out + out);
+            const double2 b = __ldcg(P + (size_t)r * n_out + sw);
+            ax += a.x; ay += a.y; bx += b.x; by += b.y;
+        }
+        Bo[out] = make_double2(ax - bx, ay - by);
+    }
+    if (tid == 0) *cnt = 0;
+}
+
 template <typename ST, typename SH>
 __global__ void __launch_bounds__(kThr, 1)
-block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ Su, const ST *__restrict__ Sd,
-                int V, int n_slices, int n_ranges, const int *__restrict__ bounds, const WeightExp ew,
-                double2 *__restrict__ partials, int *status) {
+block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ CfgPtrs cfgp, int V, int n_slices,
+                int n_ranges, int range_sites, const WeightExp ew, double2 *__restrict__ partials,
+                int *__restrict__ counters, double2 *__restrict__ blocks, int *status) {
     constexpr int NC = SH::NC, NS = SH::NS, NT = SH::NT, R = SH::R, NCTA = SH::NCTA;
     extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ unsigned s_max[48];
+    __shared__ int s_bnd[48];
+    __shared__ int s_last;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // the CTAs of one (slice, range) are adjacent in the grid: they read the same rows of S (L2 reuse)
     const int o = blockIdx.x / SH::NCT, ct = blockIdx.x % SH::NCT;
-    const int rng = blockIdx.y, slice = blockIdx.z;
+    const int rng = blockIdx.y, cs = blockIdx.z;             // cs = configuration * n_slices + slice
+    const int cfg = cs / n_slices, slice = cs - cfg * n_slices;
+    const ST *Su = static_cast<const ST *>(cfgp.su[cfg]);
+    const ST *Sd = static_cast<const ST *>(cfgp.sd[cfg]);
     const int nr0 = plan.n_rows[0], nr = nr0 + plan.n_rows[1];
     const int f1 = plan.f1[o];
     const int col0 = ct * NT;
@@ -449,7 +503,12 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
         uint4 *z = reinterpret_cast<uint4 *>(smem);
         for (int e = tid; e < 2 * (SH::A_BYTES + SH::B_BYTES) / 16; e += kThr) z[e] = make_uint4(0u, 0u, 0u, 0u);
     }
-    const int *bnd = bounds + ((size_t)slice * n_ranges + rng) * 48;
+    const int x_begin = rng * range_sites, x_end = min(V, x_begin + range_sites);
+    const int n_chunks = (x_end - x_begin + NX - 1) / NX;
+    const ST *su = Su + (size_t)slice * V * 144;
+    const ST *sd = Sd + (size_t)slice * V * 144;
+    range_bounds<ST>(plan, su, sd, x_begin, x_end, s_max, s_bnd);
+    const int *bnd = s_bnd;
     if (tid < NC) sEU[tid] = bnd[f1 * 24 + tid];
     if (tid < NT) {
         const int c23 = col0 + tid;
@@ -489,10 +548,6 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
 
-    const int x_begin = rng * kRangeSites, x_end = min(V, x_begin + kRangeSites);
-    const int n_chunks = (x_end - x_begin + NX - 1) / NX;
-    const ST *su = Su + (size_t)slice * V * 144;
-    const ST *sd = Sd + (size_t)slice * V * 144;
     __syncthreads();   // sSrc
     // stage the rows of chunk c as two planes (re, im) of [row][ic][site], flavour-0 rows first, sites
     // innermost (zeros past the range).  The last STAGERS threads (the warps with the lightest jobs)
@@ -656,7 +711,8 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
     }
 
     if (bad) {
-        // a wait ran out; the MMAs may still run: wait (bounded) for their commits before TMEM is freed
+        // a wait ran out; the MMAs may still run: wait (bounded) for their commits before TMEM is freed.
+        // The CTA still arrives below, so that the counts stay whole; the status word reports the error.
         if (tid == 0) atomicCAS(status, 0, WICK_ETIMEOUT);
         if (waited0 < issued0) (void)poll_parity(&mbar[0], waited0 & 1);
         if (waited1 < issued1) (void)poll_parity(&mbar[1], waited1 & 1);
@@ -665,6 +721,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
         __syncthreads();
         if (warp == 0)
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SH::TMEM_COLS));
+        arrive_and_reduce<SH>(plan, cs, o, n_ranges, partials, counters, blocks, &s_last);
         return;
     }
     cp_async_wait_all();
@@ -675,7 +732,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
 #pragma unroll
         for (int n = 0; n < SH::CW; ++n) comb[row * NT + cpart * SH::CW + n] = make_float2(acc[n].h, acc[n].l);
     __syncthreads();
-    double *part = reinterpret_cast<double *>(partials + ((size_t)rng * n_slices + slice) * plan.n_out);
+    double *part = reinterpret_cast<double *>(partials + ((size_t)cs * n_ranges + rng) * plan.n_out);
     for (int e = tid; e < R * NCTA; e += kThr) {
         const int rr = e / NCTA, n = e % NCTA;
         df s = {0.f, 0.f};
@@ -694,24 +751,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ S
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SH::TMEM_COLS));
-}
-
-// B = P(c1,c2,c3) - P(c2,c1,c3), summed over the site ranges in a fixed order
-__global__ void tc_reduce_kernel(const double2 *__restrict__ partials, int n_splits, int n_slices, int n_out, int nc,
-                                 double2 *__restrict__ blocks) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)n_slices * n_out) return;
-    const int slice = (int)(i / n_out), out = (int)(i % n_out);
-    const int nc2 = nc * nc, nc3 = nc2 * nc;
-    const int os = out / nc3, i1 = (out / nc2) % nc, i2 = (out / nc) % nc, i3 = out % nc;
-    const int sw = os * nc3 + i2 * nc2 + i1 * nc + i3;
-    double ax = 0, ay = 0, bx = 0, by = 0;
-    for (int s = 0; s < n_splits; ++s) {
-        const double2 a = partials[((size_t)s * n_slices + slice) * n_out + out];
-        const double2 b = partials[((size_t)s * n_slices + slice) * n_out + sw];
-        ax += a.x; ay += a.y; bx += b.x; by += b.y;
-    }
-    blocks[i] = make_double2(ax - bx, ay - by);
+    arrive_and_reduce<SH>(plan, cs, o, n_ranges, partials, counters, blocks, &s_last);
 }
 
 // Which compiled shape a plan takes (0: none, 1: upper, 2: full): weights
@@ -741,37 +781,56 @@ int tc_family(const BlockPlan &plan) {
 }
 
 template <typename SH, typename ST>
-int launch_shape(const BlockPlan &plan, const ST *Su, const ST *Sd, int V, int n_slices, int n_ranges,
-                 const int *bounds, const WeightExp &ew, double2 *part, int *status, cudaStream_t stream) {
+int launch_shape(const BlockPlan &plan, const CfgPtrs &cp, int n_cfg, int V, int n_slices, int n_ranges,
+                 int range_sites, const WeightExp &ew, double2 *part, int *counters, double2 *blocks, int *status,
+                 cudaStream_t stream) {
     auto k = block_tc_kernel<ST, SH>;
     WICK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM));
-    dim3 grid(plan.n_ops * SH::NCT, n_ranges, n_slices);
-    k<<<grid, kThr, SH::SMEM, stream>>>(plan, Su, Sd, V, n_slices, n_ranges, bounds, ew, part, status);
+    dim3 grid(plan.n_ops * SH::NCT, n_ranges, n_cfg * n_slices);
+    k<<<grid, kThr, SH::SMEM, stream>>>(plan, cp, V, n_slices, n_ranges, range_sites, ew, part, counters, blocks,
+                                        status);
+    WICK_CUDA_TRY(cudaGetLastError());
     return WICK_OK;
 }
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace
 
 bool tc_applicable(const BlockPlan &plan) { return tc_family(plan) != 0; }
 
-size_t tc_partials_bytes(const BlockPlan &plan, int V, int n_slices, int *n_splits, int *chunk) {
-    const int n_ranges = (V + kRangeSites - 1) / kRangeSites;
-    *n_splits = n_ranges;
-    *chunk = kRangeSites;
-    const size_t part = sizeof(double2) * (size_t)n_ranges * n_slices * plan.n_out;
-    const size_t bnd = sizeof(int) * (size_t)n_ranges * n_slices * 48;
-    return (part + 255) / 256 * 256 + bnd;
+int tc_range_sites(int requested) {
+    return requested >= kRoundSites && requested % kRoundSites == 0 && requested <= 4096 ? requested
+                                                                                          : kRangeSitesDefault;
 }
 
-int launch_block_tc(const BlockPlan &plan, const void *Su, const void *Sd, int dtype, int V, int n_slices,
-                    double *partials, int n_splits, double2 *blocks, int *status, cudaStream_t stream) {
+int tc_max_configs() { return kMaxCfg; }
+
+size_t tc_scratch_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites) {
+    const int rs = tc_range_sites(range_sites);
+    const size_t n_ranges = (size_t)(V + rs - 1) / rs;
+    const size_t counters = align256(sizeof(int) * (size_t)n_cfg * n_slices * plan.n_ops);
+    return counters + sizeof(double2) * n_ranges * n_cfg * n_slices * plan.n_out;
+}
+
+int launch_block_tc(const BlockPlan &plan, const void *const *Su, const void *const *Sd, int n_cfg, int dtype, int V,
+                    int n_slices, int range_sites, void *scratch, size_t scratch_bytes, double2 *blocks, int *status,
+                    cudaStream_t stream) {
     const int fam = tc_family(plan);
-    if (!fam || n_splits != (V + kRangeSites - 1) / kRangeSites || n_splits > 65535 || n_slices > 65535)
+    const int rs = tc_range_sites(range_sites);
+    const int n_ranges = (V + rs - 1) / rs;
+    if (!fam || n_cfg < 1 || n_cfg > kMaxCfg || n_ranges > 65535 || (int64_t)n_cfg * n_slices > 65535)
         return WICK_EINVAL;
-    const int n_ranges = n_splits;
-    double2 *part = reinterpret_cast<double2 *>(partials);
-    const size_t pbytes = (sizeof(double2) * (size_t)n_ranges * n_slices * plan.n_out + 255) / 256 * 256;
-    int *bounds = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(partials) + pbytes);
+    if (!scratch || (uintptr_t)scratch % 256 || scratch_bytes < tc_scratch_bytes(plan, V, n_slices, n_cfg, rs))
+        return WICK_EINVAL;
+    CfgPtrs cp{};
+    for (int c = 0; c < n_cfg; ++c) {
+        cp.su[c] = Su[c];
+        cp.sd[c] = Sd[c];
+    }
+    int *counters = static_cast<int *>(scratch);
+    double2 *part = reinterpret_cast<double2 *>(static_cast<unsigned char *>(scratch) +
+                                                align256(sizeof(int) * (size_t)n_cfg * n_slices * plan.n_ops));
     WeightExp ew = {};
     for (int o = 0; o < plan.n_ops; ++o) {
         const int b0 = plan.os_off[o * plan.n_spin];
@@ -785,26 +844,15 @@ int launch_block_tc(const BlockPlan &plan, const void *Su, const void *Sd, int d
         }
         ew.e[o] = exponent_bound(wmax);
     }
-    dim3 gb(n_ranges, n_slices);
-    int err;
-    if (dtype == WICK_C64) {
-        const float2 *u = (const float2 *)Su, *d = (const float2 *)Sd;
-        tc_bounds_kernel<float2><<<gb, 256, 0, stream>>>(plan, u, d, V, n_ranges, bounds);
-        err = fam == 1 ? launch_shape<UpperShape>(plan, u, d, V, n_slices, n_ranges, bounds, ew, part, status, stream)
-                       : launch_shape<FullShape>(plan, u, d, V, n_slices, n_ranges, bounds, ew, part, status, stream);
-    } else {
-        const double2 *u = (const double2 *)Su, *d = (const double2 *)Sd;
-        tc_bounds_kernel<double2><<<gb, 256, 0, stream>>>(plan, u, d, V, n_ranges, bounds);
-        err = fam == 1 ? launch_shape<UpperShape>(plan, u, d, V, n_slices, n_ranges, bounds, ew, part, status, stream)
-                       : launch_shape<FullShape>(plan, u, d, V, n_slices, n_ranges, bounds, ew, part, status, stream);
-    }
-    if (err) return err;
-    WICK_CUDA_TRY(cudaGetLastError());
-    const size_t n = (size_t)n_slices * plan.n_out;
-    tc_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(part, n_splits, n_slices, plan.n_out,
-                                                                      plan.n_chi, blocks);
-    WICK_CUDA_TRY(cudaGetLastError());
-    return WICK_OK;
+    if (dtype == WICK_C64)
+        return fam == 1 ? launch_shape<UpperShape, float2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, part,
+                                                           counters, blocks, status, stream)
+                        : launch_shape<FullShape, float2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, part,
+                                                          counters, blocks, status, stream);
+    return fam == 1 ? launch_shape<UpperShape, double2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, part, counters,
+                                                        blocks, status, stream)
+                    : launch_shape<FullShape, double2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, part, counters,
+                                                       blocks, status, stream);
 }
 
 }  // namespace wick

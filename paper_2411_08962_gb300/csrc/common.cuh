@@ -48,12 +48,12 @@ struct BlockPlan {
 
 int build_block_plan(const wick_nucleon_op *ops, const wick_block_layout *layout, BlockPlan *plan);
 
-// launchers (blocks.cu)
+// launchers (blocks.cu): the block build of one configuration; scratch of block_scratch_bytes
+// (zero before its first use: the tensor-core path keeps its counters there)
 int launch_block_build(const BlockPlan &plan, const void *Su, int dtype_u, const void *Sd, int dtype_d,
-                       int V, int n_slices, int precision, double *partials, int n_splits, int chunk,
+                       int V, int n_slices, int precision, int range_sites, void *scratch, size_t scratch_bytes,
                        double2 *blocks, cudaStream_t stream);
-size_t block_partials_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int *n_splits,
-                            int *chunk);
+size_t block_scratch_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int range_sites);
 // tensor-core update stage (blocks_tc.cu): upper-spin plans, double-FP32-exact
 // the 16-byte words of one site that wick_upload_rows gathers: flavour << 15 | word in the site
 constexpr int kMaxUploadWords = 2 * 12 * 12;   // both flavours, all rows, complex128
@@ -65,9 +65,15 @@ int launch_upload_rows(const UploadMap &map, const void *hu, const void *hd, con
                        size_t n_sites, int words_u, int words_d, cudaStream_t stream);
 bool tc_applicable(const BlockPlan &plan);
 int block_build_launches(const BlockPlan &plan, int precision);  // kernels one launch_block_build issues
-size_t tc_partials_bytes(const BlockPlan &plan, int V, int n_slices, int *n_splits, int *chunk);
-int launch_block_tc(const BlockPlan &plan, const void *Su, const void *Sd, int dtype, int V, int n_slices,
-                    double *partials, int n_splits, double2 *blocks, int *status, cudaStream_t stream);
+// tensor-core block build (blocks_tc.cu): one launch for up to tc_max_configs() configurations; its
+// scratch holds one counter per (configuration, slice, block type) -- zero before the first launch,
+// cleared again by every launch -- and the FP64 partials of every site range
+int tc_range_sites(int requested);               // the range size a request (0 = default) resolves to
+int tc_max_configs();
+size_t tc_scratch_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites);
+int launch_block_tc(const BlockPlan &plan, const void *const *Su, const void *const *Sd, int n_cfg, int dtype, int V,
+                    int n_slices, int range_sites, void *scratch, size_t scratch_bytes, double2 *blocks, int *status,
+                    cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Term reduction (dedup.cu)
@@ -97,20 +103,53 @@ int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc,
                cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
-// Contraction (contract.cu)
+// Contraction (contract.cu): one persistent launch over (configuration,
+// slice, table, chunk of terms) work items
 // ---------------------------------------------------------------------------
-int launch_contract(const double2 *blocks, int n_slices, int n_blk, int A, int64_t U, const uint16_t *ids,
-                    const int64_t *w, double scale, int precision, double2 *C_out, double *partials,
-                    int n_chunks, cudaStream_t stream);
-size_t contract_partials_bytes(int n_slices, int64_t U, int A, int n_blk, int *n_chunks);
-// fixed scratch of wick_contract_noalloc (complex128 partials, per device)
-constexpr size_t kNoAllocPartials = 65536;
-int noalloc_partials(double2 **ptr, size_t *capacity);
+constexpr int kMaxTables = 8;
+struct ContractTable {         // a reduced table as the contraction reads it
+    const uint16_t *ids;       // [U][AP] block ids padded to AP = 4 (A <= 4) or 8
+    const double *w;           // [U] weights as doubles (exact: |w| < 2^53)
+    int64_t U;
+    int A;
+    double scale;
+};
+struct ContractTune {          // 0 = default
+    int threads;               // per CTA: 32..512, multiple of 32 (default 256)
+    int ctas_per_sm;           // resident CTAs per SM (default: as many as fit)
+    int chunk_terms;           // terms per work item, about (default 4096)
+};
+struct ContractPlan {
+    int threads, grid, stage;
+    size_t smem;
+    int n_chunks[kMaxTables], item_off[kMaxTables];
+    int64_t chunk[kMaxTables];
+    int items_per_cs;
+    int64_t n_items;
+    size_t counters;           // (configuration, table, slice) counters
+    size_t bytes;              // scratch: item counter, counters, partials
+};
+int contract_plan(int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab, int precision,
+                  const ContractTune &tune, int64_t max_items, ContractPlan *plan);
+// scratch bytes that must be zero before the first launch (item counter and counters)
+size_t contract_counter_bytes(const ContractPlan &plan);
+int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab,
+                    int precision, const ContractPlan &plan, void *scratch, double2 *C_out, cudaStream_t stream);
+int pad_table(const uint16_t *ids, const int64_t *w, int64_t U, int A, uint16_t *ids_pad, double *wd,
+              cudaStream_t stream);
+// fixed scratch of wick_contract_noalloc (per device): item counter, 65,536 counters, 65,536 partials
+constexpr int64_t kNoAllocItems = 65536;
+constexpr size_t kNoAllocBytes = 256 + sizeof(int) * kNoAllocItems + 16 * kNoAllocItems;
+int noalloc_scratch(void **ptr, size_t *bytes);
 
 // ---------------------------------------------------------------------------
-// library workspace (api.cu)
+// library workspace, tables and tuning (api.cu)
 // ---------------------------------------------------------------------------
-// per-device cached scratch; slot 0 = block partials, slot 1 = contraction partials
+int terms_table(const wick_terms *t, ContractTable *tab, int *n_blk);
+wick_tuning current_tuning();
+ContractTune contract_tune(const wick_tuning &t);
+// per-device cached scratch, zeroed when (re)allocated; slot 0 = block partials of the FP64 and CUDA-core
+// paths, 1 = contraction scratch, 2 = determinant scratch, 3 = tensor-core block scratch
 void *workspace(int slot, size_t bytes, int *err);
 int *status_word(int *err);                     // per-device status word
 int status_read_clear(cudaStream_t stream);

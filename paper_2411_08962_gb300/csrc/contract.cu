@@ -1,16 +1,29 @@
 // Correlator from the reduced term table (Eq. 2.6 generalised in App. D):
-//   C[slice] = scale * sum_u w_u prod_k B[slice][id_{u,k}]
+//   C[cfg][table][slice] = scale * sum_u w_u prod_k B[cfg][slice][id_{u,k}]
 //
-// grid = (slice, term chunk).  A CTA stages its slice's blocks in shared
-// memory when they fit (complex128 for FP64, complex64 for MIXED), then each
-// thread walks the chunk's terms with stride blockDim (coalesced reads of the
-// uint16 ids and int64 weights), multiplies the A gathered block entries and
-// accumulates in FP64.  MIXED keeps every block entry as a double-FP32 pair
-// and forms the products with error-free float operations (about 44 bits),
-// so the float pipes do the products and only the term sum is FP64.  The CTA reduces in a fixed tree; a second kernel sums
-// the chunk partials in chunk order.  Both orders are fixed: the result is
-// bitwise reproducible.
-#include <type_traits>
+// One persistent launch evaluates any number of configurations and reduced
+// tables (nuclei) that share a block layout.  The work is cut into items
+// (configuration, slice, table, chunk of terms), ordered so that the items of
+// one (configuration, slice) are adjacent; the CTAs (a fixed number per SM)
+// take items from a device counter in that order.  For an item a CTA stages
+// the slice's blocks in shared memory -- once per slice, kept while the next
+// item is on the same slice -- (complex128 for FP64, a double-FP32 pair per
+// value for MIXED), then every thread walks the chunk's terms with stride
+// blockDim: one 8- or 16-byte load of the padded block ids (4 or 8 uint16),
+// the A gathered block entries multiplied, the product accumulated in FP64
+// with the weight.  The CTA sums its threads with warp shuffles and a fixed
+// order over warps, and writes the item's partial.  The last item of a
+// (configuration, table, slice) to finish -- an atomic count, no waiting --
+// adds the chunk partials in chunk order and writes C.  Every sum has a fixed
+// order, so the result is bitwise reproducible whichever CTA takes which item.
+// Counters reset themselves: the last item of a slice clears its count and the
+// last CTA to leave clears the item counter, so the scratch is ready for the
+// next launch without a memset.
+//
+// MIXED keeps every block entry as a double-FP32 pair and forms the products
+// with error-free float operations (about 44 bits), so the float pipes do the
+// products and only the term sum is FP64.
+#include <algorithm>
 
 #include "common.cuh"
 #include "df32.cuh"
@@ -19,8 +32,9 @@ namespace wick {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kMinTermsPerChunk = 2048;
+constexpr int kMaxThreads = 512;
+constexpr int64_t kDefaultChunkTerms = 4096;   // terms per work item unless tuned
+constexpr size_t kSmemStageLimit = 96 * 1024;   // stage a slice's blocks in shared memory up to this size
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -47,152 +61,309 @@ struct Elem<false> {
     static __device__ __forceinline__ double im(const T &a) { return a.y; }
 };
 
-template <int A, bool MIXED, bool SMEM>
-__global__ void __launch_bounds__(kThreads)
-contract_kernel(const double2 *__restrict__ blocks, int n_blk, int64_t U, const uint16_t *__restrict__ ids,
-                const int64_t *__restrict__ w, int64_t chunk, int n_slices, double2 *__restrict__ partials) {
+struct TableWork {
+    const uint16_t *ids;   // [U][AP]
+    const double *w;       // [U]
+    int64_t U;
+    int64_t chunk;         // terms per item
+    int A, n_chunks;       // chunks per (configuration, slice)
+    int item_off;          // first item of this table within a (configuration, slice)
+    double scale;
+};
+
+struct ContractWork {
+    TableWork tab[kMaxTables];
+    int n_tab;
+    const double2 *blocks;     // [n_cfg][n_slices][n_blk]
+    int n_blk, n_cfg, n_slices;
+    int items_per_cs;          // items of one (configuration, slice)
+    int64_t n_items;
+    double2 *C_out;            // [n_cfg][n_tab][n_slices]
+    double2 *partials;         // [n_items]
+    int *counters;             // [n_cfg][n_tab][n_slices]
+    unsigned long long *queue; // [0] next item, [1] CTAs that have left
+};
+
+template <typename C, bool MIXED, bool STAGE>
+__device__ __forceinline__ C load_block(const C *sB, const double2 *gB, int id) {
+    if constexpr (STAGE) return sB[id];
+    else return Elem<MIXED>::from(__ldcg(gB + id));
+}
+
+// this thread's share of terms [u0, u1) of one table, against one slice's blocks
+template <int A, bool MIXED, bool STAGE>
+__device__ __forceinline__ void eval_terms(const TableWork &tw, int64_t u0, int64_t u1,
+                                           const typename Elem<MIXED>::T *sB, const double2 *gB, double &ax,
+                                           double &ay) {
+    using E = Elem<MIXED>;
+    using C = typename E::T;
+    constexpr int AP = A <= 4 ? 4 : 8;
+    for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+        uint16_t id[AP];
+        if constexpr (AP == 4) {
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(tw.ids) + u);
+            id[0] = (uint16_t)(v.x & 0xFFFF); id[1] = (uint16_t)(v.x >> 16);
+            id[2] = (uint16_t)(v.y & 0xFFFF); id[3] = (uint16_t)(v.y >> 16);
+        } else {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(tw.ids) + u);
+            const unsigned wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                id[2 * q] = (uint16_t)(wd[q] & 0xFFFF);
+                id[2 * q + 1] = (uint16_t)(wd[q] >> 16);
+            }
+        }
+        C p = load_block<C, MIXED, STAGE>(sB, gB, id[0]);
+#pragma unroll
+        for (int k = 1; k < A; ++k) p = E::mul(p, load_block<C, MIXED, STAGE>(sB, gB, id[k]));
+        const double wu = __ldg(tw.w + u);
+        ax = fma(wu, E::re(p), ax);
+        ay = fma(wu, E::im(p), ay);
+    }
+}
+
+template <bool MIXED, bool STAGE>
+__device__ __forceinline__ void eval_any(const TableWork &tw, int64_t u0, int64_t u1,
+                                         const typename Elem<MIXED>::T *sB, const double2 *gB, double &ax,
+                                         double &ay) {
+    switch (tw.A) {
+        case 1: eval_terms<1, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
+        case 2: eval_terms<2, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
+        case 3: eval_terms<3, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
+        case 4: eval_terms<4, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
+        case 5: eval_terms<5, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
+        case 6: eval_terms<6, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
+        case 7: eval_terms<7, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
+        default: eval_terms<8, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
+    }
+}
+
+// fixed-order sum over the CTA: a shuffle tree per warp, then warp 0 over the warps' sums
+__device__ __forceinline__ double2 cta_sum(double ax, double ay, double2 *s_red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        ax += __shfl_down_sync(0xffffffffu, ax, off);
+        ay += __shfl_down_sync(0xffffffffu, ay, off);
+    }
+    if (lane == 0) s_red[warp] = make_double2(ax, ay);
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    if (warp == 0) {
+        double bx = lane < nw ? s_red[lane].x : 0.0, by = lane < nw ? s_red[lane].y : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            bx += __shfl_down_sync(0xffffffffu, bx, off);
+            by += __shfl_down_sync(0xffffffffu, by, off);
+        }
+        r = make_double2(bx, by);
+    }
+    return r;   // valid in thread 0
+}
+
+template <bool MIXED, bool STAGE>
+__global__ void __launch_bounds__(kMaxThreads)
+contract_persistent_kernel(const __grid_constant__ ContractWork wk) {
     using E = Elem<MIXED>;
     using C = typename E::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sB = reinterpret_cast<C *>(smem_raw);
-    const int slice = blockIdx.x;
-    const double2 *gB = blocks + (size_t)slice * n_blk;
-    if constexpr (SMEM) {
-        for (int i = threadIdx.x; i < n_blk; i += kThreads) sB[i] = E::from(gB[i]);
+    __shared__ long long s_item;
+    __shared__ int s_last;
+    __shared__ double2 s_red[kMaxThreads / 32];
+    long long staged = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(wk.queue, 1ull);
         __syncthreads();
-    }
-    const int64_t u0 = (int64_t)blockIdx.y * chunk;
-    const int64_t u1 = min(U, u0 + chunk);
-    double ax = 0.0, ay = 0.0;
-    for (int64_t u = u0 + threadIdx.x; u < u1; u += kThreads) {
-        const uint16_t *id = ids + u * A;
-        C p;
-        if constexpr (SMEM) p = sB[id[0]];
-        else p = E::from(__ldg(gB + id[0]));
-#pragma unroll
-        for (int k = 1; k < A; ++k) {
-            C b;
-            if constexpr (SMEM) b = sB[id[k]];
-            else b = E::from(__ldg(gB + id[k]));
-            p = E::mul(p, b);
+        const long long item = s_item;
+        if (item >= wk.n_items) break;
+        const long long cs = item / wk.items_per_cs;          // configuration * n_slices + slice
+        const int r = (int)(item - cs * wk.items_per_cs);
+        int tb = 0;
+        while (tb + 1 < wk.n_tab && r >= wk.tab[tb + 1].item_off) ++tb;
+        const TableWork &tw = wk.tab[tb];
+        const int chunk = r - tw.item_off;
+        const double2 *gB = wk.blocks + cs * wk.n_blk;
+        if constexpr (STAGE) {
+            if (cs != staged) {   // every thread is past the previous item's gathers (barrier above)
+                for (int i = threadIdx.x; i < wk.n_blk; i += blockDim.x) sB[i] = E::from(__ldcg(gB + i));
+                __syncthreads();
+                staged = cs;
+            }
         }
-        const double wu = (double)w[u];
-        ax = fma(wu, E::re(p), ax);
-        ay = fma(wu, E::im(p), ay);
-    }
-    __shared__ double rx[kThreads], ry[kThreads];
-    rx[threadIdx.x] = ax;
-    ry[threadIdx.x] = ay;
-    __syncthreads();
-    for (int off = kThreads / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < off) {
-            rx[threadIdx.x] += rx[threadIdx.x + off];
-            ry[threadIdx.x] += ry[threadIdx.x + off];
+        const int64_t u0 = (int64_t)chunk * tw.chunk;
+        const int64_t u1 = min(tw.U, u0 + tw.chunk);
+        double ax = 0.0, ay = 0.0;
+        eval_any<MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay);
+        const double2 tot = cta_sum(ax, ay, s_red);
+        const int cfg = (int)(cs / wk.n_slices), slice = (int)(cs - (long long)cfg * wk.n_slices);
+        int *cnt = wk.counters + ((size_t)cfg * wk.n_tab + tb) * wk.n_slices + slice;
+        if (threadIdx.x == 0) {
+            wk.partials[item] = tot;
+            __threadfence();
+            s_last = atomicAdd(cnt, 1) == tw.n_chunks - 1;
         }
         __syncthreads();
+        if (s_last && threadIdx.x == 0) {
+            // every chunk of this (configuration, table, slice) has written its partial: sum them in chunk order
+            __threadfence();
+            const double2 *p = wk.partials + (item - chunk);
+            double x = 0.0, y = 0.0;
+            for (int c = 0; c < tw.n_chunks; ++c) {
+                const double2 v = __ldcg(p + c);
+                x += v.x;
+                y += v.y;
+            }
+            wk.C_out[((size_t)cfg * wk.n_tab + tb) * wk.n_slices + slice] = make_double2(tw.scale * x, tw.scale * y);
+            *cnt = 0;
+        }
+        // the next iteration's first barrier orders the reuse of s_item and s_last
     }
-    if (threadIdx.x == 0) partials[(size_t)blockIdx.y * n_slices + slice] = make_double2(rx[0], ry[0]);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(wk.queue + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
+            wk.queue[0] = 0ull;   // every CTA has left: ready for the next launch
+            wk.queue[1] = 0ull;
+        }
+    }
 }
 
-__global__ void contract_finish_kernel(const double2 *__restrict__ partials, int n_chunks, int n_slices,
-                                       double scale, double2 *__restrict__ out) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_slices) return;
-    double x = 0, y = 0;
-    for (int c = 0; c < n_chunks; ++c) {
-        const double2 v = partials[(size_t)c * n_slices + s];
-        x += v.x;
-        y += v.y;
-    }
-    out[s] = make_double2(scale * x, scale * y);
-}
-
-template <int A, bool MIXED>
-int launch_a(const double2 *blocks, int n_slices, int n_blk, int64_t U, const uint16_t *ids, const int64_t *w,
-             int64_t chunk, int n_chunks, double2 *partials, cudaStream_t stream) {
-    const size_t smem = sizeof(typename Elem<MIXED>::T) * (size_t)n_blk;
-    dim3 grid(n_slices, n_chunks);
-    if (smem <= 200 * 1024) {
-        auto k = contract_kernel<A, MIXED, true>;
-        WICK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<grid, kThreads, smem, stream>>>(blocks, n_blk, U, ids, w, chunk, n_slices, partials);
-    } else {
-        contract_kernel<A, MIXED, false><<<grid, kThreads, 0, stream>>>(blocks, n_blk, U, ids, w, chunk, n_slices,
-                                                                        partials);
-    }
+template <bool MIXED, bool STAGE>
+int launch_typed(const ContractWork &wk, int grid, int threads, size_t smem, cudaStream_t stream) {
+    auto k = contract_persistent_kernel<MIXED, STAGE>;
+    if (smem > 48 * 1024) WICK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<grid, threads, smem, stream>>>(wk);
     WICK_CUDA_TRY(cudaGetLastError());
     return WICK_OK;
 }
 
-template <bool MIXED>
-int launch_p(int A, const double2 *blocks, int n_slices, int n_blk, int64_t U, const uint16_t *ids,
-             const int64_t *w, int64_t chunk, int n_chunks, double2 *partials, cudaStream_t stream) {
-    switch (A) {
-        case 1: return launch_a<1, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
-        case 2: return launch_a<2, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
-        case 3: return launch_a<3, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
-        case 4: return launch_a<4, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
-        case 5: return launch_a<5, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
-        case 6: return launch_a<6, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
-        case 7: return launch_a<7, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
-        case 8: return launch_a<8, MIXED>(blocks, n_slices, n_blk, U, ids, w, chunk, n_chunks, partials, stream);
-        default: return WICK_EINVAL;
+template <bool MIXED, bool STAGE>
+int max_ctas_per_sm(int threads, size_t smem) {
+    int n = 0;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(contract_persistent_kernel<MIXED, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 1;
     }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, contract_persistent_kernel<MIXED, STAGE>, threads, smem) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    return n < 1 ? 1 : n;
 }
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Fixed scratch of wick_contract_noalloc: the FP64 partial sums, one complex128
-// per (term chunk, slice), in a file-scope device array instead of the
-// library's cudaMalloc'd workspace.  Every device that loads the library holds
-// these kNoAllocPartials * 16 bytes (1 MiB) until the process exits.  Each call
-// writes every partial it later reads, so nothing has to start at zero.
+// Planning: term chunks, grid, scratch.  The chunking of a table depends on
+// its own size and the tuning only -- about chunk_terms terms per item, split
+// evenly -- so a batch and the single calls of its configurations add the
+// same partial sums in the same order (bitwise equal results).  A plan of
+// more than max_items items takes longer chunks.
 // ---------------------------------------------------------------------------
-static __device__ __align__(256) double2 g_noalloc_partials[kNoAllocPartials];
+int contract_plan(int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab, int precision,
+                  const ContractTune &tune, int64_t max_items, ContractPlan *plan) {
+    if (n_tab < 1 || n_tab > kMaxTables || n_cfg < 1 || n_slices < 1 || n_blk < 1) return WICK_EINVAL;
+    ContractPlan &P = *plan;
+    P = ContractPlan{};
+    const bool mixed = precision == WICK_MIXED;
+    P.threads = tune.threads > 0 ? tune.threads : 256;
+    if (P.threads % 32 || P.threads < 32 || P.threads > kMaxThreads) return WICK_EINVAL;
+    const size_t elem = 16;   // complex128 or a double-FP32 complex pair
+    P.stage = (size_t)n_blk * elem <= kSmemStageLimit;
+    P.smem = P.stage ? (size_t)n_blk * elem : 0;
+    int dev = 0, n_sm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int occ = mixed ? (P.stage ? max_ctas_per_sm<true, true>(P.threads, P.smem)
+                                     : max_ctas_per_sm<true, false>(P.threads, P.smem))
+                          : (P.stage ? max_ctas_per_sm<false, true>(P.threads, P.smem)
+                                     : max_ctas_per_sm<false, false>(P.threads, P.smem));
+    const int per_sm = tune.ctas_per_sm > 0 ? std::min(tune.ctas_per_sm, occ) : occ;
+    const int64_t n_cs = (int64_t)n_cfg * n_slices;
+    for (int k = 0; k < n_tab; ++k)
+        if (tabs[k].U < 0 || tabs[k].A < 1 || tabs[k].A > kMaxA) return WICK_EINVAL;
+    int64_t target = tune.chunk_terms > 0 ? tune.chunk_terms : kDefaultChunkTerms;
+    for (;;) {
+        int64_t ips = 0;
+        for (int k = 0; k < n_tab; ++k) ips += std::max<int64_t>(1, (tabs[k].U + target - 1) / target);
+        if (ips * n_cs <= max_items) break;
+        if (ips == n_tab) return WICK_ESCRATCH;   // one chunk per table and still too many items
+        target *= 2;
+    }
+    int off = 0;
+    for (int k = 0; k < n_tab; ++k) {
+        const int nc = (int)std::max<int64_t>(1, (tabs[k].U + target - 1) / target);
+        P.n_chunks[k] = nc;
+        P.chunk[k] = std::max<int64_t>(1, (tabs[k].U + nc - 1) / nc);
+        P.item_off[k] = off;
+        off += nc;
+    }
+    P.items_per_cs = off;
+    P.n_items = (int64_t)off * n_cs;
+    const int64_t most = (int64_t)n_sm * per_sm;
+    P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(most, P.n_items));
+    P.counters = (size_t)n_cfg * n_tab * n_slices;
+    P.bytes = 256 + align256(sizeof(int) * P.counters) + align256(sizeof(double2) * (size_t)P.n_items);
+    return WICK_OK;
+}
 
-int noalloc_partials(double2 **ptr, size_t *capacity) {
+size_t contract_counter_bytes(const ContractPlan &P) { return 256 + align256(sizeof(int) * P.counters); }
+
+int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab,
+                    int precision, const ContractPlan &P, void *scratch, double2 *C_out, cudaStream_t stream) {
+    if (!scratch || (uintptr_t)scratch % 256) return WICK_EINVAL;
+    ContractWork wk{};
+    wk.n_tab = n_tab;
+    for (int k = 0; k < n_tab; ++k) {
+        wk.tab[k] = {tabs[k].ids, tabs[k].w, tabs[k].U, P.chunk[k], tabs[k].A, P.n_chunks[k], P.item_off[k],
+                     tabs[k].scale};
+    }
+    wk.blocks = blocks;
+    wk.n_blk = n_blk;
+    wk.n_cfg = n_cfg;
+    wk.n_slices = n_slices;
+    wk.items_per_cs = P.items_per_cs;
+    wk.n_items = P.n_items;
+    wk.C_out = C_out;
+    unsigned char *base = static_cast<unsigned char *>(scratch);
+    wk.queue = reinterpret_cast<unsigned long long *>(base);
+    wk.counters = reinterpret_cast<int *>(base + 256);
+    wk.partials = reinterpret_cast<double2 *>(base + contract_counter_bytes(P));
+    const bool mixed = precision == WICK_MIXED;
+    if (mixed) return P.stage ? launch_typed<true, true>(wk, P.grid, P.threads, P.smem, stream)
+                              : launch_typed<true, false>(wk, P.grid, P.threads, P.smem, stream);
+    return P.stage ? launch_typed<false, true>(wk, P.grid, P.threads, P.smem, stream)
+                   : launch_typed<false, false>(wk, P.grid, P.threads, P.smem, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Fixed scratch of wick_contract_noalloc, in a file-scope device array instead
+// of the library's cudaMalloc'd workspace: the item counter, one counter per
+// slice and the FP64 partial sums (one complex128 per work item).  Every
+// device that loads the library holds these kNoAllocBytes until the process
+// exits.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+int noalloc_scratch(void **ptr, size_t *bytes) {
     // In host code the array's name is only a host-side stand-in; its device
     // address comes from the runtime for the device that is current now.  It
     // is looked up on every call (no allocation, a table lookup once the
     // module is loaded), so a context that was reset or replaced never sees a
     // stale address.
     void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
         (void)cudaGetLastError();
         return WICK_ECUDA;
     }
-    *ptr = static_cast<double2 *>(p);
-    *capacity = kNoAllocPartials;
-    return WICK_OK;
-}
-
-size_t contract_partials_bytes(int n_slices, int64_t U, int A, int n_blk, int *n_chunks) {
-    (void)A; (void)n_blk;
-    int dev = 0, n_sm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    // enough CTAs for two waves, but never chunks of fewer than kMinTermsPerChunk terms
-    int64_t want = (2 * (int64_t)n_sm + n_slices - 1) / n_slices;
-    const int64_t most = (U + kMinTermsPerChunk - 1) / kMinTermsPerChunk;
-    if (want > most) want = most;
-    if (want < 1) want = 1;
-    *n_chunks = (int)want;
-    return sizeof(double2) * (size_t)want * n_slices;
-}
-
-int launch_contract(const double2 *blocks, int n_slices, int n_blk, int A, int64_t U, const uint16_t *ids,
-                    const int64_t *w, double scale, int precision, double2 *C_out, double *partials_raw,
-                    int n_chunks, cudaStream_t stream) {
-    double2 *partials = reinterpret_cast<double2 *>(partials_raw);
-    const int64_t chunk = (U + n_chunks - 1) / n_chunks;
-    int e = precision == WICK_MIXED
-                ? launch_p<true>(A, blocks, n_slices, n_blk, U, ids, w, chunk > 0 ? chunk : 1, n_chunks, partials, stream)
-                : launch_p<false>(A, blocks, n_slices, n_blk, U, ids, w, chunk > 0 ? chunk : 1, n_chunks, partials, stream);
-    if (e) return e;
-    contract_finish_kernel<<<(n_slices + 127) / 128, 128, 0, stream>>>(partials, n_chunks, n_slices, scale, C_out);
-    WICK_CUDA_TRY(cudaGetLastError());
+    *ptr = p;
+    *bytes = kNoAllocBytes;
     return WICK_OK;
 }
 
@@ -202,7 +373,25 @@ __global__ void product_kernel(const double2 *__restrict__ a, const double2 *__r
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = cmul(a[i], b[i]);
 }
+
+// contraction copies of a reduced table: ids padded to [U][AP], weights as doubles (exact below 2^53)
+__global__ void pad_table_kernel(const uint16_t *__restrict__ ids, const int64_t *__restrict__ w, int64_t U, int A,
+                                 int AP, uint16_t *__restrict__ ids_pad, double *__restrict__ wd) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= U) return;
+    for (int k = 0; k < AP; ++k) ids_pad[u * AP + k] = k < A ? ids[u * A + k] : (uint16_t)0;
+    wd[u] = (double)w[u];
+}
 }  // namespace
+
+int pad_table(const uint16_t *ids, const int64_t *w, int64_t U, int A, uint16_t *ids_pad, double *wd,
+              cudaStream_t stream) {
+    if (U <= 0) return WICK_OK;
+    const int AP = A <= 4 ? 4 : 8;
+    pad_table_kernel<<<(unsigned)((U + 255) / 256), 256, 0, stream>>>(ids, w, U, A, AP, ids_pad, wd);
+    WICK_CUDA_TRY(cudaGetLastError());
+    return WICK_OK;
+}
 
 }  // namespace wick
 

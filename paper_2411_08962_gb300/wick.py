@@ -30,7 +30,8 @@ EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_upload_rows", "wick_re
            "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_contract_noalloc",
            "wick_status", "wick_batch_create", "wick_batch_run", "wick_batch_launches", "wick_batch_free",
            "wick_synth_propagator", "wick_cluster_product", "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats",
-           "wick_det_element_offsets", "wick_det_copy", "wick_det_contract", "wick_det_contract_3pt", "wick_det_free", "wick_strerror", "wick_version")
+           "wick_det_element_offsets", "wick_det_copy", "wick_det_contract", "wick_det_contract_3pt", "wick_det_free", "wick_set_tuning", "wick_get_tuning",
+           "wick_strerror", "wick_version")
 
 
 class WickError(RuntimeError):
@@ -57,6 +58,11 @@ class wick_nucleus(C.Structure):
                 ("sink_spin", C.POINTER(C.c_int8)), ("sink_w", C.POINTER(C.c_int64)), ("n_src", C.c_int),
                 ("src_chi", C.POINTER(C.c_int8)), ("src_w", C.POINTER(C.c_int64)),
                 ("src_flav", C.POINTER(C.c_int8)), ("scale", C.c_double)]
+
+
+class wick_tuning(C.Structure):
+    _fields_ = [("range_sites", C.c_int), ("contract_threads", C.c_int), ("contract_ctas_per_sm", C.c_int),
+                ("contract_chunk_terms", C.c_int)]
 
 
 class wick_quark_operator(C.Structure):
@@ -118,6 +124,8 @@ def load(path: str = LIB_PATH):
                                                 C.c_int, vp, vp]
             L.wick_det_free.argtypes = [vp]
             L.wick_det_free.restype = None
+            L.wick_set_tuning.argtypes = [P(wick_tuning)]
+            L.wick_get_tuning.argtypes = [P(wick_tuning)]
             L.wick_strerror.argtypes = [C.c_int]
             L.wick_strerror.restype = C.c_char_p
             L.wick_version.restype = C.c_char_p
@@ -126,7 +134,8 @@ def load(path: str = LIB_PATH):
                       "wick_contract", "wick_contract_noalloc", "wick_status", "wick_batch_create",
                       "wick_batch_run", "wick_batch_launches", "wick_synth_propagator", "wick_cluster_product",
                       "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats", "wick_det_element_offsets",
-                      "wick_det_copy", "wick_det_contract", "wick_det_contract_3pt"):
+                      "wick_det_copy", "wick_det_contract", "wick_det_contract_3pt", "wick_set_tuning",
+                      "wick_get_tuning"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -386,6 +395,21 @@ def wick_cluster_product(Ca, Cb, out, stream=None):
     po = _buf(out, "out", _C128, n, exact=True)
     _check(load().wick_cluster_product(pa, pb, n, po, _stream(stream)),
            "wick_cluster_product")
+
+
+TUNING_FIELDS = ("range_sites", "contract_threads", "contract_ctas_per_sm", "contract_chunk_terms")
+
+
+def wick_set_tuning(tuning=None):
+    """Process-wide launch tuning (a dict with any of TUNING_FIELDS, 0 = default; None = all defaults)."""
+    t = wick_tuning(*[int((tuning or {}).get(f, 0)) for f in TUNING_FIELDS])
+    _check(load().wick_set_tuning(C.byref(t)), "wick_set_tuning")
+
+
+def wick_get_tuning() -> dict:
+    t = wick_tuning()
+    _check(load().wick_get_tuning(C.byref(t)), "wick_get_tuning")
+    return {f: int(getattr(t, f)) for f in TUNING_FIELDS}
 
 
 def wick_status(stream=None) -> int:

@@ -160,3 +160,20 @@ def test_binding_rejects_bad_tensors_before_the_library(lib):
                                   torch.zeros(4, dtype=torch.complex128))
     with pytest.raises(ValueError):
         wick.wick_synth_propagator(1, 0, 0, L, T, torch.zeros(n_prop // n_src - 1, dtype=torch.complex64))
+
+
+def test_tuning_is_validated_and_kept(lib):
+    """wick_set_tuning checks every field and is read back by wick_get_tuning (host-only calls)."""
+    try:
+        wick.wick_set_tuning({"range_sites": 1024, "contract_threads": 128, "contract_chunk_terms": 2048})
+        assert wick.wick_get_tuning() == {"range_sites": 1024, "contract_threads": 128, "contract_ctas_per_sm": 0,
+                                          "contract_chunk_terms": 2048}
+        for bad in ({"range_sites": 100}, {"range_sites": 8192}, {"contract_threads": 100},
+                    {"contract_threads": 1024}, {"contract_ctas_per_sm": -1}, {"contract_chunk_terms": 10}):
+            with pytest.raises(wick.WickError) as e:
+                wick.wick_set_tuning(bad)
+            assert e.value.code == wick.WICK_EINVAL
+        assert wick.wick_get_tuning()["range_sites"] == 1024      # a refused tuning changes nothing
+    finally:
+        wick.wick_set_tuning(None)
+    assert wick.wick_get_tuning() == {f: 0 for f in wick.TUNING_FIELDS}

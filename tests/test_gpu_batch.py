@@ -4,7 +4,11 @@
   definition; CUDA's log/sincospi may move the last bits);
 * a captured batch (wick_batch_create / wick_batch_run) gives bit-for-bit the
   results of the individual calls, for several configurations and the three
-  nuclei sharing one block build per configuration;
+  nuclei sharing one block build per configuration, in two kernel launches
+  with the tensor-core block build (one for every configuration's blocks, one
+  persistent contraction over every configuration, nucleus, slice and chunk);
+* the autotuner's trials and choice, and bit-for-bit equal results of a batch
+  and its single calls under a non-default tuning;
 * the batched workload's lattice (L=32, T=64, two sources, complex64,
   device-generated) on sampled slices against the CPU reference.
 """
@@ -69,9 +73,10 @@ def test_batch_equals_individual_calls():
         blocks = torch.zeros((n_cfg, n_src, T, nb), dtype=torch.complex128, device="cuda")
         C = torch.zeros((n_cfg, len(NUCLEI), n_src, T), dtype=torch.complex128, device="cuda")
         batch = wick.Batch([c[0] for c in cfgs], [c[1] for c in cfgs], tabs, terms, prec, blocks, C, L, T, n_src)
-        # block build: grid bounds + tensor-core kernel + reduction (mixed) or partials + reduction (FP64)
-        n_block = 3 if prec == wick.WICK_MIXED else 2
-        assert batch.launches == n_cfg * (n_block + 2 * len(NUCLEI))
+        # mixed: one tensor-core block-build launch for all configurations; FP64: partials + reduction per
+        # configuration; then one persistent contraction launch
+        n_block = 1 if prec == wick.WICK_MIXED else 2 * n_cfg
+        assert batch.launches == n_block + 1
         batch.run()
         batch.run()                                       # a second launch reproduces the first
         torch.cuda.synchronize()
@@ -85,6 +90,43 @@ def test_batch_equals_individual_calls():
                 torch.cuda.synchronize()
                 assert torch.equal(c1, C[c, k])
         batch.free()
+
+
+def test_tuned_batch_equals_individual_calls_and_autotuner():
+    from paper_2411_08962_gb300 import autotune
+    L, T, n_src, n_cfg = 8, 4, 2, 2
+    tabs = wick.Tables(operators.nucleus("he4"))
+    terms = [wick.wick_reduce_terms(wick.Tables(operators.nucleus(n))) for n in NUCLEI]
+    cfgs = [device_props(2000 + c, L, T, n_src) for c in range(n_cfg)]
+    res = autotune.tune_batch([c[0] for c in cfgs], [c[1] for c in cfgs], tabs, terms, wick.WICK_MIXED, L, T, n_src,
+                              reps=1, warmup=1, space={"range_sites": (256,), "contract_chunk_terms": (64, 1024),
+                                                       "contract_threads": (128,)})
+    assert set(res["choice"]) == set(wick.TUNING_FIELDS)
+    assert len(res["trials"]) == 5 and all(t["accepted"] for t in res["trials"])
+    assert wick.wick_get_tuning() == {f: 0 for f in wick.TUNING_FIELDS}     # left as it was
+    tuning = {"range_sites": 256, "contract_threads": 128, "contract_ctas_per_sm": 2, "contract_chunk_terms": 64}
+    wick.wick_set_tuning(tuning)
+    try:
+        assert wick.wick_get_tuning() == tuning
+        nb = tabs.nuc.n_blk
+        blocks = torch.zeros((n_cfg, n_src, T, nb), dtype=torch.complex128, device="cuda")
+        C = torch.zeros((n_cfg, len(NUCLEI), n_src, T), dtype=torch.complex128, device="cuda")
+        batch = wick.Batch([c[0] for c in cfgs], [c[1] for c in cfgs], tabs, terms, wick.WICK_MIXED, blocks, C,
+                           L, T, n_src)
+        batch.run()
+        torch.cuda.synchronize()
+        for c, (Su, Sd) in enumerate(cfgs):
+            b1 = torch.empty((n_src, T, nb), dtype=torch.complex128, device="cuda")
+            wick.wick_build_blocks(Su, Sd, tabs, wick.WICK_MIXED, b1, L, T, n_src)
+            assert torch.equal(b1, blocks[c])
+            for k, t in enumerate(terms):
+                c1 = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
+                wick.wick_contract(b1, n_src, T, t, wick.WICK_MIXED, c1)
+                torch.cuda.synchronize()
+                assert torch.equal(c1, C[c, k])
+        batch.free()
+    finally:
+        wick.wick_set_tuning(None)
 
 
 def test_batched_workload_lattice_sampled():

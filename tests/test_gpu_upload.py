@@ -7,6 +7,8 @@ hold NaN must give the same blocks, bit for bit, as the fully copied
 propagator (tensor-core mixed, CUDA-core mixed and FP64 paths), and the byte
 count must be exactly those rows.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -68,8 +70,14 @@ def test_upload_rejects_pageable_and_mismatch():
     tabs = wick.Tables(nuc)
     h = torch.from_numpy(synth.propagator(1, 0, L, T, n_src, dtype=np.complex64))   # pageable
     d = h.cuda()
-    with pytest.raises(wick.WickError):
+    with pytest.raises(ValueError):            # the binding refuses it before the library sees it
         wick.wick_upload_rows(h, h, d, d, tabs, L, T, n_src)
+    # and so does the C ABI itself, called directly
+    hp_, dp_ = (wick.wick_prop(x.data_ptr(), L, T, n_src, wick.WICK_C64) for x in (h, d))
+    n = ctypes.c_size_t(0)
+    assert wick.load().wick_upload_rows(ctypes.byref(hp_), ctypes.byref(hp_), ctypes.byref(dp_), ctypes.byref(dp_),
+                                        tabs.ops, ctypes.byref(tabs.layout), wick.WICK_UPLOAD_DMA, ctypes.byref(n),
+                                        None) == wick.WICK_EINVAL
     hp = h.pin_memory()
     d128 = torch.zeros(h.shape, dtype=torch.complex128, device="cuda")
     with pytest.raises(wick.WickError):
