@@ -37,9 +37,8 @@ namespace wick {
 // ---------------------------------------------------------------------------
 namespace {
 struct DevState {
-    // block partials (FP64 / CUDA-core paths), contraction scratch, determinant scratch, tensor-core block scratch
-    void *ws[4] = {nullptr, nullptr, nullptr, nullptr};
-    size_t ws_bytes[4] = {0, 0, 0, 0};
+    void *ws[kWsSlots] = {};   // see common.cuh (kWs*)
+    size_t ws_bytes[kWsSlots] = {};
     int *status = nullptr;
 };
 std::mutex g_mu;
@@ -358,12 +357,14 @@ int wick_build_blocks(const wick_prop *Su, const wick_prop *Sd, const wick_nucle
     const int64_t n_slices = (int64_t)Su->n_src * Su->T;
     if (V > (1 << 24) || n_slices > 65535) return WICK_EINVAL;
     const int rs = current_tuning().range_sites;
-    const size_t bytes = block_scratch_bytes(plan, (int)V, (int)n_slices, precision, rs);
-    // the tensor-core path keeps its counters in its scratch: a slot of its own, never written by the others
-    void *ws = workspace(precision == WICK_MIXED && tc_applicable(plan) ? 3 : 0, bytes, &err);
+    const size_t pbytes = block_partial_bytes(plan, (int)V, (int)n_slices, precision, rs);
+    const size_t cbytes = block_counter_bytes(plan, (int)n_slices, precision);
+    void *part = workspace(kWsBlockPartials, pbytes, &err);
+    if (err) return err;
+    void *cnt = cbytes ? workspace(kWsBlockCounters, cbytes, &err) : nullptr;
     if (err) return err;
     return launch_block_build(plan, Su->data, Su->dtype, Sd->data, Sd->dtype, (int)V, (int)n_slices, precision, rs,
-                              ws, bytes, (double2 *)blocks, (cudaStream_t)stream);
+                              (int *)cnt, part, (double2 *)blocks, (cudaStream_t)stream);
 }
 
 int wick_reduce_terms(const wick_nucleus *nuc, const wick_nucleon_op *ops, const wick_block_layout *layout,
@@ -687,10 +688,12 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *t, int
     ContractPlan plan;
     err = contract_plan(n_blk, 1, n_slices, &tab, 1, precision, contract_tune(current_tuning()), INT64_MAX, &plan);
     if (err) return err;
-    void *ws = workspace(1, plan.bytes, &err);
+    void *part = workspace(kWsContractPartials, plan.partial_bytes, &err);
     if (err) return err;
-    return launch_contract((const double2 *)blocks, n_blk, 1, n_slices, &tab, 1, precision, plan, ws,
-                           (double2 *)C_out, (cudaStream_t)stream);
+    void *cnt = workspace(kWsContractCounters, plan.counter_bytes, &err);
+    if (err) return err;
+    return launch_contract((const double2 *)blocks, n_blk, 1, n_slices, &tab, 1, precision, plan, cnt,
+                           (double2 *)part, (double2 *)C_out, (cudaStream_t)stream);
 }
 
 int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms *t, int precision, void *C_out,
@@ -709,11 +712,13 @@ int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms
     err = contract_plan(n_blk, 1, (int)n_slices, &tab, 1, precision, contract_tune(current_tuning()), kNoAllocItems,
                         &plan);
     if (err) return err;
-    if (plan.bytes > cap || plan.counters > (size_t)kNoAllocItems) return WICK_ESCRATCH;
+    if (plan.counter_bytes > kNoAllocCounterBytes || plan.partial_bytes > cap - kNoAllocCounterBytes)
+        return WICK_ESCRATCH;
     // the array keeps the last call's contents: clear the counters this launch starts from
-    WICK_CUDA_TRY(cudaMemsetAsync(scratch, 0, contract_counter_bytes(plan), (cudaStream_t)stream));
+    WICK_CUDA_TRY(cudaMemsetAsync(scratch, 0, plan.counter_bytes, (cudaStream_t)stream));
+    double2 *partials = reinterpret_cast<double2 *>(static_cast<unsigned char *>(scratch) + kNoAllocCounterBytes);
     return launch_contract((const double2 *)blocks, n_blk, 1, (int)n_slices, &tab, 1, precision, plan, scratch,
-                           (double2 *)C_out, (cudaStream_t)stream);
+                           partials, (double2 *)C_out, (cudaStream_t)stream);
 }
 
 int wick_set_tuning(const wick_tuning *t) {

@@ -65,14 +65,16 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
     const int rs = tune.range_sites;
     const bool tc = precision == WICK_MIXED && tc_applicable(plan);
     int group = 1;
-    size_t bbytes = block_scratch_bytes(plan, (int)V, (int)n_slices, precision, rs);
+    size_t pbytes = block_partial_bytes(plan, (int)V, (int)n_slices, precision, rs), cbytes = 0;
     if (tc) {
-        const size_t per_cfg = tc_scratch_bytes(plan, (int)V, (int)n_slices, 1, rs);
+        const size_t per_cfg = tc_partial_bytes(plan, (int)V, (int)n_slices, 1, rs);
         group = (int)std::max<size_t>(1, std::min<size_t>(kGroupBytes / per_cfg, (size_t)tc_max_configs()));
         group = std::min(group, n_cfg);
         while ((int64_t)group * n_slices > 65535) --group;
-        bbytes = tc_scratch_bytes(plan, (int)V, (int)n_slices, group, rs);
+        pbytes = tc_partial_bytes(plan, (int)V, (int)n_slices, group, rs);
+        cbytes = tc_counter_bytes(plan, (int)n_slices, group);
     }
+    const size_t bbytes = cbytes + pbytes;   // counters first (256-byte multiple), then partials
     ContractPlan cplan;
     err = contract_plan(plan.n_out, n_cfg, (int)n_slices, tabs.data(), n_tables, precision, contract_tune(tune),
                         INT64_MAX, &cplan);
@@ -89,11 +91,14 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
         return e;
     };
     if (cudaMalloc(&bt->block_scratch, bbytes) != cudaSuccess ||
-        cudaMalloc(&bt->contract_scratch, cplan.bytes) != cudaSuccess)
+        cudaMalloc(&bt->contract_scratch, cplan.counter_bytes + cplan.partial_bytes) != cudaSuccess)
         return fail(WICK_ENOMEM);
     if (cudaMemset(bt->block_scratch, 0, bbytes) != cudaSuccess ||
-        cudaMemset(bt->contract_scratch, 0, cplan.bytes) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        cudaMemset(bt->contract_scratch, 0, cplan.counter_bytes + cplan.partial_bytes) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
         return fail(WICK_ECUDA);
+    unsigned char *bsc = static_cast<unsigned char *>(bt->block_scratch);
+    unsigned char *csc = static_cast<unsigned char *>(bt->contract_scratch);
     int serr = WICK_OK;
     int *status = status_word(&serr);  // the device status word exists before capture (kernels report timeouts there)
     if (serr) return fail(serr);
@@ -114,21 +119,22 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
         for (int c0 = 0; c0 < n_cfg && !launch_err; c0 += group) {
             const int gn = std::min(group, n_cfg - c0);
             launch_err = launch_block_tc(plan, su.data() + c0, sd.data() + c0, gn, dtype, (int)V, (int)n_slices, rs,
-                                         bt->block_scratch, bbytes, (double2 *)blocks + (size_t)c0 * blk_stride,
-                                         status, cap);
+                                         (int *)bsc, (double2 *)(bsc + cbytes),
+                                         (double2 *)blocks + (size_t)c0 * blk_stride, status, cap);
             bt->n_launches += 1;
         }
     } else {
         for (int c = 0; c < n_cfg && !launch_err; ++c) {
             launch_err = launch_block_build(plan, Su[c].data, dtype, Sd[c].data, dtype, (int)V, (int)n_slices,
-                                            precision, rs, bt->block_scratch, bbytes,
-                                            (double2 *)blocks + (size_t)c * blk_stride, cap);
+                                            precision, rs, nullptr, bsc, (double2 *)blocks + (size_t)c * blk_stride,
+                                            cap);
             bt->n_launches += block_build_launches(plan, precision);
         }
     }
     if (!launch_err) {
         launch_err = launch_contract((const double2 *)blocks, plan.n_out, n_cfg, (int)n_slices, tabs.data(), n_tables,
-                                     precision, cplan, bt->contract_scratch, (double2 *)C_out, cap);
+                                     precision, cplan, csc, (double2 *)(csc + cplan.counter_bytes), (double2 *)C_out,
+                                     cap);
         bt->n_launches += 1;
     }
     const cudaError_t ec = cudaStreamEndCapture(cap, &bt->graph);

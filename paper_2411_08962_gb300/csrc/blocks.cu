@@ -294,10 +294,14 @@ int launch_typed(const BlockPlan &plan, const void *Su, const void *Sd, int V, i
 
 }  // namespace
 
-size_t block_scratch_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int range_sites) {
-    if (precision == WICK_MIXED && tc_applicable(plan)) return tc_scratch_bytes(plan, V, n_slices, 1, range_sites);
+size_t block_partial_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int range_sites) {
+    if (precision == WICK_MIXED && tc_applicable(plan)) return tc_partial_bytes(plan, V, n_slices, 1, range_sites);
     const int n_splits = (V + kChunk - 1) / kChunk;
     return sizeof(double2) * (size_t)n_splits * n_slices * plan.n_out;
+}
+
+size_t block_counter_bytes(const BlockPlan &plan, int n_slices, int precision) {
+    return precision == WICK_MIXED && tc_applicable(plan) ? tc_counter_bytes(plan, n_slices, 1) : 0;
 }
 
 int block_build_launches(const BlockPlan &plan, int precision) {
@@ -305,18 +309,17 @@ int block_build_launches(const BlockPlan &plan, int precision) {
 }
 
 int launch_block_build(const BlockPlan &plan, const void *Su, int dtype_u, const void *Sd, int dtype_d, int V,
-                       int n_slices, int precision, int range_sites, void *scratch, size_t scratch_bytes,
-                       double2 *blocks, cudaStream_t stream) {
-    if (dtype_u != dtype_d) return WICK_EINVAL;
-    if (scratch_bytes < block_scratch_bytes(plan, V, n_slices, precision, range_sites)) return WICK_EINVAL;
+                       int n_slices, int precision, int range_sites, int *counters, void *partials, double2 *blocks,
+                       cudaStream_t stream) {
+    if (dtype_u != dtype_d || !partials) return WICK_EINVAL;
     if (precision == WICK_MIXED && tc_applicable(plan)) {
         int err = WICK_OK;
         int *status = status_word(&err);
         if (err) return err;
-        return launch_block_tc(plan, &Su, &Sd, 1, dtype_u, V, n_slices, range_sites, scratch, scratch_bytes, blocks,
-                               status, stream);
+        return launch_block_tc(plan, &Su, &Sd, 1, dtype_u, V, n_slices, range_sites, counters,
+                               static_cast<double2 *>(partials), blocks, status, stream);
     }
-    double2 *part = static_cast<double2 *>(scratch);
+    double2 *part = static_cast<double2 *>(partials);
     const int chunk = kChunk, n_splits = (V + kChunk - 1) / kChunk;
     if (precision == WICK_MIXED || precision == WICK_MIXED_SIMT) {
         if (plan.pow2_w) {

@@ -806,31 +806,30 @@ int tc_range_sites(int requested) {
 
 int tc_max_configs() { return kMaxCfg; }
 
-size_t tc_scratch_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites) {
+size_t tc_counter_bytes(const BlockPlan &plan, int n_slices, int n_cfg) {
+    return align256(sizeof(int) * (size_t)n_cfg * n_slices * plan.n_ops);
+}
+
+size_t tc_partial_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites) {
     const int rs = tc_range_sites(range_sites);
     const size_t n_ranges = (size_t)(V + rs - 1) / rs;
-    const size_t counters = align256(sizeof(int) * (size_t)n_cfg * n_slices * plan.n_ops);
-    return counters + sizeof(double2) * n_ranges * n_cfg * n_slices * plan.n_out;
+    return sizeof(double2) * n_ranges * n_cfg * n_slices * plan.n_out;
 }
 
 int launch_block_tc(const BlockPlan &plan, const void *const *Su, const void *const *Sd, int n_cfg, int dtype, int V,
-                    int n_slices, int range_sites, void *scratch, size_t scratch_bytes, double2 *blocks, int *status,
+                    int n_slices, int range_sites, int *counters, double2 *part, double2 *blocks, int *status,
                     cudaStream_t stream) {
     const int fam = tc_family(plan);
     const int rs = tc_range_sites(range_sites);
     const int n_ranges = (V + rs - 1) / rs;
     if (!fam || n_cfg < 1 || n_cfg > kMaxCfg || n_ranges > 65535 || (int64_t)n_cfg * n_slices > 65535)
         return WICK_EINVAL;
-    if (!scratch || (uintptr_t)scratch % 256 || scratch_bytes < tc_scratch_bytes(plan, V, n_slices, n_cfg, rs))
-        return WICK_EINVAL;
+    if (!counters || !part) return WICK_EINVAL;
     CfgPtrs cp{};
     for (int c = 0; c < n_cfg; ++c) {
         cp.su[c] = Su[c];
         cp.sd[c] = Sd[c];
     }
-    int *counters = static_cast<int *>(scratch);
-    double2 *part = reinterpret_cast<double2 *>(static_cast<unsigned char *>(scratch) +
-                                                align256(sizeof(int) * (size_t)n_cfg * n_slices * plan.n_ops));
     WeightExp ew = {};
     for (int o = 0; o < plan.n_ops; ++o) {
         const int b0 = plan.os_off[o * plan.n_spin];

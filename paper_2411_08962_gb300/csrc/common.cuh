@@ -48,12 +48,14 @@ struct BlockPlan {
 
 int build_block_plan(const wick_nucleon_op *ops, const wick_block_layout *layout, BlockPlan *plan);
 
-// launchers (blocks.cu): the block build of one configuration; scratch of block_scratch_bytes
-// (zero before its first use: the tensor-core path keeps its counters there)
+// launchers (blocks.cu): the block build of one configuration.  partials: block_partial_bytes;
+// counters: block_counter_bytes (the tensor-core path; zero before its first use, cleared again by
+// every launch; a region that holds nothing else)
 int launch_block_build(const BlockPlan &plan, const void *Su, int dtype_u, const void *Sd, int dtype_d,
-                       int V, int n_slices, int precision, int range_sites, void *scratch, size_t scratch_bytes,
+                       int V, int n_slices, int precision, int range_sites, int *counters, void *partials,
                        double2 *blocks, cudaStream_t stream);
-size_t block_scratch_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int range_sites);
+size_t block_partial_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int range_sites);
+size_t block_counter_bytes(const BlockPlan &plan, int n_slices, int precision);
 // tensor-core update stage (blocks_tc.cu): upper-spin plans, double-FP32-exact
 // the 16-byte words of one site that wick_upload_rows gathers: flavour << 15 | word in the site
 constexpr int kMaxUploadWords = 2 * 12 * 12;   // both flavours, all rows, complex128
@@ -70,9 +72,10 @@ int block_build_launches(const BlockPlan &plan, int precision);  // kernels one 
 // cleared again by every launch -- and the FP64 partials of every site range
 int tc_range_sites(int requested);               // the range size a request (0 = default) resolves to
 int tc_max_configs();
-size_t tc_scratch_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites);
+size_t tc_counter_bytes(const BlockPlan &plan, int n_slices, int n_cfg);
+size_t tc_partial_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites);
 int launch_block_tc(const BlockPlan &plan, const void *const *Su, const void *const *Sd, int n_cfg, int dtype, int V,
-                    int n_slices, int range_sites, void *scratch, size_t scratch_bytes, double2 *blocks, int *status,
+                    int n_slices, int range_sites, int *counters, double2 *partials, double2 *blocks, int *status,
                     cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
@@ -127,19 +130,23 @@ struct ContractPlan {
     int items_per_cs;
     int64_t n_items;
     size_t counters;           // (configuration, table, slice) counters
-    size_t bytes;              // scratch: item counter, counters, partials
+    size_t counter_bytes;      // the item counters and the counters: zero before the first launch
+    size_t partial_bytes;      // one complex128 per work item
 };
 int contract_plan(int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab, int precision,
                   const ContractTune &tune, int64_t max_items, ContractPlan *plan);
-// scratch bytes that must be zero before the first launch (item counter and counters)
-size_t contract_counter_bytes(const ContractPlan &plan);
+// counters: plan.counter_bytes, zero before the first launch (cleared again by every launch; a region
+// that holds nothing else); partials: plan.partial_bytes
 int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab,
-                    int precision, const ContractPlan &plan, void *scratch, double2 *C_out, cudaStream_t stream);
+                    int precision, const ContractPlan &plan, void *counters, double2 *partials, double2 *C_out,
+                    cudaStream_t stream);
 int pad_table(const uint16_t *ids, const int64_t *w, int64_t U, int A, uint16_t *ids_pad, double *wd,
               cudaStream_t stream);
-// fixed scratch of wick_contract_noalloc (per device): item counter, 65,536 counters, 65,536 partials
+// fixed scratch of wick_contract_noalloc (per device): the item counters and 65,536 counters, then
+// 65,536 partials at a fixed offset
 constexpr int64_t kNoAllocItems = 65536;
-constexpr size_t kNoAllocBytes = 256 + sizeof(int) * kNoAllocItems + 16 * kNoAllocItems;
+constexpr size_t kNoAllocCounterBytes = 256 + sizeof(int) * kNoAllocItems;
+constexpr size_t kNoAllocBytes = kNoAllocCounterBytes + 16 * kNoAllocItems;
 int noalloc_scratch(void **ptr, size_t *bytes);
 
 // ---------------------------------------------------------------------------
@@ -148,8 +155,11 @@ int noalloc_scratch(void **ptr, size_t *bytes);
 int terms_table(const wick_terms *t, ContractTable *tab, int *n_blk);
 wick_tuning current_tuning();
 ContractTune contract_tune(const wick_tuning &t);
-// per-device cached scratch, zeroed when (re)allocated; slot 0 = block partials of the FP64 and CUDA-core
-// paths, 1 = contraction scratch, 2 = determinant scratch, 3 = tensor-core block scratch
+// per-device cached scratch, zeroed when (re)allocated: 0 = block partials, 1 = contraction partials,
+// 2 = determinant scratch, 3 = block-build counters, 4 = contraction counters (the counter slots hold
+// nothing but counters, which every launch leaves at zero)
+constexpr int kWsBlockPartials = 0, kWsContractPartials = 1, kWsDet = 2, kWsBlockCounters = 3,
+              kWsContractCounters = 4, kWsSlots = 5;
 void *workspace(int slot, size_t bytes, int *err);
 int *status_word(int *err);                     // per-device status word
 int status_read_clear(cudaStream_t stream);

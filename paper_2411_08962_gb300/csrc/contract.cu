@@ -308,15 +308,15 @@ int contract_plan(int n_blk, int n_cfg, int n_slices, const ContractTable *tabs,
     const int64_t most = (int64_t)n_sm * per_sm;
     P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(most, P.n_items));
     P.counters = (size_t)n_cfg * n_tab * n_slices;
-    P.bytes = 256 + align256(sizeof(int) * P.counters) + align256(sizeof(double2) * (size_t)P.n_items);
+    P.counter_bytes = 256 + align256(sizeof(int) * P.counters);
+    P.partial_bytes = align256(sizeof(double2) * (size_t)P.n_items);
     return WICK_OK;
 }
 
-size_t contract_counter_bytes(const ContractPlan &P) { return 256 + align256(sizeof(int) * P.counters); }
-
 int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab,
-                    int precision, const ContractPlan &P, void *scratch, double2 *C_out, cudaStream_t stream) {
-    if (!scratch || (uintptr_t)scratch % 256) return WICK_EINVAL;
+                    int precision, const ContractPlan &P, void *counters, double2 *partials, double2 *C_out,
+                    cudaStream_t stream) {
+    if (!counters || !partials || (uintptr_t)counters % 256 || (uintptr_t)partials % 16) return WICK_EINVAL;
     ContractWork wk{};
     wk.n_tab = n_tab;
     for (int k = 0; k < n_tab; ++k) {
@@ -330,10 +330,10 @@ int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, c
     wk.items_per_cs = P.items_per_cs;
     wk.n_items = P.n_items;
     wk.C_out = C_out;
-    unsigned char *base = static_cast<unsigned char *>(scratch);
+    unsigned char *base = static_cast<unsigned char *>(counters);
     wk.queue = reinterpret_cast<unsigned long long *>(base);
     wk.counters = reinterpret_cast<int *>(base + 256);
-    wk.partials = reinterpret_cast<double2 *>(base + contract_counter_bytes(P));
+    wk.partials = partials;
     const bool mixed = precision == WICK_MIXED;
     if (mixed) return P.stage ? launch_typed<true, true>(wk, P.grid, P.threads, P.smem, stream)
                               : launch_typed<true, false>(wk, P.grid, P.threads, P.smem, stream);
@@ -343,10 +343,10 @@ int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, c
 
 // ---------------------------------------------------------------------------
 // Fixed scratch of wick_contract_noalloc, in a file-scope device array instead
-// of the library's cudaMalloc'd workspace: the item counter, one counter per
-// slice and the FP64 partial sums (one complex128 per work item).  Every
-// device that loads the library holds these kNoAllocBytes until the process
-// exits.
+// of the library's cudaMalloc'd workspace: the item counters and one counter
+// per slice (kNoAllocCounterBytes), then at that fixed offset the FP64 partial
+// sums (one complex128 per work item).  Every device that loads the library
+// holds these kNoAllocBytes until the process exits.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
