@@ -9,18 +9,21 @@
 //
 // Exactness (an Ozaki-type error-free splitting).  Every U value is cut into
 // 5 slices on a fixed-point grid 2^E (E bounds the |components| of its colour
-// c1 over the CTA's sites), every X value -- a double-FP32 number -- into 6
-// slices on a grid 2^F of its column (2^F >= sum|w| max|u| max|d|):
-//     v = 2^(E-7) * sum_i q_i 2^(-8i),   |q_i| <= 128   (39 / 47 bits)
-// Slice i is stored at its own weight, q_i 2^(-8i): at most 8 significant
-// bits, exact in bf16.  The products of the pair (i, j) are multiples of
-// 2^(-8(i+j)) of magnitude at most 2^(14-8(i+j)), and a sum of K <= 768 of
-// them (128 sites) stays below 2^(24-8(i+j)), so the FP32 accumulation in TMEM
-// is exact for a whole round of 128 sites, and every accumulator is read with
-// the one factor 2^(E+F-14).  Pairs with i + j <= 5 are kept.  The grids bound the largest values of a
-// 512-site range, so typical X values sit ~6 bits below 2^F: with 5 x 5 slices
-// and i + j <= 4 the blocks came out ~1e-9 relative, with 5 x 6 and i + j <= 5
-// ~5e-12 (the same class as the double-FP32 CUDA-core kernel).
+// c1 over the CTA's sites), every X value into 6 slices on a grid 2^F of its
+// column (2^F >= sum|w| max|u| max|d|):
+//     v = 2^(E-7) * sum_i q_i 2^(-8i),   |q_i| <= 128 (U) / 144 (X)   (39 / 47 bits)
+// X is formed from the float propagator entries in a fixed-exponent float
+// accumulator on the grid 2^(F-22) plus a float sum of the FMA-exact rounding
+// remainders (facc below: four operations per product), accurate to about
+// 2^-35 of 2^F.  Slice i is stored at its own weight, q_i 2^(-8i): at most 8
+// significant bits, exact in bf16.  The products of the pair (i, j) are
+// multiples of 2^(-8(i+j)) of magnitude below 2^(15-8(i+j)), and a sum of
+// K <= 768 of them (128 sites) stays below 2^(24-8(i+j)), so the FP32
+// accumulation in TMEM is exact for a whole round of 128 sites, and every
+// accumulator is read with the one factor 2^(E+F-14).  Pairs with i + j <= 5
+// are kept.  The grids bound the largest values of a 512-site range, so
+// typical X values sit ~6 bits below 2^F; blocks come out ~1e-11 relative
+// (the class of the double-FP32 CUDA-core kernel).
 // Each round's accumulators are added in double-FP32 relative to 2^(E+F-14);
 // the five U-slice rows of an output are combined at the end and converted to
 // FP64.
@@ -223,31 +226,47 @@ __device__ __forceinline__ void slice_u2(f2x v, float sc, uint32_t *w) {
     }
 }
 
-// X = (h + l) lane-wise (two sites): r = X 2^(7-F) = sum_j q_j 2^(-8j) + e, |e| <= 2^-40; one bf16x2 word per
-// slice; sc = 2^(7-F).  |r| <= 128 and the low part |l 2^(7-F)| <= 2^-13 (the list's rounding
-// errors).  The low part joins the remainder after the first slice by a TwoSum (t, e0): then
-// |t| <= 1/2 + 2^-13 (slice 1 still within 128) and |e0| <= 2^-25.  Slices 1 and 2 take t alone
-// (exact remainders, the second within 2^-17); e0 joins after slice 2 with one rounding of at most
-// 2^-41, below slice 3's grid 2^-24; slices 3 to 5 round that single float.
-__device__ __forceinline__ void slice_x2(f2x h, f2x l, float sc, uint32_t *w) {
-    const f2x s2 = pk(sc, sc);
-    const f2x rh = mul2(h, s2), rl = mul2(l, s2);
+// The diquark value X of a site pair is accumulated in units of 2^(F-7) (|X| <= 128 there: 2^F bounds
+// sum |w| max|u| max|d| over the range) in a fixed-exponent float a = M + X, M = 384 = 1.5 * 2^8: every
+// partial sum stays in [256, 512], so a is on the grid 2^-15 and each step rounds to that grid.  Per
+// product A*B (A = w 2^(7-F) u, exact: w = +-2^k; B = d) the step is
+//     n = fma(A, B, a),  nz = a - n (exact),  lo += fma(A, B, nz)
+// where fma(A, B, nz) = A*B - (n - a), the rounding error of the step, is exact up to one rounding at
+// 2^-40 (it is below 2^-16 and A*B has 48 bits above 2^-40 when |A*B| <= 128).  lo (below 2^-12 in
+// magnitude: 16 products) is an ordinary float sum; its rounding errors stay below 2^-32 and are
+// typically 2^-35.  Four f32x2 operations per product, against ten for a TwoProd-and-TwoSum chain.
+constexpr float kFixedM = 384.f;
+
+__device__ __forceinline__ void facc(f2x &a, f2x &lo, f2x A, f2x B) {
+    const f2x n = fma2(A, B, a);
+    const f2x nz = sub2(a, n);
+    lo = add2(lo, fma2(A, B, nz));
+    a = n;
+}
+
+// Slices of X = hi + lo (units 2^(F-7), lanes = two sites) at their own weight, one bf16x2 word each:
+// hi = a - M is on the grid 2^-15 with |hi| <= 128, |lo| <= 2^-12.
+//   q0 = hi rounded to an integer, q1 = the rest rounded to 2^-8 (both exact remainders);
+//   q2 = the rest of hi (on 2^-15, |.| <= 2^-9) plus lo rounded to 2^-16: |q2| < 2^-8 on the grid 2^-16,
+//        8 significant bits (|q2| 2^16 <= 144: products with a U slice stay below 2^15, so a 128-site
+//        round of K = 768 products is still an exact float sum);
+//   q3, q4, q5 = the rest of lo (|.| <= 2^-17) on the grids 2^-24, 2^-32, 2^-40.
+// Representation error <= 2^-41 plus the rounding of lo.
+__device__ __forceinline__ void slice_x2(f2x hi, f2x lo, uint32_t *w) {
     auto word = [](f2x q) {
-        uint32_t lo, hi;
-        asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(q));
-        return __byte_perm(lo, hi, 0x7632);
+        uint32_t l, h;
+        asm("mov.b64 {%0, %1}, %2;" : "=r"(l), "=r"(h) : "l"(q));
+        return __byte_perm(l, h, 0x7632);
     };
-    f2x q = round_grid(rh, 0);
+    f2x q = round_grid(hi, 0);
     w[0] = word(q);
-    const f2x d0 = sub2(rh, q);
-    const f2x t = add2(d0, rl), bb = sub2(t, d0);
-    const f2x e0 = add2(sub2(d0, sub2(t, bb)), sub2(rl, bb));
-    q = round_grid(t, 1);
+    f2x r = sub2(hi, q);
+    q = round_grid(r, 1);
     w[1] = word(q);
-    const f2x d1 = sub2(t, q);
-    q = round_grid(d1, 2);
-    w[2] = word(q);
-    f2x r = add2(sub2(d1, q), e0);
+    r = sub2(r, q);
+    const f2x l2 = round_grid(lo, 2);
+    w[2] = word(add2(r, l2));
+    r = sub2(lo, l2);
 #pragma unroll
     for (int j = 3; j < kSlicesX; ++j) {
         q = round_grid(r, j);
@@ -258,13 +277,13 @@ __device__ __forceinline__ void slice_x2(f2x h, f2x l, float sc, uint32_t *w) {
 
 __device__ __forceinline__ f2x lds2(const float *p) { return *reinterpret_cast<const f2x *>(p); }
 
-// The pair of sites (s, s + 1) of one column of the X_{o,a} list in double-FP32, lanes = sites:
-// re += w (ur dr - ui di), im += w (ur di + ui dr) per term, every product exact (TwoProd) and
-// summed by TwoSum.  term[t] = (float offset of the u row, of the d row, w, w), wn[t] = (-w, -w);
+// The pair of sites (s, s + 1) of one column of the X_{o,a} list, lanes = sites, in units of 2^(F-7):
+// re = sum_t w (ur dr - ui di), im = sum_t w (ur di + ui dr) as (a - M, lo) pairs (see facc).
+// term[t] = (float offset of the u row, of the d row, w, w), wn[t] = (-w, -w); sc2 = (2^(7-F), 2^(7-F));
 // the re / im planes are PS floats apart.  All loads first.
 template <int PS>
-__device__ __forceinline__ void x_pair(const int4 *term, const f2x *wn, const float *bu, const float *bd, pdf &re,
-                                       pdf &im) {
+__device__ __forceinline__ void x_pair(const int4 *term, const f2x *wn, f2x sc2, const float *bu, const float *bd,
+                                       f2x &re_hi, f2x &re_lo, f2x &im_hi, f2x &im_lo) {
     f2x ur[kListLen], ui[kListLen], dr[kListLen], di[kListLen], ww[kListLen], nw[kListLen];
 #pragma unroll
     for (int t = 0; t < kListLen; ++t) {
@@ -276,27 +295,21 @@ __device__ __forceinline__ void x_pair(const int4 *term, const f2x *wn, const fl
         asm("mov.b64 %0, {%1, %2};" : "=l"(ww[t]) : "r"(tt.z), "r"(tt.w));
         nw[t] = wn[t];
     }
-    {   // the first products start the accumulators without a TwoSum
-        const f2x a = mul2(ur[0], ww[0]), na = mul2(ur[0], nw[0]);
-        f2x np = mul2(na, dr[0]);
-        re.h = sub2(0ull, np);
-        re.l = fma2(a, dr[0], np);
-        np = mul2(na, di[0]);
-        im.h = sub2(0ull, np);
-        im.l = fma2(a, di[0], np);
-        const f2x b = mul2(ui[0], ww[0]), nb = mul2(ui[0], nw[0]);
-        pacc_exact(re, nb, b, di[0]);   // - w ui di
-        pacc_exact(im, b, nb, dr[0]);
-    }
+    const f2x M = pk(kFixedM, kFixedM);
+    f2x ra = M, ia = M, rl = 0ull, il = 0ull;
 #pragma unroll
-    for (int t = 1; t < kListLen; ++t) {
-        const f2x a = mul2(ur[t], ww[t]), na = mul2(ur[t], nw[t]);   // exact: w = +-2^k
-        const f2x b = mul2(ui[t], ww[t]), nb = mul2(ui[t], nw[t]);
-        pacc_exact(re, a, na, dr[t]);
-        pacc_exact(re, nb, b, di[t]);
-        pacc_exact(im, a, na, di[t]);
-        pacc_exact(im, b, nb, dr[t]);
+    for (int t = 0; t < kListLen; ++t) {
+        const f2x w = mul2(ww[t], sc2), n = mul2(nw[t], sc2);   // +-w 2^(7-F): exact
+        const f2x a = mul2(ur[t], w), b = mul2(ui[t], w), nb = mul2(ui[t], n);
+        facc(ra, rl, a, dr[t]);
+        facc(ra, rl, nb, di[t]);
+        facc(ia, il, a, di[t]);
+        facc(ia, il, b, dr[t]);
     }
+    re_hi = sub2(ra, M);
+    im_hi = sub2(ia, M);
+    re_lo = rl;
+    im_lo = il;
 }
 
 // Job jb over (row or column n < NN, colour term a < kKa, site pair sp < NSP) -> (n, a, sp).  A
@@ -355,11 +368,12 @@ template <typename SH>
 __device__ __forceinline__ void x_job(const Job &j, const int4 *sTerm, const f2x *sTermN, const float *S,
                                       __nv_bfloat16 *B) {
     constexpr int NT = SH::NT, NX = SH::NX, KC = SH::KC;
-    pdf re, im;
-    x_pair<SH::PS>(sTerm + j.a * kListLen, sTermN + j.a * kListLen, S + j.s1, S + j.s2, re, im);
+    f2x rh, rl, ih, il;
+    x_pair<SH::PS>(sTerm + j.a * kListLen, sTermN + j.a * kListLen, pk(j.sc, j.sc), S + j.s1, S + j.s2, rh, rl, ih,
+                   il);
     uint32_t wr[kSlicesX], wi[kSlicesX];
-    slice_x2(re.h, re.l, j.sc, wr);
-    slice_x2(im.h, im.l, j.sc, wi);
+    slice_x2(rh, rl, wr);
+    slice_x2(ih, il, wi);
     __nv_bfloat16 *dst = B + j.d1;
 #pragma unroll
     for (int i = 0; i < kSlicesX; ++i) {
