@@ -132,6 +132,14 @@ template <int NC_, int NS_, int NT_, int NMT_, int NX_, int MR_, int EP_> struct
     static constexpr int B_BYTES = kSlicesX * NT * KC * 2;
     static constexpr int S_BYTES = 2 * PS * 4;              // two float planes
     static constexpr int SCAN_BYTES = (2 * SPC + 1) * SCANNERS * 8;   // two scan slots and the running maxima
+    // the kernel's carve-up of its dynamic shared memory, in order: operand buffers, staging planes, scan
+    // slots and maxima, sEU[16], sF[256], sTerm (int4 x kKa kListLen), sTermN (8 B x kKa kListLen),
+    // sR1[16], sSrc[kMaxRows * 12], mbar[2] (8 B each), tslot (4 B)
+    static constexpr int OFF_SCAN = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES;
+    static constexpr int OFF_EU = OFF_SCAN + SCAN_BYTES;
+    static constexpr int OFF_TERM = OFF_EU + 4 * (16 + 256);
+    static constexpr int OFF_MBAR = OFF_TERM + (16 + 8) * kKa * kListLen + 4 * 16 + 4 * kMaxRows * 12;
+    static constexpr int LAYOUT_END = OFF_MBAR + 2 * 8 + 4;
     static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES + SCAN_BYTES + 4 * (16 + 256) +
                                 (16 + 8) * kKa * kListLen + 4 * 16 + 4 * kMaxRows * 12 + 32;
     static_assert(NMT * 128 >= kSlices * R && (NMT - 1) * 128 < kSlices * R, "M tiles");
@@ -144,6 +152,8 @@ template <int NC_, int NS_, int NT_, int NMT_, int NX_, int MR_, int EP_> struct
     static_assert(R % 8 == 0, "U slices start on a core-matrix row group");
     static_assert(kSlices * R * NT * 8 <= 2 * (A_BYTES + B_BYTES), "combine buffer");
     static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(LAYOUT_END <= SMEM && OFF_TERM % 16 == 0 && OFF_MBAR % 8 == 0 && OFF_SCAN % 16 == 0,
+                  "shared-memory carve-up");
 };
 using UpperShape = Shape<6, 2, 48, 1, 16, 12, 20>;   // nucleon upper spin components: 2 x 216 per type
 using FullShape = Shape<12, 4, 16, 4, 8, 24, 8>;     // all four spins: 4 x 1728 per type
@@ -526,7 +536,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
     float *sS0 = reinterpret_cast<float *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES));
     float2 *sScan = reinterpret_cast<float2 *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES) + kStage * SH::S_BYTES);
     float2 *sScanMax = sScan + 2 * SPC * SH::SCANNERS;       // [SCANNERS] running (max |.|, max |re| + |im|)
-    int *sEU = reinterpret_cast<int *>(sScanMax + kThr);
+    int *sEU = reinterpret_cast<int *>(sScanMax + SH::SCANNERS);
     int *sF = sEU + 16;                                       // [256] grid of X per column
     int4 *sTerm = reinterpret_cast<int4 *>(sF + 256);         // [kKa][kListLen] the op's diquark list terms
     f2x *sTermN = reinterpret_cast<f2x *>(sTerm + kKa * kListLen);  // [kKa][kListLen] (-w, -w)
@@ -534,6 +544,14 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
     int *sSrc = sR1 + 16;                                     // [kMaxRows * NC] flavour << 16 | row * 12 + chi
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sSrc + kMaxRows * 12);   // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    // the carve-up above must match the Shape's (checked there against SMEM)
+    if (reinterpret_cast<unsigned char *>(sScan) != smem + SH::OFF_SCAN ||
+        reinterpret_cast<unsigned char *>(sEU) != smem + SH::OFF_EU ||
+        reinterpret_cast<unsigned char *>(sTerm) != smem + SH::OFF_TERM ||
+        reinterpret_cast<unsigned char *>(mbar) != smem + SH::OFF_MBAR) {
+        if (tid == 0) atomicCAS(status, 0, WICK_EINVAL);
+        return;
+    }
 
     for (int e = tid; e < nr * NC; e += kThr) {
         const int rc = e / NC, ic = e - rc * NC;
