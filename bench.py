@@ -48,8 +48,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the Li-7 and batched sub-records")
     ap.add_argument("--workload", choices=["he4", "li7", "batched", "point"], default="he4",
                     help="he4: the metric's workload (default); li7 / batched: the other scope rows")
-    ap.add_argument("--profile-slab", choices=["mixed", "fp64"], default=None,
-                    help="only run the block build on one source of the workload (for ncu captures)")
+    ap.add_argument("--profile-slab", choices=["mixed", "fp64", "li7"], default=None,
+                    help="only run the block build on one source of the He-4 workload (mixed / fp64), or on "
+                         "8 time slices of the Li-7 workload (full-spin tables, mixed), for ncu captures")
     return ap.parse_args()
 
 
@@ -560,20 +561,31 @@ def run_ours(args):
 
 
 def run_profile_slab(args):
-    """Block build only, on source 0 of the workload (32 slices, 302 MB of
-    complex64 input): the launch that ncu captures for the kernel summaries."""
+    """Block build only, on source 0 of the He-4 workload (32 slices, 302 MB of complex64 input) or on
+    8 time slices of the Li-7 workload (full-spin tables; 254 MB): the launch that ncu captures for the
+    kernel summaries."""
     import torch
 
     from paper_2411_08962_gb300 import build, operators, synth, wick
     build.build()
     wick.load()
-    w = synth.WORKLOADS["he4"]
-    L, T = w["L"], w["T"]
-    Su = torch.from_numpy(synth.propagator(w["seed"], 0, L, T, 1, dtype=np.complex64)).cuda()
-    Sd = torch.from_numpy(synth.propagator(w["seed"], 1, L, T, 1, dtype=np.complex64)).cuda()
-    tabs = wick.Tables(operators.nucleus("he4"))
+    if args.profile_slab == "li7":
+        w = synth.WORKLOADS["li7"]
+        L, T = w["L"], 8
+        Su = torch.empty((1, T, L ** 3, 3, 4, 3, 4), dtype=torch.complex64, device="cuda")
+        Sd = torch.empty_like(Su)
+        wick.wick_synth_propagator(w["seed"], 0, 0, L, T, Su[0])
+        wick.wick_synth_propagator(w["seed"], 1, 0, L, T, Sd[0])
+        tabs = wick.Tables(operators.cluster("triton"))
+        prec = wick.WICK_MIXED
+    else:
+        w = synth.WORKLOADS["he4"]
+        L, T = w["L"], w["T"]
+        Su = torch.from_numpy(synth.propagator(w["seed"], 0, L, T, 1, dtype=np.complex64)).cuda()
+        Sd = torch.from_numpy(synth.propagator(w["seed"], 1, L, T, 1, dtype=np.complex64)).cuda()
+        tabs = wick.Tables(operators.nucleus("he4"))
+        prec = wick.WICK_MIXED if args.profile_slab == "mixed" else wick.WICK_FP64
     B = torch.empty((1, T, tabs.nuc.n_blk), dtype=torch.complex128, device="cuda")
-    prec = wick.WICK_MIXED if args.profile_slab == "mixed" else wick.WICK_FP64
     for _ in range(max(2, args.warmup)):
         wick.wick_build_blocks(Su, Sd, tabs, prec, B, L, T, 1)
     torch.cuda.synchronize()

@@ -54,7 +54,6 @@
 // then clears the counter for the next launch.
 #include <cuda_bf16.h>
 
-#include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
@@ -70,6 +69,17 @@ constexpr int kSlicesX = 6;                        // slices of X
 constexpr int kMaxPair = 5;                        // kept slice pairs: i + j <= kMaxPair
 constexpr int kKa = 3;                             // colour-term slots per site
 constexpr int kRoundSites = 128;                   // sites per exact TMEM accumulation
+// Level accumulators (full-spin family): the MMA of U slice i (rows i R .. i R + 127 of the stacked
+// slices; rows past R are the next slice's, and their TMEM lanes are not read) with X slice j adds into
+// accumulator 0 for (0, 0), 1 for (0, 1), 2 for (1, 0) and 1 + i + j for the levels i + j >= 2.  Products
+// of a level-k pair are multiples of 2^(-8k) below 2^(15-8k): the three accumulators of one pair each
+// stay exact for K <= 511 (85 sites) -- a round is 64 sites -- while a level-k >= 2 sum of up to five
+// pairs may round at 2^(-8k-7) of its scale, below 2^-36 of the level-0 sum.
+constexpr int kLevelAccs = 7;
+constexpr int kLevelRoundSites = 64;
+__host__ __device__ constexpr int level_acc(int i, int j) {
+    return i + j >= 2 ? 1 + i + j : (i == 0 ? j : 2);
+}
 constexpr int kRangeSitesDefault = 512;            // sites per CTA (one grid, one partial) unless tuned
 constexpr int kMaxCfg = 64;                        // configurations per launch
 constexpr int kSpinLimit = 1 << 22;                // mbarrier polls before giving up
@@ -89,27 +99,21 @@ struct CfgPtrs {
 };
 
 // Compile-time shape of a table family: NC colours chi, NS spins, NT columns
-// per MMA (multiple of 16), NMT M tiles, NX sites per operand chunk, MR staged
-// rows of S at most (both flavours), EP floats per staged (row, colour) run of
-// NX sites (NX plus padding that spreads the diquark loads over the banks).
-template <int NC_, int NS_, int NT_, int NMT_, int NX_, int MR_, int EP_> struct Shape {
-    static constexpr int NC = NC_, NS = NS_, NT = NT_, NMT = NMT_, NX = NX_, MR = MR_, EP = EP_;
+// per MMA (multiple of 16), NMT M tiles, NX sites per operand chunk.
+// LV_ = 1: one TMEM accumulator per slice level instead of per M tile and X slice (see LEVEL_ACCS).
+template <int NC_, int NS_, int NT_, int NMT_, int NX_, int LV_ = 0> struct Shape {
+    static constexpr int NC = NC_, NS = NS_, NT = NT_, NMT = NMT_, NX = NX_, LEVELS = LV_;
     static constexpr int KC = NX * kKa * 2;                 // K per chunk
-    static constexpr int CHUNKS_PER_ROUND = kRoundSites / NX;
+    static constexpr int CHUNKS_PER_ROUND = (LEVELS ? kLevelRoundSites : kRoundSites) / NX;
     static constexpr int NC2 = NC * NC;
     static constexpr int R = 2 * NS * NC;                   // real rows per U slice
     static constexpr int NCTA = NT >= NC2 ? NC2 : NT;       // (c2, c3) columns per CTA
     static constexpr int NCT = (NC2 + NT - 1) / NT;         // column tiles
-    static constexpr int PER_TILE = 4 / NMT;                // warps of a lane quarter per M tile
-    static constexpr int CW = NT / PER_TILE;                // readout columns per thread
+    static constexpr int PER_TILE = LEVELS ? 1 : 4 / NMT;   // warps of a lane quarter per M tile
+    static constexpr int CW = LEVELS ? NT / 4 : NT / PER_TILE;   // readout columns per thread
     static constexpr int NSP = NX / 2;                      // site pairs per chunk
-    static constexpr int PS = MR * NC * EP;                 // floats per staged plane (re or im)
-    static constexpr int STAGERS = MR * NC * NX / 8;        // staging threads: one site, 8 (row, colour) runs each
-    static constexpr int SGROUPS = STAGERS / NX;            // stagers per site
-    // scan copies per thread and chunk: NX sites of MR * NC runs over the scanning threads
-    static constexpr int SCAN_PARTS = kThr / (MR * NC) > 0 ? kThr / (MR * NC) : 1;
-    static constexpr int SPC = (NX + SCAN_PARTS - 1) / SCAN_PARTS;
-    static constexpr int SCANNERS = MR * NC * SCAN_PARTS <= kThr ? MR * NC * SCAN_PARTS : kThr;
+    static constexpr int PS = kMaxRows * NC * NX;           // floats per staged plane (re or im)
+    static constexpr int STAGERS = kMaxRows * NC * NX / 8;   // staging threads: one (row, colour), 8 sites each
     static constexpr int NXJOB = NCTA * kKa * NSP;          // two X values (a site pair) each
     static constexpr int NUJOB = NS * NC * kKa * NSP;       // two U values (a site pair) each
     // rotation of the thread -> job map in round r: the last round goes to the threads whose earlier
@@ -125,38 +129,27 @@ template <int NC_, int NS_, int NT_, int NMT_, int NX_, int MR_, int EP_> struct
         for (int u = 0; u < t; ++u) c += jmax(u) * NT;
         return c + j * NT;
     }
-    static constexpr int TMEM_USED = toff(NMT - 1, 0) + jmax(NMT - 1) * NT;
+    static constexpr int TMEM_USED = LEVELS ? kLevelAccs * NT : toff(NMT - 1, 0) + jmax(NMT - 1) * NT;
     static constexpr int TMEM_COLS = TMEM_USED <= 32 ? 32 : TMEM_USED <= 64 ? 64 : TMEM_USED <= 128 ? 128
                                    : TMEM_USED <= 256 ? 256 : 512;
     static constexpr int A_BYTES = NMT * 128 * KC * 2;
     static constexpr int B_BYTES = kSlicesX * NT * KC * 2;
     static constexpr int S_BYTES = 2 * PS * 4;              // two float planes
-    static constexpr int SCAN_BYTES = (2 * SPC + 1) * SCANNERS * 8;   // two scan slots and the running maxima
-    // the kernel's carve-up of its dynamic shared memory, in order: operand buffers, staging planes, scan
-    // slots and maxima, sEU[16], sF[256], sTerm (int4 x kKa kListLen), sTermN (8 B x kKa kListLen),
-    // sR1[16], sSrc[kMaxRows * 12], mbar[2] (8 B each), tslot (4 B)
-    static constexpr int OFF_SCAN = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES;
-    static constexpr int OFF_EU = OFF_SCAN + SCAN_BYTES;
-    static constexpr int OFF_TERM = OFF_EU + 4 * (16 + 256);
-    static constexpr int OFF_MBAR = OFF_TERM + (16 + 8) * kKa * kListLen + 4 * 16 + 4 * kMaxRows * 12;
-    static constexpr int LAYOUT_END = OFF_MBAR + 2 * 8 + 4;
-    static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES + SCAN_BYTES + 4 * (16 + 256) +
+    static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES + 4 * (16 + 256) +
                                 (16 + 8) * kKa * kListLen + 4 * 16 + 4 * kMaxRows * 12 + 32;
     static_assert(NMT * 128 >= kSlices * R && (NMT - 1) * 128 < kSlices * R, "M tiles");
+    static_assert(!LEVELS || ((kSlices - 1) * R + 128 <= NMT * 128 && R <= 96 && R % 8 == 0), "level tiles");
     static_assert(NC2 <= NT || NC2 % NT == 0, "column tiles");
     static_assert(TMEM_USED <= 512 && CW % 4 == 0 && CW <= 32, "TMEM / readout");
     static_assert(NXJOB % 32 == 0 && NUJOB % 32 == 0, "jobs fill whole warps");
     static_assert(NX % 8 == 0, "site pairs in groups of 4 per warp");
-    static_assert(STAGERS <= kThr && STAGERS % NX == 0 && MR <= kMaxRows && EP >= NX && EP % 2 == 0,
-                  "staging threads / layout");
+    static_assert(STAGERS <= kThr, "staging threads");
     static_assert(R % 8 == 0, "U slices start on a core-matrix row group");
-    static_assert(kSlices * R * NT * 8 <= 2 * (A_BYTES + B_BYTES), "combine buffer");
+    static_assert(LEVELS || kSlices * R * NT * 8 <= 2 * (A_BYTES + B_BYTES), "combine buffer");
     static_assert(SMEM <= 227 * 1024, "shared memory");
-    static_assert(LAYOUT_END <= SMEM && OFF_TERM % 16 == 0 && OFF_MBAR % 8 == 0 && OFF_SCAN % 16 == 0,
-                  "shared-memory carve-up");
 };
-using UpperShape = Shape<6, 2, 48, 1, 16, 12, 20>;   // nucleon upper spin components: 2 x 216 per type
-using FullShape = Shape<12, 4, 16, 4, 8, 24, 8>;     // all four spins: 4 x 1728 per type
+using UpperShape = Shape<6, 2, 48, 1, 16>;   // nucleon upper spin components: 2 x 216 per type
+using FullShape = Shape<12, 4, 48, 4, 8, 1>; // all four spins: 4 x 1728 per type, level accumulators
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -370,14 +363,14 @@ __device__ __forceinline__ Job make_job(int jb, int col0, int n_a, const int *sF
         job_map<SH::NCTA, SH::NSP>(jb, n, a, sp);
         if (a >= n_a) return j;
         const int c23 = col0 + n;
-        j = {1, a, (c23 / NC) * SH::EP + 2 * sp, (c23 % NC) * SH::EP + 2 * sp, tile_off<KC>(n, a * 2 * NX + 2 * sp), 0,
+        j = {1, a, (c23 / NC) * NX + 2 * sp, (c23 % NC) * NX + 2 * sp, tile_off<KC>(n, a * 2 * NX + 2 * sp), 0,
              exp2i(7 - sF[n])};
     } else if (jb < SH::NXJOB + SH::NUJOB) {
         int m, a, sp;
         job_map<NS * NC, SH::NSP>(jb - SH::NXJOB, m, a, sp);
         if (a >= n_a) return j;
         const int s = m / NC, c1 = m % NC;
-        j = {2, a, sR1[s * kKa + a] + c1 * SH::EP + 2 * sp, 0, tile_off<KC>(m, a * 2 * NX + 2 * sp),
+        j = {2, a, sR1[s * kKa + a] + c1 * NX + 2 * sp, 0, tile_off<KC>(m, a * 2 * NX + 2 * sp),
              tile_off<KC>(NS * NC + m, a * 2 * NX + 2 * sp), exp2i(7 - sEU[c1])};
     }
     return j;
@@ -432,24 +425,43 @@ __device__ __forceinline__ void range_bounds(const BlockPlan &plan, const ST *su
     if (tid < 48) smax[tid] = 0u;
     __syncthreads();
     const int nc = plan.n_chi, nr0 = plan.n_rows[0], nr = nr0 + plan.n_rows[1];
-    const int cols = nr * nc;
+    // the kept columns in adjacent pairs (chi, chi + 1), as in the upper- and full-spin layouts: one
+    // 16-byte load covers a pair of complex64 values (half the loads in flight per byte)
+    bool pairs = sizeof(ST) == 8 && nc % 2 == 0;
+    for (int i = 0; pairs && i < nc; i += 2) pairs = plan.chi[i] % 2 == 0 && plan.chi[i + 1] == plan.chi[i] + 1;
+    const int per = pairs ? 2 : 1;                 // columns per load
+    const int cols = nr * (nc / per);
     const int parts = max(1, (int)blockDim.x / cols);
     if (tid < cols * parts) {
         const int col = tid % cols, part = tid / cols;
-        const int rc = col / nc, ic = col % nc;
+        const int rc = col / (nc / per), ic = (col % (nc / per)) * per;
         const int f = rc < nr0 ? 0 : 1;
         const int row = f == 0 ? plan.rows[0][rc] : plan.rows[1][rc - nr0];
         const ST *src = (f == 0 ? su : sd) + row * 12 + plan.chi[ic];
-        float m1 = 0.f, m2 = 0.f;
+        float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;   // columns ic and ic + 1
+        if (pairs) {
+#pragma unroll 12
+            for (int x = x_begin + part; x < x_end; x += parts) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(src + (size_t)x * 144));
+                a1 = fmaxf(a1, fmaxf(fabsf(v.x), fabsf(v.y)));
+                a2 = fmaxf(a2, __fadd_ru(fabsf(v.x), fabsf(v.y)));   // rounded up: a bound of |re| + |im|
+                b1 = fmaxf(b1, fmaxf(fabsf(v.z), fabsf(v.w)));
+                b2 = fmaxf(b2, __fadd_ru(fabsf(v.z), fabsf(v.w)));
+            }
+        } else {
 #pragma unroll 8
-        for (int x = x_begin + part; x < x_end; x += parts) {
-            const float2 v = to_f2(src[(size_t)x * 144]);
-            const float ax = fabsf(v.x), ay = fabsf(v.y);
-            m1 = fmaxf(m1, fmaxf(ax, ay));
-            m2 = fmaxf(m2, __fadd_ru(ax, ay));  // rounded up: still a bound of |re| + |im|
+            for (int x = x_begin + part; x < x_end; x += parts) {
+                const float2 v = to_f2(src[(size_t)x * 144]);
+                a1 = fmaxf(a1, fmaxf(fabsf(v.x), fabsf(v.y)));
+                a2 = fmaxf(a2, __fadd_ru(fabsf(v.x), fabsf(v.y)));
+            }
         }
-        atomicMax(&smax[f * 24 + ic], __float_as_uint(m1));
-        atomicMax(&smax[f * 24 + 12 + ic], __float_as_uint(m2));
+        atomicMax(&smax[f * 24 + ic], __float_as_uint(a1));
+        atomicMax(&smax[f * 24 + 12 + ic], __float_as_uint(a2));
+        if (pairs) {
+            atomicMax(&smax[f * 24 + ic + 1], __float_as_uint(b1));
+            atomicMax(&smax[f * 24 + 12 + ic + 1], __float_as_uint(b2));
+        }
     }
     __syncthreads();
     if (tid < 48) {
@@ -495,48 +507,35 @@ __device__ __forceinline__ void arrive_and_reduce(const BlockPlan &plan, int cs,
     if (tid == 0) *cnt = 0;
 }
 
-// One work item: (configuration x slice cs, site range rng, block type o, column tile ct); the items
-// of one (cs, rng) are adjacent, so CTAs that read the same rows of S run at the same time.
-struct Item {
-    int cs, rng, o, ct;
-};
-
-__device__ __forceinline__ Item decode_item(int i, int n_ops, int nct, int n_ranges) {
-    const int oc = i % (n_ops * nct), rest = i / (n_ops * nct);
-    return {rest / n_ranges, rest % n_ranges, oc / nct, oc % nct};
-}
-
-// 8-byte copy (both components of a complex64 value); src_bytes 0 writes zeros
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-
-// The CTAs are persistent: CTA b takes the items b, b + gridDim.x, ...  The grid exponents of an item
-// are scanned while the CTA works on the one before it: in chunk c the scanning threads copy (cp.async,
-// in the chunk's staging group) the values at the same site positions of the next item's range into a
-// slot of shared memory, and fold them into per-thread maxima one chunk later.  Only a CTA's first item
-// is scanned in a prologue.
 template <typename ST, typename SH>
 __global__ void __launch_bounds__(kThr, 1)
 block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ CfgPtrs cfgp, int V, int n_slices,
-                int n_ranges, int range_sites, int n_items, const WeightExp ew, double2 *__restrict__ partials,
+                int n_ranges, int range_sites, const WeightExp ew, double2 *__restrict__ partials,
                 int *__restrict__ counters, double2 *__restrict__ blocks, int *status) {
     constexpr int NC = SH::NC, NS = SH::NS, NT = SH::NT, R = SH::R, NCTA = SH::NCTA;
-    constexpr int NX = SH::NX, KC = SH::KC, PS = SH::PS, SPC = SH::SPC;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ unsigned s_max[48];
     __shared__ int s_bnd[48];
     __shared__ int s_last;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the CTAs of one (slice, range) are adjacent in the grid: they read the same rows of S (L2 reuse)
+    const int o = blockIdx.x / SH::NCT, ct = blockIdx.x % SH::NCT;
+    const int rng = blockIdx.y, cs = blockIdx.z;             // cs = configuration * n_slices + slice
+    const int cfg = cs / n_slices, slice = cs - cfg * n_slices;
+    const ST *Su = static_cast<const ST *>(cfgp.su[cfg]);
+    const ST *Sd = static_cast<const ST *>(cfgp.sd[cfg]);
     const int nr0 = plan.n_rows[0], nr = nr0 + plan.n_rows[1];
+    const int f1 = plan.f1[o];
+    const int col0 = ct * NT;
+    const int t0 = plan.os_off[o * NS];
+    const int n_a = plan.os_off[o * NS + 1] - t0;
+    constexpr int NX = SH::NX, KC = SH::KC, PS = SH::PS;
+    const int rc1 = f1 == 0 ? 0 : nr0, rc2 = f1 == 0 ? nr0 : 0;  // first staged row of either flavour
 
     __nv_bfloat16 *sA0 = reinterpret_cast<__nv_bfloat16 *>(smem);
     __nv_bfloat16 *sB0 = reinterpret_cast<__nv_bfloat16 *>(smem + 2 * SH::A_BYTES);
     float *sS0 = reinterpret_cast<float *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES));
-    float2 *sScan = reinterpret_cast<float2 *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES) + kStage * SH::S_BYTES);
-    float2 *sScanMax = sScan + 2 * SPC * SH::SCANNERS;       // [SCANNERS] running (max |.|, max |re| + |im|)
-    int *sEU = reinterpret_cast<int *>(sScanMax + SH::SCANNERS);
+    int *sEU = reinterpret_cast<int *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES) + kStage * SH::S_BYTES);
     int *sF = sEU + 16;                                       // [256] grid of X per column
     int4 *sTerm = reinterpret_cast<int4 *>(sF + 256);         // [kKa][kListLen] the op's diquark list terms
     f2x *sTermN = reinterpret_cast<f2x *>(sTerm + kKa * kListLen);  // [kKa][kListLen] (-w, -w)
@@ -544,15 +543,40 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
     int *sSrc = sR1 + 16;                                     // [kMaxRows * NC] flavour << 16 | row * 12 + chi
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sSrc + kMaxRows * 12);   // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
-    // the carve-up above must match the Shape's (checked there against SMEM)
-    if (reinterpret_cast<unsigned char *>(sScan) != smem + SH::OFF_SCAN ||
-        reinterpret_cast<unsigned char *>(sEU) != smem + SH::OFF_EU ||
-        reinterpret_cast<unsigned char *>(sTerm) != smem + SH::OFF_TERM ||
-        reinterpret_cast<unsigned char *>(mbar) != smem + SH::OFF_MBAR) {
-        if (tid == 0) atomicCAS(status, 0, WICK_EINVAL);
-        return;
-    }
 
+    // zero both operand buffers once: padding rows and unused colour terms stay zero
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(smem);
+        for (int e = tid; e < 2 * (SH::A_BYTES + SH::B_BYTES) / 16; e += kThr) z[e] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const int x_begin = rng * range_sites, x_end = min(V, x_begin + range_sites);
+    const int n_chunks = (x_end - x_begin + NX - 1) / NX;
+    const ST *su = Su + (size_t)slice * V * 144;
+    const ST *sd = Sd + (size_t)slice * V * 144;
+    range_bounds<ST>(plan, su, sd, x_begin, x_end, s_max, s_bnd);
+    const int *bnd = s_bnd;
+    if (tid < NC) sEU[tid] = bnd[f1 * 24 + tid];
+    if (tid < NT) {
+        const int c23 = col0 + tid;
+        sF[tid] = tid < NCTA ? bnd[f1 * 24 + 12 + c23 / NC] + bnd[(1 - f1) * 24 + 12 + c23 % NC] + ew.e[o] : 0;
+    }
+    if (tid < kKa * kListLen) {
+        const int a = tid / kListLen, t = tid % kListLen;
+        int4 v = make_int4(0, 0, 0, 0);
+        float w = 0.f;
+        if (a < n_a) {
+            const int q = plan.x_off[plan.os_x[t0 + a]] + t;
+            w = plan.xt_w[q];
+            v = make_int4((rc1 + plan.xt_r2[q]) * NC * NX, (rc2 + plan.xt_r3[q]) * NC * NX, __float_as_int(w),
+                          __float_as_int(w));
+        }
+        sTerm[tid] = v;
+        sTermN[tid] = pk(-w, -w);
+    }
+    if (tid >= 32 && tid < 32 + NS * kKa) {
+        const int s = (tid - 32) / kKa, a = (tid - 32) % kKa;
+        sR1[s * kKa + a] = a < n_a ? (rc1 + plan.os_r1[plan.os_off[o * NS + s] + a]) * NC * NX : 0;
+    }
     for (int e = tid; e < nr * NC; e += kThr) {
         const int rc = e / NC, ic = e - rc * NC;
         const int f = rc < nr0 ? 0 : 1;
@@ -569,30 +593,47 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
                      "r"(SH::TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    int item = blockIdx.x;
-    if (item < n_items) {   // the first item's grid exponents: a prologue scan
-        const Item it = decode_item(item, plan.n_ops, SH::NCT, n_ranges);
-        const int cfg = it.cs / n_slices, slice = it.cs - cfg * n_slices;
-        const size_t so = (size_t)slice * V * 144;
-        const int xb = it.rng * range_sites;
-        range_bounds<ST>(plan, static_cast<const ST *>(cfgp.su[cfg]) + so, static_cast<const ST *>(cfgp.sd[cfg]) + so,
-                         xb, min(V, xb + range_sites), s_max, s_bnd);
+
+    __syncthreads();   // sSrc
+    // stage the rows of chunk c as two planes (re, im) of [row][ic][site], flavour-0 rows first, sites
+    // innermost (zeros past the range).  The last STAGERS threads (the warps with the lightest jobs)
+    // each copy one (row, colour) for 8 consecutive sites, from offsets computed once.
+    const int st_t = tid - (kThr - SH::STAGERS);
+    const int st_rcc = st_t >= 0 ? st_t / (NX / 8) : 0, st_part = st_t >= 0 ? st_t % (NX / 8) : 0;
+    const bool stager = st_t >= 0 && st_rcc < nr * NC;
+    const ST *st_src = su;
+    if (stager) {
+        const int src_off = sSrc[st_rcc];
+        st_src = ((src_off >> 16) ? sd : su) + (src_off & 0xFFFF);
     }
+    auto stage = [&](int c) {
+        if (stager) {
+            float *dst = sS0 + (c % kStage) * (2 * PS) + st_rcc * NX + st_part * 8;
+            const int xb = x_begin + c * NX + st_part * 8;
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8) {
+                const bool in = xb + s8 < x_end;
+                const ST *src = st_src + (size_t)(in ? xb + s8 : x_begin) * 144;
+                if constexpr (sizeof(ST) == 8) {
+                    cp_async4(dst + s8, reinterpret_cast<const float *>(src), in ? 4 : 0);
+                    cp_async4(dst + s8 + PS, reinterpret_cast<const float *>(src) + 1, in ? 4 : 0);
+                } else {
+                    const float2 v = in ? to_f2(*src) : make_float2(0.f, 0.f);
+                    dst[s8] = v.x;
+                    dst[s8 + PS] = v.y;
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    stage(0);
+    cp_async_wait_all();
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tbase = *tslot;
+    if (n_chunks > 1) stage(1);
 
-    // staging threads: the last STAGERS threads, one site of the chunk and 8 (row, colour) runs each (a
-    // warp's copies land on consecutive words of the planes: no bank conflicts)
-    const int st_t = tid - (kThr - SH::STAGERS);
-    const bool stager = st_t >= 0;
-    const int st_site = stager ? st_t % NX : 0, st_g = stager ? st_t / NX : 0;
-    const int n_runs = nr * NC;
-    // scanning threads: run sc_col (row, colour), sites sc_part + sc_parts * k of each chunk's block
-    constexpr int sc_parts = SH::SCAN_PARTS;
-    const bool scanner = tid < n_runs * sc_parts;   // <= SCANNERS
-    const int sc_col = scanner ? tid % n_runs : 0, sc_part = scanner ? tid / n_runs : 0;
     // readout ownership: lane quarter q of M tile t_own, column part cpart of the tile's columns
     const int q = warp & 3, g = warp >> 2;
     const int t_own = g / SH::PER_TILE, cpart = g % SH::PER_TILE;
@@ -605,322 +646,224 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
     for (int t = 0; t < SH::NMT; ++t)
         if (t == t_own) jmax_own = SH::jmax(t);
     const int j_warp = min(kMaxPair - i_warp, jmax_own - 1);
+    df acc[SH::CW];
+#pragma unroll
+    for (int n = 0; n < SH::CW; ++n) acc[n] = {0.f, 0.f};
+
+    // one job per thread and round: X jobs first, then U jobs; both fill whole warps, so every branch
+    // is warp-uniform.  The last round goes to the threads that took U jobs before.
     constexpr int NR = (SH::NXJOB + SH::NUJOB + kThr - 1) / kThr;
+    Job job[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+        job[r] = make_job<SH>(r * kThr + (tid + kThr - SH::rot(r)) % kThr, col0, n_a, sF, sR1, sEU);
+
     constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
     int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0, bad = 0;
 
-    for (; item < n_items && !bad; item += gridDim.x) {
-        const Item it = decode_item(item, plan.n_ops, SH::NCT, n_ranges);
-        const int o = it.o, rng = it.rng, cs = it.cs;
-        const int cfg = cs / n_slices, slice = cs - cfg * n_slices;
-        const ST *su = static_cast<const ST *>(cfgp.su[cfg]) + (size_t)slice * V * 144;
-        const ST *sd = static_cast<const ST *>(cfgp.sd[cfg]) + (size_t)slice * V * 144;
-        const int f1 = plan.f1[o];
-        const int col0 = it.ct * NT;
-        const int t0 = plan.os_off[o * NS];
-        const int n_a = plan.os_off[o * NS + 1] - t0;
-        const int rc1 = f1 == 0 ? 0 : nr0, rc2 = f1 == 0 ? nr0 : 0;  // first staged row of either flavour
-        const int x_begin = rng * range_sites, x_end = min(V, x_begin + range_sites);
-        const int n_chunks = (x_end - x_begin + NX - 1) / NX;
-        // the next item of this CTA, whose grid exponents this item's chunks scan
-        const int nitem = item + gridDim.x;
-        const bool has_next = nitem < n_items;
-        const ST *nsu = su, *nsd = sd;
-        int nx_begin = 0, nx_end = 0;
-        if (has_next) {
-            const Item nt = decode_item(nitem, plan.n_ops, SH::NCT, n_ranges);
-            const int ncfg = nt.cs / n_slices, nslice = nt.cs - ncfg * n_slices;
-            nsu = static_cast<const ST *>(cfgp.su[ncfg]) + (size_t)nslice * V * 144;
-            nsd = static_cast<const ST *>(cfgp.sd[ncfg]) + (size_t)nslice * V * 144;
-            nx_begin = nt.rng * range_sites;
-            nx_end = min(V, nx_begin + range_sites);
+    for (int c = 0; c < n_chunks; ++c) {
+        const int buf = c & 1;
+        __nv_bfloat16 *A = sA0 + buf * (SH::A_BYTES / 2);
+        __nv_bfloat16 *B = sB0 + buf * (SH::B_BYTES / 2);
+        const float *S = sS0 + (c % kStage) * (2 * PS);
+        // the MMAs of chunk c - 2 read this operand buffer
+        if (buf == 0 && waited0 < issued0) {
+            if (poll_parity(&mbar[0], waited0 & 1)) ++waited0;
+            else bad = 1;
+        } else if (buf == 1 && waited1 < issued1) {
+            if (poll_parity(&mbar[1], waited1 & 1)) ++waited1;
+            else bad = 1;
         }
-        const ST *sc_src = su;
-        if (scanner) {
-            const int so = sSrc[sc_col];
-            sc_src = ((so >> 16) ? nsd : nsu) + (so & 0xFFFF);
-        }
-
-        // zero both operand buffers: padding rows and unused colour terms stay zero
-        {
-            uint4 *z = reinterpret_cast<uint4 *>(smem);
-            for (int e = tid; e < 2 * (SH::A_BYTES + SH::B_BYTES) / 16; e += kThr) z[e] = make_uint4(0u, 0u, 0u, 0u);
-        }
-        const int *bnd = s_bnd;
-        if (tid < NC) sEU[tid] = bnd[f1 * 24 + tid];
-        if (tid < NT) {
-            const int c23 = col0 + tid;
-            sF[tid] = tid < NCTA ? bnd[f1 * 24 + 12 + c23 / NC] + bnd[(1 - f1) * 24 + 12 + c23 % NC] + ew.e[o] : 0;
-        }
-        if (tid < kKa * kListLen) {
-            const int a = tid / kListLen, t = tid % kListLen;
-            int4 v = make_int4(0, 0, 0, 0);
-            float w = 0.f;
-            if (a < n_a) {
-                const int qq = plan.x_off[plan.os_x[t0 + a]] + t;
-                w = plan.xt_w[qq];
-                v = make_int4((rc1 + plan.xt_r2[qq]) * NC * SH::EP, (rc2 + plan.xt_r3[qq]) * NC * SH::EP,
-                              __float_as_int(w), __float_as_int(w));
-            }
-            sTerm[tid] = v;
-            sTermN[tid] = pk(-w, -w);
-        }
-        if (tid >= 32 && tid < 32 + NS * kKa) {
-            const int s_ = (tid - 32) / kKa, a = (tid - 32) % kKa;
-            sR1[s_ * kKa + a] = a < n_a ? (rc1 + plan.os_r1[plan.os_off[o * NS + s_] + a]) * NC * SH::EP : 0;
-        }
-        if (tid < SH::SCANNERS) sScanMax[tid] = make_float2(0.f, 0.f);
-        __syncthreads();   // grids, tables; s_bnd consumed
-        if (tid < 48) s_max[tid] = 0u;
-
-        auto stage = [&](int c) {
-            if (stager) {
-                float *plane = sS0 + (c % kStage) * (2 * PS);
-                const int x = x_begin + c * NX + st_site;
-                const bool in = x < x_end;
-                const size_t xo = (size_t)(in ? x : x_begin) * 144;
+        if (!bad) {
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int e = st_g + SH::SGROUPS * k;
-                    if (e < n_runs) {
-                        const int src_off = sSrc[e];
-                        const ST *src = ((src_off >> 16) ? sd : su) + (src_off & 0xFFFF) + xo;
-                        float *dst = plane + e * SH::EP + st_site;
-                        if constexpr (sizeof(ST) == 8) {
-                            cp_async4(dst, reinterpret_cast<const float *>(src), in ? 4 : 0);
-                            cp_async4(dst + PS, reinterpret_cast<const float *>(src) + 1, in ? 4 : 0);
-                        } else {
-                            const float2 v = in ? to_f2(*src) : make_float2(0.f, 0.f);
-                            dst[0] = v.x;
-                            dst[PS] = v.y;
-                        }
-                    }
-                }
+            for (int r = 0; r < NR; ++r) {
+                if (job[r].kind == 1) x_job<SH>(job[r], sTerm, sTermN, S, B);
+                else if (job[r].kind == 2) u_job<SH>(job[r], S, A);
             }
-        };
-        // the next item's values at the site positions of chunk c, into scan slot c & 1
-        auto scan_copy = [&](int c) {
-            if (scanner && has_next) {
-                float2 *slot = sScan + (c & 1) * SPC * SH::SCANNERS;
-#pragma unroll
-                for (int k = 0; k < SPC; ++k) {
-                    const int xs = c * NX + sc_part + sc_parts * k;
-                    const int x = nx_begin + xs;
-                    const bool in = xs < NX * (c + 1) && x < nx_end;
-                    const ST *src = sc_src + (size_t)(in ? x : nx_begin) * 144;
-                    if constexpr (sizeof(ST) == 8) {
-                        cp_async8(slot + k * SH::SCANNERS + tid, src, in ? 8 : 0);
-                    } else {
-                        slot[k * SH::SCANNERS + tid] = in ? to_f2(*src) : make_float2(0.f, 0.f);
-                    }
-                }
-            }
-        };
-        // fold scan slot c & 1 (this thread's own copies, complete after its cp.async wait)
-        auto scan_fold = [&](int c) {
-            if (scanner && has_next) {
-                const float2 *slot = sScan + (c & 1) * SPC * SH::SCANNERS;
-                float2 m = sScanMax[tid];
-#pragma unroll
-                for (int k = 0; k < SPC; ++k) {
-                    const float2 v = slot[k * SH::SCANNERS + tid];
-                    const float ax = fabsf(v.x), ay = fabsf(v.y);
-                    m.x = fmaxf(m.x, fmaxf(ax, ay));
-                    m.y = fmaxf(m.y, __fadd_ru(ax, ay));
-                }
-                sScanMax[tid] = m;
-            }
-        };
-
-        stage(0);
-        cp_async_commit();
+        }
+        // staged rows of chunk c + 1 complete (this thread's copies); operands of chunk c written
         cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+        if (__syncthreads_or(bad)) {
+            bad = 1;
+            break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (n_chunks > 1) stage(1);
-        cp_async_commit();
-
-        df acc[SH::CW];
+        const bool fresh = c % SH::CHUNKS_PER_ROUND == 0;
+        if (SH::LEVELS && tid == kThr - 1) {
+            const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
 #pragma unroll
-        for (int n = 0; n < SH::CW; ++n) acc[n] = {0.f, 0.f};
-        // one job per thread and round: X jobs first, then U jobs; both fill whole warps, so every branch
-        // is warp-uniform.  The last round goes to the threads that took U jobs before.
-        Job job[NR];
+            for (int ks = 0; ks < KC / 16; ++ks)
 #pragma unroll
-        for (int r = 0; r < NR; ++r)
-            job[r] = make_job<SH>(r * kThr + (tid + kThr - SH::rot(r)) % kThr, col0, n_a, sF, sR1, sEU);
+                for (int i = 0; i < kSlices; ++i) {
+                    const uint64_t da = smem_desc<KC>(a0 + (uint32_t)(i * R * KC * 2 + ks * 256));
+#pragma unroll
+                    for (int j = 0; j < kSlicesX && i + j <= kMaxPair; ++j) {
+                        const uint64_t db = smem_desc<KC>(b0 + (uint32_t)(j * NT * KC * 2 + ks * 256));
+                        const int ac = level_acc(i, j);
+                        const uint32_t acc_in = (fresh && ks == 0 && (i == 0 || ac == 2)) ? 0u : 1u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                                tbase + (uint32_t)(ac * NT)),
+                            "l"(da), "l"(db), "r"(idesc), "r"(acc_in));
+                    }
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar[buf])));
+        }
+        if (!SH::LEVELS && tid == kThr - 1) {  // the last warp has the fewest jobs
+            const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+#pragma unroll
+            for (int ks = 0; ks < KC / 16; ++ks)
+#pragma unroll
+                for (int t = 0; t < SH::NMT; ++t) {
+                    const uint64_t da = smem_desc<KC>(a0 + (uint32_t)(t * 128 * KC * 2 + ks * 256));
+#pragma unroll
+                    for (int j = 0; j < SH::jmax(t); ++j) {
+                        const uint64_t db = smem_desc<KC>(b0 + (uint32_t)(j * NT * KC * 2 + ks * 256));
+                        const uint32_t acc_in = (fresh && ks == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                                tbase + (uint32_t)SH::toff(t, j)),
+                            "l"(da), "l"(db), "r"(idesc), "r"(acc_in));
+                    }
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar[buf])));
+        }
+        if (buf) ++issued1;
+        else ++issued0;
+        // stage chunk c + 2 into the buffer chunk c - 1 was built from
+        if (c + 2 < n_chunks) stage(c + 2);
 
-        for (int c = 0; c < n_chunks; ++c) {
-            const int buf = c & 1;
-            __nv_bfloat16 *A = sA0 + buf * (SH::A_BYTES / 2);
-            __nv_bfloat16 *B = sB0 + buf * (SH::B_BYTES / 2);
-            const float *S = sS0 + (c % kStage) * (2 * PS);
-            // the MMAs of chunk c - 2 read this operand buffer
-            if (buf == 0 && waited0 < issued0) {
+        // end of a round: read the accumulators out of TMEM
+        if (c % SH::CHUNKS_PER_ROUND == SH::CHUNKS_PER_ROUND - 1 || c == n_chunks - 1) {
+            if (waited0 < issued0) {
                 if (poll_parity(&mbar[0], waited0 & 1)) ++waited0;
                 else bad = 1;
-            } else if (buf == 1 && waited1 < issued1) {
+            }
+            if (waited1 < issued1) {
                 if (poll_parity(&mbar[1], waited1 & 1)) ++waited1;
                 else bad = 1;
             }
-            if (!bad) {
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    if (job[r].kind == 1) x_job<SH>(job[r], sTerm, sTermN, S, B);
-                    else if (job[r].kind == 2) u_job<SH>(job[r], S, A);
-                }
-            }
-            // staged rows of chunk c + 1 and the scan copies of chunk c - 1 complete (this thread's copies);
-            // operands of chunk c written
-            cp_async_wait_all();
-            if (c > 0) scan_fold(c - 1);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;");
             if (__syncthreads_or(bad)) {
                 bad = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const bool fresh = c % SH::CHUNKS_PER_ROUND == 0;
-            if (tid == kThr - 1) {  // the last warp has the fewest jobs
-                const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+            if constexpr (SH::LEVELS) {
+                if (q < 3) {   // lanes 96..127 hold rows of the next slice: not read
 #pragma unroll
-                for (int ks = 0; ks < KC / 16; ++ks)
+                    for (int ac = 0; ac < kLevelAccs; ++ac) {
+                        uint32_t r[SH::CW];
+                        const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(ac * NT + cpart * SH::CW);
 #pragma unroll
-                    for (int t = 0; t < SH::NMT; ++t) {
-                        const uint64_t da = smem_desc<KC>(a0 + (uint32_t)(t * 128 * KC * 2 + ks * 256));
+                        for (int c4 = 0; c4 < SH::CW; c4 += 4)
+                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                                         : "=r"(r[c4]), "=r"(r[c4 + 1]), "=r"(r[c4 + 2]), "=r"(r[c4 + 3])
+                                         : "r"(taddr + (uint32_t)c4));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-                        for (int j = 0; j < SH::jmax(t); ++j) {
-                            const uint64_t db = smem_desc<KC>(b0 + (uint32_t)(j * NT * KC * 2 + ks * 256));
-                            const uint32_t acc_in = (fresh && ks == 0) ? 0u : 1u;
-                            asm volatile(
-                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-                                    tbase + (uint32_t)SH::toff(t, j)),
-                                "l"(da), "l"(db), "r"(idesc), "r"(acc_in));
+                        for (int n = 0; n < SH::CW; ++n) {
+                            // the exact accumulators join by TwoSum; the small levels (>= 2) join the low part
+                            if (ac < 3) acc_add(acc[n], df{__uint_as_float(r[n]), 0.f});
+                            else acc[n].l = __fadd_rn(acc[n].l, __uint_as_float(r[n]));
                         }
                     }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&mbar[buf])));
-            }
-            if (buf) ++issued1;
-            else ++issued0;
-            // stage chunk c + 2 into the buffer chunk c - 1 was built from; scan the next item at chunk c
-            if (c + 2 < n_chunks) stage(c + 2);
-            scan_copy(c);
-            cp_async_commit();
-
-            // end of a round: read the accumulators out of TMEM
-            if (c % SH::CHUNKS_PER_ROUND == SH::CHUNKS_PER_ROUND - 1 || c == n_chunks - 1) {
-                if (waited0 < issued0) {
-                    if (poll_parity(&mbar[0], waited0 & 1)) ++waited0;
-                    else bad = 1;
                 }
-                if (waited1 < issued1) {
-                    if (poll_parity(&mbar[1], waited1 & 1)) ++waited1;
-                    else bad = 1;
-                }
-                if (__syncthreads_or(bad)) {
-                    bad = 1;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                for (int j = 0; j <= j_warp; ++j) {
-                    uint32_t r[SH::CW];
-                    int toffj = 0;
-#pragma unroll
-                    for (int t = 0; t < SH::NMT; ++t)
-                        if (t == t_own) toffj = SH::toff(t, 0) + j * NT;
-                    const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(toffj + cpart * SH::CW);
-#pragma unroll
-                    for (int c4 = 0; c4 < SH::CW; c4 += 4)
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                                     : "=r"(r[c4]), "=r"(r[c4 + 1]), "=r"(r[c4 + 2]), "=r"(r[c4 + 3])
-                                     : "r"(taddr + (uint32_t)c4));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;");
-                    if (row_ok && my_i + j <= kMaxPair) {
-#pragma unroll
-                        for (int n = 0; n < SH::CW; ++n) acc_add(acc[n], df{__uint_as_float(r[n]), 0.f});
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncthreads();
             }
-        }
-        if (bad) break;
-        cp_async_wait_all();
-        scan_fold(n_chunks - 1);
-
-        // combine the five U-slice rows of every output (double-FP32, relative to 2^(E+F)), then FP64
-        float2 *comb = reinterpret_cast<float2 *>(smem);   // [kSlices * R][NT], reuses the operand buffers
-        if (row_ok)
+            for (int j = 0; !SH::LEVELS && j <= j_warp; ++j) {
+                uint32_t r[SH::CW];
+                int toffj = 0;
 #pragma unroll
-            for (int n = 0; n < SH::CW; ++n) comb[row * NT + cpart * SH::CW + n] = make_float2(acc[n].h, acc[n].l);
-        __syncthreads();
-        double *part = reinterpret_cast<double *>(partials + ((size_t)cs * n_ranges + rng) * plan.n_out);
-        for (int e = tid; e < R * NCTA; e += kThr) {
-            const int rr = e / NCTA, n = e % NCTA;
-            df s_ = {0.f, 0.f};
+                for (int t = 0; t < SH::NMT; ++t)
+                    if (t == t_own) toffj = SH::toff(t, 0) + j * NT;
+                const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(toffj + cpart * SH::CW);
 #pragma unroll
-            for (int i = 0; i < kSlices; ++i) {
-                const float2 v = comb[(i * R + rr) * NT + n];
-                s_ = df_add(s_, df{v.x, v.y});
-            }
-            const int pp = rr / (NS * NC), sc1 = rr % (NS * NC);   // part, (s, c1)
-            const int sp_ = sc1 / NC, c1 = sc1 % NC;
-            const double v = ((double)s_.h + (double)s_.l) * exp2d(sEU[c1] + sF[n] - 14);
-            const size_t out = ((size_t)(o * NS + sp_) * NC + c1) * SH::NC2 + col0 + n;
-            part[2 * out + pp] = v;
-        }
-        arrive_and_reduce<SH>(plan, cs, o, n_ranges, partials, counters, blocks, &s_last);
-
-        // the next item's grid exponents: the chunk scans, plus the sites past this item's chunks (a
-        // shorter range here) read directly
-        if (has_next) {
-            float2 m = scanner ? sScanMax[tid] : make_float2(0.f, 0.f);
-            if (scanner)
-                for (int xs = n_chunks * NX + sc_part; nx_begin + xs < nx_end; xs += sc_parts) {
-                    const float2 v = to_f2(sc_src[(size_t)(nx_begin + xs) * 144]);
-                    const float ax = fabsf(v.x), ay = fabsf(v.y);
-                    m.x = fmaxf(m.x, fmaxf(ax, ay));
-                    m.y = fmaxf(m.y, __fadd_ru(ax, ay));
+                for (int c4 = 0; c4 < SH::CW; c4 += 4)
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                                 : "=r"(r[c4]), "=r"(r[c4 + 1]), "=r"(r[c4 + 2]), "=r"(r[c4 + 3])
+                                 : "r"(taddr + (uint32_t)c4));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (row_ok && my_i + j <= kMaxPair) {
+#pragma unroll
+                    for (int n = 0; n < SH::CW; ++n) acc_add(acc[n], df{__uint_as_float(r[n]), 0.f});
                 }
-            if (scanner) {
-                const int rc = sc_col / NC, ic = sc_col % NC;
-                const int f = rc < nr0 ? 0 : 1;
-                atomicMax(&s_max[f * 24 + ic], __float_as_uint(m.x));
-                atomicMax(&s_max[f * 24 + 12 + ic], __float_as_uint(m.y));
             }
-            __syncthreads();
-            if (tid < 48) {
-                const int ic = tid % 12;
-                s_bnd[tid] = ic < plan.n_chi ? exponent_bound(__uint_as_float(s_max[tid])) : -100;
-            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
         }
     }
 
     if (bad) {
         // a wait ran out; the MMAs may still run: wait (bounded) for their commits before TMEM is freed.
-        // The CTA still arrives for this item and its remaining ones, so that the counts stay whole; the
-        // status word reports the error.
+        // The CTA still arrives below, so that the counts stay whole; the status word reports the error.
         if (tid == 0) atomicCAS(status, 0, WICK_ETIMEOUT);
         if (waited0 < issued0) (void)poll_parity(&mbar[0], waited0 & 1);
         if (waited1 < issued1) (void)poll_parity(&mbar[1], waited1 & 1);
         cp_async_wait_all();
         asm volatile("tcgen05.fence::after_thread_sync;");
         __syncthreads();
-        for (; item < n_items; item += gridDim.x) {
-            const Item it = decode_item(item, plan.n_ops, SH::NCT, n_ranges);
-            arrive_and_reduce<SH>(plan, it.cs, it.o, n_ranges, partials, counters, blocks, &s_last);
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SH::TMEM_COLS));
+        arrive_and_reduce<SH>(plan, cs, o, n_ranges, partials, counters, blocks, &s_last);
+        return;
+    }
+    cp_async_wait_all();
+
+    if constexpr (SH::LEVELS) {
+        // every slice level is in this thread's accumulators: scale and write its row's partials
+        if (q < 3) {
+            double *part = reinterpret_cast<double *>(partials + ((size_t)cs * n_ranges + rng) * plan.n_out);
+            const int rr = q * 32 + lane;                          // < R
+            const int pp = rr / (NS * NC), sc1 = rr % (NS * NC);   // part, (s, c1)
+            const int s_ = sc1 / NC, c1 = sc1 % NC;
+#pragma unroll
+            for (int n0 = 0; n0 < SH::CW; ++n0) {
+                const int n = cpart * SH::CW + n0;
+                const double v = ((double)acc[n0].h + (double)acc[n0].l) * exp2d(sEU[c1] + sF[n] - 14);
+                const size_t out = ((size_t)(o * NS + s_) * NC + c1) * SH::NC2 + col0 + n;
+                part[2 * out + pp] = v;
+            }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SH::TMEM_COLS));
+        arrive_and_reduce<SH>(plan, cs, o, n_ranges, partials, counters, blocks, &s_last);
+        return;
+    }
+    // combine the five U-slice rows of every output (double-FP32, relative to 2^(E+F)), then FP64
+    float2 *comb = reinterpret_cast<float2 *>(smem);   // [kSlices * R][NT], reuses the operand buffers
+    if (row_ok)
+#pragma unroll
+        for (int n = 0; n < SH::CW; ++n) comb[row * NT + cpart * SH::CW + n] = make_float2(acc[n].h, acc[n].l);
+    __syncthreads();
+    double *part = reinterpret_cast<double *>(partials + ((size_t)cs * n_ranges + rng) * plan.n_out);
+    for (int e = tid; e < R * NCTA; e += kThr) {
+        const int rr = e / NCTA, n = e % NCTA;
+        df s = {0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < kSlices; ++i) {
+            const float2 v = comb[(i * R + rr) * NT + n];
+            s = df_add(s, df{v.x, v.y});
+        }
+        const int pp = rr / (NS * NC), sc1 = rr % (NS * NC);   // part, (s, c1)
+        const int s_ = sc1 / NC, c1 = sc1 % NC;
+        const double v = ((double)s.h + (double)s.l) * exp2d(sEU[c1] + sF[n] - 14);
+        const size_t out = ((size_t)(o * NS + s_) * NC + c1) * SH::NC2 + col0 + n;
+        part[2 * out + pp] = v;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SH::TMEM_COLS));
+    arrive_and_reduce<SH>(plan, cs, o, n_ranges, partials, counters, blocks, &s_last);
 }
 
 // Which compiled shape a plan takes (0: none, 1: upper, 2: full): weights
@@ -928,7 +871,6 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
 // same lists for every spin, and at most 12 staged rows per flavour.
 int tc_family(const BlockPlan &plan) {
     if (!plan.pow2_w || plan.n_ops < 1 || plan.n_rows[0] + plan.n_rows[1] > kMaxRows) return 0;
-    const int n_rows = plan.n_rows[0] + plan.n_rows[1];
     const int ns = plan.n_spin;
     for (int o = 0; o < plan.n_ops; ++o) {
         const int b0 = plan.os_off[o * ns];
@@ -945,8 +887,8 @@ int tc_family(const BlockPlan &plan) {
                 if (plan.os_x[t0 + a] != plan.os_x[b0 + a]) return 0;
         }
     }
-    if (plan.n_chi == UpperShape::NC && ns == UpperShape::NS && n_rows <= UpperShape::MR) return 1;
-    if (plan.n_chi == FullShape::NC && ns == FullShape::NS && n_rows <= FullShape::MR) return 2;
+    if (plan.n_chi == UpperShape::NC && ns == UpperShape::NS) return 1;
+    if (plan.n_chi == FullShape::NC && ns == FullShape::NS) return 2;
     return 0;
 }
 
@@ -956,14 +898,9 @@ int launch_shape(const BlockPlan &plan, const CfgPtrs &cp, int n_cfg, int V, int
                  cudaStream_t stream) {
     auto k = block_tc_kernel<ST, SH>;
     WICK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM));
-    const int64_t n_items = (int64_t)plan.n_ops * SH::NCT * n_ranges * n_cfg * n_slices;
-    if (n_items > 2147483647) return WICK_EINVAL;
-    int dev = 0, n_sm = 148;
-    WICK_CUDA_TRY(cudaGetDevice(&dev));
-    WICK_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    const int grid = (int)std::min<int64_t>(n_items, n_sm);   // one CTA per SM (shared memory), persistent
-    k<<<grid, kThr, SH::SMEM, stream>>>(plan, cp, V, n_slices, n_ranges, range_sites, (int)n_items, ew, part, counters,
-                                        blocks, status);
+    dim3 grid(plan.n_ops * SH::NCT, n_ranges, n_cfg * n_slices);
+    k<<<grid, kThr, SH::SMEM, stream>>>(plan, cp, V, n_slices, n_ranges, range_sites, ew, part, counters, blocks,
+                                        status);
     WICK_CUDA_TRY(cudaGetLastError());
     return WICK_OK;
 }
