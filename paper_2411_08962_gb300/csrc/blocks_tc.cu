@@ -109,7 +109,7 @@ template <int NC_, int NS_, int NT_, int NMT_, int NX_, int LV_ = 0> struct Shap
     static constexpr int R = 2 * NS * NC;                   // real rows per U slice
     static constexpr int NCTA = NT >= NC2 ? NC2 : NT;       // (c2, c3) columns per CTA
     static constexpr int NCT = (NC2 + NT - 1) / NT;         // column tiles
-    static constexpr int PER_TILE = LEVELS ? 1 : 4 / NMT;   // warps of a lane quarter per M tile
+    static constexpr int PER_TILE = LEVELS ? 4 : 4 / NMT;   // warps of a lane quarter per M tile (LEVELS: one tile)
     static constexpr int CW = LEVELS ? NT / 4 : NT / PER_TILE;   // readout columns per thread
     static constexpr int NSP = NX / 2;                      // site pairs per chunk
     static constexpr int PS = kMaxRows * NC * NX;           // floats per staged plane (re or im)
@@ -636,7 +636,8 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
 
     // readout ownership: lane quarter q of M tile t_own, column part cpart of the tile's columns
     const int q = warp & 3, g = warp >> 2;
-    const int t_own = g / SH::PER_TILE, cpart = g % SH::PER_TILE;
+    // (level accumulators: every warp of a lane quarter reads its own quarter of the NT columns)
+    const int t_own = SH::LEVELS ? 0 : g / SH::PER_TILE, cpart = SH::LEVELS ? g : g % SH::PER_TILE;
     const int row = t_own * 128 + q * 32 + lane;        // stacked row of this thread
     const int my_i = row / R;
     const bool row_ok = row < kSlices * R;
