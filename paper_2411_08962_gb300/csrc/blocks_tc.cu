@@ -71,15 +71,17 @@ constexpr int kKa = 3;                             // colour-term slots per site
 constexpr int kRoundSites = 128;                   // sites per exact TMEM accumulation
 // Level accumulators (full-spin family): the MMA of U slice i (rows i R .. i R + 127 of the stacked
 // slices; rows past R are the next slice's, and their TMEM lanes are not read) with X slice j adds into
-// accumulator 0 for (0, 0), 1 for (0, 1), 2 for (1, 0) and 1 + i + j for the levels i + j >= 2.  Products
-// of a level-k pair are multiples of 2^(-8k) below 2^(15-8k): the three accumulators of one pair each
-// stay exact for K <= 511 (85 sites) -- a round is 64 sites -- while a level-k >= 2 sum of up to five
-// pairs may round at 2^(-8k-7) of its scale, below 2^-36 of the level-0 sum.
-constexpr int kLevelAccs = 7;
+// an accumulator of its own for each pair of level i + j <= 2 -- (0,0), (0,1), (1,0), (0,2), (1,1),
+// (2,0) -> 0..5 -- and into accumulator 3 + i + j for the levels 3, 4, 5.  Products of a level-k pair
+// are multiples of 2^(-8k) below 2^(15-8k), so a one-pair accumulator stays exact for K <= 511 (85
+// sites; a round is 64 sites); a level-k >= 3 sum of up to five pairs may round at 2^(-8k-6), below
+// 2^-40 of a level-0 sum.
+constexpr int kLevelAccs = 9;
 constexpr int kLevelRoundSites = 64;
 __host__ __device__ constexpr int level_acc(int i, int j) {
-    return i + j >= 2 ? 1 + i + j : (i == 0 ? j : 2);
+    return i + j >= 3 ? 3 + i + j : (i + j == 2 ? 3 + i : (i + j == 1 ? 1 + i : 0));
 }
+__host__ __device__ constexpr bool level_acc_exact(int a) { return a < 6; }
 constexpr int kRangeSitesDefault = 512;            // sites per CTA (one grid, one partial) unless tuned
 constexpr int kMaxCfg = 64;                        // configurations per launch
 constexpr int kSpinLimit = 1 << 22;                // mbarrier polls before giving up
@@ -704,7 +706,8 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
                     for (int j = 0; j < kSlicesX && i + j <= kMaxPair; ++j) {
                         const uint64_t db = smem_desc<KC>(b0 + (uint32_t)(j * NT * KC * 2 + ks * 256));
                         const int ac = level_acc(i, j);
-                        const uint32_t acc_in = (fresh && ks == 0 && (i == 0 || ac == 2)) ? 0u : 1u;
+                        // the first MMA into an accumulator in a round starts it (merged levels: i = 0 comes first)
+                        const uint32_t acc_in = (fresh && ks == 0 && (level_acc_exact(ac) || i == 0)) ? 0u : 1u;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
@@ -770,8 +773,8 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
                         asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
                         for (int n = 0; n < SH::CW; ++n) {
-                            // the exact accumulators join by TwoSum; the small levels (>= 2) join the low part
-                            if (ac < 3) acc_add(acc[n], df{__uint_as_float(r[n]), 0.f});
+                            // the one-pair accumulators join by TwoSum; the levels >= 3 join the low part
+                            if (level_acc_exact(ac)) acc_add(acc[n], df{__uint_as_float(r[n]), 0.f});
                             else acc[n].l = __fadd_rn(acc[n].l, __uint_as_float(r[n]));
                         }
                     }
