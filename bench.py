@@ -114,15 +114,16 @@ CMAC_PER_SITE = 2 * 3 * 36 * 4 + 2 * 2 * 216 * 3
 # FP32-pipe work of preparing the operands, in lane operations (an f32x2
 # instruction is two) --
 #   216 diquark values (2 types x 3 lists x 36 entries), two sites per packed
-#   instruction: 4 terms x (4 weight products + 4 exact product-accumulations
-#   of 10 f32x2 ops each), less 14 f32x2 ops for the first term, = 162 f32x2
-#   ops per value; 6 slices at their own weight, 26 f32x2 ops per real part
-#   pair = 52 -> 214 f32x2 ops = 428 lane ops per site pair, 214 per value;
+#   instruction: 4 terms x (2 weight scalings + 3 operand products + 4
+#   fixed-exponent product-accumulations of 4 f32x2 ops each) = 84, 4 more to
+#   start and finish the accumulators, and 6 slices per real part from the
+#   (hi, lo) pair, 18 f32x2 ops each = 36 -> 124 f32x2 ops per site pair, 124
+#   lane ops per value and site;
 #   72 propagator values (2 types x 2 spins x 6 x 3 terms): 5 slices, 15 f32x2
 #   ops per real part pair = 30 lane ops per value
 # -- and the MMA work: per type 6 MMAs of M=128 (5 stacked slices x 24 rows,
 # padded), N=48 (36 columns, padded), over K = 6 per site.
-TC_LANE_OPS_PER_SITE = 216 * 214 + 72 * 30
+TC_LANE_OPS_PER_SITE = 216 * 124 + 72 * 30
 TC_MMA_FLOPS_PER_SITE = 2 * 6 * 2 * 128 * 48 * 6
 
 
@@ -792,21 +793,23 @@ def li7_record(steps: int) -> dict:
     ms64 = _timed(lambda: step(wick.WICK_FP64), max(1, min(3, steps)), 1, stream)
     rel = float(((c_mixed - Cli).abs() / Cli.abs()).max().item())
     # roofline of the full-spin tensor-core block build: the operand preparation per site (4 block
-    # types x 144 columns x 3 lists diquark values at 214 lane ops, 4 x 48 rows x 3 lists propagator
-    # values at 30, each counted once although the kernel rebuilds the U slices and restages S for
-    # each of its 9 column tiles) against the FP32 lanes, and the useful complex MACs of the update
-    # (4 types x 4 spins x 1728 entries x 3 lists per site)
+    # types x 144 columns x 3 lists diquark values at 124 lane ops; 4 x 48 rows x 3 lists propagator
+    # values at 30, once per column tile: 3 tiles of 48 columns) against the FP32 lanes; the useful
+    # complex MACs of the update (4 types x 4 spins x 1728 entries x 3 lists per site); and the MMAs
+    # issued (per type, tile and site: 20 slice pairs x M=128 x N=48 x K=6)
     _, sm_mhz, _ = peaks()
     sites = n_src * T * L ** 3
-    ops = sites * (4 * 144 * 3 * 214 + 4 * 48 * 3 * 30)
+    ops = sites * (4 * 144 * 3 * 124 + 4 * 48 * 3 * 30 * 3)
     alu_peak = N_SM * FP32_LANES * sm_mhz * 1e6 / 1e12
     achieved = ops / (phases["blocks"] / 1e3) / 1e12
     useful_tflops = sites * 4 * 4 * 1728 * 3 * 8 / (phases["blocks"] / 1e3) / 1e12
-    roofline = {"kernel": "block_tc_kernel<float2, Shape<12,4,16,4,8>> (full spin)", "bound": "alu",
-                "achieved": achieved, "peak": alu_peak, "unit": "Top/s", "frac": achieved / alu_peak,
-                "useful_update_tflops": useful_tflops, "tensor_peak_tflops": bf16_peak_tflops(),
-                "note": "U slices and staged rows are rebuilt by each of the 9 column tiles (TMEM holds 16 "
-                        "columns x 17 slice-pair blocks per CTA)"}
+    mma_tflops = sites * 4 * 3 * 20 * 2 * 128 * 48 * 6 / (phases["blocks"] / 1e3) / 1e12
+    roofline = {"kernel": "block_tc_kernel<float2, Shape<12,4,48,4,8,1>> (full spin, level accumulators)",
+                "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s", "frac": achieved / alu_peak,
+                "useful_update_tflops": useful_tflops, "mma_issued_tflops": mma_tflops,
+                "tensor_peak_tflops": bf16_peak_tflops(), "mma_frac_of_tensor_peak": mma_tflops / bf16_peak_tflops(),
+                "note": "3 column tiles of 48 per block type; nine TMEM accumulators (one per slice pair up to "
+                        "level 2, levels 3-5 merged), 64-site rounds"}
     return {"workload": "li7", "metric": "Li-7 correlator ms/config (He-4 cluster x triton)",
                       "value": ms, "unit": UNIT, "higher_is_better": False, "steps": steps,
                       "config": {"L": L, "T": T, "n_src": n_src, "block_types": 4, "spins": 4,
