@@ -245,6 +245,21 @@ int wick_terms_stats(const wick_terms *terms, int64_t stats[4], double *bound);
  * table is replaced by the terms perm[0..n-1] (indices into the current
  * table), re-sorted by representative.  Used for top-fraction evaluation. */
 int wick_terms_select(wick_terms *terms, const int64_t *perm, int64_t n);
+/*
+ * Top-fraction evaluation (Sec. V.C: the terms of a table are spread around zero, a small
+ * fraction of them with large values carries the correlator, and the same terms dominate on every
+ * gauge configuration).
+ * wick_terms_magnitudes: each term's share of the correlator on the given blocks,
+ *   mag[u] = sum_{slice < n_slices} | scale * w_u * prod_k B[slice][id_{u,k}] |
+ * (FP64; blocks: device complex128 [n_slices][n_blk], for example a few time slices of a small
+ * lattice; mag: host, U doubles, written).  Synchronises `stream`.  Errors: WICK_EINVAL,
+ * WICK_ENOMEM, WICK_ECUDA.
+ * wick_terms_top: keeps the ceil(fraction * U) terms of largest mag (ties: the earlier term in the
+ * table first), 0 < fraction <= 1, through wick_terms_select.  Errors: WICK_EINVAL.
+ */
+int wick_terms_magnitudes(const void *blocks, int n_slices, const wick_terms *terms, double *mag,
+                          wick_stream_t stream);
+int wick_terms_top(wick_terms *terms, const double *mag, double fraction);
 /* Binary term-table file (versioned header + arrays). */
 int wick_terms_save(const wick_terms *terms, const char *path);
 int wick_terms_load(const char *path, wick_terms **out);

@@ -171,6 +171,29 @@ def table_correlator(nuc, Bhat: np.ndarray, table) -> np.ndarray:
     return out.reshape(shp)
 
 
+def term_contributions(nuc, Bhat: np.ndarray, table) -> np.ndarray:
+    """Each reduced term's contribution to C (Sec. V.C): c[u][slice] = scale w_u prod_k B[slice][id_{u,k}]
+    with the antisymmetric blocks, slices = the flattened leading axes of Bhat.  Their sum over u is
+    table_correlator (written separately, in numpy)."""
+    B = antisymmetric_blocks(np.asarray(Bhat, dtype=np.complex128), nuc)
+    B = B.reshape(-1, B.shape[-1])
+    ids = np.asarray(table["ids"], dtype=np.int64)
+    w = np.asarray(table["w"], dtype=np.float64)
+    prod = np.ones((len(w), B.shape[0]), dtype=np.complex128)
+    for k in range(ids.shape[1]):
+        prod = prod * B[:, ids[:, k]].T
+    return float(nuc["scale"]) * w[:, None] * prod
+
+
+def top_terms(mag: np.ndarray, fraction: float) -> np.ndarray:
+    """Indices of the ceil(fraction * U) largest magnitudes, ties to the smaller index (Sec. V.C),
+    in ascending index order."""
+    U = len(mag)
+    n = max(1, min(U, int(np.ceil(fraction * U - 1e-9)))) if U else 0
+    order = sorted(range(U), key=lambda u: (-mag[u], u))
+    return np.array(sorted(order[:n]), dtype=np.int64)
+
+
 def source_multisets(nuc):
     """Antisymmetrised source: dict(Mu[n_M][n_u], Md[n_M][n_d], CM[n_M], n_red)."""
     pk = _Packed(nuc)

@@ -584,6 +584,42 @@ int wick_terms_select(wick_terms *t, const int64_t *perm, int64_t n) {
     return upload_terms(t);
 }
 
+int wick_terms_magnitudes(const void *blocks, int n_slices, const wick_terms *t, double *mag, wick_stream_t stream) {
+    if (!blocks || !t || !mag || n_slices < 1 || (uintptr_t)blocks % 16) return WICK_EINVAL;
+    ContractTable tab;
+    int n_blk = 0;
+    int err = terms_table(t, &tab, &n_blk);
+    if (err) return err;
+    if (t->U == 0) return WICK_OK;
+    double *d_mag = nullptr;
+    if (cudaMalloc(&d_mag, sizeof(double) * (size_t)t->U) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return WICK_ENOMEM;
+    }
+    err = launch_magnitudes((const double2 *)blocks, n_blk, n_slices, tab, d_mag, (cudaStream_t)stream);
+    if (!err && (cudaMemcpyAsync(mag, d_mag, sizeof(double) * (size_t)t->U, cudaMemcpyDeviceToHost,
+                                 (cudaStream_t)stream) != cudaSuccess ||
+                 cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)) {
+        (void)cudaGetLastError();
+        err = WICK_ECUDA;
+    }
+    cudaFree(d_mag);
+    return err;
+}
+
+int wick_terms_top(wick_terms *t, const double *mag, double fraction) {
+    if (!t || !mag || !(fraction > 0.0) || fraction > 1.0) return WICK_EINVAL;
+    const int64_t U = t->U;
+    int64_t n = (int64_t)ceil(fraction * (double)U - 1e-9);
+    n = std::max<int64_t>(std::min<int64_t>(n, U), U > 0 ? 1 : 0);
+    std::vector<int64_t> order((size_t)U);
+    std::iota(order.begin(), order.end(), (int64_t)0);
+    for (int64_t u = 0; u < U; ++u)
+        if (!(mag[u] >= 0.0)) return WICK_EINVAL;   // negative or NaN
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return mag[a] > mag[b]; });
+    return wick_terms_select(t, order.data(), n);
+}
+
 // file format: "WICKTBL1" | u32 version | header fields | arrays | u64 FNV-1a of the arrays
 static uint64_t fnv1a(const void *p, size_t n, uint64_t h) {
     const unsigned char *c = (const unsigned char *)p;

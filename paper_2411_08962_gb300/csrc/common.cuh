@@ -142,6 +142,9 @@ int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, c
                     cudaStream_t stream);
 int pad_table(const uint16_t *ids, const int64_t *w, int64_t U, int A, uint16_t *ids_pad, double *wd,
               cudaStream_t stream);
+// per-term contribution magnitudes on n_slices slices of blocks (device, mag: U doubles)
+int launch_magnitudes(const double2 *blocks, int n_blk, int n_slices, const ContractTable &tab, double *mag,
+                      cudaStream_t stream);
 // fixed scratch of wick_contract_noalloc (per device): the item counters and 65,536 counters, then
 // 65,536 partials at a fixed offset
 constexpr int64_t kNoAllocItems = 65536;

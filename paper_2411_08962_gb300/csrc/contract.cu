@@ -374,6 +374,23 @@ __global__ void product_kernel(const double2 *__restrict__ a, const double2 *__r
     if (i < n) out[i] = cmul(a[i], b[i]);
 }
 
+// Contribution magnitudes (Sec. V.C): mag[u] = sum over slices of |scale w_u prod_k B[slice][id_{u,k}]|,
+// FP64, one thread per term
+__global__ void magnitude_kernel(const double2 *__restrict__ blocks, int n_blk, int n_slices,
+                                 const uint16_t *__restrict__ ids, const double *__restrict__ w, int64_t U, int A,
+                                 int AP, double scale, double *__restrict__ mag) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= U) return;
+    double m = 0.0;
+    for (int s = 0; s < n_slices; ++s) {
+        const double2 *B = blocks + (size_t)s * n_blk;
+        double2 p = B[ids[u * AP]];
+        for (int k = 1; k < A; ++k) p = cmul(p, B[ids[u * AP + k]]);
+        m += hypot(p.x, p.y);
+    }
+    mag[u] = m * fabs(w[u] * scale);
+}
+
 // contraction copies of a reduced table: ids padded to [U][AP], weights as doubles (exact below 2^53)
 __global__ void pad_table_kernel(const uint16_t *__restrict__ ids, const int64_t *__restrict__ w, int64_t U, int A,
                                  int AP, uint16_t *__restrict__ ids_pad, double *__restrict__ wd) {
@@ -383,6 +400,16 @@ __global__ void pad_table_kernel(const uint16_t *__restrict__ ids, const int64_t
     wd[u] = (double)w[u];
 }
 }  // namespace
+
+int launch_magnitudes(const double2 *blocks, int n_blk, int n_slices, const ContractTable &tab, double *mag,
+                      cudaStream_t stream) {
+    if (tab.U <= 0) return WICK_OK;
+    const int AP = tab.A <= 4 ? 4 : 8;
+    magnitude_kernel<<<(unsigned)((tab.U + 255) / 256), 256, 0, stream>>>(blocks, n_blk, n_slices, tab.ids, tab.w,
+                                                                          tab.U, tab.A, AP, tab.scale, mag);
+    WICK_CUDA_TRY(cudaGetLastError());
+    return WICK_OK;
+}
 
 int pad_table(const uint16_t *ids, const int64_t *w, int64_t U, int A, uint16_t *ids_pad, double *wd,
               cudaStream_t stream) {

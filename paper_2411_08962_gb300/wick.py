@@ -27,7 +27,7 @@ WICK_U, WICK_D = 0, 1
 
 EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_upload_rows", "wick_reduce_terms", "wick_terms_count",
            "wick_terms_nucleons", "wick_terms_block_count", "wick_terms_copy", "wick_terms_stats", "wick_terms_select",
-           "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_contract_noalloc",
+           "wick_terms_magnitudes", "wick_terms_top", "wick_terms_save", "wick_terms_load", "wick_terms_free", "wick_contract", "wick_contract_noalloc",
            "wick_status", "wick_batch_create", "wick_batch_run", "wick_batch_launches", "wick_batch_free",
            "wick_synth_propagator", "wick_cluster_product", "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats",
            "wick_det_element_offsets", "wick_det_copy", "wick_det_contract", "wick_det_contract_3pt", "wick_det_free", "wick_set_tuning", "wick_get_tuning",
@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH):
             L.wick_terms_copy.argtypes = [vp, vp, vp, vp]
             L.wick_terms_stats.argtypes = [vp, P(C.c_int64), P(C.c_double)]
             L.wick_terms_select.argtypes = [vp, P(C.c_int64), C.c_int64]
+            L.wick_terms_magnitudes.argtypes = [vp, C.c_int, vp, P(C.c_double), vp]
+            L.wick_terms_top.argtypes = [vp, P(C.c_double), C.c_double]
             L.wick_terms_save.argtypes = [vp, C.c_char_p]
             L.wick_terms_load.argtypes = [C.c_char_p, P(vp)]
             L.wick_terms_free.argtypes = [vp]
@@ -129,8 +131,9 @@ def load(path: str = LIB_PATH):
             L.wick_strerror.argtypes = [C.c_int]
             L.wick_strerror.restype = C.c_char_p
             L.wick_version.restype = C.c_char_p
-            for f in ("wick_build_blocks", "wick_reduce_terms", "wick_terms_nucleons", "wick_terms_block_count", "wick_terms_copy",
-                      "wick_terms_stats", "wick_terms_select", "wick_terms_save", "wick_terms_load",
+            for f in ("wick_build_blocks", "wick_reduce_terms", "wick_terms_nucleons", "wick_terms_copy",
+                      "wick_terms_stats", "wick_terms_select", "wick_terms_magnitudes", "wick_terms_top", "wick_terms_save",
+                      "wick_terms_load",
                       "wick_contract", "wick_contract_noalloc", "wick_status", "wick_batch_create",
                       "wick_batch_run", "wick_batch_launches", "wick_synth_propagator", "wick_cluster_product",
                       "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats", "wick_det_element_offsets",
@@ -305,6 +308,21 @@ class Terms:
     def select(self, perm):
         p = np.ascontiguousarray(perm, dtype=np.int64)
         _check(load().wick_terms_select(self.h, _np_ptr(p, C.c_int64), len(p)), "wick_terms_select")
+
+    def magnitudes(self, blocks, n_slices: int, stream=None) -> np.ndarray:
+        """Each term's |contribution| summed over the n_slices slices of `blocks` (Sec. V.C)."""
+        pb = _buf(blocks, "blocks", _C128, n_slices * self.block_count)
+        mag = np.zeros(max(self.count, 1), dtype=np.float64)
+        _check(load().wick_terms_magnitudes(pb, n_slices, self.h, _np_ptr(mag, C.c_double), _stream(stream)),
+               "wick_terms_magnitudes")
+        return mag[:self.count]
+
+    def top(self, mag, fraction: float):
+        """Keep the ceil(fraction * U) terms of largest magnitude (wick_terms_top)."""
+        m = np.ascontiguousarray(mag, dtype=np.float64)
+        if len(m) != self.count:
+            raise ValueError("one magnitude per term is needed")
+        _check(load().wick_terms_top(self.h, _np_ptr(m, C.c_double), float(fraction)), "wick_terms_top")
 
     def save(self, path: str):
         _check(load().wick_terms_save(self.h, path.encode()), "wick_terms_save")

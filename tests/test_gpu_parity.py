@@ -272,6 +272,33 @@ def test_top_fraction_selection():
     assert rel_per_t(C, ref) < FP64_TOL
 
 
+@pytest.mark.parametrize("name,fraction", [("he3", 0.05), ("he4", 0.01)])
+def test_top_fraction_by_contribution(name, fraction):
+    """Sec. V.C as the paper does it: rank the terms by their contribution on a small lattice (a few
+    time slices), keep the top fraction, evaluate those on another configuration.  Magnitudes, the
+    kept set and the truncated correlator against the oracle."""
+    onuc = oops.nucleus(name)
+    tabs = wick.Tables(operators.nucleus(name))
+    terms, _, _ = gpu_table(name)
+    o = O.dedup(onuc)
+    # ranking lattice: L=2, three time slices
+    Su, Sd = props(2, 3, 1, seed=0x70F)
+    Bh = O.blocks_single(Su, Sd, onuc)
+    mag_ref = np.abs(O.term_contributions(onuc, Bh, o)).sum(axis=1)
+    mag = terms.magnitudes(gpu_blocks(Su, Sd, tabs, "fp64"), 3)
+    assert np.max(np.abs(mag - mag_ref) / np.max(mag_ref)) < FP64_TOL
+    keep = O.top_terms(mag_ref, fraction)
+    terms.top(mag, fraction)
+    got = terms.copy()
+    assert terms.count == len(keep)
+    assert np.array_equal(got["ids"], o["ids"][keep]) and np.array_equal(got["w"], o["w"][keep])
+    # evaluation lattice: another configuration
+    Su2, Sd2 = props(4, 2, 1, seed=0x710)
+    C = gpu_contract(gpu_blocks(Su2, Sd2, tabs, "fp64"), terms, "fp64")
+    ref = O.table_correlator(onuc, O.blocks_single(Su2, Sd2, onuc), dict(ids=o["ids"][keep], w=o["w"][keep]))
+    assert rel_per_t(C, ref) < FP64_TOL
+
+
 def test_contract_deterministic():
     Su, Sd = props(4, 4, 2, seed=4)
     terms, _, _ = gpu_table("he3")
