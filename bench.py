@@ -209,7 +209,7 @@ def code_tokens(text: str) -> str:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("blocks_tc.cu", "common.cuh", "df32.cuh"):
+    for f in ("blocks_tc.cu", "df32.cuh"):
         h.update(code_tokens(open(os.path.join(ROOT, "paper_2411_08962_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 

@@ -236,7 +236,8 @@ int wick_terms_nucleons(const wick_terms *terms);      /* A */
 /* Block entries per (src, t) of the layout the table was reduced for
  * (wick_block_count of that layout), or a negative error. */
 int64_t wick_terms_block_count(const wick_terms *terms);
-/* Copy to host arrays: ids [U][A] uint16, w [U] int64, rep [U] int64 (any may be NULL). */
+/* Copy to host arrays: ids [U][A] uint16, w [U] int64, rep [U] int64 (any may be NULL; not for
+ * correlation-matrix tables: wick_terms_copy_matrix). */
 int wick_terms_copy(const wick_terms *terms, uint16_t *ids, int64_t *w, int64_t *rep);
 /* stats[0] raw terms, [1] identically zero, [2] distinct keys, [3] kept terms;
  * *bound = the false-merge probability bound of App. C for this reduction. */
@@ -273,7 +274,8 @@ void wick_terms_free(wick_terms *terms);
  *   precision  WICK_FP64: FP64 products and sums.  WICK_MIXED: block entries
  *              split into float pairs, products in double-FP32 on the float
  *              pipes, FP64 sum over terms.
- *   C_out      device complex128 [n_src][T], caller-owned, overwritten.
+ *   C_out      device complex128 [n_src][T], caller-owned, overwritten ([N * N][n_src][T] for a
+ *              correlation-matrix table of wick_reduce_terms_matrix).
  * One persistent kernel launch: CTAs take (slice, chunk of terms) work items
  * from a device counter; each slice's blocks are staged in shared memory; the
  * chunk sums are added in chunk order by the last chunk of a slice to finish.
@@ -342,6 +344,51 @@ int wick_get_tuning(wick_tuning *tuning);
  */
 int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms *terms, int precision,
                           void *C_out, wick_stream_t stream);
+
+/*
+ * Three-point functions with the plane-wave sink (Sec. IV.A "Three-point functions", Eq.
+ * Proton3pt_seq, generalised to nuclei): the connected contribution of a current on `flavour`
+ * (WICK_U or WICK_D), inserted through the sequential propagator Sig (device, the wick_prop layout,
+ * same L, T, n_src and dtype as Su, Sd; obtained by inverting the Dirac operator on the current's
+ * source, an input here), replaces one quark line of that flavour in every Wick term by Sig, summed
+ * over the lines.  In block form that is the derivative of the correlator in the direction Sig:
+ *   C3[src][t] = scale * sum_u w_u sum_k D[src][t][id_{u,k}] prod_{j != k} B[src][t][id_{u,j}]
+ * with D the derivative blocks, a third block type beside B^p and B^n:
+ * wick_build_blocks_3pt writes D (device complex128, the block layout of wick_build_blocks): every
+ * block with each of its quark lines of `flavour` replaced by Sig in turn (Eq. 2.4 differentiated;
+ * the exchange term included).  FP64, or WICK_MIXED (double-FP32 on the CUDA cores: the tensor-core
+ * update is not used here).  Uses the library workspace; asynchronous.
+ * wick_contract_3pt evaluates C3 from B (wick_build_blocks) and D with the reduced table of the
+ * two-point function; C_out device complex128 [n_src][T].  One persistent launch; deterministic.
+ * Errors: WICK_EINVAL (shapes, dtypes, flavour, precision), WICK_ENOMEM, WICK_ECUDA.
+ */
+int wick_build_blocks_3pt(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig, int flavour,
+                          const wick_nucleon_op *ops, const wick_block_layout *layout, int precision,
+                          void *dblocks, wick_stream_t stream);
+int wick_contract_3pt(const void *blocks, const void *dblocks, int n_src, int T, const wick_terms *terms,
+                      int precision, void *C_out, wick_stream_t stream);
+
+/*
+ * Correlation matrix with the plane-wave sink (Sec. "Application ... to the generalized eigenvalue
+ * problem", Eqs. E1-E3): for N = n_nuc operators O_i with the same quark content (nuclei[i]; their
+ * sink and source halves), element (i, j) = i * N + j is the correlator with the sink of O_i and the
+ * source of O_j, scale sqrt(scale_i * scale_j).  Every element is reduced as wick_reduce_terms does;
+ * the terms of all elements are then merged by their identity-testing keys (the same evaluation mod
+ * 2^61 - 1 at the same random points), so a block product shared by several elements is one term
+ * with a weight per element.  The result is a table with N * N weight columns
+ * (wick_terms_elements): wick_contract evaluates each product once and writes C_out device
+ * complex128 [N * N][n_src][T].  2 <= N <= 4, A <= 4.  Matrix tables are for wick_contract (and the
+ * accessors below) only: wick_terms_copy, _select, _top, _magnitudes, _save, wick_contract_noalloc
+ * and batches return WICK_EINVAL for them.  Synchronises `stream`.
+ * Errors: as wick_reduce_terms, WICK_EINVAL for operators of different quark content.
+ */
+int wick_reduce_terms_matrix(const wick_nucleus *nuclei, int n_nuc, const wick_nucleon_op *ops,
+                             const wick_block_layout *layout, uint64_t seed, int trials, int sites,
+                             wick_terms **out, wick_stream_t stream);
+/* Number of weight columns (matrix elements) of a table: 1, or N * N for a correlation matrix. */
+int wick_terms_elements(const wick_terms *terms);
+/* Copy ids [U][A] uint16, weights [U][n_el] int64 and the element scales [n_el] (any may be NULL). */
+int wick_terms_copy_matrix(const wick_terms *terms, uint16_t *ids, int64_t *w, double *el_scale);
 
 /*
  * Cluster sink (Sec. V.A: Li-7 as a He-4 cluster and a triton cluster, each

@@ -414,3 +414,34 @@ def deuteron_basis():
         terms = [((NEUTRON, PROTON), (a, b), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b]]
         out.append(grouped_operator(nucs, terms))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Plane-wave operators for the correlation matrix and the 2H operator of Eq. NP_op
+# (block form, each nucleon projected to zero momentum on its own).
+# ----------------------------------------------------------------------------
+def nucleus_from_terms(name: str, types, spin_terms, form: str = "upper", ops=None, scale: float = 1.0):
+    """A nucleus sum_t coef_t prod_k N^{types_k}_{spins_k} (the same combination at sink and source)."""
+    ops = nucleon_ops(form) if ops is None else ops
+    n_spin = 2 if form == "upper" else 4
+    return dict(A=len(types), ops=ops, n_spin=n_spin, chi=[c for c in range(12) if (c % 4) < n_spin],
+                sink=sorted((tuple(types), tuple(sp), w) for sp, w in spin_terms),
+                src=source_terms(ops, tuple(types), spin_terms), src_flav=source_flavours(ops, tuple(types)),
+                scale=scale, name=name)
+
+
+def deuteron_pw_basis():
+    """Three plane-wave deuteron operators with upper-spin nucleons, one quark content:
+    p(up) n(up), p(up) n(down) + p(down) n(up), p(down) n(down)."""
+    types = (PROTON, NEUTRON)
+    return [nucleus_from_terms("pn uu", types, [((0, 0), 1)]),
+            nucleus_from_terms("pn ud+du", types, [((0, 1), 1), ((1, 0), 1)]),
+            nucleus_from_terms("pn dd", types, [((1, 1), 1)])]
+
+
+def deuteron_np_planewave():
+    """Eq. NP_op with a plane-wave sink: n^T (C gamma5 P+) p, plain nucleons of Eqs. 1000/1001 with all
+    four spins, the paper's P+ (paper_projector)."""
+    G = integer_matrix(cg5() @ paper_projector(+1))
+    terms = [((a, b), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b]]
+    return nucleus_from_terms("2H NP", (NEUTRON, PROTON), terms, form="full")

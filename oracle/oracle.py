@@ -194,6 +194,42 @@ def top_terms(mag: np.ndarray, fraction: float) -> np.ndarray:
     return np.array(sorted(order[:n]), dtype=np.int64)
 
 
+def three_point_planewave(Su, Sd, Sig, flavour: int, nuc, table=None) -> np.ndarray:
+    """Three-point function with the plane-wave sink (Sec. IV.A, Eq. Proton3pt_seq generalised):
+    the connected term of a current on `flavour` (0 = u, 1 = d) through the sequential propagator
+    Sig, i.e. every Wick term with one line of that flavour replaced by Sig, summed over the lines:
+    the linear coefficient of C(S_f + e Sig) in e.  C is a polynomial of degree n_f (the quarks of
+    that flavour) in e, so the coefficient is extracted exactly by the discrete Fourier transform over
+    the m = n_f + 1 roots of unity: c_1 = (1/m) sum_k C(w^k) w^(-k), w = exp(2 pi i / m).  Each C is the
+    plain definition (single-product blocks and the raw Wick sum), or the reduced-table sum of
+    `table` when given."""
+    nu, nd = ops_quark_counts(nuc)
+    m = (nu if flavour == 0 else nd) + 1
+    acc = 0.0
+    for k in range(m):
+        e = np.exp(2j * np.pi * k / m)
+        su = Su + e * Sig if flavour == 0 else Su
+        sd = Sd + e * Sig if flavour == 1 else Sd
+        Bh = blocks_single(su, sd, nuc)
+        C = table_correlator(nuc, Bh, table) if table is not None else raw_correlator(nuc, Bh)
+        acc = acc + C * np.conj(e)
+    return acc / m
+
+
+def ops_quark_counts(nuc):
+    nu = sum(1 for f in nuc["src_flav"] if f == 0)
+    return nu, len(nuc["src_flav"]) - nu
+
+
+def matrix_element(nuc_sink, nuc_source):
+    """The correlator with the sink of one operator and the source of another (Eq. E1): a nucleus
+    dict with the sink half of nuc_sink and the source half of nuc_source, scale sqrt(s_i s_j)."""
+    el = dict(nuc_sink)
+    el["src"] = nuc_source["src"]
+    el["scale"] = float(np.sqrt(nuc_sink["scale"] * nuc_source["scale"]))
+    return el
+
+
 def source_multisets(nuc):
     """Antisymmetrised source: dict(Mu[n_M][n_u], Md[n_M][n_d], CM[n_M], n_red)."""
     pk = _Packed(nuc)

@@ -28,6 +28,10 @@ struct wick_terms {
     uint16_t *d_ids_pad = nullptr;  // the contraction's copies: ids padded to 4 or 8, weights as doubles
     double *d_wd = nullptr;
     int device = 0;
+    // correlation-matrix tables (wick_reduce_terms_matrix): n_el weights per term, one scale per element
+    int n_el = 1;
+    std::vector<int64_t> wm;        // [U][n_el]
+    std::vector<double> el_scale;   // [n_el]
 };
 
 namespace wick {
@@ -112,7 +116,7 @@ int terms_table(const wick_terms *t, ContractTable *tab, int *n_blk) {
     cudaGetDevice(&dev);
     if (dev != t->device) return WICK_EINVAL;  // the device copies live on another GPU
     if (t->U > 0 && (!t->d_ids_pad || !t->d_wd)) return WICK_EINVAL;
-    *tab = {t->d_ids_pad, t->d_wd, t->U, t->A, t->scale};
+    *tab = {t->d_ids_pad, t->d_wd, t->U, t->A, t->scale, t->n_el > 1 ? t->el_scale.data() : nullptr};
     *n_blk = t->n_blk;
     return WICK_OK;
 }
@@ -245,7 +249,7 @@ static int prop_ok(const wick_prop *p) {
 
 using namespace wick;
 
-// the contraction's copies of a table (padded ids, FP64 weights), from its device ids and weights
+// the contraction's copies of a table (padded ids, FP64 weights), from its device ids and its weights
 static int make_contract_copies(wick_terms *t) {
     cudaFree(t->d_ids_pad);
     cudaFree(t->d_wd);
@@ -254,14 +258,19 @@ static int make_contract_copies(wick_terms *t) {
     const size_t U = (size_t)(t->U ? t->U : 1);
     const int AP = t->A <= 4 ? 4 : 8;
     if (cudaMalloc(&t->d_ids_pad, sizeof(uint16_t) * U * AP) != cudaSuccess ||
-        cudaMalloc(&t->d_wd, sizeof(double) * U) != cudaSuccess) {
+        cudaMalloc(&t->d_wd, sizeof(double) * U * t->n_el) != cudaSuccess) {
         (void)cudaGetLastError();
         return WICK_ENOMEM;
     }
-    for (int64_t u = 0; u < t->U; ++u)
-        if (t->w[(size_t)u] >= (1ll << 53) || t->w[(size_t)u] <= -(1ll << 53)) return WICK_EOVERFLOW;
-    int err = pad_table(t->d_ids, t->d_w, t->U, t->A, t->d_ids_pad, t->d_wd, nullptr);
+    const std::vector<int64_t> &w = t->n_el > 1 ? t->wm : t->w;
+    for (int64_t v : w)
+        if (v >= (1ll << 53) || v <= -(1ll << 53)) return WICK_EOVERFLOW;
+    int err = pad_table(t->d_ids, t->n_el > 1 ? nullptr : t->d_w, t->U, t->A, t->d_ids_pad, t->d_wd, nullptr);
     if (err) return err;
+    if (t->n_el > 1 && t->U > 0) {
+        std::vector<double> wd(w.begin(), w.end());
+        WICK_CUDA_TRY(cudaMemcpy(t->d_wd, wd.data(), sizeof(double) * wd.size(), cudaMemcpyHostToDevice));
+    }
     WICK_CUDA_TRY(cudaDeviceSynchronize());
     return WICK_OK;
 }
@@ -526,7 +535,7 @@ int wick_terms_nucleons(const wick_terms *t) { return t ? t->A : WICK_EINVAL; }
 int64_t wick_terms_block_count(const wick_terms *t) { return t ? (int64_t)t->n_blk : WICK_EINVAL; }
 
 int wick_terms_copy(const wick_terms *t, uint16_t *ids, int64_t *w, int64_t *rep) {
-    if (!t) return WICK_EINVAL;
+    if (!t || t->n_el > 1) return WICK_EINVAL;
     if (ids && !t->ids.empty()) memcpy(ids, t->ids.data(), sizeof(uint16_t) * t->ids.size());
     if (w && !t->w.empty()) memcpy(w, t->w.data(), sizeof(int64_t) * t->w.size());
     if (rep && !t->rep.empty()) memcpy(rep, t->rep.data(), sizeof(int64_t) * t->rep.size());
@@ -560,7 +569,7 @@ static int upload_terms(wick_terms *t) {
 }
 
 int wick_terms_select(wick_terms *t, const int64_t *perm, int64_t n) {
-    if (!t || n < 0 || n > t->U || (n > 0 && !perm)) return WICK_EINVAL;
+    if (!t || t->n_el > 1 || n < 0 || n > t->U || (n > 0 && !perm)) return WICK_EINVAL;
     std::vector<int64_t> keep(perm, perm + n);
     std::vector<char> seen((size_t)t->U, 0);
     for (int64_t v : keep) {
@@ -585,7 +594,7 @@ int wick_terms_select(wick_terms *t, const int64_t *perm, int64_t n) {
 }
 
 int wick_terms_magnitudes(const void *blocks, int n_slices, const wick_terms *t, double *mag, wick_stream_t stream) {
-    if (!blocks || !t || !mag || n_slices < 1 || (uintptr_t)blocks % 16) return WICK_EINVAL;
+    if (!blocks || !t || !mag || n_slices < 1 || (uintptr_t)blocks % 16 || t->n_el > 1) return WICK_EINVAL;
     ContractTable tab;
     int n_blk = 0;
     int err = terms_table(t, &tab, &n_blk);
@@ -628,7 +637,7 @@ static uint64_t fnv1a(const void *p, size_t n, uint64_t h) {
 }
 
 int wick_terms_save(const wick_terms *t, const char *path) {
-    if (!t || !path) return WICK_EINVAL;
+    if (!t || !path || t->n_el > 1) return WICK_EINVAL;
     FILE *f = fopen(path, "wb");
     if (!f) return WICK_EIO;
     const char magic[8] = {'W', 'I', 'C', 'K', 'T', 'B', 'L', '1'};
@@ -722,7 +731,8 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *t, int
     if (err) return err;
     const int n_slices = n_src * T;
     ContractPlan plan;
-    err = contract_plan(n_blk, 1, n_slices, &tab, 1, precision, contract_tune(current_tuning()), INT64_MAX, &plan);
+    err = contract_plan(n_blk, 1, n_slices, &tab, 1, precision, contract_tune(current_tuning()), INT64_MAX, &plan,
+                        t->n_el > 1 ? t->n_el : 0);
     if (err) return err;
     void *part = workspace(kWsContractPartials, plan.partial_bytes, &err);
     if (err) return err;
@@ -739,6 +749,7 @@ int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms
     int err = contract_args(blocks, n_src, T, t, precision, C_out, &tab, &n_blk);
     if (err) return err;
     const int64_t n_slices = (int64_t)n_src * T;
+    if (t->n_el > 1) return WICK_EINVAL;
     if (n_slices > kNoAllocItems) return WICK_ESCRATCH;
     void *scratch = nullptr;
     size_t cap = 0;
@@ -755,6 +766,163 @@ int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms
     double2 *partials = reinterpret_cast<double2 *>(static_cast<unsigned char *>(scratch) + kNoAllocCounterBytes);
     return launch_contract((const double2 *)blocks, n_blk, 1, (int)n_slices, &tab, 1, precision, plan, scratch,
                            partials, (double2 *)C_out, (cudaStream_t)stream);
+}
+
+int wick_terms_elements(const wick_terms *t) { return t ? t->n_el : WICK_EINVAL; }
+
+int wick_terms_copy_matrix(const wick_terms *t, uint16_t *ids, int64_t *w, double *el_scale) {
+    if (!t) return WICK_EINVAL;
+    if (ids && !t->ids.empty()) memcpy(ids, t->ids.data(), sizeof(uint16_t) * t->ids.size());
+    const std::vector<int64_t> &src = t->n_el > 1 ? t->wm : t->w;
+    if (w && !src.empty()) memcpy(w, src.data(), sizeof(int64_t) * src.size());
+    if (el_scale) {
+        if (t->n_el > 1) memcpy(el_scale, t->el_scale.data(), sizeof(double) * t->n_el);
+        else el_scale[0] = t->scale;
+    }
+    return WICK_OK;
+}
+
+int wick_reduce_terms_matrix(const wick_nucleus *nuclei, int n_nuc, const wick_nucleon_op *ops,
+                             const wick_block_layout *layout, uint64_t seed, int trials, int sites, wick_terms **out,
+                             wick_stream_t stream) {
+    if (!out) return WICK_EINVAL;
+    *out = nullptr;
+    if (!nuclei || n_nuc < 2 || n_nuc > 4) return WICK_EINVAL;
+    const int A = nuclei[0].A, nq = 3 * A;
+    if (A < 1 || A > 4) return WICK_EINVAL;
+    for (int i = 0; i < n_nuc; ++i) {
+        if (nuclei[i].A != A || !nuclei[i].src_flav || !(nuclei[i].scale > 0.0)) return WICK_EINVAL;
+        for (int q = 0; q < nq; ++q)
+            if (nuclei[i].src_flav[q] != nuclei[0].src_flav[q]) return WICK_EINVAL;   // same quark content
+    }
+    BlockPlan bp;
+    int err = build_block_plan(ops, layout, &bp);
+    if (err) return err;
+    const int n_blk = (int)wick_block_count(layout);
+    const int n_el = n_nuc * n_nuc;
+    wick_terms *t = new (std::nothrow) wick_terms();
+    if (!t) return WICK_ENOMEM;
+    t->A = A;
+    t->n_blk = n_blk;
+    t->n_ops = layout->n_ops;
+    t->n_spin = layout->n_spin;
+    t->n_chi = layout->n_chi;
+    memcpy(t->chi, layout->chi, sizeof(t->chi));
+    t->scale = 1.0;
+    t->n_el = n_el;
+    t->el_scale.resize(n_el);
+    std::map<std::pair<uint64_t, uint64_t>, int64_t> index;   // key -> merged term
+    std::vector<int8_t> eps_rep;
+    double pairs = 0.0;
+    for (int i = 0; i < n_nuc && !err; ++i)
+        for (int j = 0; j < n_nuc && !err; ++j) {
+            // element (i, j): the sink of operator i, the source of operator j (Eq. E1)
+            wick_nucleus el = nuclei[i];
+            el.n_src = nuclei[j].n_src;
+            el.src_chi = nuclei[j].src_chi;
+            el.src_w = nuclei[j].src_w;
+            el.scale = sqrt(nuclei[i].scale * nuclei[j].scale);
+            const int e = i * n_nuc + j;
+            t->el_scale[e] = el.scale;
+            wick_terms *te = nullptr;
+            err = wick_reduce_terms(&el, ops, layout, seed, trials, sites, &te, stream);
+            if (err) break;
+            std::vector<uint64_t> keys(2 * (size_t)(te->U ? te->U : 1));
+            std::vector<int8_t> eps((size_t)(te->U ? te->U : 1));
+            err = term_keys(bp, n_blk, te->d_ids, te->U, A, seed, trials, sites, keys.data(), eps.data(),
+                            (cudaStream_t)stream);
+            for (int64_t u = 0; !err && u < te->U; ++u) {
+                if (eps[u] == 0) { err = WICK_EINVAL; break; }   // a kept term has a non-zero key
+                const auto key = std::make_pair(keys[2 * u], keys[2 * u + 1]);
+                auto it = index.find(key);
+                int64_t m;
+                if (it == index.end()) {
+                    m = t->U++;
+                    index.emplace(key, m);
+                    t->ids.insert(t->ids.end(), te->ids.begin() + u * A, te->ids.begin() + (u + 1) * A);
+                    t->wm.resize((size_t)t->U * n_el, 0);
+                    eps_rep.push_back(eps[u]);
+                } else {
+                    m = it->second;
+                }
+                // term value = eps_u * canonical value = eps_u * eps_rep * (product of the merged term's ids)
+                t->wm[(size_t)m * n_el + e] += te->w[u] * eps[u] * eps_rep[m];
+            }
+            t->stats[0] += te->stats[0];
+            t->stats[1] += te->stats[1];
+            pairs += (double)te->stats[0];
+            wick_terms_free(te);
+        }
+    if (err) {
+        wick_terms_free(t);
+        return err;
+    }
+    t->stats[2] = t->stats[3] = t->U;
+    t->bound = std::min(1.0, 0.5 * pairs * pairs * pow(3.0 * A / 2305843009213693951.0, trials));
+    t->w.assign(t->U, 0);
+    t->rep.resize(t->U);
+    std::iota(t->rep.begin(), t->rep.end(), (int64_t)0);
+    cudaGetDevice(&t->device);
+    const size_t U = (size_t)(t->U ? t->U : 1);
+    if (cudaMalloc(&t->d_ids, sizeof(uint16_t) * U * A) != cudaSuccess ||
+        cudaMalloc(&t->d_w, sizeof(int64_t) * U) != cudaSuccess || cudaMalloc(&t->d_rep, sizeof(int64_t) * U) != cudaSuccess) {
+        (void)cudaGetLastError();
+        wick_terms_free(t);
+        return WICK_ENOMEM;
+    }
+    if (t->U > 0 &&
+        cudaMemcpy(t->d_ids, t->ids.data(), sizeof(uint16_t) * t->ids.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        (void)cudaGetLastError();
+        wick_terms_free(t);
+        return WICK_ECUDA;
+    }
+    err = make_contract_copies(t);
+    if (err) {
+        wick_terms_free(t);
+        return err;
+    }
+    *out = t;
+    return WICK_OK;
+}
+
+int wick_build_blocks_3pt(const wick_prop *Su, const wick_prop *Sd, const wick_prop *Sig, int flavour,
+                          const wick_nucleon_op *ops, const wick_block_layout *layout, int precision, void *dblocks,
+                          wick_stream_t stream) {
+    if (!prop_ok(Su) || !prop_ok(Sd) || !prop_ok(Sig) || !dblocks || (uintptr_t)dblocks % 16) return WICK_EINVAL;
+    if (Su->L != Sd->L || Su->T != Sd->T || Su->n_src != Sd->n_src || Su->dtype != Sd->dtype) return WICK_EINVAL;
+    if (Sig->L != Su->L || Sig->T != Su->T || Sig->n_src != Su->n_src || Sig->dtype != Su->dtype) return WICK_EINVAL;
+    if (flavour != WICK_U && flavour != WICK_D) return WICK_EINVAL;
+    if (precision != WICK_FP64 && precision != WICK_MIXED) return WICK_EINVAL;
+    BlockPlan plan;
+    int err = build_block_plan(ops, layout, &plan);
+    if (err) return err;
+    const int64_t V = (int64_t)Su->L * Su->L * Su->L;
+    const int64_t n_slices = (int64_t)Su->n_src * Su->T;
+    if (V > (1 << 24) || n_slices > 65535) return WICK_EINVAL;
+    const size_t bytes = block_3pt_partial_bytes(plan, (int)V, (int)n_slices);
+    void *ws = workspace(kWsBlockPartials, bytes, &err);
+    if (err) return err;
+    return launch_block_build_3pt(plan, Su->data, Sd->data, Sig->data, Su->dtype, flavour, (int)V, (int)n_slices,
+                                  precision, ws, (double2 *)dblocks, (cudaStream_t)stream);
+}
+
+int wick_contract_3pt(const void *blocks, const void *dblocks, int n_src, int T, const wick_terms *t, int precision,
+                      void *C_out, wick_stream_t stream) {
+    ContractTable tab;
+    int n_blk = 0;
+    int err = contract_args(blocks, n_src, T, t, precision, C_out, &tab, &n_blk);
+    if (err) return err;
+    if (!dblocks || (uintptr_t)dblocks % 16 || t->n_el > 1) return WICK_EINVAL;
+    const int n_slices = n_src * T;
+    ContractPlan plan;
+    err = contract_plan(n_blk, 1, n_slices, &tab, 1, precision, contract_tune(current_tuning()), INT64_MAX, &plan, 1);
+    if (err) return err;
+    void *part = workspace(kWsContractPartials, plan.partial_bytes, &err);
+    if (err) return err;
+    void *cnt = workspace(kWsContractCounters, plan.counter_bytes, &err);
+    if (err) return err;
+    return launch_contract((const double2 *)blocks, n_blk, 1, n_slices, &tab, 1, precision, plan, cnt, (double2 *)part,
+                           (double2 *)C_out, (cudaStream_t)stream, (const double2 *)dblocks);
 }
 
 int wick_set_tuning(const wick_tuning *t) {

@@ -60,6 +60,7 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
         err = terms_table(tables[k], &tabs[k], &n_blk);
         if (err) return err;
         if (n_blk != plan.n_out) return WICK_EINVAL;  // reduced for another layout
+        if (tabs[k].el_scale) return WICK_EINVAL;     // correlation-matrix tables: wick_contract only
     }
     const wick_tuning tune = current_tuning();
     const int rs = tune.range_sites;

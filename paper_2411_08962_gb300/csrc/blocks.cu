@@ -106,15 +106,31 @@ __device__ __forceinline__ void p_term(Acc<kDF32> &acc, float2 a, const cdf &x) 
 template <int MODE, typename ST>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restrict__ Su, const ST *__restrict__ Sd,
-                     int V, int n_slices, int chunk, int ns_tile, double2 *__restrict__ partials) {
+                     const ST *__restrict__ Sg, int sub_flav, int sub_pass, int split0, int V, int n_slices, int chunk,
+                     int ns_tile, double2 *__restrict__ partials) {
     constexpr bool DF = MODE != kFP64;
     using SC = typename Types<MODE>::S;
     using XC = typename Types<MODE>::X;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nc = plan.n_chi, nc2 = nc * nc, nc3 = nc2 * nc;
-    const int nr0 = plan.n_rows[0], nr1 = plan.n_rows[1], nr = nr0 + nr1;
+    const int nr0 = plan.n_rows[0], nr1 = plan.n_rows[1];
+    // staged rows: flavour u, flavour d, then (a three-point build) the rows of the sequential
+    // propagator Sg, which stands in for flavour sub_flav in one slot of every nucleon
+    const int nrs = sub_flav >= 0 ? plan.n_rows[sub_flav] : 0;
+    const int nr = nr0 + nr1 + nrs;
     SC *sS = reinterpret_cast<SC *>(smem_raw);
     XC *sX = reinterpret_cast<XC *>(smem_raw + sizeof(SC) * (size_t)ns_tile * nr * nc);
+    // the staged section (first row) each slot of a type with pair flavour f1 reads: slot 1 (the U rows),
+    // slot 2 (the first diquark factor), slot 3 (the second); pass 0 puts Sg into the first slot of flavour
+    // sub_flav, pass 1 into the second (a type with one quark of that flavour then adds nothing)
+    auto sec = [&](int f) { return f == 0 ? 0 : nr0; };
+    auto slot_sec = [&](int f1, int slot) {
+        const int f = slot == 3 ? 1 - f1 : f1;
+        const bool sub = sub_flav == f && ((slot == 1 && sub_pass == 0) || (slot == 2 && sub_pass == 1) ||
+                                           (slot == 3 && sub_pass == 0));
+        return sub ? nr0 + nr1 : sec(f);
+    };
+    auto silent = [&](int f1) { return sub_flav == 1 - f1 && sub_pass == 1; };
 
     const int slice = blockIdx.x;
     const int x_begin = blockIdx.y * chunk;
@@ -136,6 +152,7 @@ block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restric
             g_i23[k] = 3 * j;
             g_cnt[k] = min(3, nc2 - 3 * j);
             g_f[k] = plan.f1[g_os[k] / plan.n_spin];
+            if (silent(g_f[k])) g_cnt[k] = -g_cnt[k];   // outputs written as zeros
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) zero(acc[k][q]);
@@ -157,6 +174,7 @@ block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restric
 
     const ST *slice_u = Su + (size_t)slice * V * 144;
     const ST *slice_d = Sd + (size_t)slice * V * 144;
+    const ST *slice_g = Sg ? Sg + (size_t)slice * V * 144 : slice_u;
     for (int xb = x_begin; xb < x_end; xb += ns_tile) {
         const int ns = min(ns_tile, x_end - xb);
         // stage the rows of S used by the tables: sS[site][row][i], flavour-0 rows first
@@ -164,10 +182,10 @@ block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restric
             const int site = e / (nr * nc);
             const int rem = e - site * nr * nc;
             const int rc = rem / nc, ic = rem - rc * nc;
-            const int f = rc < nr0 ? 0 : 1;
-            const int row = f == 0 ? plan.rows[0][rc] : plan.rows[1][rc - nr0];
+            const int f = rc < nr0 ? 0 : (rc < nr0 + nr1 ? 1 : 2);
+            const int row = f == 0 ? plan.rows[0][rc] : (f == 1 ? plan.rows[1][rc - nr0] : plan.rows[sub_flav][rc - nr0 - nr1]);
             const size_t idx = (size_t)(xb + site) * 144 + row * 12 + plan.chi[ic];
-            const ST v = f == 0 ? slice_u[idx] : slice_d[idx];
+            const ST v = f == 0 ? slice_u[idx] : (f == 1 ? slice_d[idx] : slice_g[idx]);
             if constexpr (DF) sS[e] = to_f2(v);
             else sS[e] = to_d2(v);
         }
@@ -180,8 +198,8 @@ block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restric
             const int e = (site * plan.n_x + l) * nc2 + i23;
             const int i2 = i23 / nc, i3 = i23 - i2 * nc;
             const int f1 = plan.f1[plan.x_op[l]];
-            const SC *s1 = sS + (size_t)site * nr * nc + (f1 == 0 ? 0 : nr0 * nc);
-            const SC *s2 = sS + (size_t)site * nr * nc + (f1 == 0 ? nr0 * nc : 0);
+            const SC *s1 = sS + (size_t)site * nr * nc + slot_sec(f1, 2) * nc;
+            const SC *s2 = sS + (size_t)site * nr * nc + slot_sec(f1, 3) * nc;
             if constexpr (MODE == kDF32X2) {
                 // lanes (re, im) += w a.x (b.x, b.y);  lanes (im, re) += w a.y (b.x, -b.y)
                 pdf va, vb;
@@ -208,10 +226,10 @@ block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restric
         // P update: three outputs per group share the S1 entry
 #pragma unroll
         for (int k = 0; k < kGroups; ++k) {
-            if (g_cnt[k] == 0) continue;
+            if (g_cnt[k] <= 0) continue;
             const int os = g_os[k];
             for (int site = 0; site < ns; ++site) {
-                const SC *s1 = sS + (size_t)site * nr * nc + (g_f[k] == 0 ? 0 : nr0 * nc);
+                const SC *s1 = sS + (size_t)site * nr * nc + slot_sec(g_f[k], 1) * nc;
                 const XC *xs = sX + (size_t)site * plan.n_x * nc2 + g_i23[k];
                 for (int t = plan.os_off[os]; t < plan.os_off[os + 1]; ++t) {
                     const SC a = s1[plan.os_r1[t] * nc + g_i1[k]];
@@ -240,11 +258,12 @@ block_partial_kernel(const __grid_constant__ BlockPlan plan, const ST *__restric
 #pragma unroll
     for (int k = 0; k < kGroups; ++k) {
         if (g_cnt[k] == 0) continue;
+        const int cnt = g_cnt[k] < 0 ? -g_cnt[k] : g_cnt[k];
         const int out0 = (g_os[k] * nc + g_i1[k]) * nc2 + g_i23[k];
-        double2 *dst = partials + ((size_t)blockIdx.y * n_slices + slice) * plan.n_out + out0;
+        double2 *dst = partials + ((size_t)(split0 + blockIdx.y) * n_slices + slice) * plan.n_out + out0;
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-            if (q < g_cnt[k]) dst[q] = out_d2(acc[k][q]);
+            if (q < cnt) dst[q] = out_d2(acc[k][q]);
     }
     (void)nc3;
 }
@@ -268,11 +287,11 @@ __global__ void block_reduce_kernel(const double2 *__restrict__ partials, int n_
 }
 
 template <int MODE, typename ST>
-int launch_typed(const BlockPlan &plan, const void *Su, const void *Sd, int V, int n_slices, double2 *partials,
-                 int n_splits, int chunk, double2 *blocks, cudaStream_t stream) {
+int launch_typed(const BlockPlan &plan, const void *Su, const void *Sd, const void *Sg, int sub_flav, int V,
+                 int n_slices, double2 *partials, int n_splits, int chunk, double2 *blocks, cudaStream_t stream) {
     using SC = typename Types<MODE>::S;
     using XC = typename Types<MODE>::X;
-    const int nr = plan.n_rows[0] + plan.n_rows[1];
+    const int nr = plan.n_rows[0] + plan.n_rows[1] + (sub_flav >= 0 ? plan.n_rows[sub_flav] : 0);
     const size_t per_site = sizeof(SC) * (size_t)nr * plan.n_chi + sizeof(XC) * (size_t)plan.n_x * plan.n_chi * plan.n_chi;
     int ns = (int)(kSmemBudget / per_site);
     ns = ns < 1 ? 1 : (ns > kMaxNs ? kMaxNs : ns);
@@ -283,11 +302,16 @@ int launch_typed(const BlockPlan &plan, const void *Su, const void *Sd, int V, i
     const int n_groups = plan.n_ops * plan.n_spin * plan.n_chi * gpr;
     const int n_oc = (n_groups + kThreads * kGroups - 1) / (kThreads * kGroups);
     dim3 grid(n_slices, n_splits, n_oc);
-    kern<<<grid, kThreads, smem, stream>>>(plan, (const ST *)Su, (const ST *)Sd, V, n_slices, chunk, ns, partials);
-    WICK_CUDA_TRY(cudaGetLastError());
+    // a three-point build (sub_flav >= 0) runs two passes into two sets of splits, summed by the reduction
+    const int passes = sub_flav >= 0 ? 2 : 1;
+    for (int pass = 0; pass < passes; ++pass) {
+        kern<<<grid, kThreads, smem, stream>>>(plan, (const ST *)Su, (const ST *)Sd, (const ST *)Sg, sub_flav, pass,
+                                               pass * n_splits, V, n_slices, chunk, ns, partials);
+        WICK_CUDA_TRY(cudaGetLastError());
+    }
     const size_t n = (size_t)n_slices * plan.n_out;
-    block_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(partials, n_splits, n_slices, plan.n_out,
-                                                                         plan.n_chi, blocks);
+    block_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(partials, passes * n_splits, n_slices,
+                                                                         plan.n_out, plan.n_chi, blocks);
     WICK_CUDA_TRY(cudaGetLastError());
     return WICK_OK;
 }
@@ -324,16 +348,48 @@ int launch_block_build(const BlockPlan &plan, const void *Su, int dtype_u, const
     if (precision == WICK_MIXED || precision == WICK_MIXED_SIMT) {
         if (plan.pow2_w) {
             if (dtype_u == WICK_C64)
-                return launch_typed<kDF32X2, float2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
-            return launch_typed<kDF32X2, double2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
+                return launch_typed<kDF32X2, float2>(plan, Su, Sd, nullptr, -1, V, n_slices, part, n_splits, chunk, blocks, stream);
+            return launch_typed<kDF32X2, double2>(plan, Su, Sd, nullptr, -1, V, n_slices, part, n_splits, chunk, blocks, stream);
         }
         if (dtype_u == WICK_C64)
-            return launch_typed<kDF32, float2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
-        return launch_typed<kDF32, double2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
+            return launch_typed<kDF32, float2>(plan, Su, Sd, nullptr, -1, V, n_slices, part, n_splits, chunk, blocks, stream);
+        return launch_typed<kDF32, double2>(plan, Su, Sd, nullptr, -1, V, n_slices, part, n_splits, chunk, blocks, stream);
     }
     if (dtype_u == WICK_C64)
-        return launch_typed<kFP64, float2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
-    return launch_typed<kFP64, double2>(plan, Su, Sd, V, n_slices, part, n_splits, chunk, blocks, stream);
+        return launch_typed<kFP64, float2>(plan, Su, Sd, nullptr, -1, V, n_slices, part, n_splits, chunk, blocks, stream);
+    return launch_typed<kFP64, double2>(plan, Su, Sd, nullptr, -1, V, n_slices, part, n_splits, chunk, blocks, stream);
+}
+
+size_t block_3pt_partial_bytes(const BlockPlan &plan, int V, int n_slices) {
+    const int n_splits = (V + kChunk - 1) / kChunk;
+    return 2 * sizeof(double2) * (size_t)n_splits * n_slices * plan.n_out;
+}
+
+int launch_block_build_3pt(const BlockPlan &plan, const void *Su, const void *Sd, const void *Sg, int dtype,
+                           int sub_flav, int V, int n_slices, int precision, void *partials, double2 *dblocks,
+                           cudaStream_t stream) {
+    if (!partials || (sub_flav != WICK_U && sub_flav != WICK_D)) return WICK_EINVAL;
+    double2 *part = static_cast<double2 *>(partials);
+    const int chunk = kChunk, n_splits = (V + kChunk - 1) / kChunk;
+    if (precision == WICK_MIXED || precision == WICK_MIXED_SIMT) {
+        if (plan.pow2_w) {
+            if (dtype == WICK_C64)
+                return launch_typed<kDF32X2, float2>(plan, Su, Sd, Sg, sub_flav, V, n_slices, part, n_splits, chunk,
+                                                     dblocks, stream);
+            return launch_typed<kDF32X2, double2>(plan, Su, Sd, Sg, sub_flav, V, n_slices, part, n_splits, chunk,
+                                                  dblocks, stream);
+        }
+        if (dtype == WICK_C64)
+            return launch_typed<kDF32, float2>(plan, Su, Sd, Sg, sub_flav, V, n_slices, part, n_splits, chunk, dblocks,
+                                               stream);
+        return launch_typed<kDF32, double2>(plan, Su, Sd, Sg, sub_flav, V, n_slices, part, n_splits, chunk, dblocks,
+                                            stream);
+    }
+    if (dtype == WICK_C64)
+        return launch_typed<kFP64, float2>(plan, Su, Sd, Sg, sub_flav, V, n_slices, part, n_splits, chunk, dblocks,
+                                           stream);
+    return launch_typed<kFP64, double2>(plan, Su, Sd, Sg, sub_flav, V, n_slices, part, n_splits, chunk, dblocks,
+                                        stream);
 }
 
 }  // namespace wick

@@ -55,6 +55,13 @@ int launch_block_build(const BlockPlan &plan, const void *Su, int dtype_u, const
                        int V, int n_slices, int precision, int range_sites, int *counters, void *partials,
                        double2 *blocks, cudaStream_t stream);
 size_t block_partial_bytes(const BlockPlan &plan, int V, int n_slices, int precision, int range_sites);
+// three-point blocks: the derivative of the blocks in the direction of the sequential propagator Sg of
+// flavour sub_flav (each quark line of that flavour replaced by Sg in turn), on the CUDA cores (FP64 or
+// double-FP32); partials: block_3pt_partial_bytes
+size_t block_3pt_partial_bytes(const BlockPlan &plan, int V, int n_slices);
+int launch_block_build_3pt(const BlockPlan &plan, const void *Su, const void *Sd, const void *Sg, int dtype,
+                           int sub_flav, int V, int n_slices, int precision, void *partials, double2 *dblocks,
+                           cudaStream_t stream);
 size_t block_counter_bytes(const BlockPlan &plan, int n_slices, int precision);
 // tensor-core update stage (blocks_tc.cu): upper-spin plans, double-FP32-exact
 // the 16-byte words of one site that wick_upload_rows gathers: flavour << 15 | word in the site
@@ -100,6 +107,10 @@ struct ReduceResult {
 // Antisymmetrised source (host-prepared): n_M multisets, each the sorted
 // layout indices of its u quarks (Mu, n_M x nu) and d quarks (Md, n_M x nd),
 // with the summed signed source weight CM.
+// identity-testing keys (two values mod p, canonical sign eps; eps = 0 for a zero key) of given terms
+// (device ids [U][A]) with the block values mod p of run_reduce for the same seed, trials and sites
+int term_keys(const BlockPlan &bp, int n_blk, const uint16_t *ids, int64_t U, int A, uint64_t seed, int trials,
+              int sites, uint64_t *keys, int8_t *eps, cudaStream_t stream);
 int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc, const int8_t *Mu,
                const int8_t *Md, const int64_t *CM, const int8_t *sink_flav, const int8_t *sink_ord,
                const int8_t *sink_eta, uint64_t seed, int trials, int sites, ReduceResult *out,
@@ -112,10 +123,11 @@ int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc,
 constexpr int kMaxTables = 8;
 struct ContractTable {         // a reduced table as the contraction reads it
     const uint16_t *ids;       // [U][AP] block ids padded to AP = 4 (A <= 4) or 8
-    const double *w;           // [U] weights as doubles (exact: |w| < 2^53)
+    const double *w;           // [U][n_el] weights as doubles (exact: |w| < 2^53)
     int64_t U;
     int A;
     double scale;
+    const double *el_scale = nullptr;   // matrix tables: scale of each of the n_el elements (host)
 };
 struct ContractTune {          // 0 = default
     int threads;               // per CTA: 32..512, multiple of 32 (default 256)
@@ -123,6 +135,7 @@ struct ContractTune {          // 0 = default
     int chunk_terms;           // terms per work item, about (default 4096)
 };
 struct ContractPlan {
+    int kind;                  // 0 correlator, 1 three-point (derivative blocks), 4 / 9 / 16 matrix elements
     int threads, grid, stage;
     size_t smem;
     int n_chunks[kMaxTables], item_off[kMaxTables];
@@ -134,12 +147,12 @@ struct ContractPlan {
     size_t partial_bytes;      // one complex128 per work item
 };
 int contract_plan(int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab, int precision,
-                  const ContractTune &tune, int64_t max_items, ContractPlan *plan);
+                  const ContractTune &tune, int64_t max_items, ContractPlan *plan, int kind = 0);
 // counters: plan.counter_bytes, zero before the first launch (cleared again by every launch; a region
 // that holds nothing else); partials: plan.partial_bytes
 int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab,
                     int precision, const ContractPlan &plan, void *counters, double2 *partials, double2 *C_out,
-                    cudaStream_t stream);
+                    cudaStream_t stream, const double2 *dblocks = nullptr);
 int pad_table(const uint16_t *ids, const int64_t *w, int64_t U, int A, uint16_t *ids_pad, double *wd,
               cudaStream_t stream);
 // per-term contribution magnitudes on n_slices slices of blocks (device, mag: U doubles)

@@ -49,6 +49,8 @@ struct Elem<true> {
     using T = cdf;
     static __device__ __forceinline__ T from(double2 v) { return to_cdf(v); }
     static __device__ __forceinline__ T mul(const T &a, const T &b) { return cdf_mul(a, b); }
+    static __device__ __forceinline__ T add(const T &a, const T &b) { return {df_add(a.x, b.x), df_add(a.y, b.y)}; }
+    static __device__ __forceinline__ T one() { return {{1.f, 0.f}, {0.f, 0.f}}; }
     static __device__ __forceinline__ double re(const T &a) { return to_double(a.x); }
     static __device__ __forceinline__ double im(const T &a) { return to_double(a.y); }
 };
@@ -57,13 +59,25 @@ struct Elem<false> {
     using T = double2;
     static __device__ __forceinline__ T from(double2 v) { return v; }
     static __device__ __forceinline__ T mul(const T &a, const T &b) { return cmul(a, b); }
+    static __device__ __forceinline__ T add(const T &a, const T &b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ T one() { return make_double2(1.0, 0.0); }
     static __device__ __forceinline__ double re(const T &a) { return a.x; }
     static __device__ __forceinline__ double im(const T &a) { return a.y; }
 };
 
+// What a launch evaluates per term: KIND 0 the product of the A blocks (a correlator); KIND 1 the
+// sum over k of the product with block k taken from the derivative blocks D (a three-point
+// function); KIND 4, 9, 16 the product once, added into that many matrix elements with weights of
+// their own (a correlation matrix).
+template <int KIND>
+struct Kind {
+    static constexpr bool DERIV = KIND == 1;
+    static constexpr int NEL = KIND >= 4 ? KIND : 1;
+};
+
 struct TableWork {
     const uint16_t *ids;   // [U][AP]
-    const double *w;       // [U]
+    const double *w;       // [U][NEL]
     int64_t U;
     int64_t chunk;         // terms per item
     int A, n_chunks;       // chunks per (configuration, slice)
@@ -75,13 +89,15 @@ struct ContractWork {
     TableWork tab[kMaxTables];
     int n_tab;
     const double2 *blocks;     // [n_cfg][n_slices][n_blk]
+    const double2 *dblocks;    // derivative blocks (KIND 1), same layout
     int n_blk, n_cfg, n_slices;
     int items_per_cs;          // items of one (configuration, slice)
     int64_t n_items;
-    double2 *C_out;            // [n_cfg][n_tab][n_slices]
-    double2 *partials;         // [n_items]
+    double2 *C_out;            // [n_cfg][n_tab][NEL][n_slices]
+    double2 *partials;         // [n_items][NEL]
     int *counters;             // [n_cfg][n_tab][n_slices]
     unsigned long long *queue; // [0] next item, [1] CTAs that have left
+    double el_scale[16];       // matrix elements: scale of each element
 };
 
 template <typename C, bool MIXED, bool STAGE>
@@ -90,13 +106,14 @@ __device__ __forceinline__ C load_block(const C *sB, const double2 *gB, int id) 
     else return Elem<MIXED>::from(__ldcg(gB + id));
 }
 
-// this thread's share of terms [u0, u1) of one table, against one slice's blocks
-template <int A, bool MIXED, bool STAGE>
+// this thread's share of terms [u0, u1) of one table, against one slice's blocks (and derivative blocks)
+template <int A, bool MIXED, bool STAGE, int KIND>
 __device__ __forceinline__ void eval_terms(const TableWork &tw, int64_t u0, int64_t u1,
-                                           const typename Elem<MIXED>::T *sB, const double2 *gB, double &ax,
-                                           double &ay) {
+                                           const typename Elem<MIXED>::T *sB, const typename Elem<MIXED>::T *sD,
+                                           const double2 *gB, const double2 *gD, double *ax, double *ay) {
     using E = Elem<MIXED>;
     using C = typename E::T;
+    using K = Kind<KIND>;
     constexpr int AP = A <= 4 ? 4 : 8;
     for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
         uint16_t id[AP];
@@ -113,28 +130,57 @@ __device__ __forceinline__ void eval_terms(const TableWork &tw, int64_t u0, int6
                 id[2 * q + 1] = (uint16_t)(wd[q] >> 16);
             }
         }
-        C p = load_block<C, MIXED, STAGE>(sB, gB, id[0]);
+        C p;
+        if constexpr (K::DERIV) {
+            // sum_k D_k prod_{j != k} B_j: prefix products forward, the suffix product backward
+            C pre[A];
+            pre[0] = E::one();
 #pragma unroll
-        for (int k = 1; k < A; ++k) p = E::mul(p, load_block<C, MIXED, STAGE>(sB, gB, id[k]));
-        const double wu = __ldg(tw.w + u);
-        ax = fma(wu, E::re(p), ax);
-        ay = fma(wu, E::im(p), ay);
+            for (int k = 1; k < A; ++k) pre[k] = E::mul(pre[k - 1], load_block<C, MIXED, STAGE>(sB, gB, id[k - 1]));
+            C suf = E::one();
+            p = E::mul(pre[A - 1], load_block<C, MIXED, STAGE>(sD, gD, id[A - 1]));
+#pragma unroll
+            for (int k = A - 2; k >= 0; --k) {
+                suf = E::mul(suf, load_block<C, MIXED, STAGE>(sB, gB, id[k + 1]));
+                p = E::add(p, E::mul(E::mul(pre[k], load_block<C, MIXED, STAGE>(sD, gD, id[k])), suf));
+            }
+        } else {
+            p = load_block<C, MIXED, STAGE>(sB, gB, id[0]);
+#pragma unroll
+            for (int k = 1; k < A; ++k) p = E::mul(p, load_block<C, MIXED, STAGE>(sB, gB, id[k]));
+        }
+        const double pr = E::re(p), pi = E::im(p);
+#pragma unroll
+        for (int e = 0; e < K::NEL; ++e) {
+            const double wu = __ldg(tw.w + u * K::NEL + e);
+            ax[e] = fma(wu, pr, ax[e]);
+            ay[e] = fma(wu, pi, ay[e]);
+        }
     }
 }
 
-template <bool MIXED, bool STAGE>
+template <bool MIXED, bool STAGE, int KIND>
 __device__ __forceinline__ void eval_any(const TableWork &tw, int64_t u0, int64_t u1,
-                                         const typename Elem<MIXED>::T *sB, const double2 *gB, double &ax,
-                                         double &ay) {
-    switch (tw.A) {
-        case 1: eval_terms<1, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
-        case 2: eval_terms<2, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
-        case 3: eval_terms<3, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
-        case 4: eval_terms<4, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
-        case 5: eval_terms<5, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
-        case 6: eval_terms<6, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
-        case 7: eval_terms<7, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
-        default: eval_terms<8, MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay); break;
+                                         const typename Elem<MIXED>::T *sB, const typename Elem<MIXED>::T *sD,
+                                         const double2 *gB, const double2 *gD, double *ax, double *ay) {
+    if constexpr (Kind<KIND>::NEL > 1) {   // correlation matrices: nuclei up to A = 4
+        switch (tw.A) {
+            case 1: eval_terms<1, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            case 2: eval_terms<2, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            case 3: eval_terms<3, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            default: eval_terms<4, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+        }
+    } else {
+        switch (tw.A) {
+            case 1: eval_terms<1, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            case 2: eval_terms<2, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            case 3: eval_terms<3, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            case 4: eval_terms<4, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            case 5: eval_terms<5, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            case 6: eval_terms<6, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            case 7: eval_terms<7, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            default: eval_terms<8, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+        }
     }
 }
 
@@ -158,16 +204,20 @@ __device__ __forceinline__ double2 cta_sum(double ax, double ay, double2 *s_red)
         }
         r = make_double2(bx, by);
     }
+    __syncthreads();   // s_red free for the next sum
     return r;   // valid in thread 0
 }
 
-template <bool MIXED, bool STAGE>
+template <bool MIXED, bool STAGE, int KIND>
 __global__ void __launch_bounds__(kMaxThreads)
 contract_persistent_kernel(const __grid_constant__ ContractWork wk) {
     using E = Elem<MIXED>;
     using C = typename E::T;
+    using K = Kind<KIND>;
+    constexpr int NEL = K::NEL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sB = reinterpret_cast<C *>(smem_raw);
+    C *sD = sB + (K::DERIV ? wk.n_blk : 0);
     __shared__ long long s_item;
     __shared__ int s_last;
     __shared__ double2 s_red[kMaxThreads / 32];
@@ -184,38 +234,49 @@ contract_persistent_kernel(const __grid_constant__ ContractWork wk) {
         const TableWork &tw = wk.tab[tb];
         const int chunk = r - tw.item_off;
         const double2 *gB = wk.blocks + cs * wk.n_blk;
+        const double2 *gD = K::DERIV ? wk.dblocks + cs * wk.n_blk : gB;
         if constexpr (STAGE) {
             if (cs != staged) {   // every thread is past the previous item's gathers (barrier above)
-                for (int i = threadIdx.x; i < wk.n_blk; i += blockDim.x) sB[i] = E::from(__ldcg(gB + i));
+                for (int i = threadIdx.x; i < wk.n_blk; i += blockDim.x) {
+                    sB[i] = E::from(__ldcg(gB + i));
+                    if constexpr (K::DERIV) sD[i] = E::from(__ldcg(gD + i));
+                }
                 __syncthreads();
                 staged = cs;
             }
         }
         const int64_t u0 = (int64_t)chunk * tw.chunk;
         const int64_t u1 = min(tw.U, u0 + tw.chunk);
-        double ax = 0.0, ay = 0.0;
-        eval_any<MIXED, STAGE>(tw, u0, u1, sB, gB, ax, ay);
-        const double2 tot = cta_sum(ax, ay, s_red);
+        double ax[NEL], ay[NEL];
+#pragma unroll
+        for (int e = 0; e < NEL; ++e) ax[e] = ay[e] = 0.0;
+        eval_any<MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay);
         const int cfg = (int)(cs / wk.n_slices), slice = (int)(cs - (long long)cfg * wk.n_slices);
         int *cnt = wk.counters + ((size_t)cfg * wk.n_tab + tb) * wk.n_slices + slice;
+#pragma unroll
+        for (int e = 0; e < NEL; ++e) {
+            const double2 tot = cta_sum(ax[e], ay[e], s_red);
+            if (threadIdx.x == 0) wk.partials[item * NEL + e] = tot;
+        }
         if (threadIdx.x == 0) {
-            wk.partials[item] = tot;
             __threadfence();
             s_last = atomicAdd(cnt, 1) == tw.n_chunks - 1;
         }
         __syncthreads();
-        if (s_last && threadIdx.x == 0) {
-            // every chunk of this (configuration, table, slice) has written its partial: sum them in chunk order
+        if (s_last && threadIdx.x < NEL) {
+            // every chunk of this (configuration, table, slice) has written its partials: sum them in chunk order
+            const int e = threadIdx.x;
             __threadfence();
-            const double2 *p = wk.partials + (item - chunk);
+            const double2 *p = wk.partials + (item - chunk) * NEL + e;
             double x = 0.0, y = 0.0;
             for (int c = 0; c < tw.n_chunks; ++c) {
-                const double2 v = __ldcg(p + c);
+                const double2 v = __ldcg(p + (size_t)c * NEL);
                 x += v.x;
                 y += v.y;
             }
-            wk.C_out[((size_t)cfg * wk.n_tab + tb) * wk.n_slices + slice] = make_double2(tw.scale * x, tw.scale * y);
-            *cnt = 0;
+            const double sc = NEL > 1 ? wk.el_scale[e] : tw.scale;
+            wk.C_out[(((size_t)cfg * wk.n_tab + tb) * NEL + e) * wk.n_slices + slice] = make_double2(sc * x, sc * y);
+            if (e == 0) *cnt = 0;
         }
         // the next iteration's first barrier orders the reuse of s_item and s_last
     }
@@ -228,30 +289,44 @@ contract_persistent_kernel(const __grid_constant__ ContractWork wk) {
     }
 }
 
-template <bool MIXED, bool STAGE>
+template <bool MIXED, bool STAGE, int KIND>
 int launch_typed(const ContractWork &wk, int grid, int threads, size_t smem, cudaStream_t stream) {
-    auto k = contract_persistent_kernel<MIXED, STAGE>;
+    auto k = contract_persistent_kernel<MIXED, STAGE, KIND>;
     if (smem > 48 * 1024) WICK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<grid, threads, smem, stream>>>(wk);
     WICK_CUDA_TRY(cudaGetLastError());
     return WICK_OK;
 }
 
-template <bool MIXED, bool STAGE>
+template <bool MIXED, bool STAGE, int KIND>
 int max_ctas_per_sm(int threads, size_t smem) {
     int n = 0;
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(contract_persistent_kernel<MIXED, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
+        cudaFuncSetAttribute(contract_persistent_kernel<MIXED, STAGE, KIND>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         (void)cudaGetLastError();
         return 1;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, contract_persistent_kernel<MIXED, STAGE>, threads, smem) !=
-        cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, contract_persistent_kernel<MIXED, STAGE, KIND>, threads,
+                                                      smem) != cudaSuccess) {
         (void)cudaGetLastError();
         return 1;
     }
     return n < 1 ? 1 : n;
+}
+
+template <int KIND>
+int occupancy(bool mixed, bool stage, int threads, size_t smem) {
+    return mixed ? (stage ? max_ctas_per_sm<true, true, KIND>(threads, smem) : max_ctas_per_sm<true, false, KIND>(threads, smem))
+                 : (stage ? max_ctas_per_sm<false, true, KIND>(threads, smem) : max_ctas_per_sm<false, false, KIND>(threads, smem));
+}
+
+template <int KIND>
+int launch_kind(const ContractWork &wk, bool mixed, bool stage, int grid, int threads, size_t smem, cudaStream_t stream) {
+    if (mixed) return stage ? launch_typed<true, true, KIND>(wk, grid, threads, smem, stream)
+                            : launch_typed<true, false, KIND>(wk, grid, threads, smem, stream);
+    return stage ? launch_typed<false, true, KIND>(wk, grid, threads, smem, stream)
+                 : launch_typed<false, false, KIND>(wk, grid, threads, smem, stream);
 }
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -266,32 +341,36 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 // more than max_items items takes longer chunks.
 // ---------------------------------------------------------------------------
 int contract_plan(int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab, int precision,
-                  const ContractTune &tune, int64_t max_items, ContractPlan *plan) {
+                  const ContractTune &tune, int64_t max_items, ContractPlan *plan, int kind) {
     if (n_tab < 1 || n_tab > kMaxTables || n_cfg < 1 || n_slices < 1 || n_blk < 1) return WICK_EINVAL;
+    if (kind != 0 && kind != 1 && kind != 4 && kind != 9 && kind != 16) return WICK_EINVAL;
     ContractPlan &P = *plan;
     P = ContractPlan{};
+    P.kind = kind;
+    const int nel = kind >= 4 ? kind : 1;
     const bool mixed = precision == WICK_MIXED;
     P.threads = tune.threads > 0 ? tune.threads : 256;
     if (P.threads % 32 || P.threads < 32 || P.threads > kMaxThreads) return WICK_EINVAL;
-    const size_t elem = 16;   // complex128 or a double-FP32 complex pair
+    const size_t elem = 16 * (kind == 1 ? 2 : 1);   // complex128 or a double-FP32 complex pair (and D)
     P.stage = (size_t)n_blk * elem <= kSmemStageLimit;
     P.smem = P.stage ? (size_t)n_blk * elem : 0;
     int dev = 0, n_sm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    const int occ = mixed ? (P.stage ? max_ctas_per_sm<true, true>(P.threads, P.smem)
-                                     : max_ctas_per_sm<true, false>(P.threads, P.smem))
-                          : (P.stage ? max_ctas_per_sm<false, true>(P.threads, P.smem)
-                                     : max_ctas_per_sm<false, false>(P.threads, P.smem));
+    const int occ = kind == 0 ? occupancy<0>(mixed, P.stage, P.threads, P.smem)
+                  : kind == 1 ? occupancy<1>(mixed, P.stage, P.threads, P.smem)
+                  : kind == 4 ? occupancy<4>(mixed, P.stage, P.threads, P.smem)
+                  : kind == 9 ? occupancy<9>(mixed, P.stage, P.threads, P.smem)
+                              : occupancy<16>(mixed, P.stage, P.threads, P.smem);
     const int per_sm = tune.ctas_per_sm > 0 ? std::min(tune.ctas_per_sm, occ) : occ;
     const int64_t n_cs = (int64_t)n_cfg * n_slices;
     for (int k = 0; k < n_tab; ++k)
-        if (tabs[k].U < 0 || tabs[k].A < 1 || tabs[k].A > kMaxA) return WICK_EINVAL;
+        if (tabs[k].U < 0 || tabs[k].A < 1 || tabs[k].A > (nel > 1 ? 4 : kMaxA)) return WICK_EINVAL;
     int64_t target = tune.chunk_terms > 0 ? tune.chunk_terms : kDefaultChunkTerms;
     for (;;) {
         int64_t ips = 0;
         for (int k = 0; k < n_tab; ++k) ips += std::max<int64_t>(1, (tabs[k].U + target - 1) / target);
-        if (ips * n_cs <= max_items) break;
+        if (ips * n_cs * nel <= max_items) break;
         if (ips == n_tab) return WICK_ESCRATCH;   // one chunk per table and still too many items
         target *= 2;
     }
@@ -309,21 +388,25 @@ int contract_plan(int n_blk, int n_cfg, int n_slices, const ContractTable *tabs,
     P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(most, P.n_items));
     P.counters = (size_t)n_cfg * n_tab * n_slices;
     P.counter_bytes = 256 + align256(sizeof(int) * P.counters);
-    P.partial_bytes = align256(sizeof(double2) * (size_t)P.n_items);
+    P.partial_bytes = align256(sizeof(double2) * (size_t)P.n_items * nel);
     return WICK_OK;
 }
 
 int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab,
                     int precision, const ContractPlan &P, void *counters, double2 *partials, double2 *C_out,
-                    cudaStream_t stream) {
+                    cudaStream_t stream, const double2 *dblocks) {
     if (!counters || !partials || (uintptr_t)counters % 256 || (uintptr_t)partials % 16) return WICK_EINVAL;
+    if (P.kind == 1 && !dblocks) return WICK_EINVAL;
     ContractWork wk{};
     wk.n_tab = n_tab;
     for (int k = 0; k < n_tab; ++k) {
         wk.tab[k] = {tabs[k].ids, tabs[k].w, tabs[k].U, P.chunk[k], tabs[k].A, P.n_chunks[k], P.item_off[k],
                      tabs[k].scale};
+        if (P.kind >= 4)
+            for (int e = 0; e < P.kind; ++e) wk.el_scale[e] = tabs[k].el_scale ? tabs[k].el_scale[e] : tabs[k].scale;
     }
     wk.blocks = blocks;
+    wk.dblocks = dblocks;
     wk.n_blk = n_blk;
     wk.n_cfg = n_cfg;
     wk.n_slices = n_slices;
@@ -335,10 +418,14 @@ int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, c
     wk.counters = reinterpret_cast<int *>(base + 256);
     wk.partials = partials;
     const bool mixed = precision == WICK_MIXED;
-    if (mixed) return P.stage ? launch_typed<true, true>(wk, P.grid, P.threads, P.smem, stream)
-                              : launch_typed<true, false>(wk, P.grid, P.threads, P.smem, stream);
-    return P.stage ? launch_typed<false, true>(wk, P.grid, P.threads, P.smem, stream)
-                   : launch_typed<false, false>(wk, P.grid, P.threads, P.smem, stream);
+    switch (P.kind) {
+        case 0: return launch_kind<0>(wk, mixed, P.stage, P.grid, P.threads, P.smem, stream);
+        case 1: return launch_kind<1>(wk, mixed, P.stage, P.grid, P.threads, P.smem, stream);
+        case 4: return launch_kind<4>(wk, mixed, P.stage, P.grid, P.threads, P.smem, stream);
+        case 9: return launch_kind<9>(wk, mixed, P.stage, P.grid, P.threads, P.smem, stream);
+        case 16: return launch_kind<16>(wk, mixed, P.stage, P.grid, P.threads, P.smem, stream);
+        default: return WICK_EINVAL;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -397,7 +484,7 @@ __global__ void pad_table_kernel(const uint16_t *__restrict__ ids, const int64_t
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= U) return;
     for (int k = 0; k < AP; ++k) ids_pad[u * AP + k] = k < A ? ids[u * A + k] : (uint16_t)0;
-    wd[u] = (double)w[u];
+    if (w) wd[u] = (double)w[u];
 }
 }  // namespace
 

@@ -540,4 +540,43 @@ int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc,
     return WICK_ENOMEM;
 }
 
+namespace {
+// keys of given reduced terms under the identity-testing evaluation of run_reduce (same R tables)
+__global__ void key_kernel(const uint64_t *__restrict__ R, int n_blk, int trials, const uint16_t *__restrict__ ids,
+                           int64_t U, int A, uint64_t *__restrict__ keys, int8_t *__restrict__ eps) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= U) return;
+    EnumPlan ep;
+    ep.A = A;
+    ep.n_blk = n_blk;
+    TermTables tt;
+    tt.R = R;
+    int id[kMaxA];
+    for (int k = 0; k < A; ++k) id[k] = ids[u * A + k];
+    uint64_t h0 = 0, h1 = 0;
+    int e = 0;
+    if (!term_key(ep, tt, trials, id, &h0, &h1, &e)) e = 0;
+    keys[2 * u] = h0;
+    keys[2 * u + 1] = h1;
+    eps[u] = (int8_t)e;
+}
+}  // namespace
+
+int term_keys(const BlockPlan &bp, int n_blk, const uint16_t *ids, int64_t U, int A, uint64_t seed, int trials,
+              int sites, uint64_t *keys, int8_t *eps, cudaStream_t stream) {
+    if (U <= 0) return WICK_OK;
+    DevBuf<uint64_t> d_R, d_keys;
+    DevBuf<int8_t> d_eps;
+    int err;
+    if ((err = d_R.alloc((size_t)trials * n_blk)) || (err = d_keys.alloc(2 * (size_t)U)) || (err = d_eps.alloc(U)))
+        return err;
+    modp_blocks_kernel<<<(trials * n_blk + 127) / 128, 128, 0, stream>>>(bp, seed, trials, sites, d_R.p, n_blk);
+    key_kernel<<<(unsigned)((U + 255) / 256), 256, 0, stream>>>(d_R.p, n_blk, trials, ids, U, A, d_keys.p, d_eps.p);
+    WICK_CUDA_TRY(cudaGetLastError());
+    WICK_CUDA_TRY(cudaMemcpyAsync(keys, d_keys.p, sizeof(uint64_t) * 2 * (size_t)U, cudaMemcpyDeviceToHost, stream));
+    WICK_CUDA_TRY(cudaMemcpyAsync(eps, d_eps.p, (size_t)U, cudaMemcpyDeviceToHost, stream));
+    WICK_CUDA_TRY(cudaStreamSynchronize(stream));
+    return WICK_OK;
+}
+
 }  // namespace wick

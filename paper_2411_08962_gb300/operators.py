@@ -310,3 +310,38 @@ def deuteron_basis():
         w = np.array([x for _, x in table], dtype=np.int64)
         out.append(QuarkOperator(name, n_u, len(flav) - n_u, chi, w, 1.0))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Plane-wave operators given as nucleon products: a basis for a correlation
+# matrix (Eqs. E1-E3) and the 2H operator of Eq. NP_op with a plane-wave sink.
+# ---------------------------------------------------------------------------
+def nucleus_from_terms(name: str, types, combos, form: str = "upper", scale: float = 1.0) -> Nucleus:
+    """sum_t coef_t prod_k N^{types_k}_{spins_k}, the same combination at sink and source; combos =
+    [(spins tuple, coef)]."""
+    ops = standard_ops(form)
+    n_spin = 2 if form == "upper" else 4
+    chi = [c for c in range(12) if c % 4 < n_spin]
+    flav = []
+    for o in types:
+        f = ops[o].flav_pair
+        flav += [f, f, 1 - f]
+    sink = sorted((tuple(types), tuple(s), w) for s, w in combos)
+    return Nucleus(name, len(types), ops, n_spin, chi, sink, _source_table(ops, tuple(types), combos), flav, scale)
+
+
+def deuteron_pw_basis():
+    """Three plane-wave deuteron operators with upper-spin nucleons and one quark content:
+    p(up) n(up), p(up) n(down) + p(down) n(up), p(down) n(down) -- a 3 x 3 correlation matrix."""
+    t = (PROTON, NEUTRON)
+    return [nucleus_from_terms("pn uu", t, [((0, 0), 1)]),
+            nucleus_from_terms("pn ud+du", t, [((0, 1), 1), ((1, 0), 1)]),
+            nucleus_from_terms("pn dd", t, [((1, 1), 1)])]
+
+
+def deuteron_np() -> Nucleus:
+    """Eq. NP_op with a plane-wave sink: n^T (C gamma5 P+) p with the plain nucleons of Eqs. 1000/1001
+    (all four spins) and the paper's P+ = (1 - gamma4)/2 of this basis."""
+    G = diquark_matrix(-1)
+    combos = [((a, b), int(G[a, b])) for a in range(4) for b in range(4) if G[a, b]]
+    return nucleus_from_terms("2H NP", (NEUTRON, PROTON), combos, form="full")

@@ -31,7 +31,8 @@ EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_upload_rows", "wick_re
            "wick_status", "wick_batch_create", "wick_batch_run", "wick_batch_launches", "wick_batch_free",
            "wick_synth_propagator", "wick_cluster_product", "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats",
            "wick_det_element_offsets", "wick_det_copy", "wick_det_contract", "wick_det_contract_3pt", "wick_det_free", "wick_set_tuning", "wick_get_tuning",
-           "wick_strerror", "wick_version")
+           "wick_build_blocks_3pt", "wick_contract_3pt", "wick_reduce_terms_matrix", "wick_terms_elements",
+           "wick_terms_copy_matrix", "wick_strerror", "wick_version")
 
 
 class WickError(RuntimeError):
@@ -126,6 +127,13 @@ def load(path: str = LIB_PATH):
                                                 C.c_int, vp, vp]
             L.wick_det_free.argtypes = [vp]
             L.wick_det_free.restype = None
+            L.wick_build_blocks_3pt.argtypes = [P(wick_prop), P(wick_prop), P(wick_prop), C.c_int, P(wick_nucleon_op),
+                                                P(wick_block_layout), C.c_int, vp, vp]
+            L.wick_contract_3pt.argtypes = [vp, vp, C.c_int, C.c_int, vp, C.c_int, vp, vp]
+            L.wick_reduce_terms_matrix.argtypes = [P(wick_nucleus), C.c_int, P(wick_nucleon_op), P(wick_block_layout),
+                                                   C.c_uint64, C.c_int, C.c_int, P(vp), vp]
+            L.wick_terms_elements.argtypes = [vp]
+            L.wick_terms_copy_matrix.argtypes = [vp, vp, vp, vp]
             L.wick_set_tuning.argtypes = [P(wick_tuning)]
             L.wick_get_tuning.argtypes = [P(wick_tuning)]
             L.wick_strerror.argtypes = [C.c_int]
@@ -138,7 +146,8 @@ def load(path: str = LIB_PATH):
                       "wick_batch_run", "wick_batch_launches", "wick_synth_propagator", "wick_cluster_product",
                       "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats", "wick_det_element_offsets",
                       "wick_det_copy", "wick_det_contract", "wick_det_contract_3pt", "wick_set_tuning",
-                      "wick_get_tuning"):
+                      "wick_get_tuning", "wick_build_blocks_3pt", "wick_contract_3pt", "wick_reduce_terms_matrix",
+                      "wick_terms_elements", "wick_terms_copy_matrix"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -284,6 +293,20 @@ class Terms:
         return int(load().wick_terms_nucleons(self.h))
 
     @property
+    def elements(self) -> int:
+        """Weight columns: 1, or N * N for a correlation-matrix table."""
+        return int(load().wick_terms_elements(self.h))
+
+    def copy_matrix(self):
+        U, A, E = self.count, self.nucleons, self.elements
+        ids = np.zeros((max(U, 1), A), dtype=np.uint16)
+        w = np.zeros((max(U, 1), E), dtype=np.int64)
+        sc = np.zeros(E, dtype=np.float64)
+        _check(load().wick_terms_copy_matrix(self.h, ids.ctypes.data, w.ctypes.data, sc.ctypes.data),
+               "wick_terms_copy_matrix")
+        return dict(ids=ids[:U], w=w[:U], scale=sc)
+
+    @property
     def block_count(self) -> int:
         """Block entries per (source, time slice) of the layout the table was reduced for."""
         n = int(load().wick_terms_block_count(self.h))
@@ -343,7 +366,8 @@ def wick_reduce_terms(tables: Tables, seed: int = 0x2411, trials: int = 2, sites
 
 def _contract_args(blocks, n_src, T, terms, C_out):
     nb = terms.block_count
-    return (_buf(blocks, "blocks", _C128, n_src * T * nb), _buf(C_out, "C_out", _C128, n_src * T))
+    n_el = getattr(terms, "elements", 1)
+    return (_buf(blocks, "blocks", _C128, n_src * T * nb), _buf(C_out, "C_out", _C128, n_el * n_src * T))
 
 
 def wick_contract(blocks, n_src: int, T: int, terms: Terms, precision: int, C_out, stream=None):
@@ -357,6 +381,36 @@ def wick_contract_noalloc(blocks, n_src: int, T: int, terms: Terms, precision: i
     pb, pc = _contract_args(blocks, n_src, T, terms, C_out)
     _check(load().wick_contract_noalloc(pb, n_src, T, terms.h, precision, pc, _stream(stream)),
            "wick_contract_noalloc")
+
+
+def wick_reduce_terms_matrix(tables_list, seed: int = 0x2411, trials: int = 2, sites: int = 1, stream=None) -> Terms:
+    """Correlation-matrix table of N operators (`Tables` of nuclei with the same nucleon operators and
+    quark content; element i * N + j: sink of operator i, source of operator j)."""
+    n = len(tables_list)
+    arr = (wick_nucleus * n)(*[t.nucleus for t in tables_list])
+    h = C.c_void_p(None)
+    t0 = tables_list[0]
+    _check(load().wick_reduce_terms_matrix(arr, n, t0.ops, C.byref(t0.layout), seed, trials, sites, C.byref(h),
+                                           _stream(stream)), "wick_reduce_terms_matrix")
+    return Terms(h.value)
+
+
+def wick_build_blocks_3pt(Su, Sd, Sig, flavour: int, tables: Tables, precision: int, dblocks, L: int, T: int,
+                          n_src: int, stream=None):
+    """Derivative blocks D[src][t][n_blk] (complex128) of a current on `flavour` through Sig."""
+    pu, pd = _prop(Su, L, T, n_src, "Su"), _prop(Sd, L, T, n_src, "Sd")
+    pg = _prop(Sig, L, T, n_src, "Sig")
+    pb = _buf(dblocks, "dblocks", _C128, n_src * T * tables.nuc.n_blk)
+    _check(load().wick_build_blocks_3pt(C.byref(pu), C.byref(pd), C.byref(pg), flavour, tables.ops,
+                                        C.byref(tables.layout), precision, pb, _stream(stream)),
+           "wick_build_blocks_3pt")
+
+
+def wick_contract_3pt(blocks, dblocks, n_src: int, T: int, terms: Terms, precision: int, C_out, stream=None):
+    """Three-point function C3[src][t] from the blocks, the derivative blocks and the two-point table."""
+    pb, pc = _contract_args(blocks, n_src, T, terms, C_out)
+    pdb = _buf(dblocks, "dblocks", _C128, n_src * T * terms.block_count)
+    _check(load().wick_contract_3pt(pb, pdb, n_src, T, terms.h, precision, pc, _stream(stream)), "wick_contract_3pt")
 
 
 class Batch:

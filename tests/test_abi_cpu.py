@@ -177,3 +177,16 @@ def test_tuning_is_validated_and_kept(lib):
     finally:
         wick.wick_set_tuning(None)
     assert wick.wick_get_tuning() == {f: 0 for f in wick.TUNING_FIELDS}
+
+
+def test_product_planewave_operators_equal_oracle():
+    """The correlation-matrix basis and the plane-wave NP operator: the product's tables equal the
+    oracle's, built by separate code from the same definitions."""
+    pairs = list(zip(operators.deuteron_pw_basis(), oops.deuteron_pw_basis()))
+    pairs.append((operators.deuteron_np(), oops.deuteron_np_planewave()))
+    for a, b in pairs:
+        assert a.A == b["A"] and a.n_spin == b["n_spin"] and list(a.chi) == list(b["chi"])
+        for (f, tab), op in zip(b["ops"], a.ops):
+            assert f == op.flav_pair and [tuple(e) for e in tab] == [tuple(e) for e in op.entries]
+        assert [tuple(s) for s in a.sink] == [tuple(s) for s in b["sink"]]
+        assert a.src == b["src"] and list(a.src_flav) == list(b["src_flav"])
