@@ -431,12 +431,12 @@ def nucleus_from_terms(name: str, types, spin_terms, form: str = "upper", ops=No
 
 
 def deuteron_pw_basis():
-    """Three plane-wave deuteron operators with upper-spin nucleons, one quark content:
-    p(up) n(up), p(up) n(down) + p(down) n(up), p(down) n(down)."""
+    """Three plane-wave deuteron operators with upper-spin nucleons, one quark content, spin
+    projection 0: p(up) n(down), p(down) n(up), and their sum."""
     types = (PROTON, NEUTRON)
-    return [nucleus_from_terms("pn uu", types, [((0, 0), 1)]),
-            nucleus_from_terms("pn ud+du", types, [((0, 1), 1), ((1, 0), 1)]),
-            nucleus_from_terms("pn dd", types, [((1, 1), 1)])]
+    return [nucleus_from_terms("pn ud", types, [((0, 1), 1)]),
+            nucleus_from_terms("pn du", types, [((1, 0), 1)]),
+            nucleus_from_terms("pn ud+du", types, [((0, 1), 1), ((1, 0), 1)])]
 
 
 def deuteron_np_planewave():

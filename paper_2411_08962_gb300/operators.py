@@ -331,12 +331,13 @@ def nucleus_from_terms(name: str, types, combos, form: str = "upper", scale: flo
 
 
 def deuteron_pw_basis():
-    """Three plane-wave deuteron operators with upper-spin nucleons and one quark content:
-    p(up) n(up), p(up) n(down) + p(down) n(up), p(down) n(down) -- a 3 x 3 correlation matrix."""
+    """Three plane-wave deuteron operators with upper-spin nucleons, one quark content and spin
+    projection 0: p(up) n(down), p(down) n(up) and their sum (the triplet) -- a 3 x 3 correlation
+    matrix whose elements share terms (the third operator contains the first two)."""
     t = (PROTON, NEUTRON)
-    return [nucleus_from_terms("pn uu", t, [((0, 0), 1)]),
-            nucleus_from_terms("pn ud+du", t, [((0, 1), 1), ((1, 0), 1)]),
-            nucleus_from_terms("pn dd", t, [((1, 1), 1)])]
+    return [nucleus_from_terms("pn ud", t, [((0, 1), 1)]),
+            nucleus_from_terms("pn du", t, [((1, 0), 1)]),
+            nucleus_from_terms("pn ud+du", t, [((0, 1), 1), ((1, 0), 1)])]
 
 
 def deuteron_np() -> Nucleus:

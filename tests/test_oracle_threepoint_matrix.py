@@ -75,6 +75,10 @@ def test_matrix_elements():
     assert el["sink"] == basis[0]["sink"] and el["src"] == basis[1]["src"]
     c01 = O.correlator(Su, Sd, el)
     assert np.all(np.abs(c01) > 0)
+    # the third operator is the sum of the first two: its elements are the sums of theirs (linearity)
+    for i in range(3):
+        c = [O.correlator(Su, Sd, O.matrix_element(basis[i], basis[j])) for j in range(3)]
+        assert rel(c[2], c[0] + c[1]) < 1e-12
     # the reduced table of the pair reproduces its plain Wick sum
     Bh = O.blocks_single(Su, Sd, el)
     assert rel(O.table_correlator(el, Bh, O.dedup(el)), O.raw_correlator(el, Bh)) < 1e-12
