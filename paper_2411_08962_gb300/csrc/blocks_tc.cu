@@ -85,6 +85,7 @@ __host__ __device__ constexpr bool level_acc_exact(int a) { return a < 6; }
 constexpr int kRangeSitesDefault = 512;            // sites per CTA (one grid, one partial) unless tuned
 constexpr int kMaxCfg = 64;                        // configurations per launch
 constexpr int kSpinLimit = 1 << 22;                // mbarrier polls before giving up
+constexpr int kStage = 3;                          // staging buffers
 constexpr int kMaxRows = 24;                       // staged S rows (both flavours)
 constexpr int kListLen = 4;                        // terms per diquark list the tensor-core path takes (exactly)
 
@@ -102,10 +103,8 @@ struct CfgPtrs {
 // Compile-time shape of a table family: NC colours chi, NS spins, NT columns
 // per MMA (multiple of 16), NMT M tiles, NX sites per operand chunk.
 // LV_ = 1: one TMEM accumulator per slice level instead of per M tile and X slice (see LEVEL_ACCS).
-// MR_: staged rows of S at most (both flavours); RUNS_: runs of consecutive rows at most, each a bulk
-// copy per site.
-template <int NC_, int NS_, int NT_, int NMT_, int NX_, int LV_, int MR_, int RUNS_> struct Shape {
-    static constexpr int NC = NC_, NS = NS_, NT = NT_, NMT = NMT_, NX = NX_, LEVELS = LV_, MR = MR_, RUNS = RUNS_;
+template <int NC_, int NS_, int NT_, int NMT_, int NX_, int LV_ = 0> struct Shape {
+    static constexpr int NC = NC_, NS = NS_, NT = NT_, NMT = NMT_, NX = NX_, LEVELS = LV_;
     static constexpr int KC = NX * kKa * 2;                 // K per chunk
     static constexpr int CHUNKS_PER_ROUND = (LEVELS ? kLevelRoundSites : kRoundSites) / NX;
     static constexpr int NC2 = NC * NC;
@@ -115,11 +114,8 @@ template <int NC_, int NS_, int NT_, int NMT_, int NX_, int LV_, int MR_, int RU
     static constexpr int PER_TILE = LEVELS ? 4 : 4 / NMT;   // warps of a lane quarter per M tile (LEVELS: one tile)
     static constexpr int CW = LEVELS ? NT / 4 : NT / PER_TILE;   // readout columns per thread
     static constexpr int NSP = NX / 2;                      // site pairs per chunk
-    static constexpr int PS = MR * NC * NX;                 // floats per staged plane (re or im)
-    static constexpr int STAGERS = MR * NC * NX / 8;        // staging threads: 8 (row, colour, site) values each
-    // raw bulk-copy tile of a chunk: per run of rows, NX sites of len x 24 floats, 4 floats of padding
-    // per site (the transposing loads then spread over the banks)
-    static constexpr int RAW_FLOATS = NX * (MR * 24 + 4 * RUNS);
+    static constexpr int PS = kMaxRows * NC * NX;           // floats per staged plane (re or im)
+    static constexpr int STAGERS = kMaxRows * NC * NX / 8;   // staging threads: one (row, colour), 8 sites each
     static constexpr int NXJOB = NCTA * kKa * NSP;          // two X values (a site pair) each
     static constexpr int NUJOB = NS * NC * kKa * NSP;       // two U values (a site pair) each
     // rotation of the thread -> job map in round r: the last round goes to the threads whose earlier
@@ -141,23 +137,21 @@ template <int NC_, int NS_, int NT_, int NMT_, int NX_, int LV_, int MR_, int RU
     static constexpr int A_BYTES = NMT * 128 * KC * 2;
     static constexpr int B_BYTES = kSlicesX * NT * KC * 2;
     static constexpr int S_BYTES = 2 * PS * 4;              // two float planes
-    // operand buffers, two plane buffers, two raw tiles, sEU/sF, list terms, sR1, sSrc, row maps,
-    // four mbarriers and the TMEM address
-    static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + 2 * S_BYTES + 2 * RAW_FLOATS * 4 + 4 * (16 + 256) +
-                                (16 + 8) * kKa * kListLen + 4 * 16 + 4 * kMaxRows * 12 + 4 * 2 * kMaxRows + 48;
+    static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES + 4 * (16 + 256) +
+                                (16 + 8) * kKa * kListLen + 4 * 16 + 4 * kMaxRows * 12 + 32;
     static_assert(NMT * 128 >= kSlices * R && (NMT - 1) * 128 < kSlices * R, "M tiles");
     static_assert(!LEVELS || ((kSlices - 1) * R + 128 <= NMT * 128 && R <= 96 && R % 8 == 0), "level tiles");
     static_assert(NC2 <= NT || NC2 % NT == 0, "column tiles");
     static_assert(TMEM_USED <= 512 && CW % 4 == 0 && CW <= 32, "TMEM / readout");
     static_assert(NXJOB % 32 == 0 && NUJOB % 32 == 0, "jobs fill whole warps");
     static_assert(NX % 8 == 0, "site pairs in groups of 4 per warp");
-    static_assert(STAGERS <= kThr && RUNS * NX <= STAGERS && MR <= kMaxRows, "staging threads");
+    static_assert(STAGERS <= kThr, "staging threads");
     static_assert(R % 8 == 0, "U slices start on a core-matrix row group");
     static_assert(LEVELS || kSlices * R * NT * 8 <= 2 * (A_BYTES + B_BYTES), "combine buffer");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
-using UpperShape = Shape<6, 2, 48, 1, 16, 0, 12, 6>;   // nucleon upper spin components: 2 x 216 per type
-using FullShape = Shape<12, 4, 48, 4, 8, 1, 24, 2>;    // all four spins: 4 x 1728 per type, level accumulators
+using UpperShape = Shape<6, 2, 48, 1, 16>;   // nucleon upper spin components: 2 x 216 per type
+using FullShape = Shape<12, 4, 48, 4, 8, 1>; // all four spins: 4 x 1728 per type, level accumulators
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -200,18 +194,13 @@ template <int KC> __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 __device__ __forceinline__ float2 to_f2(float2 v) { return v; }
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
-// bulk copy (the TMA unit) of `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to
-// shared memory, completing on the mbarrier's transaction count
-__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
-    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+// 4-byte copy; src_bytes 0 writes a zero
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
                  : "memory");
 }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
-                 : "memory");
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Poll the mbarrier for `parity` at most kSpinLimit times (this thread only).
 __device__ __forceinline__ bool poll_parity(uint64_t *mbar, int parity) {
@@ -530,7 +519,6 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
     __shared__ unsigned s_max[48];
     __shared__ int s_bnd[48];
     __shared__ int s_last;
-    __shared__ int s_runs;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // the CTAs of one (slice, range) are adjacent in the grid: they read the same rows of S (L2 reuse)
     const int o = blockIdx.x / SH::NCT, ct = blockIdx.x % SH::NCT;
@@ -548,18 +536,15 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
 
     __nv_bfloat16 *sA0 = reinterpret_cast<__nv_bfloat16 *>(smem);
     __nv_bfloat16 *sB0 = reinterpret_cast<__nv_bfloat16 *>(smem + 2 * SH::A_BYTES);
-    float *sS0 = reinterpret_cast<float *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES));        // 2 plane buffers
-    float *sRaw = sS0 + 2 * 2 * PS;                                                          // 2 raw tiles
-    int *sEU = reinterpret_cast<int *>(sRaw + 2 * SH::RAW_FLOATS);
+    float *sS0 = reinterpret_cast<float *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES));
+    int *sEU = reinterpret_cast<int *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES) + kStage * SH::S_BYTES);
     int *sF = sEU + 16;                                       // [256] grid of X per column
     int4 *sTerm = reinterpret_cast<int4 *>(sF + 256);         // [kKa][kListLen] the op's diquark list terms
     f2x *sTermN = reinterpret_cast<f2x *>(sTerm + kKa * kListLen);  // [kKa][kListLen] (-w, -w)
     int *sR1 = reinterpret_cast<int *>(sTermN + kKa * kListLen);    // [NS][kKa] staged offset of U's row
     int *sSrc = sR1 + 16;                                     // [kMaxRows * NC] flavour << 16 | row * 12 + chi
-    int *sRowOff = sSrc + kMaxRows * 12;                      // [kMaxRows] raw offset of staged row rc (site 0)
-    int *sRowStride = sRowOff + kMaxRows;                     // [kMaxRows] raw floats per site of rc's run
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sRowStride + kMaxRows);  // [4]: MMA buffers 0, 1; raw tiles 0, 1
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 4);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sSrc + kMaxRows * 12);   // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
 
     // zero both operand buffers once: padding rows and unused colour terms stay zero
     {
@@ -600,27 +585,9 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
         const int row = f == 0 ? plan.rows[0][rc] : plan.rows[1][rc - nr0];
         sSrc[e] = f << 16 | (row * 12 + plan.chi[ic]);
     }
-    // runs of consecutive rows per flavour (rows ascending): one bulk copy per run and site, landing in
-    // the raw tile at [run][site][row in run][24 floats] with a per-site stride of len * 24 + 4 floats
     if (tid == 0) {
-        int roff = 0, n_run = 0;
-        for (int f = 0; f < 2; ++f) {
-            const int base = f == 0 ? 0 : nr0;
-            for (int i = 0; i < plan.n_rows[f];) {
-                int j = i + 1;
-                while (j < plan.n_rows[f] && plan.rows[f][j] == plan.rows[f][j - 1] + 1) ++j;
-                const int stride = (j - i) * 24 + 4;
-                for (int k = i; k < j; ++k) {
-                    sRowOff[base + k] = roff + (k - i) * 24;
-                    sRowStride[base + k] = stride;
-                }
-                roff += NX * stride;
-                ++n_run;
-                i = j;
-            }
-        }
-        s_runs = n_run;
-        for (int m = 0; m < 4; ++m) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[m])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
@@ -629,112 +596,45 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
 
-    __syncthreads();   // sSrc, row maps, mbarriers
-    if (s_runs > SH::RUNS || nr > SH::MR) {   // the host launches only plans that fit
-        if (tid == 0) atomicCAS(status, 0, WICK_EINVAL);
-        if (warp == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(SH::TMEM_COLS));
-        }
-        return;
-    }
-    // Staging.  The rows of chunk c become two planes (re, im) of [row][ic][site] -- flavour-0 rows first,
-    // sites innermost, zeros past the range -- in plane buffer c & 1.  complex64 input: the TMA unit
-    // brings each site's runs of rows into raw tile c & 1 by bulk copies (issued two chunks ahead, one per
-    // run and site, counted on the tile's mbarrier), and the last STAGERS threads (the warps with the
-    // lightest jobs) transpose the tile into the planes one chunk ahead: thread st_t takes the plane
-    // entries st_t + k STAGERS, so a warp writes consecutive words.  complex128 input: the same threads
-    // load and round the values directly.
+    __syncthreads();   // sSrc
+    // stage the rows of chunk c as two planes (re, im) of [row][ic][site], flavour-0 rows first, sites
+    // innermost (zeros past the range).  The last STAGERS threads (the warps with the lightest jobs)
+    // each copy one (row, colour) for 8 consecutive sites, from offsets computed once.
     const int st_t = tid - (kThr - SH::STAGERS);
-    const bool stager = st_t >= 0;
-    int n_copy = 0;   // this thread's bulk copy: run, site offsets
-    const ST *cp_src = su;
-    uint32_t cp_bytes = 0;
-    int cp_dst = 0, cp_site = 0;
-    uint32_t chunk_bytes = 0;   // bytes of a full chunk's copies
-    if constexpr (sizeof(ST) == 8) {
-        int k = 0, roff = 0;
-        for (int f = 0; f < 2; ++f)
-            for (int i = 0; i < plan.n_rows[f];) {
-                int j = i + 1;
-                while (j < plan.n_rows[f] && plan.rows[f][j] == plan.rows[f][j - 1] + 1) ++j;
-                const int stride = (j - i) * 24 + 4;
-                chunk_bytes += (uint32_t)(j - i) * 96 * NX;
-                if (stager && st_t >= k * NX && st_t < (k + 1) * NX) {
-                    n_copy = 1;
-                    cp_site = st_t - k * NX;
-                    cp_src = (f == 0 ? su : sd) + plan.rows[f][i] * 12;
-                    cp_bytes = (uint32_t)(j - i) * 96;
-                    cp_dst = roff + cp_site * stride;
-                }
-                roff += NX * stride;
-                ++k;
-                i = j;
-            }
+    const int st_rcc = st_t >= 0 ? st_t / (NX / 8) : 0, st_part = st_t >= 0 ? st_t % (NX / 8) : 0;
+    const bool stager = st_t >= 0 && st_rcc < nr * NC;
+    const ST *st_src = su;
+    if (stager) {
+        const int src_off = sSrc[st_rcc];
+        st_src = ((src_off >> 16) ? sd : su) + (src_off & 0xFFFF);
     }
-    int last_issued[2] = {-1, -1};   // the last chunk whose copies went to raw tile 0 / 1 (every thread)
-    auto issue = [&](int c) {   // bulk copies of chunk c into raw tile c & 1
-        last_issued[c & 1] = c;
-        if constexpr (sizeof(ST) == 8) {
-            const int valid = min(NX, x_end - (x_begin + c * NX));
-            if (st_t == 0) mbar_expect_tx(&mbar[2 + (c & 1)], chunk_bytes / NX * (uint32_t)valid);
-            if (n_copy && cp_site < valid)
-                bulk_copy(sRaw + (c & 1) * SH::RAW_FLOATS + cp_dst,
-                          cp_src + (size_t)(x_begin + c * NX + cp_site) * 144, cp_bytes, &mbar[2 + (c & 1)]);
-        }
-    };
-    const int n_plane = nr * NC * NX;
-    auto prepare = [&](int c) -> bool {   // planes of chunk c into plane buffer c & 1; false: a wait ran out
-        if (!stager) return true;
-        float *plane = sS0 + (c & 1) * (2 * PS);
-        const int valid = min(NX, x_end - (x_begin + c * NX));
-        if constexpr (sizeof(ST) == 8) {
-            if (!poll_parity(&mbar[2 + (c & 1)], (c >> 1) & 1)) return false;
-            const float *raw = sRaw + (c & 1) * SH::RAW_FLOATS;
+    auto stage = [&](int c) {
+        if (stager) {
+            float *dst = sS0 + (c % kStage) * (2 * PS) + st_rcc * NX + st_part * 8;
+            const int xb = x_begin + c * NX + st_part * 8;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int e = st_t + SH::STAGERS * k;
-                if (e < n_plane) {
-                    const int site = e % NX, rcc = e / NX, rc = rcc / NC, ic = rcc - rc * NC;
-                    float2 v = make_float2(0.f, 0.f);
-                    if (site < valid)
-                        v = *reinterpret_cast<const float2 *>(raw + sRowOff[rc] + site * sRowStride[rc] + 2 * plan.chi[ic]);
-                    plane[e] = v.x;
-                    plane[e + PS] = v.y;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int e = st_t + SH::STAGERS * k;
-                if (e < n_plane) {
-                    const int site = e % NX, rcc = e / NX;
-                    const int so = sSrc[rcc];
-                    const ST *src = ((so >> 16) ? sd : su) + (so & 0xFFFF);
-                    const float2 v = site < valid ? to_f2(src[(size_t)(x_begin + c * NX + site) * 144])
-                                                  : make_float2(0.f, 0.f);
-                    plane[e] = v.x;
-                    plane[e + PS] = v.y;
+            for (int s8 = 0; s8 < 8; ++s8) {
+                const bool in = xb + s8 < x_end;
+                const ST *src = st_src + (size_t)(in ? xb + s8 : x_begin) * 144;
+                if constexpr (sizeof(ST) == 8) {
+                    cp_async4(dst + s8, reinterpret_cast<const float *>(src), in ? 4 : 0);
+                    cp_async4(dst + s8 + PS, reinterpret_cast<const float *>(src) + 1, in ? 4 : 0);
+                } else {
+                    const float2 v = in ? to_f2(*src) : make_float2(0.f, 0.f);
+                    dst[s8] = v.x;
+                    dst[s8 + PS] = v.y;
                 }
             }
         }
-        return true;
+        cp_async_commit();
     };
-    // before the CTA leaves, no bulk copy may still be writing its shared memory: wait (bounded) for the
-    // last copies into either tile (earlier ones were waited for before their tile was reused)
-    auto drain_copies = [&]() {
-        if constexpr (sizeof(ST) == 8) {
-            for (int q2 = 0; q2 < 2; ++q2)
-                if (last_issued[q2] >= 0) (void)poll_parity(&mbar[2 + q2], (last_issued[q2] >> 1) & 1);
-        }
-    };
-    issue(0);
-    if (n_chunks > 1) issue(1);
-    int bad = prepare(0) ? 0 : 1;
+    stage(0);
+    cp_async_wait_all();
     asm volatile("tcgen05.fence::before_thread_sync;");
-    bad = __syncthreads_or(bad);
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tbase = *tslot;
+    if (n_chunks > 1) stage(1);
 
     // readout ownership: lane quarter q of M tile t_own, column part cpart of the tile's columns
     const int q = warp & 3, g = warp >> 2;
@@ -763,13 +663,13 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
 
     constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
-    int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0;
+    int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0, bad = 0;
 
     for (int c = 0; c < n_chunks; ++c) {
         const int buf = c & 1;
         __nv_bfloat16 *A = sA0 + buf * (SH::A_BYTES / 2);
         __nv_bfloat16 *B = sB0 + buf * (SH::B_BYTES / 2);
-        const float *S = sS0 + (c & 1) * (2 * PS);
+        const float *S = sS0 + (c % kStage) * (2 * PS);
         // the MMAs of chunk c - 2 read this operand buffer
         if (buf == 0 && waited0 < issued0) {
             if (poll_parity(&mbar[0], waited0 & 1)) ++waited0;
@@ -785,8 +685,8 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
                 else if (job[r].kind == 2) u_job<SH>(job[r], S, A);
             }
         }
-        // the planes of chunk c + 1 (the staging threads); operands of chunk c written
-        if (!bad && c + 1 < n_chunks && !prepare(c + 1)) bad = 1;
+        // staged rows of chunk c + 1 complete (this thread's copies); operands of chunk c written
+        cp_async_wait_all();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         if (__syncthreads_or(bad)) {
@@ -841,8 +741,8 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
         }
         if (buf) ++issued1;
         else ++issued0;
-        // bulk copies of chunk c + 2 into the raw tile chunk c came in (transposed during chunk c - 1)
-        if (c + 2 < n_chunks) issue(c + 2);
+        // stage chunk c + 2 into the buffer chunk c - 1 was built from
+        if (c + 2 < n_chunks) stage(c + 2);
 
         // end of a round: read the accumulators out of TMEM
         if (c % SH::CHUNKS_PER_ROUND == SH::CHUNKS_PER_ROUND - 1 || c == n_chunks - 1) {
@@ -909,7 +809,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
         if (tid == 0) atomicCAS(status, 0, WICK_ETIMEOUT);
         if (waited0 < issued0) (void)poll_parity(&mbar[0], waited0 & 1);
         if (waited1 < issued1) (void)poll_parity(&mbar[1], waited1 & 1);
-        drain_copies();
+        cp_async_wait_all();
         asm volatile("tcgen05.fence::after_thread_sync;");
         __syncthreads();
         if (warp == 0)
@@ -917,7 +817,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
         arrive_and_reduce<SH>(plan, cs, o, n_ranges, partials, counters, blocks, &s_last);
         return;
     }
-    drain_copies();
+    cp_async_wait_all();
 
     if constexpr (SH::LEVELS) {
         // every slice level is in this thread's accumulators: scale and write its row's partials
@@ -991,16 +891,8 @@ int tc_family(const BlockPlan &plan) {
                 if (plan.os_x[t0 + a] != plan.os_x[b0 + a]) return 0;
         }
     }
-    // staged rows and runs of consecutive rows (one bulk copy per run and site) within the family's room
-    int n_run = 0;
-    for (int f = 0; f < 2; ++f)
-        for (int i = 0; i < plan.n_rows[f]; ++i)
-            if (i == 0 || plan.rows[f][i] != plan.rows[f][i - 1] + 1) ++n_run;
-    const int n_rows = plan.n_rows[0] + plan.n_rows[1];
-    if (plan.n_chi == UpperShape::NC && ns == UpperShape::NS && n_rows <= UpperShape::MR && n_run <= UpperShape::RUNS)
-        return 1;
-    if (plan.n_chi == FullShape::NC && ns == FullShape::NS && n_rows <= FullShape::MR && n_run <= FullShape::RUNS)
-        return 2;
+    if (plan.n_chi == UpperShape::NC && ns == UpperShape::NS) return 1;
+    if (plan.n_chi == FullShape::NC && ns == FullShape::NS) return 2;
     return 0;
 }
 
