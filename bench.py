@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the Li-7 and batched sub-records")
     ap.add_argument("--workload", choices=["he4", "li7", "batched", "point"], default="he4",
                     help="he4: the metric's workload (default); li7 / batched: the other scope rows")
-    ap.add_argument("--profile-slab", choices=["mixed", "fp64", "li7"], default=None,
+    ap.add_argument("--profile-slab", choices=["mixed", "fp64", "li7", "contract", "contract_li7"], default=None,
                     help="only run the block build on one source of the He-4 workload (mixed / fp64), or on "
                          "8 time slices of the Li-7 workload (full-spin tables, mixed), for ncu captures")
     return ap.parse_args()
@@ -87,6 +87,36 @@ def fp64_peak_tflops():
         del a, b
         torch.cuda.empty_cache()
     return _FP64_PEAK
+
+
+_L2_PEAK = None
+
+
+def l2_copy_gbs():
+    """L2 roof of this GPU, measured: a device copy between two 24 MB buffers (48 MB, resident in the
+    129 MB L2 after the first pass), read + write bytes over the CUDA-event time, best of 5 runs of 50
+    copies.  MEASURED_PEAKS has no L2 entry."""
+    global _L2_PEAK
+    if _L2_PEAK is None:
+        import torch
+        n = 24 << 20
+        a = torch.empty(n, dtype=torch.uint8, device="cuda").fill_(1)
+        b = torch.empty_like(a)
+        for _ in range(10):
+            b.copy_(a)
+        best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(50):
+                b.copy_(a)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 50)
+        _L2_PEAK = 2 * n / (best / 1e3) / 1e9
+        del a, b
+        torch.cuda.empty_cache()
+    return _L2_PEAK
 
 
 def peaks():
@@ -545,6 +575,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["batched"] = batched_record(2)
         torch.cuda.empty_cache()
+        line["scope"] = scope_records(max(3, min(10, args.steps)))
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         tab = he4_oracle_table()
         Su, Sd = host_np[0]
@@ -570,6 +602,27 @@ def run_profile_slab(args):
     from paper_2411_08962_gb300 import build, operators, synth, wick
     build.build()
     wick.load()
+    if args.profile_slab in ("contract", "contract_li7"):
+        # the contraction alone (MIXED) on resident blocks: the He-4 table on the He-4 lattice's 128
+        # slices, or the Li-7 triton table on 48 slices of 24^3 (blocks gathered from L2)
+        name = "he4" if args.profile_slab == "contract" else "triton"
+        tabs = wick.Tables(operators.nucleus("he4") if name == "he4" else operators.cluster("triton"))
+        terms = wick.wick_reduce_terms(tabs)
+        n_src, T = (4, 32) if name == "he4" else (1, 48)
+        B = torch.randn((n_src, T, tabs.nuc.n_blk), dtype=torch.complex128, device="cuda")
+        C = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
+        for _ in range(max(2, args.warmup)):
+            wick.wick_contract(B, n_src, T, terms, wick.WICK_MIXED, C)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            wick.wick_contract(B, n_src, T, terms, wick.WICK_MIXED, C)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_slab": args.profile_slab, "terms": terms.count,
+                          "ms_per_launch": e0.elapsed_time(e1) / args.steps}))
+        return
     if args.profile_slab == "li7":
         w = synth.WORKLOADS["li7"]
         L, T = w["L"], 8
@@ -818,6 +871,143 @@ def li7_record(steps: int) -> dict:
                       "rel_err_mixed_vs_fp64_max_per_t": rel, "reduce_seconds": reduce_s,
                       "mixed_phases_ms": phases, "roofline": roofline,
                       "gpu_launches_per_step": 1 + len(tabs) + 1}
+
+
+def contraction_case(terms, B, n_src, T, steps, stream, level):
+    """wick_contract (MIXED) alone on resident blocks: time, term-slices/s and the operand bytes it reads
+    per launch -- per term and slice the A gathered block entries (16 B each) and the table entry (padded
+    ids 2 AP B + the weight 8 B) -- against the measured L2 copy rate."""
+    import torch
+
+    from paper_2411_08962_gb300 import wick
+    C = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
+    ms = _timed(lambda: wick.wick_contract(B, n_src, T, terms, wick.WICK_MIXED, C, stream), steps, 2, stream)
+    U, A = terms.count, terms.nucleons
+    ap = 4 if A <= 4 else 8
+    ts = U * n_src * T
+    bytes_ = ts * (A * 16 + 2 * ap + 8)
+    gbs = bytes_ / (ms / 1e3) / 1e9
+    l2 = l2_copy_gbs()
+    return {"terms": U, "A": A, "slices": n_src * T, "launch_ms": ms, "term_slices_per_s": ts / (ms / 1e3),
+            "operand_bytes_per_launch": bytes_, "operand_gbs": gbs, "l2_peak_gbs": l2, "frac_of_l2": gbs / l2,
+            "peak_kind": "measured L2-resident device copy (48 MB)", "gathers_from": level, "gpu_launches": 1}
+
+
+def scope_records(steps: int) -> dict:
+    """The contraction alone (c1) and the rows f2 (truncation), f3 (correlation matrix) and f4 (three-point
+    function) on the He-4 lattice: L=16, T=32, 4 sources, complex64 propagators of one configuration
+    generated on the device; the contraction also on the Li-7 triton table (24^3 x 48, 1 source)."""
+    import torch
+
+    from paper_2411_08962_gb300 import build, operators, synth, wick
+    build.build()
+    wick.load()
+    stream = torch.cuda.current_stream()
+    w = synth.WORKLOADS["he4"]
+    L, T, n_src = w["L"], w["T"], w["n_src"]
+    seed = w["seed"] + 1001
+    shape = (n_src, T, L ** 3, 3, 4, 3, 4)
+    Su = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    Sd, Sig = torch.empty_like(Su), torch.empty_like(Su)
+    for s in range(n_src):
+        wick.wick_synth_propagator(seed, 0, s, L, T, Su[s], stream)
+        wick.wick_synth_propagator(seed, 1, s, L, T, Sd[s], stream)
+        wick.wick_synth_propagator(seed + 1, 0, s, L, T, Sig[s], stream)
+    out = {}
+    tabs = wick.Tables(operators.nucleus("he4"))
+    terms = wick.wick_reduce_terms(tabs)
+    B = torch.empty((n_src, T, tabs.nuc.n_blk), dtype=torch.complex128, device="cuda")
+    wick.wick_build_blocks(Su, Sd, tabs, wick.WICK_MIXED, B, L, T, n_src, stream)
+    C = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
+    wick.wick_contract(B, n_src, T, terms, wick.WICK_MIXED, C, stream)
+    C_full = C.clone()
+
+    # c1: the contraction alone -- He-4 (the slice's blocks staged in shared memory) and the triton
+    # table of Li-7 (442 KB of blocks per slice: gathered from L2)
+    c1 = {"he4": contraction_case(terms, B, n_src, T, steps, stream, "shared memory (blocks staged per slice)")}
+    wl = synth.WORKLOADS["li7"]
+    ttab = wick.Tables(operators.cluster("triton"))
+    tterms = wick.wick_reduce_terms(ttab)
+    Bt = torch.randn((1, wl["T"], ttab.nuc.n_blk), dtype=torch.complex128, device="cuda")
+    c1["li7_triton"] = contraction_case(tterms, Bt, 1, wl["T"], steps, stream, "L2 (blocks of a slice: 442 KB)")
+    tterms.free()
+    del Bt
+    out["contraction"] = c1
+
+    # f2: rank the terms by |w prod B| on a small lattice (4^3 x 4, one source, FP64 blocks), keep the top
+    # fraction, evaluate the kept terms on the full configuration
+    Ls, Ts = 4, 4
+    su = torch.empty((1, Ts, Ls ** 3, 3, 4, 3, 4), dtype=torch.complex128, device="cuda")
+    sd = torch.empty_like(su)
+    wick.wick_synth_propagator(seed + 7, 0, 0, Ls, Ts, su[0], stream)
+    wick.wick_synth_propagator(seed + 7, 1, 0, Ls, Ts, sd[0], stream)
+    Bs = torch.empty((1, Ts, tabs.nuc.n_blk), dtype=torch.complex128, device="cuda")
+    wick.wick_build_blocks(su, sd, tabs, wick.WICK_FP64, Bs, Ls, Ts, 1, stream)
+    t0 = time.perf_counter()
+    mag = terms.magnitudes(Bs, Ts, stream)
+    rank_s = time.perf_counter() - t0
+    f2 = {"ranking_lattice": {"L": Ls, "T": Ts, "n_src": 1}, "ranking_seconds": rank_s, "full_terms": terms.count,
+          "full_contract_ms": c1["he4"]["launch_ms"], "fractions": {}}
+    for frac in (0.01, 0.1, 0.5):
+        tf = wick.wick_reduce_terms(tabs)
+        tf.top(mag, frac)
+        ms = _timed(lambda: wick.wick_contract(B, n_src, T, tf, wick.WICK_MIXED, C, stream), steps, 2, stream)
+        rel = float(((C - C_full).abs() / C_full.abs()).max().item())
+        f2["fractions"][str(frac)] = {"terms": tf.count, "contract_ms": ms, "rel_diff_vs_full_max_per_t": rel}
+        tf.free()
+    out["truncated"] = f2
+
+    # f3: the 3 x 3 correlation matrix of the plane-wave deuteron operators (p up n down, p down n up,
+    # their sum): one reduction over the 9 (sink, source) pairs, one contraction for all elements
+    basis = operators.deuteron_pw_basis()
+    tl = [wick.Tables(n) for n in basis]
+    t0 = time.perf_counter()
+    mt = wick.wick_reduce_terms_matrix(tl)
+    red_s = time.perf_counter() - t0
+    sizes = [wick.wick_reduce_terms(wick.Tables(operators.Nucleus(
+        "el", 2, basis[i].ops, 2, basis[i].chi, basis[i].sink, basis[j].src, basis[i].src_flav))).count
+        for i in range(3) for j in range(3)]
+    Bd = torch.empty((n_src, T, tl[0].nuc.n_blk), dtype=torch.complex128, device="cuda")
+    Cm = torch.empty((9, n_src, T), dtype=torch.complex128, device="cuda")
+
+    def matrix_step():
+        wick.wick_build_blocks(Su, Sd, tl[0], wick.WICK_MIXED, Bd, L, T, n_src, stream)
+        wick.wick_contract(Bd, n_src, T, mt, wick.WICK_MIXED, Cm, stream)
+
+    out["matrix"] = {"operators": [n.name for n in basis], "elements": mt.elements, "merged_terms": mt.count,
+                     "element_terms": sizes, "reduce_seconds": red_s,
+                     "ms_per_config": _timed(matrix_step, steps, 1, stream),
+                     "contract_ms": _timed(lambda: wick.wick_contract(Bd, n_src, T, mt, wick.WICK_MIXED, Cm, stream),
+                                           steps, 1, stream),
+                     "gpu_launches_per_config": 2}
+    del Bd, Cm
+
+    # f4: plane-wave three-point functions through a sequential propagator Sig (current on u): blocks,
+    # derivative blocks, contraction; mixed against FP64
+    f4 = {}
+    for name in ("deuteron", "he4"):
+        tb = wick.Tables(operators.nucleus(name))
+        tm = wick.wick_reduce_terms(tb)
+        D = torch.empty_like(B)
+        C3 = torch.empty((n_src, T), dtype=torch.complex128, device="cuda")
+
+        def step3(prec):
+            wick.wick_build_blocks(Su, Sd, tb, prec, B, L, T, n_src, stream)
+            wick.wick_build_blocks_3pt(Su, Sd, Sig, 0, tb, prec, D, L, T, n_src, stream)
+            wick.wick_contract_3pt(B, D, n_src, T, tm, prec, C3, stream)
+
+        ms = _timed(lambda: step3(wick.WICK_MIXED), steps, 1, stream)
+        cm = C3.clone()
+        ms64 = _timed(lambda: step3(wick.WICK_FP64), max(1, min(3, steps)), 1, stream)
+        f4[name] = {"terms": tm.count, "ms_per_config": ms, "fp64_ms_per_config": ms64,
+                    "rel_err_mixed_vs_fp64_max_per_t": float(((cm - C3).abs() / C3.abs()).max().item()),
+                    "current": "u"}
+        tm.free()
+    out["threepoint"] = f4
+    terms.free()
+    del Su, Sd, Sig, B
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_li7(args):

@@ -301,6 +301,11 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *terms,
  *   contract_chunk_terms   terms per contraction work item, about (64 or more; default 4096);
  *                          the chunking depends on a table's size and this value only, so a
  *                          batch reproduces the single calls of its configurations bit for bit
+ *   hash_log2_start        wick_reduce_terms / wick_reduce_terms_matrix: log2 of the first hash
+ *                          table's slots, 4..28 (default: from the raw-term count).  A table that
+ *                          fills to 3/4 is dropped and the enumeration rerun with twice the slots
+ *   hash_log2_max          log2 of the largest table tried, 4..28 (default 28); past it the
+ *                          reduction fails with WICK_ECAPACITY
  * NULL restores the defaults.  Errors: WICK_EINVAL (a field out of range).
  */
 typedef struct wick_tuning {
@@ -308,9 +313,34 @@ typedef struct wick_tuning {
     int contract_threads;
     int contract_ctas_per_sm;
     int contract_chunk_terms;
+    int hash_log2_start;
+    int hash_log2_max;
 } wick_tuning;
 int wick_set_tuning(const wick_tuning *tuning);
 int wick_get_tuning(wick_tuning *tuning);
+
+/*
+ * Failure detection, driven from the host (no GPU fault is ever provoked).
+ *
+ * wick_inject_alloc_failure: the k-th device allocation the library makes from
+ * now on (workspace, tables, batch scratch, reduction buffers; k >= 1) reports
+ * failure without calling cudaMalloc, so that the error path of every
+ * allocation point can be exercised: the call in progress frees what it took,
+ * returns WICK_ENOMEM and leaves every object it was given as it was.  k = 0
+ * cancels.  Returns the allocations that were still to go before the injected
+ * failure (0: none pending), or WICK_EINVAL for k < 0.  Process-wide.
+ *
+ * wick_selftest_wait: runs one of the library's bounded device waits on a flag
+ * that nothing sets, with a limit of `limit` polls (1 .. 2^22), in a one-thread
+ * kernel on `stream`: which = 0 the wait on a hash-table slot claimed by another
+ * thread (the reduction's insert), 1 the wait on an mbarrier phase (the
+ * tensor-core block build's wait for its MMAs).  The wait gives up, the kernel
+ * records WICK_ETIMEOUT in its status word and returns, and the context stays
+ * usable.  Synchronises `stream`.  Returns that status (WICK_ETIMEOUT when the
+ * wait ran out as designed), or WICK_EINVAL / WICK_ECUDA / WICK_ENOMEM.
+ */
+int wick_inject_alloc_failure(int k);
+int wick_selftest_wait(int which, int limit, wick_stream_t stream);
 
 /*
  * wick_contract without any device allocation.  The paper has no counterpart:

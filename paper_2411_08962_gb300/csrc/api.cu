@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <numeric>
@@ -49,6 +50,25 @@ std::mutex g_mu;
 std::map<int, DevState> g_dev;
 }  // namespace
 
+namespace {
+std::atomic<int> g_alloc_countdown{0};   // wick_inject_alloc_failure: allocations until the one that fails
+}  // namespace
+
+int dev_malloc(void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    for (int n = g_alloc_countdown.load(); n > 0;)
+        if (g_alloc_countdown.compare_exchange_weak(n, n - 1)) {
+            if (n == 1) return WICK_ENOMEM;
+            break;
+        }
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *ptr = nullptr;
+        return WICK_ENOMEM;
+    }
+    return WICK_OK;
+}
+
 void *workspace(int slot, size_t bytes, int *err) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { *err = WICK_ECUDA; return nullptr; }
@@ -60,7 +80,7 @@ void *workspace(int slot, size_t bytes, int *err) {
         d.ws[slot] = nullptr;
         d.ws_bytes[slot] = 0;
         size_t want = bytes + bytes / 4;
-        if (cudaMalloc(&d.ws[slot], want) != cudaSuccess) {
+        if (dev_malloc((void **)&d.ws[slot], want) != WICK_OK) {
             (void)cudaGetLastError();
             *err = WICK_ENOMEM;
             return nullptr;
@@ -85,7 +105,7 @@ int *status_word(int *err) {
     std::lock_guard<std::mutex> lk(g_mu);
     DevState &d = g_dev[dev];
     if (!d.status) {
-        if (cudaMalloc(&d.status, sizeof(int)) != cudaSuccess || cudaMemset(d.status, 0, sizeof(int)) != cudaSuccess) {
+        if (dev_malloc((void **)&d.status, sizeof(int)) != WICK_OK || cudaMemset(d.status, 0, sizeof(int)) != cudaSuccess) {
             (void)cudaGetLastError();
             d.status = nullptr;
             *err = WICK_ENOMEM;
@@ -126,7 +146,7 @@ int terms_table(const wick_terms *t, ContractTable *tab, int *n_blk) {
 // ---------------------------------------------------------------------------
 namespace {
 std::mutex g_tune_mu;
-wick_tuning g_tuning = {0, 0, 0, 0};
+wick_tuning g_tuning = {0, 0, 0, 0, 0, 0};
 }  // namespace
 
 wick_tuning current_tuning() {
@@ -257,8 +277,8 @@ static int make_contract_copies(wick_terms *t) {
     t->d_wd = nullptr;
     const size_t U = (size_t)(t->U ? t->U : 1);
     const int AP = t->A <= 4 ? 4 : 8;
-    if (cudaMalloc(&t->d_ids_pad, sizeof(uint16_t) * U * AP) != cudaSuccess ||
-        cudaMalloc(&t->d_wd, sizeof(double) * U * t->n_el) != cudaSuccess) {
+    if (dev_malloc((void **)&t->d_ids_pad, sizeof(uint16_t) * U * AP) != WICK_OK ||
+        dev_malloc((void **)&t->d_wd, sizeof(double) * U * t->n_el) != WICK_OK) {
         (void)cudaGetLastError();
         return WICK_ENOMEM;
     }
@@ -553,9 +573,9 @@ static int upload_terms(wick_terms *t) {
     cudaFree(t->d_ids); cudaFree(t->d_w); cudaFree(t->d_rep);
     t->d_ids = nullptr; t->d_w = nullptr; t->d_rep = nullptr;
     const size_t U = (size_t)(t->U ? t->U : 1);
-    if (cudaMalloc(&t->d_ids, sizeof(uint16_t) * U * t->A) != cudaSuccess ||
-        cudaMalloc(&t->d_w, sizeof(int64_t) * U) != cudaSuccess ||
-        cudaMalloc(&t->d_rep, sizeof(int64_t) * U) != cudaSuccess) {
+    if (dev_malloc((void **)&t->d_ids, sizeof(uint16_t) * U * t->A) != WICK_OK ||
+        dev_malloc((void **)&t->d_w, sizeof(int64_t) * U) != WICK_OK ||
+        dev_malloc((void **)&t->d_rep, sizeof(int64_t) * U) != WICK_OK) {
         (void)cudaGetLastError();
         return WICK_ENOMEM;
     }
@@ -601,7 +621,7 @@ int wick_terms_magnitudes(const void *blocks, int n_slices, const wick_terms *t,
     if (err) return err;
     if (t->U == 0) return WICK_OK;
     double *d_mag = nullptr;
-    if (cudaMalloc(&d_mag, sizeof(double) * (size_t)t->U) != cudaSuccess) {
+    if (dev_malloc((void **)&d_mag, sizeof(double) * (size_t)t->U) != WICK_OK) {
         (void)cudaGetLastError();
         return WICK_ENOMEM;
     }
@@ -864,8 +884,8 @@ int wick_reduce_terms_matrix(const wick_nucleus *nuclei, int n_nuc, const wick_n
     std::iota(t->rep.begin(), t->rep.end(), (int64_t)0);
     cudaGetDevice(&t->device);
     const size_t U = (size_t)(t->U ? t->U : 1);
-    if (cudaMalloc(&t->d_ids, sizeof(uint16_t) * U * A) != cudaSuccess ||
-        cudaMalloc(&t->d_w, sizeof(int64_t) * U) != cudaSuccess || cudaMalloc(&t->d_rep, sizeof(int64_t) * U) != cudaSuccess) {
+    if (dev_malloc((void **)&t->d_ids, sizeof(uint16_t) * U * A) != WICK_OK ||
+        dev_malloc((void **)&t->d_w, sizeof(int64_t) * U) != WICK_OK || dev_malloc((void **)&t->d_rep, sizeof(int64_t) * U) != WICK_OK) {
         (void)cudaGetLastError();
         wick_terms_free(t);
         return WICK_ENOMEM;
@@ -926,8 +946,10 @@ int wick_contract_3pt(const void *blocks, const void *dblocks, int n_src, int T,
 }
 
 int wick_set_tuning(const wick_tuning *t) {
-    wick_tuning v = {0, 0, 0, 0};
+    wick_tuning v = {0, 0, 0, 0, 0, 0};
     if (t) v = *t;
+    if (v.hash_log2_start != 0 && (v.hash_log2_start < 4 || v.hash_log2_start > 28)) return WICK_EINVAL;
+    if (v.hash_log2_max != 0 && (v.hash_log2_max < 4 || v.hash_log2_max > 28)) return WICK_EINVAL;
     if (v.range_sites < 0 || v.range_sites % 128 || v.range_sites > 4096) return WICK_EINVAL;
     if (v.contract_threads < 0 || v.contract_threads % 32 || v.contract_threads > 512) return WICK_EINVAL;
     if (v.contract_ctas_per_sm < 0 || v.contract_ctas_per_sm > 32) return WICK_EINVAL;
@@ -944,6 +966,24 @@ int wick_get_tuning(wick_tuning *t) {
 }
 
 int wick_status(wick_stream_t stream) { return status_read_clear((cudaStream_t)stream); }
+
+int wick_inject_alloc_failure(int k) {
+    if (k < 0) return WICK_EINVAL;
+    return g_alloc_countdown.exchange(k);
+}
+
+int wick_selftest_wait(int which, int limit, wick_stream_t stream) {
+    if ((which != 0 && which != 1) || limit < 1 || limit > (1 << 22)) return WICK_EINVAL;
+    const cudaStream_t s = (cudaStream_t)stream;
+    int err = WICK_OK;
+    int *status = status_word(&err);
+    if (err) return err;
+    err = status_read_clear(s);   // start from a clear word (an earlier error is dropped)
+    (void)err;
+    err = which == 0 ? selftest_hash_wait(limit, status, s) : selftest_mbar_wait(limit, status, s);
+    if (err) return err;
+    return status_read_clear(s);
+}
 
 const char *wick_strerror(int code) {
     switch (code) {

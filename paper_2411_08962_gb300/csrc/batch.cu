@@ -91,8 +91,8 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
         (void)cudaGetLastError();
         return e;
     };
-    if (cudaMalloc(&bt->block_scratch, bbytes) != cudaSuccess ||
-        cudaMalloc(&bt->contract_scratch, cplan.counter_bytes + cplan.partial_bytes) != cudaSuccess)
+    if (dev_malloc((void **)&bt->block_scratch, bbytes) != WICK_OK ||
+        dev_malloc((void **)&bt->contract_scratch, cplan.counter_bytes + cplan.partial_bytes) != WICK_OK)
         return fail(WICK_ENOMEM);
     if (cudaMemset(bt->block_scratch, 0, bbytes) != cudaSuccess ||
         cudaMemset(bt->contract_scratch, 0, cplan.counter_bytes + cplan.partial_bytes) != cudaSuccess ||

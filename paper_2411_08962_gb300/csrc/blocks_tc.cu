@@ -202,10 +202,10 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_by
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Poll the mbarrier for `parity` at most kSpinLimit times (this thread only).
-__device__ __forceinline__ bool poll_parity(uint64_t *mbar, int parity) {
+// Poll the mbarrier for `parity` at most `limit` times (this thread only).
+__device__ __forceinline__ bool poll_parity(uint64_t *mbar, int parity, int limit = kSpinLimit) {
     uint32_t done = 0;
-    for (int it = 0; it < kSpinLimit && !done; ++it)
+    for (int it = 0; it < limit && !done; ++it)
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
@@ -870,6 +870,15 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
     arrive_and_reduce<SH>(plan, cs, o, n_ranges, partials, counters, blocks, &s_last);
 }
 
+// The wait for an MMA commit on an mbarrier that nothing arrives on: the poll gives up after `limit`
+// tries and the status word gets WICK_ETIMEOUT, as in block_tc_kernel.
+__global__ void mbar_wait_selftest_kernel(int limit, int *status) {
+    __shared__ uint64_t mbar;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    if (!poll_parity(&mbar, 0, limit)) atomicCAS(status, 0, WICK_ETIMEOUT);
+}
+
 // Which compiled shape a plan takes (0: none, 1: upper, 2: full): weights
 // +-2^k, at most 3 colour lists per block type of exactly 4 terms each, the
 // same lists for every spin, and at most 12 staged rows per flavour.
@@ -914,6 +923,13 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 }  // namespace
 
 bool tc_applicable(const BlockPlan &plan) { return tc_family(plan) != 0; }
+
+int selftest_mbar_wait(int limit, int *status, cudaStream_t stream) {
+    mbar_wait_selftest_kernel<<<1, 1, 0, stream>>>(limit, status);
+    WICK_CUDA_TRY(cudaGetLastError());
+    WICK_CUDA_TRY(cudaStreamSynchronize(stream));
+    return WICK_OK;
+}
 
 int tc_range_sites(int requested) {
     return requested >= kRoundSites && requested % kRoundSites == 0 && requested <= 4096 ? requested

@@ -177,6 +177,11 @@ ContractTune contract_tune(const wick_tuning &t);
 constexpr int kWsBlockPartials = 0, kWsContractPartials = 1, kWsDet = 2, kWsBlockCounters = 3,
               kWsContractCounters = 4, kWsSlots = 5;
 void *workspace(int slot, size_t bytes, int *err);
+// every device allocation of the library: cudaMalloc, or WICK_ENOMEM injected by wick_inject_alloc_failure
+int dev_malloc(void **ptr, size_t bytes);
+// bounded-wait self tests (dedup.cu: hash-slot wait; blocks_tc.cu: mbarrier wait); status: device word
+int selftest_hash_wait(int limit, int *status, cudaStream_t stream);
+int selftest_mbar_wait(int limit, int *status, cudaStream_t stream);
 int *status_word(int *err);                     // per-device status word
 int status_read_clear(cudaStream_t stream);
 

@@ -162,7 +162,7 @@ struct HashTable {
 __device__ __forceinline__ uint64_t load_volatile(const uint64_t *p) { return *(volatile const uint64_t *)p; }
 
 // Find or claim the slot of (h0, h1); -1 on a full table or a wait that ran out.
-__device__ int64_t table_slot(const HashTable &ht, uint64_t h0, uint64_t h1, int *status) {
+__device__ int64_t table_slot(const HashTable &ht, uint64_t h0, uint64_t h1, int *status, int spin_limit = kSpinLimit) {
     uint64_t slot = mix64(h0 * 0x9E3779B97F4A7C15ull ^ h1) & ht.mask;
     for (uint64_t probe = 0; probe <= ht.mask; ++probe) {
         uint64_t k = load_volatile(ht.k0 + slot);
@@ -181,7 +181,7 @@ __device__ int64_t table_slot(const HashTable &ht, uint64_t h0, uint64_t h1, int
         }
         int spins = 0;
         while (k & BUSY) {
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 atomicCAS(status, 0, WICK_ETIMEOUT);
                 return -1;
             }
@@ -242,6 +242,12 @@ enum_hash_kernel(const __grid_constant__ EnumPlan ep, const TermTables tt, int t
             }
         }
     }
+}
+
+// The wait of table_slot on a slot that another thread has claimed (BUSY) but not yet published, on a
+// one-slot table whose slot is claimed and never published: the wait gives up after spin_limit polls.
+__global__ void hash_wait_selftest_kernel(HashTable ht, int spin_limit, int *status) {
+    (void)table_slot(ht, 1ull, 2ull, status, spin_limit);
 }
 
 // ---------------------------------------------------------------------------
@@ -372,7 +378,7 @@ struct DevBuf {
     T *p = nullptr;
     ~DevBuf() { if (p) cudaFree(p); }
     int alloc(size_t n) {
-        if (cudaMalloc(&p, sizeof(T) * (n ? n : 1)) != cudaSuccess) { (void)cudaGetLastError(); p = nullptr; return WICK_ENOMEM; }
+        if (dev_malloc((void **)&p, sizeof(T) * (n ? n : 1)) != WICK_OK) { (void)cudaGetLastError(); p = nullptr; return WICK_ENOMEM; }
         return WICK_OK;
     }
     int upload(const T *h, size_t n, cudaStream_t s) {
@@ -445,8 +451,11 @@ int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc,
     const uint64_t n_tasks = n_rows * rd_tiles;
     // table size: start from an estimate and double while it overflows
     const uint64_t upper = (uint64_t)(ep.n_raw >> ep.A) + 1024;
+    const wick_tuning tune = current_tuning();
     uint64_t cap = next_pow2(upper < (1ull << 20) ? 2 * upper : (1ull << 21));
-    const uint64_t cap_max = 1ull << 28;
+    const uint64_t cap_max = 1ull << (tune.hash_log2_max ? tune.hash_log2_max : 28);
+    if (tune.hash_log2_start) cap = 1ull << tune.hash_log2_start;
+    if (cap > cap_max) cap = cap_max;
     DevBuf<unsigned long long> d_cnt;  // [0] n_keys, [1] n_zero, [2] n_out, [3] n_keys_seen
     if ((err = d_cnt.alloc(4))) return err;
     for (;;) {
@@ -516,9 +525,9 @@ int run_reduce(const EnumPlan &ep, const BlockPlan &bp, const wick_nucleus *nuc,
         }
         uint16_t *ids = nullptr;
         int64_t *w = nullptr, *reps = nullptr;
-        if (cudaMalloc(&ids, sizeof(uint16_t) * (size_t)(U ? U : 1) * ep.A) != cudaSuccess ||
-            cudaMalloc(&w, sizeof(int64_t) * (size_t)(U ? U : 1)) != cudaSuccess ||
-            cudaMalloc(&reps, sizeof(int64_t) * (size_t)(U ? U : 1)) != cudaSuccess) {
+        if (dev_malloc((void **)&ids, sizeof(uint16_t) * (size_t)(U ? U : 1) * ep.A) != WICK_OK ||
+            dev_malloc((void **)&w, sizeof(int64_t) * (size_t)(U ? U : 1)) != WICK_OK ||
+            dev_malloc((void **)&reps, sizeof(int64_t) * (size_t)(U ? U : 1)) != WICK_OK) {
             (void)cudaGetLastError();
             cudaFree(ids); cudaFree(w); cudaFree(reps);
             return WICK_ENOMEM;
@@ -575,6 +584,22 @@ int term_keys(const BlockPlan &bp, int n_blk, const uint16_t *ids, int64_t U, in
     WICK_CUDA_TRY(cudaGetLastError());
     WICK_CUDA_TRY(cudaMemcpyAsync(keys, d_keys.p, sizeof(uint64_t) * 2 * (size_t)U, cudaMemcpyDeviceToHost, stream));
     WICK_CUDA_TRY(cudaMemcpyAsync(eps, d_eps.p, (size_t)U, cudaMemcpyDeviceToHost, stream));
+    WICK_CUDA_TRY(cudaStreamSynchronize(stream));
+    return WICK_OK;
+}
+
+int selftest_hash_wait(int limit, int *status, cudaStream_t stream) {
+    DevBuf<uint64_t> k;   // k0[0] = the claimed slot, k1[0]
+    DevBuf<unsigned long long> rest;
+    int err = k.alloc(2);
+    if (!err) err = rest.alloc(3);
+    if (err) return err;
+    const uint64_t claimed[2] = {1ull | BUSY, 0ull};
+    WICK_CUDA_TRY(cudaMemcpyAsync(k.p, claimed, sizeof(claimed), cudaMemcpyHostToDevice, stream));
+    WICK_CUDA_TRY(cudaMemsetAsync(rest.p, 0, 3 * sizeof(unsigned long long), stream));
+    HashTable ht{k.p, k.p + 1, rest.p, rest.p + 1, 0, rest.p + 2, 1};
+    hash_wait_selftest_kernel<<<1, 1, 0, stream>>>(ht, limit, status);
+    WICK_CUDA_TRY(cudaGetLastError());
     WICK_CUDA_TRY(cudaStreamSynchronize(stream));
     return WICK_OK;
 }

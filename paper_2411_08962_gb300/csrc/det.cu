@@ -637,8 +637,8 @@ int classify(const std::vector<Key> &snk, const std::vector<Key> &src, int n, ui
         cudaFree(dq);
         cudaFree(dv);
     };
-    if (cudaMalloc(&ds, hs.size()) != cudaSuccess || cudaMalloc(&dq, hq.size()) != cudaSuccess ||
-        cudaMalloc(&dv, sizeof(uint64_t) * total * trials) != cudaSuccess) {
+    if (dev_malloc((void **)&ds, hs.size()) != WICK_OK || dev_malloc((void **)&dq, hq.size()) != WICK_OK ||
+        dev_malloc((void **)&dv, sizeof(uint64_t) * total * trials) != WICK_OK) {
         cleanup();
         (void)cudaGetLastError();
         return WICK_ENOMEM;
@@ -713,7 +713,7 @@ void free_plan(wick_det_plan *p) {
 
 template <typename T> int upload(T **dst, const std::vector<T> &src) {
     const size_t bytes = sizeof(T) * std::max<size_t>(src.size(), 1);
-    if (cudaMalloc(dst, bytes) != cudaSuccess) {
+    if (dev_malloc((void **)dst, bytes) != WICK_OK) {
         (void)cudaGetLastError();
         *dst = nullptr;
         return WICK_ENOMEM;

@@ -32,7 +32,8 @@ EXPORTS = ("wick_block_count", "wick_build_blocks", "wick_upload_rows", "wick_re
            "wick_synth_propagator", "wick_cluster_product", "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats",
            "wick_det_element_offsets", "wick_det_copy", "wick_det_contract", "wick_det_contract_3pt", "wick_det_free", "wick_set_tuning", "wick_get_tuning",
            "wick_build_blocks_3pt", "wick_contract_3pt", "wick_reduce_terms_matrix", "wick_terms_elements",
-           "wick_terms_copy_matrix", "wick_strerror", "wick_version")
+           "wick_terms_copy_matrix", "wick_inject_alloc_failure", "wick_selftest_wait", "wick_strerror",
+           "wick_version")
 
 
 class WickError(RuntimeError):
@@ -63,7 +64,7 @@ class wick_nucleus(C.Structure):
 
 class wick_tuning(C.Structure):
     _fields_ = [("range_sites", C.c_int), ("contract_threads", C.c_int), ("contract_ctas_per_sm", C.c_int),
-                ("contract_chunk_terms", C.c_int)]
+                ("contract_chunk_terms", C.c_int), ("hash_log2_start", C.c_int), ("hash_log2_max", C.c_int)]
 
 
 class wick_quark_operator(C.Structure):
@@ -136,6 +137,8 @@ def load(path: str = LIB_PATH):
             L.wick_terms_copy_matrix.argtypes = [vp, vp, vp, vp]
             L.wick_set_tuning.argtypes = [P(wick_tuning)]
             L.wick_get_tuning.argtypes = [P(wick_tuning)]
+            L.wick_inject_alloc_failure.argtypes = [C.c_int]
+            L.wick_selftest_wait.argtypes = [C.c_int, C.c_int, vp]
             L.wick_strerror.argtypes = [C.c_int]
             L.wick_strerror.restype = C.c_char_p
             L.wick_version.restype = C.c_char_p
@@ -147,7 +150,8 @@ def load(path: str = LIB_PATH):
                       "wick_det_reduce", "wick_det_reduce_matrix", "wick_det_stats", "wick_det_element_offsets",
                       "wick_det_copy", "wick_det_contract", "wick_det_contract_3pt", "wick_set_tuning",
                       "wick_get_tuning", "wick_build_blocks_3pt", "wick_contract_3pt", "wick_reduce_terms_matrix",
-                      "wick_terms_elements", "wick_terms_copy_matrix"):
+                      "wick_terms_elements", "wick_terms_copy_matrix", "wick_inject_alloc_failure",
+                      "wick_selftest_wait"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -469,7 +473,8 @@ def wick_cluster_product(Ca, Cb, out, stream=None):
            "wick_cluster_product")
 
 
-TUNING_FIELDS = ("range_sites", "contract_threads", "contract_ctas_per_sm", "contract_chunk_terms")
+TUNING_FIELDS = ("range_sites", "contract_threads", "contract_ctas_per_sm", "contract_chunk_terms",
+                 "hash_log2_start", "hash_log2_max")
 
 
 def wick_set_tuning(tuning=None):
@@ -486,6 +491,24 @@ def wick_get_tuning() -> dict:
 
 def wick_status(stream=None) -> int:
     return int(load().wick_status(_stream(stream)))
+
+
+def wick_inject_alloc_failure(k: int) -> int:
+    """Make the library's k-th device allocation from now report failure (host-side fault injection;
+    0 cancels); returns the allocations that were still to go before a pending injected failure."""
+    r = int(load().wick_inject_alloc_failure(int(k)))
+    if r < 0:
+        raise WickError(r, "wick_inject_alloc_failure")
+    return r
+
+
+def wick_selftest_wait(which: int, limit: int, stream=None) -> int:
+    """Run a bounded device wait (0 hash-slot, 1 mbarrier) on a flag nothing sets; returns the status the
+    kernel recorded (WICK_ETIMEOUT when the wait ran out)."""
+    r = int(load().wick_selftest_wait(int(which), int(limit), _stream(stream)))
+    if r in (WICK_EINVAL, WICK_ENOMEM, WICK_ECUDA):
+        raise WickError(r, "wick_selftest_wait")
+    return r
 
 
 def wick_version() -> str:

@@ -167,9 +167,10 @@ def test_tuning_is_validated_and_kept(lib):
     try:
         wick.wick_set_tuning({"range_sites": 1024, "contract_threads": 128, "contract_chunk_terms": 2048})
         assert wick.wick_get_tuning() == {"range_sites": 1024, "contract_threads": 128, "contract_ctas_per_sm": 0,
-                                          "contract_chunk_terms": 2048}
+                                          "contract_chunk_terms": 2048, "hash_log2_start": 0, "hash_log2_max": 0}
         for bad in ({"range_sites": 100}, {"range_sites": 8192}, {"contract_threads": 100},
-                    {"contract_threads": 1024}, {"contract_ctas_per_sm": -1}, {"contract_chunk_terms": 10}):
+                    {"contract_threads": 1024}, {"contract_ctas_per_sm": -1}, {"contract_chunk_terms": 10},
+                    {"hash_log2_start": 3}, {"hash_log2_start": 29}, {"hash_log2_max": 2}, {"hash_log2_max": 30}):
             with pytest.raises(wick.WickError) as e:
                 wick.wick_set_tuning(bad)
             assert e.value.code == wick.WICK_EINVAL
@@ -177,6 +178,17 @@ def test_tuning_is_validated_and_kept(lib):
     finally:
         wick.wick_set_tuning(None)
     assert wick.wick_get_tuning() == {f: 0 for f in wick.TUNING_FIELDS}
+
+
+def test_alloc_failure_injection_is_host_state():
+    """The injection is a process-wide countdown on the host: set, read back, cancelled (no GPU call)."""
+    assert wick.wick_inject_alloc_failure(0) == 0
+    assert wick.wick_inject_alloc_failure(3) == 0
+    assert wick.wick_inject_alloc_failure(5) == 3      # nothing allocated since: still 3 to go
+    assert wick.wick_inject_alloc_failure(0) == 5
+    with pytest.raises(wick.WickError) as e:
+        wick.wick_inject_alloc_failure(-1)
+    assert e.value.code == wick.WICK_EINVAL
 
 
 def test_product_planewave_operators_equal_oracle():
