@@ -136,7 +136,10 @@ int terms_table(const wick_terms *t, ContractTable *tab, int *n_blk) {
     cudaGetDevice(&dev);
     if (dev != t->device) return WICK_EINVAL;  // the device copies live on another GPU
     if (t->U > 0 && (!t->d_ids_pad || !t->d_wd)) return WICK_EINVAL;
-    *tab = {t->d_ids_pad, t->d_wd, t->U, t->A, t->scale, t->n_el > 1 ? t->el_scale.data() : nullptr};
+    // the float-pair weights follow the doubles in the same allocation (make_contract_copies)
+    const size_t nw = (size_t)(t->U ? t->U : 1) * t->n_el;
+    *tab = {t->d_ids_pad, t->d_wd, t->U, t->A, t->scale, t->n_el > 1 ? t->el_scale.data() : nullptr,
+            t->d_wd ? reinterpret_cast<const float2 *>(t->d_wd + nw) : nullptr};
     *n_blk = t->n_blk;
     return WICK_OK;
 }
@@ -269,7 +272,8 @@ static int prop_ok(const wick_prop *p) {
 
 using namespace wick;
 
-// the contraction's copies of a table (padded ids, FP64 weights), from its device ids and its weights
+// the contraction's copies of a table (padded ids; the weights as doubles, then as exact float pairs for
+// the MIXED term sums), from its device ids and its weights
 static int make_contract_copies(wick_terms *t) {
     cudaFree(t->d_ids_pad);
     cudaFree(t->d_wd);
@@ -278,7 +282,7 @@ static int make_contract_copies(wick_terms *t) {
     const size_t U = (size_t)(t->U ? t->U : 1);
     const int AP = t->A <= 4 ? 4 : 8;
     if (dev_malloc((void **)&t->d_ids_pad, sizeof(uint16_t) * U * AP) != WICK_OK ||
-        dev_malloc((void **)&t->d_wd, sizeof(double) * U * t->n_el) != WICK_OK) {
+        dev_malloc((void **)&t->d_wd, (sizeof(double) + sizeof(float2)) * U * t->n_el) != WICK_OK) {
         (void)cudaGetLastError();
         return WICK_ENOMEM;
     }
@@ -291,6 +295,8 @@ static int make_contract_copies(wick_terms *t) {
         std::vector<double> wd(w.begin(), w.end());
         WICK_CUDA_TRY(cudaMemcpy(t->d_wd, wd.data(), sizeof(double) * wd.size(), cudaMemcpyHostToDevice));
     }
+    err = split_weights(t->d_wd, t->U * t->n_el, reinterpret_cast<float2 *>(t->d_wd + U * t->n_el), nullptr);
+    if (err) return err;
     WICK_CUDA_TRY(cudaDeviceSynchronize());
     return WICK_OK;
 }
@@ -758,8 +764,13 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *t, int
     if (err) return err;
     void *cnt = workspace(kWsContractCounters, plan.counter_bytes, &err);
     if (err) return err;
+    void *conv = nullptr;
+    if (plan.convert_bytes) {
+        conv = workspace(kWsContractConvert, plan.convert_bytes, &err);
+        if (err) return err;
+    }
     return launch_contract((const double2 *)blocks, n_blk, 1, n_slices, &tab, 1, precision, plan, cnt,
-                           (double2 *)part, (double2 *)C_out, (cudaStream_t)stream);
+                           (double2 *)part, (double2 *)C_out, (cudaStream_t)stream, nullptr, conv);
 }
 
 int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms *t, int precision, void *C_out,
@@ -941,8 +952,13 @@ int wick_contract_3pt(const void *blocks, const void *dblocks, int n_src, int T,
     if (err) return err;
     void *cnt = workspace(kWsContractCounters, plan.counter_bytes, &err);
     if (err) return err;
+    void *conv = nullptr;
+    if (plan.convert_bytes) {
+        conv = workspace(kWsContractConvert, plan.convert_bytes, &err);
+        if (err) return err;
+    }
     return launch_contract((const double2 *)blocks, n_blk, 1, n_slices, &tab, 1, precision, plan, cnt, (double2 *)part,
-                           (double2 *)C_out, (cudaStream_t)stream, (const double2 *)dblocks);
+                           (double2 *)C_out, (cudaStream_t)stream, (const double2 *)dblocks, conv);
 }
 
 int wick_set_tuning(const wick_tuning *t) {

@@ -92,10 +92,12 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
         return e;
     };
     if (dev_malloc((void **)&bt->block_scratch, bbytes) != WICK_OK ||
-        dev_malloc((void **)&bt->contract_scratch, cplan.counter_bytes + cplan.partial_bytes) != WICK_OK)
+        dev_malloc((void **)&bt->contract_scratch, cplan.counter_bytes + cplan.partial_bytes + cplan.convert_bytes) !=
+            WICK_OK)
         return fail(WICK_ENOMEM);
     if (cudaMemset(bt->block_scratch, 0, bbytes) != cudaSuccess ||
-        cudaMemset(bt->contract_scratch, 0, cplan.counter_bytes + cplan.partial_bytes) != cudaSuccess ||
+        cudaMemset(bt->contract_scratch, 0, cplan.counter_bytes + cplan.partial_bytes + cplan.convert_bytes) !=
+            cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess)
         return fail(WICK_ECUDA);
     unsigned char *bsc = static_cast<unsigned char *>(bt->block_scratch);
@@ -135,8 +137,9 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
     if (!launch_err) {
         launch_err = launch_contract((const double2 *)blocks, plan.n_out, n_cfg, (int)n_slices, tabs.data(), n_tables,
                                      precision, cplan, csc, (double2 *)(csc + cplan.counter_bytes), (double2 *)C_out,
-                                     cap);
-        bt->n_launches += 1;
+                                     cap, nullptr,
+                                     cplan.convert_bytes ? csc + cplan.counter_bytes + cplan.partial_bytes : nullptr);
+        bt->n_launches += cplan.convert_bytes ? 2 : 1;   // the block conversion, then the contraction
     }
     const cudaError_t ec = cudaStreamEndCapture(cap, &bt->graph);
     cudaStreamDestroy(cap);

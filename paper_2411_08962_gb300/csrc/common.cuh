@@ -128,6 +128,7 @@ struct ContractTable {         // a reduced table as the contraction reads it
     int A;
     double scale;
     const double *el_scale = nullptr;   // matrix tables: scale of each of the n_el elements (host)
+    const float2 *wf = nullptr;         // [U][n_el] the weights as exact float pairs (hi, lo) (MIXED)
 };
 struct ContractTune {          // 0 = default
     int threads;               // per CTA: 32..512, multiple of 32 (default 256)
@@ -145,16 +146,20 @@ struct ContractPlan {
     size_t counters;           // (configuration, table, slice) counters
     size_t counter_bytes;      // the item counters and the counters: zero before the first launch
     size_t partial_bytes;      // one complex128 per work item
+    size_t convert_bytes;      // MIXED without staging: the blocks (and derivative blocks) as float pairs
 };
 int contract_plan(int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab, int precision,
                   const ContractTune &tune, int64_t max_items, ContractPlan *plan, int kind = 0);
 // counters: plan.counter_bytes, zero before the first launch (cleared again by every launch; a region
-// that holds nothing else); partials: plan.partial_bytes
+// that holds nothing else); partials: plan.partial_bytes; convert: plan.convert_bytes (or null: the MIXED
+// gathers then convert each block entry as they load it)
 int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab,
                     int precision, const ContractPlan &plan, void *counters, double2 *partials, double2 *C_out,
-                    cudaStream_t stream, const double2 *dblocks = nullptr);
+                    cudaStream_t stream, const double2 *dblocks = nullptr, void *convert = nullptr);
 int pad_table(const uint16_t *ids, const int64_t *w, int64_t U, int A, uint16_t *ids_pad, double *wd,
               cudaStream_t stream);
+// wf[i] = the weight wd[i] as a pair of floats hi + lo (exact for |wd| < 2^48)
+int split_weights(const double *wd, int64_t n, float2 *wf, cudaStream_t stream);
 // per-term contribution magnitudes on n_slices slices of blocks (device, mag: U doubles)
 int launch_magnitudes(const double2 *blocks, int n_blk, int n_slices, const ContractTable &tab, double *mag,
                       cudaStream_t stream);
@@ -173,9 +178,9 @@ wick_tuning current_tuning();
 ContractTune contract_tune(const wick_tuning &t);
 // per-device cached scratch, zeroed when (re)allocated: 0 = block partials, 1 = contraction partials,
 // 2 = determinant scratch, 3 = block-build counters, 4 = contraction counters (the counter slots hold
-// nothing but counters, which every launch leaves at zero)
+// nothing but counters, which every launch leaves at zero), 5 = blocks converted for the contraction
 constexpr int kWsBlockPartials = 0, kWsContractPartials = 1, kWsDet = 2, kWsBlockCounters = 3,
-              kWsContractCounters = 4, kWsSlots = 5;
+              kWsContractCounters = 4, kWsContractConvert = 5, kWsSlots = 6;
 void *workspace(int slot, size_t bytes, int *err);
 // every device allocation of the library: cudaMalloc, or WICK_ENOMEM injected by wick_inject_alloc_failure
 int dev_malloc(void **ptr, size_t bytes);

@@ -21,8 +21,14 @@
 // next launch without a memset.
 //
 // MIXED keeps every block entry as a double-FP32 pair and forms the products
-// with error-free float operations (about 44 bits), so the float pipes do the
-// products and only the term sum is FP64.
+// with error-free float operations (about 44 bits) on the float pipes.  Each
+// thread sums its terms' weighted products in double-FP32 too (the integer
+// weights as exact float pairs) and adds that partial into its FP64 sum every
+// kMixedGroup terms (correlators, three-point functions and matrices of up
+// to 4 elements), so the FP64 pipe -- a small fraction of the float rate on
+// this GPU -- sees two conversions and two additions per component per group
+// instead of per term.  Block layouts too large to stage are converted to
+// float pairs once per launch (convert_kernel) instead of at every gather.
 #include <algorithm>
 
 #include "common.cuh"
@@ -35,6 +41,7 @@ namespace {
 constexpr int kMaxThreads = 512;
 constexpr int64_t kDefaultChunkTerms = 4096;   // terms per work item unless tuned
 constexpr size_t kSmemStageLimit = 96 * 1024;   // stage a slice's blocks in shared memory up to this size
+constexpr int kMixedGroup = 16;                 // MIXED: terms per double-FP32 partial of a thread
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -78,6 +85,7 @@ struct Kind {
 struct TableWork {
     const uint16_t *ids;   // [U][AP]
     const double *w;       // [U][NEL]
+    const float2 *wf;      // [U][NEL] the weights as exact float pairs
     int64_t U;
     int64_t chunk;         // terms per item
     int A, n_chunks;       // chunks per (configuration, slice)
@@ -90,6 +98,8 @@ struct ContractWork {
     int n_tab;
     const double2 *blocks;     // [n_cfg][n_slices][n_blk]
     const double2 *dblocks;    // derivative blocks (KIND 1), same layout
+    const cdf *fblocks;        // MIXED without staging: blocks (and derivative blocks) converted to float
+    const cdf *fdblocks;       //   pairs before the launch, or null (converted at each gather)
     int n_blk, n_cfg, n_slices;
     int items_per_cs;          // items of one (configuration, slice)
     int64_t n_items;
@@ -100,21 +110,40 @@ struct ContractWork {
     double el_scale[16];       // matrix elements: scale of each element
 };
 
+__device__ __forceinline__ cdf ldcg_cdf(const cdf *p) {
+    const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+    return {{v.x, v.y}, {v.z, v.w}};
+}
+
 template <typename C, bool MIXED, bool STAGE>
-__device__ __forceinline__ C load_block(const C *sB, const double2 *gB, int id) {
-    if constexpr (STAGE) return sB[id];
-    else return Elem<MIXED>::from(__ldcg(gB + id));
+__device__ __forceinline__ C load_block(const C *sB, const double2 *gB, const cdf *fB, int id) {
+    if constexpr (STAGE) {
+        return sB[id];
+    } else if constexpr (MIXED) {
+        if (fB) return ldcg_cdf(fB + id);
+        return Elem<MIXED>::from(__ldcg(gB + id));
+    } else {
+        return Elem<MIXED>::from(__ldcg(gB + id));
+    }
 }
 
 // this thread's share of terms [u0, u1) of one table, against one slice's blocks (and derivative blocks)
 template <int A, bool MIXED, bool STAGE, int KIND>
 __device__ __forceinline__ void eval_terms(const TableWork &tw, int64_t u0, int64_t u1,
                                            const typename Elem<MIXED>::T *sB, const typename Elem<MIXED>::T *sD,
-                                           const double2 *gB, const double2 *gD, double *ax, double *ay) {
+                                           const double2 *gB, const double2 *gD, const cdf *fB, const cdf *fD,
+                                           double *ax, double *ay) {
     using E = Elem<MIXED>;
     using C = typename E::T;
     using K = Kind<KIND>;
     constexpr int AP = A <= 4 ? 4 : 8;
+    // MIXED: double-FP32 group partials (up to 4 matrix elements; more would not fit the registers, and
+    // those sum each term in FP64)
+    constexpr bool GROUP = MIXED && K::NEL <= 4;
+    df gx[K::NEL], gy[K::NEL];
+    int in_group = 0;
+#pragma unroll
+    for (int e = 0; e < K::NEL; ++e) gx[e] = gy[e] = df{0.f, 0.f};
     for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
         uint16_t id[AP];
         if constexpr (AP == 4) {
@@ -136,25 +165,54 @@ __device__ __forceinline__ void eval_terms(const TableWork &tw, int64_t u0, int6
             C pre[A];
             pre[0] = E::one();
 #pragma unroll
-            for (int k = 1; k < A; ++k) pre[k] = E::mul(pre[k - 1], load_block<C, MIXED, STAGE>(sB, gB, id[k - 1]));
+            for (int k = 1; k < A; ++k)
+                pre[k] = E::mul(pre[k - 1], load_block<C, MIXED, STAGE>(sB, gB, fB, id[k - 1]));
             C suf = E::one();
-            p = E::mul(pre[A - 1], load_block<C, MIXED, STAGE>(sD, gD, id[A - 1]));
+            p = E::mul(pre[A - 1], load_block<C, MIXED, STAGE>(sD, gD, fD, id[A - 1]));
 #pragma unroll
             for (int k = A - 2; k >= 0; --k) {
-                suf = E::mul(suf, load_block<C, MIXED, STAGE>(sB, gB, id[k + 1]));
-                p = E::add(p, E::mul(E::mul(pre[k], load_block<C, MIXED, STAGE>(sD, gD, id[k])), suf));
+                suf = E::mul(suf, load_block<C, MIXED, STAGE>(sB, gB, fB, id[k + 1]));
+                p = E::add(p, E::mul(E::mul(pre[k], load_block<C, MIXED, STAGE>(sD, gD, fD, id[k])), suf));
             }
         } else {
-            p = load_block<C, MIXED, STAGE>(sB, gB, id[0]);
+            p = load_block<C, MIXED, STAGE>(sB, gB, fB, id[0]);
 #pragma unroll
-            for (int k = 1; k < A; ++k) p = E::mul(p, load_block<C, MIXED, STAGE>(sB, gB, id[k]));
+            for (int k = 1; k < A; ++k) p = E::mul(p, load_block<C, MIXED, STAGE>(sB, gB, fB, id[k]));
         }
-        const double pr = E::re(p), pi = E::im(p);
+        if constexpr (GROUP) {
 #pragma unroll
-        for (int e = 0; e < K::NEL; ++e) {
-            const double wu = __ldg(tw.w + u * K::NEL + e);
-            ax[e] = fma(wu, pr, ax[e]);
-            ay[e] = fma(wu, pi, ay[e]);
+            for (int e = 0; e < K::NEL; ++e) {
+                const float2 wv = __ldg(tw.wf + u * K::NEL + e);
+                const df w{wv.x, wv.y};
+                gx[e] = df_add(gx[e], df_mul(w, p.x));
+                gy[e] = df_add(gy[e], df_mul(w, p.y));
+            }
+            if (++in_group == kMixedGroup) {
+#pragma unroll
+                for (int e = 0; e < K::NEL; ++e) {
+                    ax[e] += to_double(gx[e]);
+                    ay[e] += to_double(gy[e]);
+                    gx[e] = gy[e] = df{0.f, 0.f};
+                }
+                in_group = 0;
+            }
+        } else {
+            const double pr = E::re(p), pi = E::im(p);
+#pragma unroll
+            for (int e = 0; e < K::NEL; ++e) {
+                const double wu = __ldg(tw.w + u * K::NEL + e);
+                ax[e] = fma(wu, pr, ax[e]);
+                ay[e] = fma(wu, pi, ay[e]);
+            }
+        }
+    }
+    if constexpr (GROUP) {
+        if (in_group) {
+#pragma unroll
+            for (int e = 0; e < K::NEL; ++e) {
+                ax[e] += to_double(gx[e]);
+                ay[e] += to_double(gy[e]);
+            }
         }
     }
 }
@@ -162,24 +220,25 @@ __device__ __forceinline__ void eval_terms(const TableWork &tw, int64_t u0, int6
 template <bool MIXED, bool STAGE, int KIND>
 __device__ __forceinline__ void eval_any(const TableWork &tw, int64_t u0, int64_t u1,
                                          const typename Elem<MIXED>::T *sB, const typename Elem<MIXED>::T *sD,
-                                         const double2 *gB, const double2 *gD, double *ax, double *ay) {
+                                         const double2 *gB, const double2 *gD, const cdf *fB, const cdf *fD,
+                                         double *ax, double *ay) {
     if constexpr (Kind<KIND>::NEL > 1) {   // correlation matrices: nuclei up to A = 4
         switch (tw.A) {
-            case 1: eval_terms<1, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
-            case 2: eval_terms<2, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
-            case 3: eval_terms<3, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
-            default: eval_terms<4, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            case 1: eval_terms<1, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 2: eval_terms<2, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 3: eval_terms<3, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            default: eval_terms<4, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
         }
     } else {
         switch (tw.A) {
-            case 1: eval_terms<1, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
-            case 2: eval_terms<2, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
-            case 3: eval_terms<3, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
-            case 4: eval_terms<4, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
-            case 5: eval_terms<5, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
-            case 6: eval_terms<6, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
-            case 7: eval_terms<7, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
-            default: eval_terms<8, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay); break;
+            case 1: eval_terms<1, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 2: eval_terms<2, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 3: eval_terms<3, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 4: eval_terms<4, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 5: eval_terms<5, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 6: eval_terms<6, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 7: eval_terms<7, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            default: eval_terms<8, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
         }
     }
 }
@@ -235,6 +294,8 @@ contract_persistent_kernel(const __grid_constant__ ContractWork wk) {
         const int chunk = r - tw.item_off;
         const double2 *gB = wk.blocks + cs * wk.n_blk;
         const double2 *gD = K::DERIV ? wk.dblocks + cs * wk.n_blk : gB;
+        const cdf *fB = wk.fblocks ? wk.fblocks + cs * wk.n_blk : nullptr;
+        const cdf *fD = K::DERIV && wk.fdblocks ? wk.fdblocks + cs * wk.n_blk : fB;
         if constexpr (STAGE) {
             if (cs != staged) {   // every thread is past the previous item's gathers (barrier above)
                 for (int i = threadIdx.x; i < wk.n_blk; i += blockDim.x) {
@@ -250,7 +311,7 @@ contract_persistent_kernel(const __grid_constant__ ContractWork wk) {
         double ax[NEL], ay[NEL];
 #pragma unroll
         for (int e = 0; e < NEL; ++e) ax[e] = ay[e] = 0.0;
-        eval_any<MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, ax, ay);
+        eval_any<MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay);
         const int cfg = (int)(cs / wk.n_slices), slice = (int)(cs - (long long)cfg * wk.n_slices);
         int *cnt = wk.counters + ((size_t)cfg * wk.n_tab + tb) * wk.n_slices + slice;
 #pragma unroll
@@ -286,6 +347,14 @@ contract_persistent_kernel(const __grid_constant__ ContractWork wk) {
             wk.queue[0] = 0ull;   // every CTA has left: ready for the next launch
             wk.queue[1] = 0ull;
         }
+    }
+}
+
+// the blocks as double-FP32 pairs (hi, lo of each component), once per launch
+__global__ void convert_kernel(const double2 *__restrict__ b, int64_t n, cdf *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const cdf v = to_cdf(__ldcg(b + i));
+        reinterpret_cast<float4 *>(out)[i] = make_float4(v.x.h, v.x.l, v.y.h, v.y.l);
     }
 }
 
@@ -389,19 +458,21 @@ int contract_plan(int n_blk, int n_cfg, int n_slices, const ContractTable *tabs,
     P.counters = (size_t)n_cfg * n_tab * n_slices;
     P.counter_bytes = 256 + align256(sizeof(int) * P.counters);
     P.partial_bytes = align256(sizeof(double2) * (size_t)P.n_items * nel);
+    P.convert_bytes = mixed && !P.stage ? align256(16 * (size_t)n_cfg * n_slices * n_blk) * (kind == 1 ? 2 : 1) : 0;
     return WICK_OK;
 }
 
 int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, const ContractTable *tabs, int n_tab,
                     int precision, const ContractPlan &P, void *counters, double2 *partials, double2 *C_out,
-                    cudaStream_t stream, const double2 *dblocks) {
+                    cudaStream_t stream, const double2 *dblocks, void *convert) {
     if (!counters || !partials || (uintptr_t)counters % 256 || (uintptr_t)partials % 16) return WICK_EINVAL;
     if (P.kind == 1 && !dblocks) return WICK_EINVAL;
     ContractWork wk{};
     wk.n_tab = n_tab;
     for (int k = 0; k < n_tab; ++k) {
-        wk.tab[k] = {tabs[k].ids, tabs[k].w, tabs[k].U, P.chunk[k], tabs[k].A, P.n_chunks[k], P.item_off[k],
-                     tabs[k].scale};
+        if (precision == WICK_MIXED && tabs[k].U > 0 && !tabs[k].wf) return WICK_EINVAL;
+        wk.tab[k] = {tabs[k].ids, tabs[k].w, tabs[k].wf, tabs[k].U, P.chunk[k], tabs[k].A, P.n_chunks[k],
+                     P.item_off[k], tabs[k].scale};
         if (P.kind >= 4)
             for (int e = 0; e < P.kind; ++e) wk.el_scale[e] = tabs[k].el_scale ? tabs[k].el_scale[e] : tabs[k].scale;
     }
@@ -418,6 +489,21 @@ int launch_contract(const double2 *blocks, int n_blk, int n_cfg, int n_slices, c
     wk.counters = reinterpret_cast<int *>(base + 256);
     wk.partials = partials;
     const bool mixed = precision == WICK_MIXED;
+    if (mixed && !P.stage && convert && P.convert_bytes) {
+        if ((uintptr_t)convert % 16) return WICK_EINVAL;
+        const int64_t n = (int64_t)n_cfg * n_slices * n_blk;
+        cdf *fb = static_cast<cdf *>(convert);
+        const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+        convert_kernel<<<g, 256, 0, stream>>>(blocks, n, fb);
+        WICK_CUDA_TRY(cudaGetLastError());
+        wk.fblocks = fb;
+        if (P.kind == 1) {
+            cdf *fd = reinterpret_cast<cdf *>(static_cast<unsigned char *>(convert) + P.convert_bytes / 2);
+            convert_kernel<<<g, 256, 0, stream>>>(dblocks, n, fd);
+            WICK_CUDA_TRY(cudaGetLastError());
+            wk.fdblocks = fd;
+        }
+    }
     switch (P.kind) {
         case 0: return launch_kind<0>(wk, mixed, P.stage, P.grid, P.threads, P.smem, stream);
         case 1: return launch_kind<1>(wk, mixed, P.stage, P.grid, P.threads, P.smem, stream);
@@ -486,7 +572,22 @@ __global__ void pad_table_kernel(const uint16_t *__restrict__ ids, const int64_t
     for (int k = 0; k < AP; ++k) ids_pad[u * AP + k] = k < A ? ids[u * A + k] : (uint16_t)0;
     if (w) wd[u] = (double)w[u];
 }
+
+// the weights as float pairs for the MIXED term sums: hi = wd rounded to float, lo = the rest
+__global__ void split_weights_kernel(const double *__restrict__ wd, int64_t n, float2 *__restrict__ wf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const df v = split_double(wd[i]);
+    wf[i] = make_float2(v.h, v.l);
+}
 }  // namespace
+
+int split_weights(const double *wd, int64_t n, float2 *wf, cudaStream_t stream) {
+    if (n <= 0) return WICK_OK;
+    split_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(wd, n, wf);
+    WICK_CUDA_TRY(cudaGetLastError());
+    return WICK_OK;
+}
 
 int launch_magnitudes(const double2 *blocks, int n_blk, int n_slices, const ContractTable &tab, double *mag,
                       cudaStream_t stream) {
