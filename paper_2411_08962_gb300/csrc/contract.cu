@@ -47,7 +47,29 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
-__device__ __forceinline__ cdf to_cdf(double2 v) { return {split_double(v.x), split_double(v.y)}; }
+// A double as a double-FP32 pair with integer operations only (the FP64 pipe is narrow on this GPU):
+// hi = v with its mantissa truncated to 24 significant bits, lo = the next 23 bits of v's mantissa, so
+// |v - hi - lo| < 2^-46 |v|.  Values below 2^-126 in magnitude become zero, values at or above 2^128
+// (and infinities, NaNs) an infinity of their sign.
+__device__ __forceinline__ df split_double_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const int e = (int)((hw >> 20) & 0x7FF);          // biased double exponent
+    const unsigned sign = hw & 0x80000000u;
+    const int ef = e - 1023 + 127;                     // biased float exponent of hi
+    if (ef <= 0) return {__uint_as_float(sign), __uint_as_float(sign)};
+    if (ef >= 255) return {__uint_as_float(sign | 0x7F800000u), 0.f};
+    const float h = __uint_as_float(sign | ((unsigned)ef << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+    // the next 23 mantissa bits r (bits 28..6 of the low word) weigh 2^(e - 1023 - 52 + 6) each:
+    // r is exact in a float by the 2^23 magic constant, then scaled by a power of two (zero if it underflows)
+    const unsigned r = (lw >> 6) & 0x7FFFFFu;
+    const float rf = __fsub_rn(__uint_as_float(0x4B000000u | r), 8388608.f);
+    const int es = e - 1023 - 46 + 127;
+    const float l = __fmul_rn(rf, es > 0 ? __uint_as_float((unsigned)es << 23) : 0.f);
+    return {h, sign ? -l : l};
+}
+
+__device__ __forceinline__ cdf to_cdf(double2 v) { return {split_double_bits(v.x), split_double_bits(v.y)}; }
 
 template <bool MIXED>
 struct Elem;
@@ -115,20 +137,19 @@ __device__ __forceinline__ cdf ldcg_cdf(const cdf *p) {
     return {{v.x, v.y}, {v.z, v.w}};
 }
 
-template <typename C, bool MIXED, bool STAGE>
+// a block entry from shared memory (STAGE), from the pre-converted float pairs (PRE: MIXED without
+// staging), or from the complex128 blocks.  The source is a compile-time choice: a run-time one becomes
+// one load from a selected address with the conversion predicated, and predicated-off FP64 instructions
+// still take the FP64 pipe's issue slots.
+template <typename C, bool MIXED, bool STAGE, bool PRE>
 __device__ __forceinline__ C load_block(const C *sB, const double2 *gB, const cdf *fB, int id) {
-    if constexpr (STAGE) {
-        return sB[id];
-    } else if constexpr (MIXED) {
-        if (fB) return ldcg_cdf(fB + id);
-        return Elem<MIXED>::from(__ldcg(gB + id));
-    } else {
-        return Elem<MIXED>::from(__ldcg(gB + id));
-    }
+    if constexpr (STAGE) return sB[id];
+    else if constexpr (PRE) return ldcg_cdf(fB + id);
+    else return Elem<MIXED>::from(__ldcg(gB + id));
 }
 
 // this thread's share of terms [u0, u1) of one table, against one slice's blocks (and derivative blocks)
-template <int A, bool MIXED, bool STAGE, int KIND>
+template <int A, bool MIXED, bool STAGE, int KIND, bool PRE>
 __device__ __forceinline__ void eval_terms(const TableWork &tw, int64_t u0, int64_t u1,
                                            const typename Elem<MIXED>::T *sB, const typename Elem<MIXED>::T *sD,
                                            const double2 *gB, const double2 *gD, const cdf *fB, const cdf *fD,
@@ -166,18 +187,18 @@ __device__ __forceinline__ void eval_terms(const TableWork &tw, int64_t u0, int6
             pre[0] = E::one();
 #pragma unroll
             for (int k = 1; k < A; ++k)
-                pre[k] = E::mul(pre[k - 1], load_block<C, MIXED, STAGE>(sB, gB, fB, id[k - 1]));
+                pre[k] = E::mul(pre[k - 1], load_block<C, MIXED, STAGE, PRE>(sB, gB, fB, id[k - 1]));
             C suf = E::one();
-            p = E::mul(pre[A - 1], load_block<C, MIXED, STAGE>(sD, gD, fD, id[A - 1]));
+            p = E::mul(pre[A - 1], load_block<C, MIXED, STAGE, PRE>(sD, gD, fD, id[A - 1]));
 #pragma unroll
             for (int k = A - 2; k >= 0; --k) {
-                suf = E::mul(suf, load_block<C, MIXED, STAGE>(sB, gB, fB, id[k + 1]));
-                p = E::add(p, E::mul(E::mul(pre[k], load_block<C, MIXED, STAGE>(sD, gD, fD, id[k])), suf));
+                suf = E::mul(suf, load_block<C, MIXED, STAGE, PRE>(sB, gB, fB, id[k + 1]));
+                p = E::add(p, E::mul(E::mul(pre[k], load_block<C, MIXED, STAGE, PRE>(sD, gD, fD, id[k])), suf));
             }
         } else {
-            p = load_block<C, MIXED, STAGE>(sB, gB, fB, id[0]);
+            p = load_block<C, MIXED, STAGE, PRE>(sB, gB, fB, id[0]);
 #pragma unroll
-            for (int k = 1; k < A; ++k) p = E::mul(p, load_block<C, MIXED, STAGE>(sB, gB, fB, id[k]));
+            for (int k = 1; k < A; ++k) p = E::mul(p, load_block<C, MIXED, STAGE, PRE>(sB, gB, fB, id[k]));
         }
         if constexpr (GROUP) {
 #pragma unroll
@@ -217,28 +238,28 @@ __device__ __forceinline__ void eval_terms(const TableWork &tw, int64_t u0, int6
     }
 }
 
-template <bool MIXED, bool STAGE, int KIND>
+template <bool MIXED, bool STAGE, int KIND, bool PRE>
 __device__ __forceinline__ void eval_any(const TableWork &tw, int64_t u0, int64_t u1,
                                          const typename Elem<MIXED>::T *sB, const typename Elem<MIXED>::T *sD,
                                          const double2 *gB, const double2 *gD, const cdf *fB, const cdf *fD,
                                          double *ax, double *ay) {
     if constexpr (Kind<KIND>::NEL > 1) {   // correlation matrices: nuclei up to A = 4
         switch (tw.A) {
-            case 1: eval_terms<1, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
-            case 2: eval_terms<2, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
-            case 3: eval_terms<3, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
-            default: eval_terms<4, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 1: eval_terms<1, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 2: eval_terms<2, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 3: eval_terms<3, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            default: eval_terms<4, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
         }
     } else {
         switch (tw.A) {
-            case 1: eval_terms<1, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
-            case 2: eval_terms<2, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
-            case 3: eval_terms<3, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
-            case 4: eval_terms<4, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
-            case 5: eval_terms<5, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
-            case 6: eval_terms<6, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
-            case 7: eval_terms<7, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
-            default: eval_terms<8, MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 1: eval_terms<1, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 2: eval_terms<2, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 3: eval_terms<3, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 4: eval_terms<4, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 5: eval_terms<5, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 6: eval_terms<6, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            case 7: eval_terms<7, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
+            default: eval_terms<8, MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay); break;
         }
     }
 }
@@ -267,7 +288,7 @@ __device__ __forceinline__ double2 cta_sum(double ax, double ay, double2 *s_red)
     return r;   // valid in thread 0
 }
 
-template <bool MIXED, bool STAGE, int KIND>
+template <bool MIXED, bool STAGE, int KIND, bool PRE>
 __global__ void __launch_bounds__(kMaxThreads)
 contract_persistent_kernel(const __grid_constant__ ContractWork wk) {
     using E = Elem<MIXED>;
@@ -311,7 +332,7 @@ contract_persistent_kernel(const __grid_constant__ ContractWork wk) {
         double ax[NEL], ay[NEL];
 #pragma unroll
         for (int e = 0; e < NEL; ++e) ax[e] = ay[e] = 0.0;
-        eval_any<MIXED, STAGE, KIND>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay);
+        eval_any<MIXED, STAGE, KIND, PRE>(tw, u0, u1, sB, sD, gB, gD, fB, fD, ax, ay);
         const int cfg = (int)(cs / wk.n_slices), slice = (int)(cs - (long long)cfg * wk.n_slices);
         int *cnt = wk.counters + ((size_t)cfg * wk.n_tab + tb) * wk.n_slices + slice;
 #pragma unroll
@@ -358,9 +379,9 @@ __global__ void convert_kernel(const double2 *__restrict__ b, int64_t n, cdf *__
     }
 }
 
-template <bool MIXED, bool STAGE, int KIND>
+template <bool MIXED, bool STAGE, int KIND, bool PRE = false>
 int launch_typed(const ContractWork &wk, int grid, int threads, size_t smem, cudaStream_t stream) {
-    auto k = contract_persistent_kernel<MIXED, STAGE, KIND>;
+    auto k = contract_persistent_kernel<MIXED, STAGE, KIND, PRE>;
     if (smem > 48 * 1024) WICK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<grid, threads, smem, stream>>>(wk);
     WICK_CUDA_TRY(cudaGetLastError());
@@ -371,12 +392,12 @@ template <bool MIXED, bool STAGE, int KIND>
 int max_ctas_per_sm(int threads, size_t smem) {
     int n = 0;
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(contract_persistent_kernel<MIXED, STAGE, KIND>,
+        cudaFuncSetAttribute(contract_persistent_kernel<MIXED, STAGE, KIND, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         (void)cudaGetLastError();
         return 1;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, contract_persistent_kernel<MIXED, STAGE, KIND>, threads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, contract_persistent_kernel<MIXED, STAGE, KIND, false>, threads,
                                                       smem) != cudaSuccess) {
         (void)cudaGetLastError();
         return 1;
@@ -392,8 +413,9 @@ int occupancy(bool mixed, bool stage, int threads, size_t smem) {
 
 template <int KIND>
 int launch_kind(const ContractWork &wk, bool mixed, bool stage, int grid, int threads, size_t smem, cudaStream_t stream) {
-    if (mixed) return stage ? launch_typed<true, true, KIND>(wk, grid, threads, smem, stream)
-                            : launch_typed<true, false, KIND>(wk, grid, threads, smem, stream);
+    if (mixed) return stage        ? launch_typed<true, true, KIND>(wk, grid, threads, smem, stream)
+                      : wk.fblocks ? launch_typed<true, false, KIND, true>(wk, grid, threads, smem, stream)
+                                   : launch_typed<true, false, KIND>(wk, grid, threads, smem, stream);
     return stage ? launch_typed<false, true, KIND>(wk, grid, threads, smem, stream)
                  : launch_typed<false, false, KIND>(wk, grid, threads, smem, stream);
 }
