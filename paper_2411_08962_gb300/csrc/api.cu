@@ -930,6 +930,21 @@ int wick_build_blocks_3pt(const wick_prop *Su, const wick_prop *Sd, const wick_p
     const int64_t V = (int64_t)Su->L * Su->L * Su->L;
     const int64_t n_slices = (int64_t)Su->n_src * Su->T;
     if (V > (1 << 24) || n_slices > 65535) return WICK_EINVAL;
+    if (precision == WICK_MIXED && tc_applicable_3pt(plan, flavour)) {
+        // the tensor-core build with the role passes of the sequential propagator
+        const int rs = current_tuning().range_sites;
+        const size_t pbytes = tc_partial_bytes(plan, (int)V, (int)n_slices, 1, rs, 3);
+        const size_t cbytes = tc_counter_bytes(plan, (int)n_slices, 1);
+        void *part = workspace(kWsBlockPartials, pbytes, &err);
+        if (err) return err;
+        void *cnt = workspace(kWsBlockCounters, cbytes, &err);
+        if (err) return err;
+        int *status = status_word(&err);
+        if (err) return err;
+        return launch_block_tc(plan, &Su->data, &Sd->data, 1, Su->dtype, (int)V, (int)n_slices, rs, (int *)cnt,
+                               (double2 *)part, (double2 *)dblocks, status, (cudaStream_t)stream, &Sig->data,
+                               flavour);
+    }
     const size_t bytes = block_3pt_partial_bytes(plan, (int)V, (int)n_slices);
     void *ws = workspace(kWsBlockPartials, bytes, &err);
     if (err) return err;

@@ -94,11 +94,23 @@ struct WeightExp {
     int e[kMaxOps];
 };
 
-// the propagators of the configurations of one launch
+// the propagators of the configurations of one launch, and their sequential propagators (derivative
+// blocks: the role passes below)
 struct CfgPtrs {
     const void *su[kMaxCfg];
     const void *sd[kMaxCfg];
+    const void *sg[kMaxCfg];
 };
+
+// Derivative blocks (three-point functions): a block is linear in each of its three propagator roles --
+// the U rows (pair flavour f1), the diquark rows of the pair flavour and those of the other flavour -- so
+// its derivative in the direction of a sequential propagator Sg of flavour `sub` is the sum over the
+// roles of that flavour of the block with that role's rows taken from Sg.  Pass 0 substitutes the U
+// rows, pass 1 the pair-flavour diquark rows, pass 2 the other diquark rows; a pass applies to a block
+// type when its role has flavour sub.  Without Sg (sub < 0) there is one pass, without substitution.
+__host__ __device__ __forceinline__ bool pass_applies(int pass, int sub, int f1) {
+    return sub < 0 || (pass == 0 && f1 == sub) || (pass == 1 && f1 == sub) || (pass == 2 && 1 - f1 == sub);
+}
 
 // Compile-time shape of a table family: NC colours chi, NS spins, NT columns
 // per MMA (multiple of 16), NMT M tiles, NX sites per operand chunk.
@@ -421,12 +433,13 @@ __device__ __forceinline__ void u_job(const Job &j, const float *S, __nv_bfloat1
 // rows the tables use, E = bound of max(|re|, |im|) and G = bound of max(|re| + |im|); out[f * 24 +
 // kind * 12 + ic].  Every thread of the CTA takes part; ends with the CTA's barrier.
 template <typename ST>
-__device__ __forceinline__ void range_bounds(const BlockPlan &plan, const ST *su, const ST *sd, int x_begin,
-                                             int x_end, unsigned *smax, int *out) {
+__device__ __forceinline__ void range_bounds(const BlockPlan &plan, const ST *su, const ST *sd, const ST *sg, int sub,
+                                             int x_begin, int x_end, unsigned *smax, int *out) {
     const int tid = threadIdx.x;
-    if (tid < 48) smax[tid] = 0u;
+    if (tid < 72) smax[tid] = 0u;
     __syncthreads();
-    const int nc = plan.n_chi, nr0 = plan.n_rows[0], nr = nr0 + plan.n_rows[1];
+    const int nc = plan.n_chi, nr0 = plan.n_rows[0], nr01 = nr0 + plan.n_rows[1];
+    const int nr = nr01 + (sub >= 0 ? plan.n_rows[sub] : 0);   // row group 2: the rows of Sg
     // the kept columns in adjacent pairs (chi, chi + 1), as in the upper- and full-spin layouts: one
     // 16-byte load covers a pair of complex64 values (half the loads in flight per byte)
     bool pairs = sizeof(ST) == 8 && nc % 2 == 0;
@@ -437,9 +450,9 @@ __device__ __forceinline__ void range_bounds(const BlockPlan &plan, const ST *su
     if (tid < cols * parts) {
         const int col = tid % cols, part = tid / cols;
         const int rc = col / (nc / per), ic = (col % (nc / per)) * per;
-        const int f = rc < nr0 ? 0 : 1;
-        const int row = f == 0 ? plan.rows[0][rc] : plan.rows[1][rc - nr0];
-        const ST *src = (f == 0 ? su : sd) + row * 12 + plan.chi[ic];
+        const int f = rc < nr0 ? 0 : (rc < nr01 ? 1 : 2);
+        const int row = f == 0 ? plan.rows[0][rc] : (f == 1 ? plan.rows[1][rc - nr0] : plan.rows[sub][rc - nr01]);
+        const ST *src = (f == 0 ? su : (f == 1 ? sd : sg)) + row * 12 + plan.chi[ic];
         float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;   // columns ic and ic + 1
         if (pairs) {
 #pragma unroll 12
@@ -466,7 +479,7 @@ __device__ __forceinline__ void range_bounds(const BlockPlan &plan, const ST *su
         }
     }
     __syncthreads();
-    if (tid < 48) {
+    if (tid < 72) {
         const int ic = tid % 12;
         out[tid] = ic < nc ? exponent_bound(__uint_as_float(smax[tid])) : -100;
     }
@@ -477,8 +490,8 @@ __device__ __forceinline__ void range_bounds(const BlockPlan &plan, const ST *su
 // of the n_ranges x NCT CTAs of (cs, o) sums the partials of every range in range order and writes
 // B = P(c1,c2,c3) - P(c2,c1,c3) for the type's entries, then clears the counter.
 template <typename SH>
-__device__ __forceinline__ void arrive_and_reduce(const BlockPlan &plan, int cs, int o, int n_ranges,
-                                                  const double2 *partials, int *counters, double2 *blocks,
+__device__ __forceinline__ void arrive_and_reduce(const BlockPlan &plan, int cs, int o, int n_ranges, int n_pass,
+                                                  int sub, const double2 *partials, int *counters, double2 *blocks,
                                                   int *s_last) {
     constexpr int NC = SH::NC, NS = SH::NS, NC2 = NC * NC, NC3 = NC2 * NC;
     const int tid = threadIdx.x;
@@ -486,23 +499,27 @@ __device__ __forceinline__ void arrive_and_reduce(const BlockPlan &plan, int cs,
     __syncthreads();   // every partial of this CTA is written
     if (tid == 0) {
         __threadfence();
-        *s_last = atomicAdd(cnt, 1) == n_ranges * SH::NCT - 1;
+        *s_last = atomicAdd(cnt, 1) == n_pass * n_ranges * SH::NCT - 1;
     }
     __syncthreads();
     if (!*s_last) return;
     __threadfence();
     const size_t n_out = (size_t)plan.n_out;
-    const double2 *P = partials + (size_t)cs * n_ranges * n_out;
+    const double2 *P = partials + (size_t)cs * n_pass * n_ranges * n_out;   // [pass][range][entry]
+    const int f1 = plan.f1[o];
     double2 *Bo = blocks + (size_t)cs * n_out;
     for (int e = tid; e < NS * NC3; e += blockDim.x) {
         const int out = o * NS * NC3 + e;
         const int os = out / NC3, i1 = (out / NC2) % NC, i2 = (out / NC) % NC, i3 = out % NC;
         const int sw = os * NC3 + i2 * NC2 + i1 * NC + i3;
         double ax = 0, ay = 0, bx = 0, by = 0;
-        for (int r = 0; r < n_ranges; ++r) {
-            const double2 a = __ldcg(P + (size_t)r * n_out + out);
-            const double2 b = __ldcg(P + (size_t)r * n_out + sw);
-            ax += a.x; ay += a.y; bx += b.x; by += b.y;
+        for (int p = 0; p < n_pass; ++p) {
+            if (!pass_applies(p, sub, f1)) continue;   // its CTAs wrote nothing
+            for (int r = 0; r < n_ranges; ++r) {
+                const double2 a = __ldcg(P + ((size_t)p * n_ranges + r) * n_out + out);
+                const double2 b = __ldcg(P + ((size_t)p * n_ranges + r) * n_out + sw);
+                ax += a.x; ay += a.y; bx += b.x; by += b.y;
+            }
         }
         Bo[out] = make_double2(ax - bx, ay - by);
     }
@@ -512,27 +529,42 @@ __device__ __forceinline__ void arrive_and_reduce(const BlockPlan &plan, int cs,
 template <typename ST, typename SH>
 __global__ void __launch_bounds__(kThr, 1)
 block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ CfgPtrs cfgp, int V, int n_slices,
-                int n_ranges, int range_sites, const WeightExp ew, double2 *__restrict__ partials,
-                int *__restrict__ counters, double2 *__restrict__ blocks, int *status) {
+                int n_ranges, int range_sites, const WeightExp ew, int sub, int n_pass,
+                double2 *__restrict__ partials, int *__restrict__ counters, double2 *__restrict__ blocks,
+                int *status) {
     constexpr int NC = SH::NC, NS = SH::NS, NT = SH::NT, R = SH::R, NCTA = SH::NCTA;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ unsigned s_max[48];
-    __shared__ int s_bnd[48];
+    __shared__ unsigned s_max[72];
+    __shared__ int s_bnd[72];
     __shared__ int s_last;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // the CTAs of one (slice, range) are adjacent in the grid: they read the same rows of S (L2 reuse)
-    const int o = blockIdx.x / SH::NCT, ct = blockIdx.x % SH::NCT;
+    const int pass = blockIdx.x / (plan.n_ops * SH::NCT);
+    const int ob = blockIdx.x - pass * plan.n_ops * SH::NCT;
+    const int o = ob / SH::NCT, ct = ob % SH::NCT;
     const int rng = blockIdx.y, cs = blockIdx.z;             // cs = configuration * n_slices + slice
     const int cfg = cs / n_slices, slice = cs - cfg * n_slices;
+    const int f1 = plan.f1[o];
+    if (!pass_applies(pass, sub, f1)) {   // a role pass of the other flavour: nothing to add, count it in
+        arrive_and_reduce<SH>(plan, cs, o, n_ranges, n_pass, sub, partials, counters, blocks, &s_last);
+        return;
+    }
     const ST *Su = static_cast<const ST *>(cfgp.su[cfg]);
     const ST *Sd = static_cast<const ST *>(cfgp.sd[cfg]);
-    const int nr0 = plan.n_rows[0], nr = nr0 + plan.n_rows[1];
-    const int f1 = plan.f1[o];
+    const ST *Sg = sub >= 0 ? static_cast<const ST *>(cfgp.sg[cfg]) : Su;
+    // staged row groups: the u rows, the d rows, and (derivative blocks) the rows of Sg
+    const int nr0 = plan.n_rows[0], nr01 = nr0 + plan.n_rows[1];
+    const int nr = nr01 + (sub >= 0 ? plan.n_rows[sub] : 0);
     const int col0 = ct * NT;
     const int t0 = plan.os_off[o * NS];
     const int n_a = plan.os_off[o * NS + 1] - t0;
     constexpr int NX = SH::NX, KC = SH::KC, PS = SH::PS;
-    const int rc1 = f1 == 0 ? 0 : nr0, rc2 = f1 == 0 ? nr0 : 0;  // first staged row of either flavour
+    // the first staged row and the bound group of each role: U rows and pair-flavour diquark rows from
+    // flavour f1, the other diquark rows from flavour 1 - f1, or from Sg in the pass that substitutes them
+    const bool subU = sub >= 0 && pass == 0, subX2 = sub >= 0 && pass == 1, subX3 = sub >= 0 && pass == 2;
+    const int rc1 = f1 == 0 ? 0 : nr0, rc2 = f1 == 0 ? nr0 : 0;
+    const int rcU = subU ? nr01 : rc1, rcX2 = subX2 ? nr01 : rc1, rcX3 = subX3 ? nr01 : rc2;
+    const int gU = subU ? 2 : f1, gX2 = subX2 ? 2 : f1, gX3 = subX3 ? 2 : 1 - f1;
 
     __nv_bfloat16 *sA0 = reinterpret_cast<__nv_bfloat16 *>(smem);
     __nv_bfloat16 *sB0 = reinterpret_cast<__nv_bfloat16 *>(smem + 2 * SH::A_BYTES);
@@ -555,12 +587,13 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
     const int n_chunks = (x_end - x_begin + NX - 1) / NX;
     const ST *su = Su + (size_t)slice * V * 144;
     const ST *sd = Sd + (size_t)slice * V * 144;
-    range_bounds<ST>(plan, su, sd, x_begin, x_end, s_max, s_bnd);
+    const ST *sg = Sg + (size_t)slice * V * 144;
+    range_bounds<ST>(plan, su, sd, sg, sub, x_begin, x_end, s_max, s_bnd);
     const int *bnd = s_bnd;
-    if (tid < NC) sEU[tid] = bnd[f1 * 24 + tid];
+    if (tid < NC) sEU[tid] = bnd[gU * 24 + tid];
     if (tid < NT) {
         const int c23 = col0 + tid;
-        sF[tid] = tid < NCTA ? bnd[f1 * 24 + 12 + c23 / NC] + bnd[(1 - f1) * 24 + 12 + c23 % NC] + ew.e[o] : 0;
+        sF[tid] = tid < NCTA ? bnd[gX2 * 24 + 12 + c23 / NC] + bnd[gX3 * 24 + 12 + c23 % NC] + ew.e[o] : 0;
     }
     if (tid < kKa * kListLen) {
         const int a = tid / kListLen, t = tid % kListLen;
@@ -569,7 +602,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
         if (a < n_a) {
             const int q = plan.x_off[plan.os_x[t0 + a]] + t;
             w = plan.xt_w[q];
-            v = make_int4((rc1 + plan.xt_r2[q]) * NC * NX, (rc2 + plan.xt_r3[q]) * NC * NX, __float_as_int(w),
+            v = make_int4((rcX2 + plan.xt_r2[q]) * NC * NX, (rcX3 + plan.xt_r3[q]) * NC * NX, __float_as_int(w),
                           __float_as_int(w));
         }
         sTerm[tid] = v;
@@ -577,12 +610,12 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
     }
     if (tid >= 32 && tid < 32 + NS * kKa) {
         const int s = (tid - 32) / kKa, a = (tid - 32) % kKa;
-        sR1[s * kKa + a] = a < n_a ? (rc1 + plan.os_r1[plan.os_off[o * NS + s] + a]) * NC * NX : 0;
+        sR1[s * kKa + a] = a < n_a ? (rcU + plan.os_r1[plan.os_off[o * NS + s] + a]) * NC * NX : 0;
     }
     for (int e = tid; e < nr * NC; e += kThr) {
         const int rc = e / NC, ic = e - rc * NC;
-        const int f = rc < nr0 ? 0 : 1;
-        const int row = f == 0 ? plan.rows[0][rc] : plan.rows[1][rc - nr0];
+        const int f = rc < nr0 ? 0 : (rc < nr01 ? 1 : 2);
+        const int row = f == 0 ? plan.rows[0][rc] : (f == 1 ? plan.rows[1][rc - nr0] : plan.rows[sub][rc - nr01]);
         sSrc[e] = f << 16 | (row * 12 + plan.chi[ic]);
     }
     if (tid == 0) {
@@ -606,7 +639,8 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
     const ST *st_src = su;
     if (stager) {
         const int src_off = sSrc[st_rcc];
-        st_src = ((src_off >> 16) ? sd : su) + (src_off & 0xFFFF);
+        const int grp = src_off >> 16;
+        st_src = (grp == 0 ? su : (grp == 1 ? sd : sg)) + (src_off & 0xFFFF);
     }
     auto stage = [&](int c) {
         if (stager) {
@@ -814,7 +848,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
         __syncthreads();
         if (warp == 0)
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SH::TMEM_COLS));
-        arrive_and_reduce<SH>(plan, cs, o, n_ranges, partials, counters, blocks, &s_last);
+        arrive_and_reduce<SH>(plan, cs, o, n_ranges, n_pass, sub, partials, counters, blocks, &s_last);
         return;
     }
     cp_async_wait_all();
@@ -822,7 +856,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
     if constexpr (SH::LEVELS) {
         // every slice level is in this thread's accumulators: scale and write its row's partials
         if (q < 3) {
-            double *part = reinterpret_cast<double *>(partials + ((size_t)cs * n_ranges + rng) * plan.n_out);
+            double *part = reinterpret_cast<double *>(partials + (((size_t)cs * n_pass + pass) * n_ranges + rng) * plan.n_out);
             const int rr = q * 32 + lane;                          // < R
             const int pp = rr / (NS * NC), sc1 = rr % (NS * NC);   // part, (s, c1)
             const int s_ = sc1 / NC, c1 = sc1 % NC;
@@ -839,7 +873,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (warp == 0)
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SH::TMEM_COLS));
-        arrive_and_reduce<SH>(plan, cs, o, n_ranges, partials, counters, blocks, &s_last);
+        arrive_and_reduce<SH>(plan, cs, o, n_ranges, n_pass, sub, partials, counters, blocks, &s_last);
         return;
     }
     // combine the five U-slice rows of every output (double-FP32, relative to 2^(E+F)), then FP64
@@ -848,7 +882,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
 #pragma unroll
         for (int n = 0; n < SH::CW; ++n) comb[row * NT + cpart * SH::CW + n] = make_float2(acc[n].h, acc[n].l);
     __syncthreads();
-    double *part = reinterpret_cast<double *>(partials + ((size_t)cs * n_ranges + rng) * plan.n_out);
+    double *part = reinterpret_cast<double *>(partials + (((size_t)cs * n_pass + pass) * n_ranges + rng) * plan.n_out);
     for (int e = tid; e < R * NCTA; e += kThr) {
         const int rr = e / NCTA, n = e % NCTA;
         df s = {0.f, 0.f};
@@ -867,7 +901,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(SH::TMEM_COLS));
-    arrive_and_reduce<SH>(plan, cs, o, n_ranges, partials, counters, blocks, &s_last);
+    arrive_and_reduce<SH>(plan, cs, o, n_ranges, n_pass, sub, partials, counters, blocks, &s_last);
 }
 
 // The wait for an MMA commit on an mbarrier that nothing arrives on: the poll gives up after `limit`
@@ -907,13 +941,13 @@ int tc_family(const BlockPlan &plan) {
 
 template <typename SH, typename ST>
 int launch_shape(const BlockPlan &plan, const CfgPtrs &cp, int n_cfg, int V, int n_slices, int n_ranges,
-                 int range_sites, const WeightExp &ew, double2 *part, int *counters, double2 *blocks, int *status,
-                 cudaStream_t stream) {
+                 int range_sites, const WeightExp &ew, int sub, int n_pass, double2 *part, int *counters,
+                 double2 *blocks, int *status, cudaStream_t stream) {
     auto k = block_tc_kernel<ST, SH>;
     WICK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM));
-    dim3 grid(plan.n_ops * SH::NCT, n_ranges, n_cfg * n_slices);
-    k<<<grid, kThr, SH::SMEM, stream>>>(plan, cp, V, n_slices, n_ranges, range_sites, ew, part, counters, blocks,
-                                        status);
+    dim3 grid(n_pass * plan.n_ops * SH::NCT, n_ranges, n_cfg * n_slices);
+    k<<<grid, kThr, SH::SMEM, stream>>>(plan, cp, V, n_slices, n_ranges, range_sites, ew, sub, n_pass, part, counters,
+                                        blocks, status);
     WICK_CUDA_TRY(cudaGetLastError());
     return WICK_OK;
 }
@@ -923,6 +957,11 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 }  // namespace
 
 bool tc_applicable(const BlockPlan &plan) { return tc_family(plan) != 0; }
+
+bool tc_applicable_3pt(const BlockPlan &plan, int sub) {
+    return tc_family(plan) != 0 && (sub == 0 || sub == 1) &&
+           plan.n_rows[0] + plan.n_rows[1] + plan.n_rows[sub] <= kMaxRows;
+}
 
 int selftest_mbar_wait(int limit, int *status, cudaStream_t stream) {
     mbar_wait_selftest_kernel<<<1, 1, 0, stream>>>(limit, status);
@@ -942,25 +981,29 @@ size_t tc_counter_bytes(const BlockPlan &plan, int n_slices, int n_cfg) {
     return align256(sizeof(int) * (size_t)n_cfg * n_slices * plan.n_ops);
 }
 
-size_t tc_partial_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites) {
+size_t tc_partial_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites, int n_pass) {
     const int rs = tc_range_sites(range_sites);
     const size_t n_ranges = (size_t)(V + rs - 1) / rs;
-    return sizeof(double2) * n_ranges * n_cfg * n_slices * plan.n_out;
+    return sizeof(double2) * n_pass * n_ranges * n_cfg * n_slices * plan.n_out;
 }
 
 int launch_block_tc(const BlockPlan &plan, const void *const *Su, const void *const *Sd, int n_cfg, int dtype, int V,
                     int n_slices, int range_sites, int *counters, double2 *part, double2 *blocks, int *status,
-                    cudaStream_t stream) {
+                    cudaStream_t stream, const void *const *Sg, int sub) {
     const int fam = tc_family(plan);
     const int rs = tc_range_sites(range_sites);
     const int n_ranges = (V + rs - 1) / rs;
     if (!fam || n_cfg < 1 || n_cfg > kMaxCfg || n_ranges > 65535 || (int64_t)n_cfg * n_slices > 65535)
         return WICK_EINVAL;
     if (!counters || !part) return WICK_EINVAL;
+    if (sub >= 0 && (!Sg || !tc_applicable_3pt(plan, sub))) return WICK_EINVAL;
+    const int n_pass = sub >= 0 ? 3 : 1;
     CfgPtrs cp{};
     for (int c = 0; c < n_cfg; ++c) {
         cp.su[c] = Su[c];
         cp.sd[c] = Sd[c];
+        cp.sg[c] = sub >= 0 ? Sg[c] : nullptr;
+        if (sub >= 0 && !Sg[c]) return WICK_EINVAL;
     }
     WeightExp ew = {};
     for (int o = 0; o < plan.n_ops; ++o) {
@@ -976,14 +1019,14 @@ int launch_block_tc(const BlockPlan &plan, const void *const *Su, const void *co
         ew.e[o] = exponent_bound(wmax);
     }
     if (dtype == WICK_C64)
-        return fam == 1 ? launch_shape<UpperShape, float2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, part,
-                                                           counters, blocks, status, stream)
-                        : launch_shape<FullShape, float2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, part,
-                                                          counters, blocks, status, stream);
-    return fam == 1 ? launch_shape<UpperShape, double2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, part, counters,
-                                                        blocks, status, stream)
-                    : launch_shape<FullShape, double2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, part, counters,
-                                                       blocks, status, stream);
+        return fam == 1 ? launch_shape<UpperShape, float2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, sub, n_pass,
+                                                           part, counters, blocks, status, stream)
+                        : launch_shape<FullShape, float2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, sub, n_pass,
+                                                          part, counters, blocks, status, stream);
+    return fam == 1 ? launch_shape<UpperShape, double2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, sub, n_pass,
+                                                        part, counters, blocks, status, stream)
+                    : launch_shape<FullShape, double2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, sub, n_pass,
+                                                       part, counters, blocks, status, stream);
 }
 
 }  // namespace wick

@@ -73,6 +73,8 @@ struct UploadMap {
 int launch_upload_rows(const UploadMap &map, const void *hu, const void *hd, const void *du, const void *dd,
                        size_t n_sites, int words_u, int words_d, cudaStream_t stream);
 bool tc_applicable(const BlockPlan &plan);
+// derivative blocks on the tensor cores: the rows of both flavours and of the sequential propagator fit
+bool tc_applicable_3pt(const BlockPlan &plan, int sub);
 int block_build_launches(const BlockPlan &plan, int precision);  // kernels one launch_block_build issues
 // tensor-core block build (blocks_tc.cu): one launch for up to tc_max_configs() configurations; its
 // scratch holds one counter per (configuration, slice, block type) -- zero before the first launch,
@@ -80,10 +82,12 @@ int block_build_launches(const BlockPlan &plan, int precision);  // kernels one 
 int tc_range_sites(int requested);               // the range size a request (0 = default) resolves to
 int tc_max_configs();
 size_t tc_counter_bytes(const BlockPlan &plan, int n_slices, int n_cfg);
-size_t tc_partial_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites);
+size_t tc_partial_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites, int n_pass = 1);
+// Sg, sub >= 0: the derivative blocks in the direction of the sequential propagators Sg of flavour sub
+// (three role passes; partials: tc_partial_bytes with n_pass = 3)
 int launch_block_tc(const BlockPlan &plan, const void *const *Su, const void *const *Sd, int n_cfg, int dtype, int V,
                     int n_slices, int range_sites, int *counters, double2 *partials, double2 *blocks, int *status,
-                    cudaStream_t stream);
+                    cudaStream_t stream, const void *const *Sg = nullptr, int sub = -1);
 
 // ---------------------------------------------------------------------------
 // Term reduction (dedup.cu)
