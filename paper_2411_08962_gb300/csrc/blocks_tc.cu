@@ -913,6 +913,381 @@ __global__ void mbar_wait_selftest_kernel(int limit, int *status) {
     if (!poll_parity(&mbar, 0, limit)) atomicCAS(status, 0, WICK_ETIMEOUT);
 }
 
+// ---------------------------------------------------------------------------
+// Both block types of a proton/neutron pair in one CTA (upper-spin tables).
+//
+// Exchanging the two diquark rows of a list term flips the sign of the colour
+// epsilon and of the antisymmetric spin matrix, so when the neutron's lists are
+// the proton's with the two rows exchanged (checked on the host, pair_plan), the
+// neutron's diquark values are the proton's with the columns transposed:
+// X_n(c2, c3) = X_p(c3, c2).  The CTA computes X_p once for both types.
+//
+// The update runs with the roles of the operands turned around: A = the six X
+// slices of the 36 (c2, c3) columns (row 40 j + n of two 128-row tiles; rows
+// 36..39 of each slice are padding, so a slice's rows are 40 apart and its
+// stores a constant stride apart), B = the five U slices of one type (row
+// 24 i + 12 part + (s, c1), N = 128).  Every TMEM element then holds one slice
+// pair (i, j): accumulator (type, tile) in 128 columns, four of them.  The neutron
+// accumulators see A's columns transposed: lane (j, n) contributes to the neutron
+// column n^T = (n mod 6) 6 + n / 6, whose grid is the proton column n's.
+// Readout per 128-site round: each thread reads its lane's 120 columns, adds the
+// five U slices with i + j <= 5 in double-FP32, and the six X slices of an output
+// (six lanes, in different warps) are added into double-FP32 accumulators in
+// shared memory, one slice j at a time.  Grids, slicing, exact rounds, staging,
+// bounded waits and the range reduction are those of block_tc_kernel.
+// ---------------------------------------------------------------------------
+struct PairShape {
+    static constexpr int NC = 6, NS = 2, NX = 8, NSP = NX / 2;
+    static constexpr int KC = NX * kKa * 2;                  // K per chunk: 48
+    static constexpr int NC2 = NC * NC;                      // 36 columns
+    static constexpr int XSTRIDE = 40;                       // A rows per X slice
+    static constexpr int R = 2 * NS * NC;                    // 24 U rows per slice
+    static constexpr int CHUNKS_PER_ROUND = kRoundSites / NX;
+    static constexpr int PS = kMaxRows * NC * NX;            // floats per staged plane
+    static constexpr int STAGERS = kMaxRows * NC * NX / 8;   // one (row, colour), 8 sites each
+    static constexpr int NXJOB = NC2 * kKa * NSP;            // 432: column, colour term, site pair
+    static constexpr int NUJOB = 2 * NS * NC * kKa * NSP;    // 288: type, (s, c1), colour term, site pair
+    static constexpr int A_BYTES = 256 * KC * 2;             // two M tiles of X slices
+    static constexpr int B_BYTES = 2 * 128 * KC * 2;         // the U slices of both types
+    static constexpr int S_BYTES = 2 * PS * 4;
+    static constexpr int ACC_BYTES = 2 * 2 * NS * NC * NC2 * 8;   // [type][part][(s, c1)][column] df
+    static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES + ACC_BYTES + 4 * (32 + 64) +
+                                (16 + 8) * kKa * kListLen + 4 * 16 + 4 * kMaxRows * 12 + 64;
+    static_assert(kSlicesX * XSTRIDE <= 256 && XSTRIDE % 8 == 0 && XSTRIDE >= NC2, "X rows");
+    static_assert(kSlices * R <= 128 && R % 8 == 0, "U rows");
+    static_assert(NXJOB + NUJOB <= 2 * kThr && STAGERS <= kThr, "jobs");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+template <typename ST>
+__global__ void __launch_bounds__(kThr, 1)
+block_pair_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ CfgPtrs cfgp, int V, int n_slices,
+                  int n_ranges, int range_sites, const WeightExp ew, int oP, int oN, double2 *__restrict__ partials,
+                  int *__restrict__ counters, double2 *__restrict__ blocks, int *status) {
+    using SH = PairShape;
+    constexpr int NC = SH::NC, NS = SH::NS, NX = SH::NX, KC = SH::KC, PS = SH::PS, NC2 = SH::NC2, R = SH::R;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ unsigned s_max[72];
+    __shared__ int s_bnd[72];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rng = blockIdx.y, cs = blockIdx.z;
+    const int cfg = cs / n_slices, slice = cs - cfg * n_slices;
+    const ST *Su = static_cast<const ST *>(cfgp.su[cfg]);
+    const ST *Sd = static_cast<const ST *>(cfgp.sd[cfg]);
+    const int nr0 = plan.n_rows[0], nr = nr0 + plan.n_rows[1];
+    const int tP = plan.os_off[oP * NS];
+    const int n_a = plan.os_off[oP * NS + 1] - tP;
+
+    __nv_bfloat16 *sA0 = reinterpret_cast<__nv_bfloat16 *>(smem);
+    __nv_bfloat16 *sB0 = reinterpret_cast<__nv_bfloat16 *>(smem + 2 * SH::A_BYTES);
+    float *sS0 = reinterpret_cast<float *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES));
+    float2 *sAcc = reinterpret_cast<float2 *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES) + kStage * SH::S_BYTES);
+    int *sEU = reinterpret_cast<int *>(sAcc + 2 * 2 * NS * NC * NC2);   // [type][16] grid of U per colour
+    int *sF = sEU + 32;                                       // [64] grid of X per proton column
+    int4 *sTerm = reinterpret_cast<int4 *>(sF + 64);          // [kKa][kListLen] the proton's list terms
+    f2x *sTermN = reinterpret_cast<f2x *>(sTerm + kKa * kListLen);
+    int *sR1 = reinterpret_cast<int *>(sTermN + kKa * kListLen);    // [type][NS][kKa] staged offset of U's row
+    int *sSrc = sR1 + 16;                                     // [kMaxRows * NC]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sSrc + kMaxRows * 12);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+
+    {   // zero the operand buffers (padding rows, unused colour terms) and the accumulators
+        uint4 *z = reinterpret_cast<uint4 *>(smem);
+        for (int e = tid; e < 2 * (SH::A_BYTES + SH::B_BYTES) / 16; e += kThr) z[e] = make_uint4(0u, 0u, 0u, 0u);
+        for (int e = tid; e < 2 * 2 * NS * NC * NC2; e += kThr) sAcc[e] = make_float2(0.f, 0.f);
+    }
+    const int x_begin = rng * range_sites, x_end = min(V, x_begin + range_sites);
+    const int n_chunks = (x_end - x_begin + NX - 1) / NX;
+    const ST *su = Su + (size_t)slice * V * 144;
+    const ST *sd = Sd + (size_t)slice * V * 144;
+    range_bounds<ST>(plan, su, sd, su, -1, x_begin, x_end, s_max, s_bnd);
+    const int *bnd = s_bnd;
+    if (tid < 2 * NC) {   // type 0 = the proton (U rows from u), type 1 = the neutron (from d)
+        const int ty = tid / NC, c1 = tid % NC;
+        sEU[ty * 16 + c1] = bnd[ty * 24 + c1];
+    }
+    if (tid < NC2) sF[tid] = bnd[12 + tid / NC] + bnd[24 + 12 + tid % NC] + ew.e[oP];
+    if (tid < kKa * kListLen) {
+        const int a = tid / kListLen, t = tid % kListLen;
+        int4 v = make_int4(0, 0, 0, 0);
+        float w = 0.f;
+        if (a < n_a) {
+            const int q = plan.x_off[plan.os_x[tP + a]] + t;
+            w = plan.xt_w[q];
+            v = make_int4(plan.xt_r2[q] * NC * NX, (nr0 + plan.xt_r3[q]) * NC * NX, __float_as_int(w),
+                          __float_as_int(w));
+        }
+        sTerm[tid] = v;
+        sTermN[tid] = pk(-w, -w);
+    }
+    if (tid >= 32 && tid < 32 + 2 * NS * kKa) {
+        const int e = tid - 32, ty = e / (NS * kKa), s = (e / kKa) % NS, a = e % kKa;
+        const int o = ty ? oN : oP, rc = ty ? nr0 : 0;
+        sR1[e] = a < n_a ? (rc + plan.os_r1[plan.os_off[o * NS + s] + a]) * NC * NX : 0;
+    }
+    for (int e = tid; e < nr * NC; e += kThr) {
+        const int rc = e / NC, ic = e - rc * NC;
+        const int f = rc < nr0 ? 0 : 1;
+        const int row = f == 0 ? plan.rows[0][rc] : plan.rows[1][rc - nr0];
+        sSrc[e] = f << 16 | (row * 12 + plan.chi[ic]);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+
+    // staging: the last STAGERS threads, one (row, colour) for all 8 sites of a chunk
+    const int st_t = tid - (kThr - SH::STAGERS);
+    const int st_rcc = st_t >= 0 ? st_t : 0;
+    const bool stager = st_t >= 0 && st_rcc < nr * NC;
+    const ST *st_src = su;
+    if (stager) {
+        const int src_off = sSrc[st_rcc];
+        st_src = ((src_off >> 16) ? sd : su) + (src_off & 0xFFFF);
+    }
+    auto stage = [&](int c) {
+        if (stager) {
+            float *dst = sS0 + (c % kStage) * (2 * PS) + st_rcc * NX;
+            const int xb = x_begin + c * NX;
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8) {
+                const bool in = xb + s8 < x_end;
+                const ST *src = st_src + (size_t)(in ? xb + s8 : x_begin) * 144;
+                if constexpr (sizeof(ST) == 8) {
+                    cp_async4(dst + s8, reinterpret_cast<const float *>(src), in ? 4 : 0);
+                    cp_async4(dst + s8 + PS, reinterpret_cast<const float *>(src) + 1, in ? 4 : 0);
+                } else {
+                    const float2 v = in ? to_f2(*src) : make_float2(0.f, 0.f);
+                    dst[s8] = v.x;
+                    dst[s8 + PS] = v.y;
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    stage(0);
+    cp_async_wait_all();
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tbase = *tslot;
+    if (n_chunks > 1) stage(1);
+
+    // the thread's jobs: job 0 = tid, job 1 = tid + kThr; X jobs first, then U jobs
+    int xk = -1, xs1 = 0, xs2 = 0, xd = 0;   // X job: colour term, u / d staged offsets, A offset of slice 0
+    float xsc = 0.f;
+    int uk[2] = {-1, -1}, us[2] = {0, 0}, ud1[2] = {0, 0}, ud2[2] = {0, 0};   // U jobs (at most one per round)
+    float usc[2] = {0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int jb = r * kThr + tid;
+        if (jb < SH::NXJOB) {   // (a, column n, site pair): lanes take 8 columns x 4 site pairs
+            const int a = jb / (NC2 * SH::NSP), rem = jb % (NC2 * SH::NSP), n = rem / SH::NSP, sp = rem % SH::NSP;
+            if (a < n_a) {
+                xk = a;
+                xs1 = (n / NC) * NX + 2 * sp;
+                xs2 = (n % NC) * NX + 2 * sp;
+                xd = tile_off<KC>(n, a * 2 * NX + 2 * sp);
+                xsc = exp2i(7 - sF[n]);
+            }
+        } else if (jb < SH::NXJOB + SH::NUJOB) {   // (type, a, (s, c1), site pair)
+            const int u = jb - SH::NXJOB;
+            const int ty = u / (kKa * NS * NC * SH::NSP), rem = u % (kKa * NS * NC * SH::NSP);
+            const int a = rem / (NS * NC * SH::NSP), m = (rem / SH::NSP) % (NS * NC), sp = rem % SH::NSP;
+            if (a < n_a) {
+                const int s = m / NC, c1 = m % NC;
+                uk[r] = ty;
+                us[r] = sR1[(ty * NS + s) * kKa + a] + c1 * NX + 2 * sp;
+                ud1[r] = ty * 128 * KC + tile_off<KC>(m, a * 2 * NX + 2 * sp);
+                ud2[r] = ty * 128 * KC + tile_off<KC>(NS * NC + m, a * 2 * NX + 2 * sp);
+                usc[r] = exp2i(7 - sEU[ty * 16 + c1]);
+            }
+        }
+    }
+
+    // readout ownership: accumulator (type, tile) = warp / 4, lane quarter = warp % 4
+    const int q = warp & 3, g = warp >> 2, ty_own = g >> 1, tile_own = g & 1;
+    const int xrow = tile_own * 128 + q * 32 + lane;            // A row of this thread's TMEM lane
+    const int j_own = xrow / SH::XSTRIDE, n_own = xrow % SH::XSTRIDE;
+    const bool row_ok = j_own < kSlicesX && n_own < NC2;
+    const int n_out = ty_own ? (n_own % NC) * NC + n_own / NC : n_own;   // output column of this lane
+
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+    int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0, bad = 0;
+    for (int c = 0; c < n_chunks; ++c) {
+        const int buf = c & 1;
+        __nv_bfloat16 *A = sA0 + buf * (SH::A_BYTES / 2);
+        __nv_bfloat16 *B = sB0 + buf * (SH::B_BYTES / 2);
+        const float *S = sS0 + (c % kStage) * (2 * PS);
+        if (buf == 0 && waited0 < issued0) {
+            if (poll_parity(&mbar[0], waited0 & 1)) ++waited0;
+            else bad = 1;
+        } else if (buf == 1 && waited1 < issued1) {
+            if (poll_parity(&mbar[1], waited1 & 1)) ++waited1;
+            else bad = 1;
+        }
+        if (!bad) {
+            if (xk >= 0) {   // X job: 6 slices of re and im into rows 40 j + n
+                f2x rh, rl, ih, il;
+                x_pair<PS>(sTerm + xk * kListLen, sTermN + xk * kListLen, pk(xsc, xsc), S + xs1, S + xs2, rh, rl, ih,
+                           il);
+                uint32_t wr[kSlicesX], wi[kSlicesX];
+                slice_x2(rh, rl, wr);
+                slice_x2(ih, il, wi);
+                __nv_bfloat16 *dst = A + xd;
+#pragma unroll
+                for (int j = 0; j < kSlicesX; ++j) {
+                    // row 40 j + n: 5 j row groups of 8 further on
+                    *reinterpret_cast<uint32_t *>(dst + j * (SH::XSTRIDE / 8) * (KC / 8) * 64) = wr[j];
+                    *reinterpret_cast<uint32_t *>(dst + j * (SH::XSTRIDE / 8) * (KC / 8) * 64 + NX * 8) = wi[j];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (uk[r] < 0) continue;
+                const float *p = S + us[r];
+                uint32_t qr[kSlices], qi[kSlices];
+                slice_u2(lds2(p), usc[r], qr);
+                slice_u2(lds2(p + PS), usc[r], qi);
+                __nv_bfloat16 *dre = B + ud1[r], *dim = B + ud2[r];
+#pragma unroll
+                for (int i = 0; i < kSlices; ++i) {
+                    const int o = tile_off<KC>(i * R, 0);
+                    *reinterpret_cast<uint32_t *>(dre + o) = qr[i];
+                    *reinterpret_cast<uint32_t *>(dre + o + NX * 8) = qi[i] ^ 0x80008000u;
+                    *reinterpret_cast<uint32_t *>(dim + o) = qi[i];
+                    *reinterpret_cast<uint32_t *>(dim + o + NX * 8) = qr[i];
+                }
+            }
+        }
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        if (__syncthreads_or(bad)) {
+            bad = 1;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const bool fresh = c % SH::CHUNKS_PER_ROUND == 0;
+        if (tid == kThr - 1) {   // a thread of the last warp (U jobs only)
+            const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+#pragma unroll
+            for (int ks = 0; ks < KC / 16; ++ks)
+#pragma unroll
+                for (int ty = 0; ty < 2; ++ty)
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const uint64_t da = smem_desc<KC>(a0 + (uint32_t)(t * 128 * KC * 2 + ks * 256));
+                        const uint64_t db = smem_desc<KC>(b0 + (uint32_t)(ty * 128 * KC * 2 + ks * 256));
+                        const uint32_t acc_in = (fresh && ks == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                                tbase + (uint32_t)((ty * 2 + t) * 128)),
+                            "l"(da), "l"(db), "r"(idesc), "r"(acc_in));
+                    }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar[buf])));
+        }
+        if (buf) ++issued1;
+        else ++issued0;
+        if (c + 2 < n_chunks) stage(c + 2);
+
+        if (c % SH::CHUNKS_PER_ROUND == SH::CHUNKS_PER_ROUND - 1 || c == n_chunks - 1) {
+            if (waited0 < issued0) {
+                if (poll_parity(&mbar[0], waited0 & 1)) ++waited0;
+                else bad = 1;
+            }
+            if (waited1 < issued1) {
+                if (poll_parity(&mbar[1], waited1 & 1)) ++waited1;
+                else bad = 1;
+            }
+            if (__syncthreads_or(bad)) {
+                bad = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // this lane's slice pairs: the five U slices with i + j <= 5, per (part, s, c1)
+            df part[R];
+#pragma unroll
+            for (int e = 0; e < R; ++e) part[e] = {0.f, 0.f};
+            const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)((ty_own * 2 + tile_own) * 128);
+#pragma unroll
+            for (int i = 0; i < kSlices; ++i) {
+                uint32_t v[R];
+#pragma unroll
+                for (int c8 = 0; c8 < R; c8 += 8)
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(v[c8]), "=r"(v[c8 + 1]), "=r"(v[c8 + 2]), "=r"(v[c8 + 3]), "=r"(v[c8 + 4]),
+                                   "=r"(v[c8 + 5]), "=r"(v[c8 + 6]), "=r"(v[c8 + 7])
+                                 : "r"(taddr + (uint32_t)(i * R + c8)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (row_ok && i + j_own <= kMaxPair) {
+#pragma unroll
+                    for (int e = 0; e < R; ++e) acc_add(part[e], df{__uint_as_float(v[e]), 0.f});
+                }
+            }
+            // the six X slices of an output column live in six lanes: add them one slice at a time
+            for (int jj = 0; jj < kSlicesX; ++jj) {
+                if (row_ok && j_own == jj) {
+#pragma unroll
+                    for (int e = 0; e < R; ++e) {   // e = part * 12 + (s, c1)
+                        float2 *p = sAcc + ((ty_own * 2 + e / (NS * NC)) * (NS * NC) + e % (NS * NC)) * NC2 + n_out;
+                        const df sum = df_add(df{p->x, p->y}, part[e]);
+                        *p = make_float2(sum.h, sum.l);
+                    }
+                }
+                __syncthreads();
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+        }
+    }
+
+    if (bad) {
+        if (tid == 0) atomicCAS(status, 0, WICK_ETIMEOUT);
+        if (waited0 < issued0) (void)poll_parity(&mbar[0], waited0 & 1);
+        if (waited1 < issued1) (void)poll_parity(&mbar[1], waited1 & 1);
+        cp_async_wait_all();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+        arrive_and_reduce<UpperShape>(plan, cs, oP, n_ranges, 1, -1, partials, counters, blocks, &s_last);
+        arrive_and_reduce<UpperShape>(plan, cs, oN, n_ranges, 1, -1, partials, counters, blocks, &s_last);
+        return;
+    }
+    cp_async_wait_all();
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+    // scale and write the partials of both types: output (type, s, c1, column) with the grids of its U colour
+    // and of the X column it came from (the proton column, transposed for the neutron)
+    double *part = reinterpret_cast<double *>(partials + ((size_t)cs * n_ranges + rng) * plan.n_out);
+    for (int e = tid; e < 2 * 2 * NS * NC * NC2; e += kThr) {
+        const int col = e % NC2, m = (e / NC2) % (NS * NC), pp = (e / (NC2 * NS * NC)) % 2, ty = e / (NC2 * NS * NC * 2);
+        const int s_ = m / NC, c1 = m % NC;
+        const int xcol = ty ? (col % NC) * NC + col / NC : col;
+        const float2 v = sAcc[e];
+        const double val = ((double)v.x + (double)v.y) * exp2d(sEU[ty * 16 + c1] + sF[xcol] - 14);
+        const int o = ty ? oN : oP;
+        const size_t out = ((size_t)(o * NS + s_) * NC + c1) * NC2 + col;
+        part[2 * out + pp] = val;
+    }
+    arrive_and_reduce<UpperShape>(plan, cs, oP, n_ranges, 1, -1, partials, counters, blocks, &s_last);
+    arrive_and_reduce<UpperShape>(plan, cs, oN, n_ranges, 1, -1, partials, counters, blocks, &s_last);
+}
+
 // Which compiled shape a plan takes (0: none, 1: upper, 2: full): weights
 // +-2^k, at most 3 colour lists per block type of exactly 4 terms each, the
 // same lists for every spin, and at most 12 staged rows per flavour.
@@ -953,6 +1328,71 @@ int launch_shape(const BlockPlan &plan, const CfgPtrs &cp, int n_cfg, int V, int
 }
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// exponent bound of the largest colour-list weight sum of each block type
+WeightExp weight_exponents(const BlockPlan &plan) {
+    WeightExp ew = {};
+    for (int o = 0; o < plan.n_ops; ++o) {
+        const int b0 = plan.os_off[o * plan.n_spin];
+        const int n_a = plan.os_off[o * plan.n_spin + 1] - b0;
+        float wmax = 0.f;
+        for (int a = 0; a < n_a; ++a) {
+            const int l = plan.os_x[b0 + a];
+            float w = 0.f;
+            for (int qq = plan.x_off[l]; qq < plan.x_off[l + 1]; ++qq) w += fabsf(plan.xt_w[qq]);
+            wmax = w > wmax ? w : wmax;
+        }
+        ew.e[o] = exponent_bound(wmax);
+    }
+    return ew;
+}
+
+// Upper-spin plans with a proton-like type (pair flavour u) and a neutron-like type (pair flavour d) whose
+// diquark lists are the proton's with the two rows of every term exchanged (same rows staged for both
+// flavours, same colour terms, same weight bound): block_pair_kernel builds both from one X.
+bool pair_plan(const BlockPlan &plan, int *oP, int *oN) {
+    if (tc_family(plan) != 1 || plan.n_ops != 2 || plan.f1[0] == plan.f1[1]) return false;
+    *oP = plan.f1[0] == 0 ? 0 : 1;
+    *oN = 1 - *oP;
+    if (plan.n_rows[0] != plan.n_rows[1]) return false;
+    for (int k = 0; k < plan.n_rows[0]; ++k)
+        if (plan.rows[0][k] != plan.rows[1][k]) return false;
+    const WeightExp ew = weight_exponents(plan);
+    if (ew.e[0] != ew.e[1]) return false;
+    const int ns = plan.n_spin;
+    const int tP = plan.os_off[*oP * ns], tN = plan.os_off[*oN * ns];
+    const int n_a = plan.os_off[*oP * ns + 1] - tP;
+    if (plan.os_off[*oN * ns + 1] - tN != n_a) return false;
+    for (int a = 0; a < n_a; ++a) {
+        const int lp = plan.os_x[tP + a], ln = plan.os_x[tN + a];
+        const int np = plan.x_off[lp + 1] - plan.x_off[lp];
+        if (plan.x_off[ln + 1] - plan.x_off[ln] != np) return false;
+        for (int i = 0; i < np; ++i) {   // every exchanged proton term is a neutron term
+            const int qp = plan.x_off[lp] + i;
+            bool found = false;
+            for (int k = 0; k < np && !found; ++k) {
+                const int qn = plan.x_off[ln] + k;
+                found = plan.xt_r2[qn] == plan.xt_r3[qp] && plan.xt_r3[qn] == plan.xt_r2[qp] &&
+                        plan.xt_w[qn] == plan.xt_w[qp];
+            }
+            if (!found) return false;
+        }
+    }
+    return true;
+}
+
+template <typename ST>
+int launch_pair(const BlockPlan &plan, const CfgPtrs &cp, int n_cfg, int V, int n_slices, int n_ranges,
+                int range_sites, const WeightExp &ew, int oP, int oN, double2 *part, int *counters, double2 *blocks,
+                int *status, cudaStream_t stream) {
+    auto k = block_pair_kernel<ST>;
+    WICK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, PairShape::SMEM));
+    dim3 grid(1, n_ranges, n_cfg * n_slices);
+    k<<<grid, kThr, PairShape::SMEM, stream>>>(plan, cp, V, n_slices, n_ranges, range_sites, ew, oP, oN, part,
+                                                counters, blocks, status);
+    WICK_CUDA_TRY(cudaGetLastError());
+    return WICK_OK;
+}
 
 }  // namespace
 
@@ -1005,19 +1445,13 @@ int launch_block_tc(const BlockPlan &plan, const void *const *Su, const void *co
         cp.sg[c] = sub >= 0 ? Sg[c] : nullptr;
         if (sub >= 0 && !Sg[c]) return WICK_EINVAL;
     }
-    WeightExp ew = {};
-    for (int o = 0; o < plan.n_ops; ++o) {
-        const int b0 = plan.os_off[o * plan.n_spin];
-        const int n_a = plan.os_off[o * plan.n_spin + 1] - b0;
-        float wmax = 0.f;
-        for (int a = 0; a < n_a; ++a) {
-            const int l = plan.os_x[b0 + a];
-            float w = 0.f;
-            for (int qq = plan.x_off[l]; qq < plan.x_off[l + 1]; ++qq) w += fabsf(plan.xt_w[qq]);
-            wmax = w > wmax ? w : wmax;
-        }
-        ew.e[o] = exponent_bound(wmax);
-    }
+    const WeightExp ew = weight_exponents(plan);
+    int oP = 0, oN = 1;
+    if (sub < 0 && pair_plan(plan, &oP, &oN))
+        return dtype == WICK_C64 ? launch_pair<float2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, oP, oN, part,
+                                                       counters, blocks, status, stream)
+                                 : launch_pair<double2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, oP, oN, part,
+                                                        counters, blocks, status, stream);
     if (dtype == WICK_C64)
         return fam == 1 ? launch_shape<UpperShape, float2>(plan, cp, n_cfg, V, n_slices, n_ranges, rs, ew, sub, n_pass,
                                                            part, counters, blocks, status, stream)
