@@ -140,21 +140,21 @@ BLOCK_ALG_BYTES_PER_SITE = 2 * 6 * 6 * 8
 # update 2 ops x 2 spins x 216 entries x 3 terms.
 CMAC_PER_SITE = 2 * 3 * 36 * 4 + 2 * 2 * 216 * 3
 
-# The tensor-core block build (WICK_MIXED) per site, both block types: the
-# FP32-pipe work of preparing the operands, in lane operations (an f32x2
-# instruction is two) --
-#   216 diquark values (2 types x 3 lists x 36 entries), two sites per packed
-#   instruction: 4 terms x (2 weight scalings + 3 operand products + 4
-#   fixed-exponent product-accumulations of 4 f32x2 ops each) = 84, 4 more to
-#   start and finish the accumulators, and 6 slices per real part from the
-#   (hi, lo) pair, 18 f32x2 ops each = 36 -> 124 f32x2 ops per site pair, 124
-#   lane ops per value and site;
+# The tensor-core block build (WICK_MIXED, the proton/neutron pair kernel) per
+# site, both block types: the FP32-pipe work of preparing the operands, in lane
+# operations (an f32x2 instruction is two) --
+#   108 diquark values (3 lists x 36 entries, computed once: the neutron's are
+#   the proton's transposed), two sites per packed instruction: 4 terms x (2
+#   weight scalings + 3 operand products + 4 fixed-exponent product-accumulations
+#   of 4 f32x2 ops each) = 84, 4 more to start and finish the accumulators, and 6
+#   slices per real part from the (hi, lo) pair, 18 f32x2 ops each = 36 -> 124
+#   f32x2 ops per site pair, 124 lane ops per value and site;
 #   72 propagator values (2 types x 2 spins x 6 x 3 terms): 5 slices, 15 f32x2
 #   ops per real part pair = 30 lane ops per value
-# -- and the MMA work: per type 6 MMAs of M=128 (5 stacked slices x 24 rows,
-# padded), N=48 (36 columns, padded), over K = 6 per site.
-TC_LANE_OPS_PER_SITE = 216 * 124 + 72 * 30
-TC_MMA_FLOPS_PER_SITE = 2 * 6 * 2 * 128 * 48 * 6
+# -- and the MMA work: per type two MMAs of M=128 (6 X slices x 40 rows, two
+# tiles), N=128 (5 U slices x 24 rows, padded), over K = 6 per site.
+TC_LANE_OPS_PER_SITE = 108 * 124 + 72 * 30
+TC_MMA_FLOPS_PER_SITE = 2 * 2 * 2 * 128 * 128 * 6
 
 
 class Clocks:
@@ -539,8 +539,8 @@ def run_ours(args):
         "rel_err_mixed_vs_fp64_max_per_t": rel_err,
         "reduce": {"seconds": reduce_s, "raw_terms": n_raw, "zero_terms": n_zero, "distinct_keys": n_keys,
                    "kept_terms": U, "raw_terms_per_s": n_raw / reduce_s, "false_merge_bound": bound},
-        "roofline": {"kernel": "block_tc_kernel (tensor-core block build: grid-exponent scan, sliced update "
-                               "and range reduction in one launch)",
+        "roofline": {"kernel": "block_pair_kernel (tensor-core block build of both block types: grid-exponent "
+                               "scan, sliced update and range reduction in one launch)",
                      "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved_gbs / hbm_peak, "traffic": recorded_traffic(),
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
