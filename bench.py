@@ -247,7 +247,7 @@ def kernel_source_hash():
 def recorded_traffic():
     """DRAM bytes per launch from the committed ncu record, or None when the
     kernel sources changed since the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "block_tc_he4_traffic.txt")
+    p = os.path.join(ROOT, "profiles", "block_pair_he4_traffic.txt")
     if not os.path.exists(p):
         return None
     d = {}

@@ -1,6 +1,6 @@
 """The benchmark's committed records stay tied to the sources they describe (no GPU needed).
 
-bench.py reports the block build's DRAM traffic from profiles/block_tc_he4_traffic.txt only while
+bench.py reports the block build's DRAM traffic from profiles/block_pair_he4_traffic.txt only while
 the tensor-core kernel's code is the code that was profiled; the record carries a hash of the code
 tokens (comments and blank space removed).
 """
