@@ -83,6 +83,7 @@ __host__ __device__ constexpr int level_acc(int i, int j) {
 }
 __host__ __device__ constexpr bool level_acc_exact(int a) { return a < 6; }
 constexpr int kRangeSitesDefault = 512;            // sites per CTA (one grid, one partial) unless tuned
+constexpr int kPairRangeSitesDefault = 1024;       // the same for block_pair_kernel
 constexpr int kMaxCfg = 64;                        // configurations per launch
 constexpr int kSpinLimit = 1 << 22;                // mbarrier polls before giving up
 constexpr int kStage = 3;                          // staging buffers
@@ -1415,6 +1416,16 @@ int tc_range_sites(int requested) {
                                                                                           : kRangeSitesDefault;
 }
 
+namespace {
+// the range size of a launch: the requested one, else 1024 sites for the pair kernel (its 8-site chunks
+// amortise the per-CTA scan and epilogue over more sites) and 512 for block_tc_kernel
+int range_for(const BlockPlan &plan, int requested, int n_pass) {
+    if (requested >= kRoundSites && requested % kRoundSites == 0 && requested <= 4096) return requested;
+    int oP, oN;
+    return n_pass == 1 && pair_plan(plan, &oP, &oN) ? kPairRangeSitesDefault : kRangeSitesDefault;
+}
+}  // namespace
+
 int tc_max_configs() { return kMaxCfg; }
 
 size_t tc_counter_bytes(const BlockPlan &plan, int n_slices, int n_cfg) {
@@ -1422,7 +1433,7 @@ size_t tc_counter_bytes(const BlockPlan &plan, int n_slices, int n_cfg) {
 }
 
 size_t tc_partial_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites, int n_pass) {
-    const int rs = tc_range_sites(range_sites);
+    const int rs = range_for(plan, range_sites, n_pass);
     const size_t n_ranges = (size_t)(V + rs - 1) / rs;
     return sizeof(double2) * n_pass * n_ranges * n_cfg * n_slices * plan.n_out;
 }
@@ -1431,7 +1442,7 @@ int launch_block_tc(const BlockPlan &plan, const void *const *Su, const void *co
                     int n_slices, int range_sites, int *counters, double2 *part, double2 *blocks, int *status,
                     cudaStream_t stream, const void *const *Sg, int sub) {
     const int fam = tc_family(plan);
-    const int rs = tc_range_sites(range_sites);
+    const int rs = range_for(plan, range_sites, sub >= 0 ? 3 : 1);
     const int n_ranges = (V + rs - 1) / rs;
     if (!fam || n_cfg < 1 || n_cfg > kMaxCfg || n_ranges > 65535 || (int64_t)n_cfg * n_slices > 65535)
         return WICK_EINVAL;
