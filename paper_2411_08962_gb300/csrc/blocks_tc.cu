@@ -1082,15 +1082,28 @@ block_pair_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant_
     const uint32_t tbase = *tslot;
     if (n_chunks > 1) stage(1);
 
-    // the thread's jobs: job 0 = tid, job 1 = tid + kThr; X jobs first, then U jobs
+    // the thread's jobs.  Warps 0..13 take the X jobs (32 each, warp 13 half), the nine warp-loads of U
+    // jobs go to warps 14, 15 and, as a second job, to warps 0, 1, 2, 3, 6, 7, 10, so that each of the
+    // four warp schedulers (warp % 4) gets about the same work: 4, 4, 3 and 3 X warps, 1, 1, 4 and 3 U.
     int xk = -1, xs1 = 0, xs2 = 0, xd = 0;   // X job: colour term, u / d staged offsets, A offset of slice 0
     float xsc = 0.f;
-    int uk[2] = {-1, -1}, us[2] = {0, 0}, ud1[2] = {0, 0}, ud2[2] = {0, 0};   // U jobs (at most one per round)
+    int uk[2] = {-1, -1}, us[2] = {0, 0}, ud1[2] = {0, 0}, ud2[2] = {0, 0};   // U jobs
     float usc[2] = {0.f, 0.f};
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int jb = r * kThr + tid;
-        if (jb < SH::NXJOB) {   // (a, column n, site pair): lanes take 8 columns x 4 site pairs
+    {
+        const int xw = warp < 14 ? warp : -1;
+        int uw[2] = {warp >= 14 ? warp - 14 : -1, -1};
+        switch (warp) {
+            case 0: uw[1] = 2; break;
+            case 1: uw[1] = 3; break;
+            case 2: uw[1] = 4; break;
+            case 3: uw[1] = 5; break;
+            case 6: uw[1] = 6; break;
+            case 7: uw[1] = 7; break;
+            case 10: uw[1] = 8; break;
+            default: break;
+        }
+        const int jb = xw * 32 + lane;
+        if (xw >= 0 && jb < SH::NXJOB) {   // (a, column n, site pair): lanes take 8 columns x 4 site pairs
             const int a = jb / (NC2 * SH::NSP), rem = jb % (NC2 * SH::NSP), n = rem / SH::NSP, sp = rem % SH::NSP;
             if (a < n_a) {
                 xk = a;
@@ -1099,8 +1112,12 @@ block_pair_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant_
                 xd = tile_off<KC>(n, a * 2 * NX + 2 * sp);
                 xsc = exp2i(7 - sF[n]);
             }
-        } else if (jb < SH::NXJOB + SH::NUJOB) {   // (type, a, (s, c1), site pair)
-            const int u = jb - SH::NXJOB;
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int u = uw[r] * 32 + lane;
+            if (uw[r] < 0 || u >= SH::NUJOB) continue;
+            // (type, a, (s, c1), site pair)
             const int ty = u / (kKa * NS * NC * SH::NSP), rem = u % (kKa * NS * NC * SH::NSP);
             const int a = rem / (NS * NC * SH::NSP), m = (rem / SH::NSP) % (NS * NC), sp = rem % SH::NSP;
             if (a < n_a) {
@@ -1179,7 +1196,7 @@ block_pair_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant_
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const bool fresh = c % SH::CHUNKS_PER_ROUND == 0;
-        if (tid == kThr - 1) {   // a thread of the last warp (U jobs only)
+        if (tid == kThr - 1) {   // a thread of the last warp (one U job)
             const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
 #pragma unroll
             for (int ks = 0; ks < KC / 16; ++ks)
