@@ -307,6 +307,8 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *terms,
  *                          fills to 3/4 is dropped and the enumeration rerun with twice the slots
  *   hash_log2_max          log2 of the largest table tried, 4..28 (default 28); past it the
  *                          reduction fails with WICK_ECAPACITY
+ *   no_pair_kernel         1: build one block type per CTA even when a proton/neutron pair of
+ *                          types could share its diquark values (0, the default: share them)
  * NULL restores the defaults.  Errors: WICK_EINVAL (a field out of range).
  */
 typedef struct wick_tuning {
@@ -316,6 +318,7 @@ typedef struct wick_tuning {
     int contract_chunk_terms;
     int hash_log2_start;
     int hash_log2_max;
+    int no_pair_kernel;
 } wick_tuning;
 int wick_set_tuning(const wick_tuning *tuning);
 int wick_get_tuning(wick_tuning *tuning);

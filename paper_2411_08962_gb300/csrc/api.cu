@@ -149,7 +149,7 @@ int terms_table(const wick_terms *t, ContractTable *tab, int *n_blk) {
 // ---------------------------------------------------------------------------
 namespace {
 std::mutex g_tune_mu;
-wick_tuning g_tuning = {0, 0, 0, 0, 0, 0};
+wick_tuning g_tuning = {0, 0, 0, 0, 0, 0, 0};
 }  // namespace
 
 wick_tuning current_tuning() {
@@ -977,8 +977,9 @@ int wick_contract_3pt(const void *blocks, const void *dblocks, int n_src, int T,
 }
 
 int wick_set_tuning(const wick_tuning *t) {
-    wick_tuning v = {0, 0, 0, 0, 0, 0};
+    wick_tuning v = {0, 0, 0, 0, 0, 0, 0};
     if (t) v = *t;
+    if (v.no_pair_kernel != 0 && v.no_pair_kernel != 1) return WICK_EINVAL;
     if (v.hash_log2_start != 0 && (v.hash_log2_start < 4 || v.hash_log2_start > 28)) return WICK_EINVAL;
     if (v.hash_log2_max != 0 && (v.hash_log2_max < 4 || v.hash_log2_max > 28)) return WICK_EINVAL;
     if (v.range_sites < 0 || v.range_sites % 128 || v.range_sites > 4096) return WICK_EINVAL;

@@ -1369,6 +1369,7 @@ WeightExp weight_exponents(const BlockPlan &plan) {
 // diquark lists are the proton's with the two rows of every term exchanged (same rows staged for both
 // flavours, same colour terms, same weight bound): block_pair_kernel builds both from one X.
 bool pair_plan(const BlockPlan &plan, int *oP, int *oN) {
+    if (current_tuning().no_pair_kernel) return false;
     if (tc_family(plan) != 1 || plan.n_ops != 2 || plan.f1[0] == plan.f1[1]) return false;
     *oP = plan.f1[0] == 0 ? 0 : 1;
     *oN = 1 - *oP;

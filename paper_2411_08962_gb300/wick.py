@@ -64,7 +64,8 @@ class wick_nucleus(C.Structure):
 
 class wick_tuning(C.Structure):
     _fields_ = [("range_sites", C.c_int), ("contract_threads", C.c_int), ("contract_ctas_per_sm", C.c_int),
-                ("contract_chunk_terms", C.c_int), ("hash_log2_start", C.c_int), ("hash_log2_max", C.c_int)]
+                ("contract_chunk_terms", C.c_int), ("hash_log2_start", C.c_int), ("hash_log2_max", C.c_int),
+                ("no_pair_kernel", C.c_int)]
 
 
 class wick_quark_operator(C.Structure):
@@ -474,7 +475,7 @@ def wick_cluster_product(Ca, Cb, out, stream=None):
 
 
 TUNING_FIELDS = ("range_sites", "contract_threads", "contract_ctas_per_sm", "contract_chunk_terms",
-                 "hash_log2_start", "hash_log2_max")
+                 "hash_log2_start", "hash_log2_max", "no_pair_kernel")
 
 
 def wick_set_tuning(tuning=None):

@@ -167,10 +167,12 @@ def test_tuning_is_validated_and_kept(lib):
     try:
         wick.wick_set_tuning({"range_sites": 1024, "contract_threads": 128, "contract_chunk_terms": 2048})
         assert wick.wick_get_tuning() == {"range_sites": 1024, "contract_threads": 128, "contract_ctas_per_sm": 0,
-                                          "contract_chunk_terms": 2048, "hash_log2_start": 0, "hash_log2_max": 0}
+                                          "contract_chunk_terms": 2048, "hash_log2_start": 0, "hash_log2_max": 0,
+                                          "no_pair_kernel": 0}
         for bad in ({"range_sites": 100}, {"range_sites": 8192}, {"contract_threads": 100},
                     {"contract_threads": 1024}, {"contract_ctas_per_sm": -1}, {"contract_chunk_terms": 10},
-                    {"hash_log2_start": 3}, {"hash_log2_start": 29}, {"hash_log2_max": 2}, {"hash_log2_max": 30}):
+                    {"hash_log2_start": 3}, {"hash_log2_start": 29}, {"hash_log2_max": 2}, {"hash_log2_max": 30},
+                    {"no_pair_kernel": 2}):
             with pytest.raises(wick.WickError) as e:
                 wick.wick_set_tuning(bad)
             assert e.value.code == wick.WICK_EINVAL

@@ -107,7 +107,7 @@ def test_tuned_batch_equals_individual_calls_and_autotuner():
     tuning = {"range_sites": 256, "contract_threads": 128, "contract_ctas_per_sm": 2, "contract_chunk_terms": 64}
     wick.wick_set_tuning(tuning)
     try:
-        assert wick.wick_get_tuning() == dict(tuning, hash_log2_start=0, hash_log2_max=0)
+        assert wick.wick_get_tuning() == dict(tuning, hash_log2_start=0, hash_log2_max=0, no_pair_kernel=0)
         nb = tabs.nuc.n_blk
         blocks = torch.zeros((n_cfg, n_src, T, nb), dtype=torch.complex128, device="cuda")
         C = torch.zeros((n_cfg, len(NUCLEI), n_src, T), dtype=torch.complex128, device="cuda")

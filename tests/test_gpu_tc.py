@@ -58,19 +58,46 @@ def props(L, T, n_src, seed, dtype):
     return (synth.propagator(seed, 0, L, T, n_src, dtype=dtype), synth.propagator(seed, 1, L, T, n_src, dtype=dtype))
 
 
+@pytest.fixture(params=[0, 1], ids=["pair_kernel", "one_type_per_cta"])
+def pair_mode(request):
+    """Both tensor-core kernels of the upper-spin tables: the pair kernel (one CTA builds the proton and
+    the neutron types from one computation of the diquark values) and one block type per CTA."""
+    wick.wick_set_tuning({"no_pair_kernel": request.param})
+    yield request.param
+    wick.wick_set_tuning(None)
+
+
 @pytest.mark.parametrize("L,T,n_src,dtype", [
-    (1, 1, 1, np.complex128),   # one site: a 16-site chunk with 15 empty sites
-    (3, 2, 2, np.complex128),   # 27 sites: one full chunk and a ragged one
-    (4, 4, 1, np.complex64),    # 64 sites: four full chunks
-    (7, 2, 1, np.complex128),   # 343 sites: two CTAs along sites, ragged tail of 7
-    (17, 1, 1, np.complex64),   # 4913 sites: 20 CTAs along sites
+    (1, 1, 1, np.complex128),   # one site: a chunk with empty sites
+    (3, 2, 2, np.complex128),   # 27 sites: full chunks and a ragged one
+    (4, 4, 1, np.complex64),    # 64 sites: one TMEM round of full chunks
+    (7, 2, 1, np.complex128),   # 343 sites: ragged tail of 7
+    (17, 1, 1, np.complex64),   # 4913 sites: several CTAs along sites
 ])
-def test_tc_blocks_match_oracle(L, T, n_src, dtype):
+def test_tc_blocks_match_oracle(L, T, n_src, dtype, pair_mode):
     Su, Sd = props(L, T, n_src, seed=0x7C00 + L, dtype=dtype)
     B = blocks(Su, Sd, operators.nucleus("deuteron"), wick.WICK_MIXED, L)
     onuc = oops.nucleus("deuteron")
     ref = O.antisymmetric_blocks(O.blocks_single(as_float(Su), as_float(Sd), onuc), onuc)
     assert block_err(B, ref) < TC_TOL
+
+
+def test_pair_and_one_type_kernels_agree():
+    """He-4 tables on 8^3 x 3 x 2 sources (four ranges of 128 sites, ragged none): the pair kernel and the
+    one-type-per-CTA kernel both within TC_TOL of FP64 and within 1e-10 of each other."""
+    L = 8
+    Su, Sd = props(L, 3, 2, seed=0x7C33, dtype=np.complex64)
+    nuc = operators.nucleus("he4")
+    f64 = blocks(Su, Sd, nuc, wick.WICK_FP64, L)
+    try:
+        wick.wick_set_tuning({"range_sites": 128})
+        pair = blocks(Su, Sd, nuc, wick.WICK_MIXED, L)
+        wick.wick_set_tuning({"range_sites": 128, "no_pair_kernel": 1})
+        one = blocks(Su, Sd, nuc, wick.WICK_MIXED, L)
+    finally:
+        wick.wick_set_tuning(None)
+    assert block_err(pair, f64) < TC_TOL and block_err(one, f64) < TC_TOL
+    assert block_err(pair, one) < TC_TOL
 
 
 def test_tc_matches_cuda_core_kernel():
