@@ -63,7 +63,7 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
         if (tabs[k].el_scale) return WICK_EINVAL;     // correlation-matrix tables: wick_contract only
     }
     const wick_tuning tune = current_tuning();
-    const int rs = tune.range_sites;
+    int rs = tune.range_sites;
     const bool tc = precision == WICK_MIXED && tc_applicable(plan);
     int group = 1;
     size_t pbytes = block_partial_bytes(plan, (int)V, (int)n_slices, precision, rs), cbytes = 0;
@@ -72,6 +72,8 @@ extern "C" int wick_batch_create(const wick_prop *Su, const wick_prop *Sd, int n
         group = (int)std::max<size_t>(1, std::min<size_t>(kGroupBytes / per_cfg, (size_t)tc_max_configs()));
         group = std::min(group, n_cfg);
         while ((int64_t)group * n_slices > 65535) --group;
+        // one range size for the scratch and every launch (a last, smaller group keeps it)
+        rs = tc_range_for(plan, rs, 1, group, (int)n_slices, (int)V);
         pbytes = tc_partial_bytes(plan, (int)V, (int)n_slices, group, rs);
         cbytes = tc_counter_bytes(plan, (int)n_slices, group);
     }

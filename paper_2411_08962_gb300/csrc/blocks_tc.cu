@@ -1434,15 +1434,19 @@ int tc_range_sites(int requested) {
                                                                                           : kRangeSitesDefault;
 }
 
-namespace {
-// the range size of a launch: the requested one, else 1024 sites for the pair kernel (its 8-site chunks
-// amortise the per-CTA scan and epilogue over more sites) and 512 for block_tc_kernel
-int range_for(const BlockPlan &plan, int requested, int n_pass) {
+// The range size of a launch: the requested one, else for the pair kernel 1024 sites (its 8-site chunks
+// amortise the per-CTA scan and epilogue over more sites) when that still gives at least 8 waves of CTAs,
+// and 512 otherwise (and for block_tc_kernel).
+int tc_range_for(const BlockPlan &plan, int requested, int n_pass, int n_cfg, int n_slices, int V) {
     if (requested >= kRoundSites && requested % kRoundSites == 0 && requested <= 4096) return requested;
     int oP, oN;
-    return n_pass == 1 && pair_plan(plan, &oP, &oN) ? kPairRangeSitesDefault : kRangeSitesDefault;
+    if (n_pass != 1 || !pair_plan(plan, &oP, &oN)) return kRangeSitesDefault;
+    int dev = 0, n_sm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ctas = (int64_t)n_cfg * n_slices * ((V + kPairRangeSitesDefault - 1) / kPairRangeSitesDefault);
+    return ctas >= 8 * (int64_t)n_sm ? kPairRangeSitesDefault : kRangeSitesDefault;
 }
-}  // namespace
 
 int tc_max_configs() { return kMaxCfg; }
 
@@ -1451,7 +1455,7 @@ size_t tc_counter_bytes(const BlockPlan &plan, int n_slices, int n_cfg) {
 }
 
 size_t tc_partial_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites, int n_pass) {
-    const int rs = range_for(plan, range_sites, n_pass);
+    const int rs = tc_range_for(plan, range_sites, n_pass, n_cfg, n_slices, V);
     const size_t n_ranges = (size_t)(V + rs - 1) / rs;
     return sizeof(double2) * n_pass * n_ranges * n_cfg * n_slices * plan.n_out;
 }
@@ -1460,7 +1464,7 @@ int launch_block_tc(const BlockPlan &plan, const void *const *Su, const void *co
                     int n_slices, int range_sites, int *counters, double2 *part, double2 *blocks, int *status,
                     cudaStream_t stream, const void *const *Sg, int sub) {
     const int fam = tc_family(plan);
-    const int rs = range_for(plan, range_sites, sub >= 0 ? 3 : 1);
+    const int rs = tc_range_for(plan, range_sites, sub >= 0 ? 3 : 1, n_cfg, n_slices, V);
     const int n_ranges = (V + rs - 1) / rs;
     if (!fam || n_cfg < 1 || n_cfg > kMaxCfg || n_ranges > 65535 || (int64_t)n_cfg * n_slices > 65535)
         return WICK_EINVAL;

@@ -80,6 +80,9 @@ int block_build_launches(const BlockPlan &plan, int precision);  // kernels one 
 // scratch holds one counter per (configuration, slice, block type) -- zero before the first launch,
 // cleared again by every launch -- and the FP64 partials of every site range
 int tc_range_sites(int requested);               // the range size a request (0 = default) resolves to
+// the same for a launch of n_cfg configurations of n_slices slices and V sites (n_pass: 3 for derivative
+// blocks); callers that size scratch for one shape and launch smaller ones pass its result on
+int tc_range_for(const BlockPlan &plan, int requested, int n_pass, int n_cfg, int n_slices, int V);
 int tc_max_configs();
 size_t tc_counter_bytes(const BlockPlan &plan, int n_slices, int n_cfg);
 size_t tc_partial_bytes(const BlockPlan &plan, int V, int n_slices, int n_cfg, int range_sites, int n_pass = 1);
