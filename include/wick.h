@@ -295,8 +295,9 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *terms,
  * package's autotuner (paper_2411_08962_gb300.autotune) times candidates on a
  * workload and records its choice as JSON.
  *   range_sites            tensor-core block build: sites per CTA and per FP64 partial,
- *                          a multiple of 128 up to 4096 (default 1024 when one CTA builds a
- *                          proton/neutron pair of block types, else 512)
+ *                          a multiple of 128 up to 4096 (default 1024 for the proton/neutron
+ *                          pair kernel and the full-spin tables when a launch has at least 8
+ *                          waves of such CTAs, else 512)
  *   contract_threads       contraction CTA size, a multiple of 32 up to 512 (default 256)
  *   contract_ctas_per_sm   resident contraction CTAs per SM (default: as many as fit)
  *   contract_chunk_terms   terms per contraction work item, about (64 or more; default 4096);

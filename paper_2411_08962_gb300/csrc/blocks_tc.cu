@@ -83,7 +83,7 @@ __host__ __device__ constexpr int level_acc(int i, int j) {
 }
 __host__ __device__ constexpr bool level_acc_exact(int a) { return a < 6; }
 constexpr int kRangeSitesDefault = 512;            // sites per CTA (one grid, one partial) unless tuned
-constexpr int kPairRangeSitesDefault = 1024;       // the same for block_pair_kernel
+constexpr int kPairRangeSitesDefault = 1024;       // the same for block_pair_kernel and the full-spin shape
 constexpr int kMaxCfg = 64;                        // configurations per launch
 constexpr int kSpinLimit = 1 << 22;                // mbarrier polls before giving up
 constexpr int kStage = 3;                          // staging buffers
@@ -1434,17 +1434,21 @@ int tc_range_sites(int requested) {
                                                                                           : kRangeSitesDefault;
 }
 
-// The range size of a launch: the requested one, else for the pair kernel 1024 sites (its 8-site chunks
-// amortise the per-CTA scan and epilogue over more sites) when that still gives at least 8 waves of CTAs,
-// and 512 otherwise (and for block_tc_kernel).
+// The range size of a launch: the requested one, else 1024 sites for the pair kernel and the full-spin
+// shape (the per-CTA scan and epilogue amortised over more sites: -4 to -5 % on one-source slabs) when
+// that still gives at least 8 waves of CTAs, and 512 otherwise.
 int tc_range_for(const BlockPlan &plan, int requested, int n_pass, int n_cfg, int n_slices, int V) {
     if (requested >= kRoundSites && requested % kRoundSites == 0 && requested <= 4096) return requested;
     int oP, oN;
-    if (n_pass != 1 || !pair_plan(plan, &oP, &oN)) return kRangeSitesDefault;
+    const bool pair = n_pass == 1 && pair_plan(plan, &oP, &oN);
+    const bool full = tc_family(plan) == 2;
+    if (!pair && !full) return kRangeSitesDefault;
     int dev = 0, n_sm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t ctas = (int64_t)n_cfg * n_slices * ((V + kPairRangeSitesDefault - 1) / kPairRangeSitesDefault);
+    const int64_t per_range = pair ? 1 : (int64_t)plan.n_ops * FullShape::NCT * n_pass;
+    const int64_t ctas = (int64_t)n_cfg * n_slices * per_range *
+                         ((V + kPairRangeSitesDefault - 1) / kPairRangeSitesDefault);
     return ctas >= 8 * (int64_t)n_sm ? kPairRangeSitesDefault : kRangeSitesDefault;
 }
 
