@@ -208,6 +208,32 @@ __device__ __forceinline__ float2 to_f2(float2 v) { return v; }
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
 // 4-byte copy; src_bytes 0 writes a zero
+// L2 eviction policies: the grid-exponent scan marks the rows it reads evict-last, so that they are still
+// in L2 when the CTA stages them; the pair kernel's staging (the rows' last reader) marks them evict-first
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float4 ldg4_hint(const void *p, uint64_t policy) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(policy));
+    return v;
+}
+// 4-byte copy with an L2 policy; src_bytes 0 writes a zero
+__device__ __forceinline__ void cp_async4_hint(void *dst, const void *src, int src_bytes, uint64_t policy) {
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2, %3;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes), "l"(policy)
+                 : "memory");
+}
+
 __device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
                  : "memory");
@@ -456,9 +482,10 @@ __device__ __forceinline__ void range_bounds(const BlockPlan &plan, const ST *su
         const ST *src = (f == 0 ? su : (f == 1 ? sd : sg)) + row * 12 + plan.chi[ic];
         float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;   // columns ic and ic + 1
         if (pairs) {
+            const uint64_t keep = l2_evict_last();
 #pragma unroll 12
             for (int x = x_begin + part; x < x_end; x += parts) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(src + (size_t)x * 144));
+                const float4 v = ldg4_hint(src + (size_t)x * 144, keep);
                 a1 = fmaxf(a1, fmaxf(fabsf(v.x), fabsf(v.y)));
                 a2 = fmaxf(a2, __fadd_ru(fabsf(v.x), fabsf(v.y)));   // rounded up: a bound of |re| + |im|
                 b1 = fmaxf(b1, fmaxf(fabsf(v.z), fabsf(v.w)));
@@ -1054,6 +1081,7 @@ block_pair_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant_
         const int src_off = sSrc[st_rcc];
         st_src = ((src_off >> 16) ? sd : su) + (src_off & 0xFFFF);
     }
+    const uint64_t drop = l2_evict_first();
     auto stage = [&](int c) {
         if (stager) {
             float *dst = sS0 + (c % kStage) * (2 * PS) + st_rcc * NX;
@@ -1063,8 +1091,8 @@ block_pair_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant_
                 const bool in = xb + s8 < x_end;
                 const ST *src = st_src + (size_t)(in ? xb + s8 : x_begin) * 144;
                 if constexpr (sizeof(ST) == 8) {
-                    cp_async4(dst + s8, reinterpret_cast<const float *>(src), in ? 4 : 0);
-                    cp_async4(dst + s8 + PS, reinterpret_cast<const float *>(src) + 1, in ? 4 : 0);
+                    cp_async4_hint(dst + s8, reinterpret_cast<const float *>(src), in ? 4 : 0, drop);
+                    cp_async4_hint(dst + s8 + PS, reinterpret_cast<const float *>(src) + 1, in ? 4 : 0, drop);
                 } else {
                     const float2 v = in ? to_f2(*src) : make_float2(0.f, 0.f);
                     dst[s8] = v.x;
