@@ -959,9 +959,9 @@ __global__ void mbar_wait_selftest_kernel(int limit, int *status) {
 // accumulators see A's columns transposed: lane (j, n) contributes to the neutron
 // column n^T = (n mod 6) 6 + n / 6, whose grid is the proton column n's.
 // Readout per 128-site round: each thread reads its lane's 120 columns, adds the
-// five U slices with i + j <= 5 in double-FP32, and adds the sums into a
-// double-FP32 accumulator in shared memory of its own X slice j (no two lanes
-// share an entry); the six X slices of an output are added at the end.  Grids, slicing, exact rounds, staging,
+// five U slices with i + j <= 5 in double-FP32, and the six X slices of an output
+// (six lanes, in different warps) are added into double-FP32 accumulators in
+// shared memory, one slice j at a time.  Grids, slicing, exact rounds, staging,
 // bounded waits and the range reduction are those of block_tc_kernel.
 // ---------------------------------------------------------------------------
 struct PairShape {
@@ -978,7 +978,7 @@ struct PairShape {
     static constexpr int A_BYTES = 256 * KC * 2;             // two M tiles of X slices
     static constexpr int B_BYTES = 2 * 128 * KC * 2;         // the U slices of both types
     static constexpr int S_BYTES = 2 * PS * 4;
-    static constexpr int ACC_BYTES = 2 * kSlicesX * 2 * NS * NC * NC2 * 8;   // [type][j][part][(s, c1)][column] df
+    static constexpr int ACC_BYTES = 2 * 2 * NS * NC * NC2 * 8;   // [type][part][(s, c1)][column] df
     static constexpr int SMEM = 2 * (A_BYTES + B_BYTES) + kStage * S_BYTES + ACC_BYTES + 4 * (32 + 64) +
                                 (16 + 8) * kKa * kListLen + 4 * 16 + 4 * kMaxRows * 12 + 64;
     static_assert(kSlicesX * XSTRIDE <= 256 && XSTRIDE % 8 == 0 && XSTRIDE >= NC2, "X rows");
@@ -1011,7 +1011,7 @@ block_pair_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant_
     __nv_bfloat16 *sB0 = reinterpret_cast<__nv_bfloat16 *>(smem + 2 * SH::A_BYTES);
     float *sS0 = reinterpret_cast<float *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES));
     float2 *sAcc = reinterpret_cast<float2 *>(smem + 2 * (SH::A_BYTES + SH::B_BYTES) + kStage * SH::S_BYTES);
-    int *sEU = reinterpret_cast<int *>(sAcc + 2 * kSlicesX * 2 * NS * NC * NC2);   // [type][16] grid of U per colour
+    int *sEU = reinterpret_cast<int *>(sAcc + 2 * 2 * NS * NC * NC2);   // [type][16] grid of U per colour
     int *sF = sEU + 32;                                       // [64] grid of X per proton column
     int4 *sTerm = reinterpret_cast<int4 *>(sF + 64);          // [kKa][kListLen] the proton's list terms
     f2x *sTermN = reinterpret_cast<f2x *>(sTerm + kKa * kListLen);
@@ -1023,7 +1023,7 @@ block_pair_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant_
     {   // zero the operand buffers (padding rows, unused colour terms) and the accumulators
         uint4 *z = reinterpret_cast<uint4 *>(smem);
         for (int e = tid; e < 2 * (SH::A_BYTES + SH::B_BYTES) / 16; e += kThr) z[e] = make_uint4(0u, 0u, 0u, 0u);
-        for (int e = tid; e < 2 * kSlicesX * 2 * NS * NC * NC2; e += kThr) sAcc[e] = make_float2(0.f, 0.f);
+        for (int e = tid; e < 2 * 2 * NS * NC * NC2; e += kThr) sAcc[e] = make_float2(0.f, 0.f);
     }
     const int x_begin = rng * range_sites, x_end = min(V, x_begin + range_sites);
     const int n_chunks = (x_end - x_begin + NX - 1) / NX;
@@ -1269,8 +1269,6 @@ block_pair_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant_
             const uint32_t taddr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)((ty_own * 2 + tile_own) * 128);
 #pragma unroll
             for (int i = 0; i < kSlices; ++i) {
-                const bool mine = row_ok && i + j_own <= kMaxPair;
-                if (!__any_sync(0xffffffffu, mine)) continue;   // no lane of the warp keeps this U slice
                 uint32_t v[R];
 #pragma unroll
                 for (int c8 = 0; c8 < R; c8 += 8)
@@ -1279,20 +1277,22 @@ block_pair_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant_
                                    "=r"(v[c8 + 5]), "=r"(v[c8 + 6]), "=r"(v[c8 + 7])
                                  : "r"(taddr + (uint32_t)(i * R + c8)));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
-                if (mine) {
+                if (row_ok && i + j_own <= kMaxPair) {
 #pragma unroll
                     for (int e = 0; e < R; ++e) acc_add(part[e], df{__uint_as_float(v[e]), 0.f});
                 }
             }
-            // into this lane's own accumulators: X slice j_own of the output column
-            if (row_ok) {
+            // the six X slices of an output column live in six lanes: add them one slice at a time
+            for (int jj = 0; jj < kSlicesX; ++jj) {
+                if (row_ok && j_own == jj) {
 #pragma unroll
-                for (int e = 0; e < R; ++e) {   // e = part * 12 + (s, c1)
-                    float2 *p = sAcc + (((ty_own * kSlicesX + j_own) * 2 + e / (NS * NC)) * (NS * NC) + e % (NS * NC)) *
-                                           NC2 + n_out;
-                    const df sum = df_add(df{p->x, p->y}, part[e]);
-                    *p = make_float2(sum.h, sum.l);
+                    for (int e = 0; e < R; ++e) {   // e = part * 12 + (s, c1)
+                        float2 *p = sAcc + ((ty_own * 2 + e / (NS * NC)) * (NS * NC) + e % (NS * NC)) * NC2 + n_out;
+                        const df sum = df_add(df{p->x, p->y}, part[e]);
+                        *p = make_float2(sum.h, sum.l);
+                    }
                 }
+                __syncthreads();
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
@@ -1324,13 +1324,8 @@ block_pair_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant_
         const int col = e % NC2, m = (e / NC2) % (NS * NC), pp = (e / (NC2 * NS * NC)) % 2, ty = e / (NC2 * NS * NC * 2);
         const int s_ = m / NC, c1 = m % NC;
         const int xcol = ty ? (col % NC) * NC + col / NC : col;
-        df sum = {0.f, 0.f};   // the six X slices, in slice order
-#pragma unroll
-        for (int j = 0; j < kSlicesX; ++j) {
-            const float2 v = sAcc[(((ty * kSlicesX + j) * 2 + pp) * (NS * NC) + m) * NC2 + col];
-            sum = df_add(sum, df{v.x, v.y});
-        }
-        const double val = ((double)sum.h + (double)sum.l) * exp2d(sEU[ty * 16 + c1] + sF[xcol] - 14);
+        const float2 v = sAcc[e];
+        const double val = ((double)v.x + (double)v.y) * exp2d(sEU[ty * 16 + c1] + sF[xcol] - 14);
         const int o = ty ? oN : oP;
         const size_t out = ((size_t)(o * NS + s_) * NC + c1) * NC2 + col;
         part[2 * out + pp] = val;
