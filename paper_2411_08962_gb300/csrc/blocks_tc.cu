@@ -36,7 +36,7 @@
 // the grid so that the CTAs reading the same rows of S run together.  Per chunk
 // of 16 sites (upper tables; 8 for the full-spin ones, for shared memory):
 // the CTA builds the U and X slices of chunk c into one of two operand buffers
-// from S staged two chunks ahead (three staging buffers, 4-byte cp.async into
+// from S staged two chunks ahead (two staging buffers, 4-byte cp.async into
 // re / im planes with sites innermost), meets at one barrier, and one thread of
 // the least-loaded warp issues the chunk's MMAs and commits them to the
 // buffer's mbarrier while the others go on to chunk c + 1.  The work of a
@@ -86,7 +86,8 @@ constexpr int kRangeSitesDefault = 512;            // sites per CTA (one grid, o
 constexpr int kPairRangeSitesDefault = 1024;       // the same for block_pair_kernel and the full-spin shape
 constexpr int kMaxCfg = 64;                        // configurations per launch
 constexpr int kSpinLimit = 1 << 22;                // mbarrier polls before giving up
-constexpr int kStage = 3;                          // staging buffers
+// staging buffers: chunk c + 2 is issued after the barrier that ends chunk c's jobs, into chunk c's buffer
+constexpr int kStage = 2;
 constexpr int kMaxRows = 24;                       // staged S rows (both flavours)
 constexpr int kListLen = 4;                        // terms per diquark list the tensor-core path takes (exactly)
 
@@ -803,7 +804,7 @@ block_tc_kernel(const __grid_constant__ BlockPlan plan, const __grid_constant__ 
         }
         if (buf) ++issued1;
         else ++issued0;
-        // stage chunk c + 2 into the buffer chunk c - 1 was built from
+        // stage chunk c + 2 into the buffer chunk c was built from (its jobs are done)
         if (c + 2 < n_chunks) stage(c + 2);
 
         // end of a round: read the accumulators out of TMEM
