@@ -151,7 +151,11 @@ size_t wick_block_count(const wick_block_layout *layout);
  *               sliced product: U in 5 and the double-FP32 diquark values in 6
  *               fixed-point slices of 8 bits, slice pairs i + j <= 5, every
  *               128-site sum exact in FP32, rounds combined in double-FP32 (same
- *               accuracy class).
+ *               accuracy class).  When the tables hold a proton-like and a
+ *               neutron-like type whose diquark lists are each other's with the
+ *               two rows exchanged (the nucleon operators of Eqs. 1000/1001), one
+ *               CTA builds both types from one computation of the diquark values
+ *               (wick_tuning.no_pair_kernel = 1 builds one type per CTA instead).
  *               WICK_MIXED_SIMT requests the CUDA-core double-FP32 kernel.
  *   blocks      device, caller-owned, complex128 [n_src][T][wick_block_count]
  * Uses a library-cached device workspace for the per-chunk FP64 partials
