@@ -301,12 +301,16 @@ int wick_contract(const void *blocks, int n_src, int T, const wick_terms *terms,
  *   range_sites            tensor-core block build: sites per CTA and per FP64 partial,
  *                          a multiple of 128 up to 4096 (default 1024 for the proton/neutron
  *                          pair kernel and the full-spin tables when a launch has at least 8
- *                          waves of such CTAs, else 512)
+ *                          waves of such CTAs, else 512).  The range size sets the order of
+ *                          the site sums: a batch reproduces its single calls bit for bit when
+ *                          both take the same size -- always with a size set here; with the
+ *                          default a large batch may take 1024 where a single call takes 512,
+ *                          and the blocks then agree to rounding (about 1e-12)
  *   contract_threads       contraction CTA size, a multiple of 32 up to 512 (default 256)
  *   contract_ctas_per_sm   resident contraction CTAs per SM (default: as many as fit)
  *   contract_chunk_terms   terms per contraction work item, about (64 or more; default 4096);
- *                          the chunking depends on a table's size and this value only, so a
- *                          batch reproduces the single calls of its configurations bit for bit
+ *                          the chunking depends on a table's size and this value only, so the
+ *                          contraction of a batch adds in the same order as its single calls
  *   hash_log2_start        wick_reduce_terms / wick_reduce_terms_matrix: log2 of the first hash
  *                          table's slots, 4..28 (default: from the raw-term count).  A table that
  *                          fills to 3/4 is dropped and the enumeration rerun with twice the slots

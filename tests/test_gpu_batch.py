@@ -3,7 +3,8 @@
 * wick_synth_propagator reproduces the host generator (same counter-based
   definition; CUDA's log/sincospi may move the last bits);
 * a captured batch (wick_batch_create / wick_batch_run) gives bit-for-bit the
-  results of the individual calls, for several configurations and the three
+  results of the individual calls (at these sizes both take the same block-build
+  range size), for several configurations and the three
   nuclei sharing one block build per configuration, in two kernel launches
   with the tensor-core block build (one for every configuration's blocks, one
   persistent contraction over every configuration, nucleus, slice and chunk);
