@@ -399,8 +399,12 @@ int wick_contract_noalloc(const void *blocks, int n_src, int T, const wick_terms
  * with D the derivative blocks, a third block type beside B^p and B^n:
  * wick_build_blocks_3pt writes D (device complex128, the block layout of wick_build_blocks): every
  * block with each of its quark lines of `flavour` replaced by Sig in turn (Eq. 2.4 differentiated;
- * the exchange term included).  FP64, or WICK_MIXED (double-FP32 on the CUDA cores: the tensor-core
- * update is not used here).  Uses the library workspace; asynchronous.
+ * the exchange term included).  FP64 on the CUDA cores, or WICK_MIXED: for the tables the mixed
+ * wick_build_blocks runs on the tensor cores (when the rows of Su, Sd and Sig fit the staging, as for
+ * the upper-spin tables) the same exact sliced update in three role passes -- the U rows, the
+ * pair-flavour diquark rows and the other diquark rows taken from Sig where their flavour is
+ * `flavour` -- summed per block; otherwise double-FP32 on the CUDA cores.  Uses the library
+ * workspace; asynchronous.
  * wick_contract_3pt evaluates C3 from B (wick_build_blocks) and D with the reduced table of the
  * two-point function; C_out device complex128 [n_src][T].  One persistent launch; deterministic.
  * Errors: WICK_EINVAL (shapes, dtypes, flavour, precision), WICK_ENOMEM, WICK_ECUDA.
