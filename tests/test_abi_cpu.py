@@ -182,6 +182,32 @@ def test_tuning_is_validated_and_kept(lib):
     assert wick.wick_get_tuning() == {f: 0 for f in wick.TUNING_FIELDS}
 
 
+def test_autotune_choice_round_trips(lib, tmp_path):
+    """A tuner result saved as JSON loads back and applies as the process-wide tuning (host only)."""
+    from paper_2411_08962_gb300 import autotune
+    res = {"choice": dict({f: 0 for f in wick.TUNING_FIELDS}, range_sites=2048, contract_chunk_terms=16384),
+           "ms_per_run": 1.0, "default_ms_per_run": 1.1, "trials": []}
+    path = str(tmp_path / "tuning.json")
+    autotune.save(res, path)
+    back = autotune.load(path)
+    assert back == res
+    try:
+        autotune.apply(back)
+        assert wick.wick_get_tuning() == back["choice"]
+    finally:
+        wick.wick_set_tuning(None)
+    assert wick.wick_get_tuning() == {f: 0 for f in wick.TUNING_FIELDS}
+
+
+def test_selftest_wait_checks_its_arguments(lib):
+    """The bounded-wait self-test refuses an unknown wait or a limit outside 1 .. 2^22 before touching
+    the device."""
+    for which, limit in ((2, 100), (-1, 100), (0, 0), (1, (1 << 22) + 1)):
+        with pytest.raises(wick.WickError) as e:
+            wick.wick_selftest_wait(which, limit)
+        assert e.value.code == wick.WICK_EINVAL
+
+
 def test_alloc_failure_injection_is_host_state():
     """The injection is a process-wide countdown on the host: set, read back, cancelled (no GPU call)."""
     assert wick.wick_inject_alloc_failure(0) == 0
