@@ -230,3 +230,19 @@ def test_product_planewave_operators_equal_oracle():
             assert f == op.flav_pair and [tuple(e) for e in tab] == [tuple(e) for e in op.entries]
         assert [tuple(s) for s in a.sink] == [tuple(s) for s in b["sink"]]
         assert a.src == b["src"] and list(a.src_flav) == list(b["src_flav"])
+
+
+@pytest.mark.parametrize("name", ["deuteron", "he3", "he4"])
+def test_nucleon_tables_are_symmetric_under_diquark_exchange(name):
+    """The tensor-core build shares one computation of the diquark values between the proton and the
+    neutron type (their values are each other's with the columns transposed) only when each table is
+    unchanged by exchanging the two diquark slots: swapping the colours of the epsilon and the spins of
+    the antisymmetric C gamma5 flips two signs.  Pinned on the product's tables for the upper-spin
+    nuclei, and the two types hold the same table with opposite pair flavours."""
+    nuc = operators.nucleus(name)
+    assert len(nuc.ops) == 2 and {op.flav_pair for op in nuc.ops} == {0, 1}
+    assert nuc.ops[0].entries == nuc.ops[1].entries
+    for op in nuc.ops:
+        entries = {tuple(e) for e in op.entries}
+        swapped = {(s, q1, q3, q2, w) for s, q1, q2, q3, w in op.entries}
+        assert entries == swapped
